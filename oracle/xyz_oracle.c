@@ -1,0 +1,438 @@
+/*
+ * Plain CPU oracle for the binary xyz interaction search
+ * (Thanei, Meinshausen & Shah, "The xyz algorithm for fast interaction
+ * search in high-dimensional data", Section 2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library calls this file.  It is
+ * loaded by the tests, by __graft_entry__.smoke() and by the CPU-baseline leg
+ * of bench.py, and by nothing else.  It shares no code, header, table or
+ * helper with the CUDA path; the only thing the two sides have in common is
+ * the seeded synthetic input they are handed.
+ *
+ * Everything is written for clarity, not speed: int8 loops over the +-1
+ * data, qsort for the equal-pairs search, one run at a time.
+ *
+ * Data convention (both sides): X is n x p, column-major int8
+ * (X[j*n + i] = X_ij, entries -1 or +1); Y is n int8 entries -1 or +1.
+ * Column and row indices are 0-based.
+ *
+ * Readings of the paper taken here (where it is silent or ambiguous):
+ *   R1  rows of a run are drawn i.i.d. uniform on {0..n-1} WITH replacement
+ *       (subsampling with replacement, Section 2, eq. projR and class (b);
+ *       the retention probability gamma^M of Section 2.3 holds exactly only
+ *       with replacement).
+ *   R2  the random stream is a counter-based splitmix64 (Steele, Lea & Flood
+ *       2014): draw t of a search with seed s is mix(s + (t+1)*0x9E3779B97F4A7C15)
+ *       with t = run*M + m, and the row is floor(u * n / 2^64).
+ *   R3  the projection R of eq. projR with F = U[0,1] (Algorithm 2, step 3)
+ *       makes x_j = z_k exactly when X_{i_m j} = Z_{i_m k} for every sampled
+ *       row (Section 2, the remark after the definition of the classes);
+ *       keys are therefore the M sampled bits, bit(v) = 1 iff v = -1.
+ *       orc_project_real() computes the paper's real projection as well, so
+ *       the tests can check that both give the same equal pairs.
+ *   R4  the diagonal j = k is not an interaction; candidates are reported as
+ *       unordered pairs j < k (the model of eq. inter_mod sums over j < k).
+ *   R5  the verification keeps gamma_jk >= gamma (Algorithm 2, step 5), in
+ *       kappa form: keep (2a - n) >= kappa*n, with a the agreement count of
+ *       eq. def_gamma.  a_min is the least integer a in [0, n] with
+ *       (double)(2a - n) >= kappa * (double)n (one IEEE double multiply).
+ *   R6  the output of a search is the union over runs, each pair once,
+ *       sorted by (j, k), with its exact integer agreement count.
+ *
+ * Parity unpinned: the splitmix64 row stream beyond its published first
+ * outputs is a project convention; it is pinned only by agreement with the
+ * CUDA path.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- stream */
+
+/* splitmix64 output function (Steele, Lea & Flood 2014): finaliser applied to
+ * a Weyl sequence with increment 0x9E3779B97F4A7C15. */
+static uint64_t orc_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Output number t (0-based) of the splitmix64 generator started at state
+ * `seed`: the state after t+1 increments, finalised. */
+uint64_t orc_splitmix64_at(uint64_t seed, uint64_t t)
+{
+    return orc_mix64(seed + (t + 1) * 0x9E3779B97F4A7C15ULL);
+}
+
+/* Reading R1/R2: the M row indices i_1..i_M of run `run`, i.i.d. uniform on
+ * {0..n-1} with replacement (eq. projR, subsampling class). */
+void orc_draw_rows(uint64_t seed, int64_t run, int32_t M, int64_t n,
+                   int64_t *rows)
+{
+    for (int32_t m = 0; m < M; m++) {
+        uint64_t u = orc_splitmix64_at(seed, (uint64_t)run * (uint64_t)M + (uint64_t)m);
+        unsigned __int128 prod = (unsigned __int128)u * (unsigned __int128)(uint64_t)n;
+        rows[m] = (int64_t)(uint64_t)(prod >> 64);
+    }
+}
+
+/* ------------------------------------------------------------- strengths */
+
+/* eq. def_gamma: a_jk = sum_i 1{Y_i = X_ij X_ik}; gamma_jk = a_jk / n. */
+int64_t orc_agree(const int8_t *X, const int8_t *Y, int64_t n,
+                  int64_t j, int64_t k)
+{
+    int64_t a = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int prod = (int)X[j * n + i] * (int)X[k * n + i];
+        if ((int)Y[i] == prod)
+            a++;
+    }
+    return a;
+}
+
+/* Reading R5: least a in [0, n] with (double)(2a - n) >= kappa * (double)n;
+ * n + 1 when no a qualifies (then nothing passes). */
+int64_t orc_amin(int64_t n, double kappa)
+{
+    double rhs = kappa * (double)n;
+    for (int64_t a = 0; a <= n; a++) {
+        if ((double)(2 * a - n) >= rhs)
+            return a;
+    }
+    return n + 1;
+}
+
+/* Input check shared by the entry points below: entries must be -1 or +1. */
+int orc_check_pm1(const int8_t *v, int64_t count)
+{
+    for (int64_t i = 0; i < count; i++)
+        if (v[i] != 1 && v[i] != -1)
+            return 0;
+    return 1;
+}
+
+/* eq. inter_search1 with the >= reading (R5): every pair j < k with
+ * a_jk >= a_min, by looping over all p(p-1)/2 pairs (the naive O(np^2)
+ * search of the Introduction).  Writes up to `cap` triples (j, k, a) and
+ * returns how many pairs qualify. */
+int64_t orc_brute_force(const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
+                        double kappa, int32_t *out, int64_t cap)
+{
+    int64_t amin = orc_amin(n, kappa);
+    int64_t cnt = 0;
+    for (int64_t j = 0; j < p; j++) {
+        for (int64_t k = j + 1; k < p; k++) {
+            int64_t a = orc_agree(X, Y, n, j, k);
+            if (a >= amin) {
+                if (cnt < cap) {
+                    out[3 * cnt + 0] = (int32_t)j;
+                    out[3 * cnt + 1] = (int32_t)k;
+                    out[3 * cnt + 2] = (int32_t)a;
+                }
+                cnt++;
+            }
+        }
+    }
+    return cnt;
+}
+
+/* ------------------------------------------------------------ projection */
+
+/* Reading R3: x_j = sum_m 2^m bit(X_{i_m j}), z_k = sum_m 2^m bit(Z_{i_m k})
+ * with Z_ik = Y_i X_ik (Algorithm 2, step 1) and bit(v) = 1 iff v = -1.
+ * Two columns get equal keys exactly when they agree on every sampled row. */
+void orc_keys(const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
+              const int64_t *rows, int32_t M, uint64_t *x, uint64_t *z)
+{
+    for (int64_t j = 0; j < p; j++) {
+        uint64_t kx = 0, kz = 0;
+        for (int32_t m = 0; m < M; m++) {
+            int64_t i = rows[m];
+            int xv = X[j * n + i];
+            int zv = (int)Y[i] * xv;
+            if (xv == -1)
+                kx |= (uint64_t)1 << m;
+            if (zv == -1)
+                kz |= (uint64_t)1 << m;
+        }
+        x[j] = kx;
+        z[j] = kz;
+    }
+}
+
+/* The paper's own projection (eq. projR, Algorithm 2 step 3):
+ * R_i = sum_m D_m 1{i_m = i}, x = X^T R, z = Z^T R, in double precision.
+ * D holds the M weights (drawn from U[0,1] by the caller). */
+void orc_project_real(const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
+                      const int64_t *rows, int32_t M, const double *D,
+                      double *x, double *z)
+{
+    double *R = (double *)calloc((size_t)n, sizeof(double));
+    for (int32_t m = 0; m < M; m++)
+        R[rows[m]] += D[m];
+    for (int64_t j = 0; j < p; j++) {
+        double sx = 0.0, sz = 0.0;
+        for (int64_t i = 0; i < n; i++) {
+            if (R[i] == 0.0)
+                continue;
+            sx += (double)X[j * n + i] * R[i];
+            sz += (double)((int)Y[i] * (int)X[j * n + i]) * R[i];
+        }
+        x[j] = sx;
+        z[j] = sz;
+    }
+    free(R);
+}
+
+/* --------------------------------------------------- equal-pairs search */
+
+/* One point of the concatenation (x, z) in R^{2p}: its value, its colour
+ * (0 = from x, 1 = from z) and its index. */
+typedef struct {
+    uint64_t v;
+    int32_t colour;
+    int32_t idx;
+} orc_point;
+
+static int orc_point_cmp(const void *pa, const void *pb)
+{
+    const orc_point *a = (const orc_point *)pa, *b = (const orc_point *)pb;
+    if (a->v != b->v)
+        return a->v < b->v ? -1 : 1;
+    if (a->colour != b->colour)
+        return a->colour - b->colour;
+    return a->idx - b->idx;
+}
+
+typedef struct {
+    double v;
+    int32_t colour;
+    int32_t idx;
+} orc_rpoint;
+
+static int orc_rpoint_cmp(const void *pa, const void *pb)
+{
+    const orc_rpoint *a = (const orc_rpoint *)pa, *b = (const orc_rpoint *)pb;
+    if (a->v != b->v)
+        return a->v < b->v ? -1 : 1;
+    if (a->colour != b->colour)
+        return a->colour - b->colour;
+    return a->idx - b->idx;
+}
+
+/* Algorithm 2 step 4 by the procedure of Section 2.2 (Figure 2): sort the 2p
+ * values of (x, z), walk the distinct values, and wherever both colours are
+ * present record the Cartesian product {j : x_j = v} x {k : z_k = v}.
+ * Writes up to `cap` ORDERED pairs (j, k) with x_j = z_k (the diagonal
+ * included) and returns their number. */
+int64_t orc_equal_pairs(const uint64_t *x, const uint64_t *z, int64_t p,
+                        int32_t *out, int64_t cap)
+{
+    orc_point *pts = (orc_point *)malloc((size_t)(2 * p) * sizeof(orc_point));
+    for (int64_t j = 0; j < p; j++) {
+        pts[j].v = x[j];
+        pts[j].colour = 0;
+        pts[j].idx = (int32_t)j;
+        pts[p + j].v = z[j];
+        pts[p + j].colour = 1;
+        pts[p + j].idx = (int32_t)j;
+    }
+    qsort(pts, (size_t)(2 * p), sizeof(orc_point), orc_point_cmp);
+    int64_t cnt = 0;
+    int64_t s = 0;
+    while (s < 2 * p) {
+        int64_t e = s;
+        while (e < 2 * p && pts[e].v == pts[s].v)
+            e++;
+        /* points [s, e) share one value; x-colour first (sort order) */
+        int64_t mid = s;
+        while (mid < e && pts[mid].colour == 0)
+            mid++;
+        for (int64_t a = s; a < mid; a++) {
+            for (int64_t b = mid; b < e; b++) {
+                if (cnt < cap) {
+                    out[2 * cnt + 0] = pts[a].idx;
+                    out[2 * cnt + 1] = pts[b].idx;
+                }
+                cnt++;
+            }
+        }
+        s = e;
+    }
+    free(pts);
+    return cnt;
+}
+
+/* The same walk over the paper's real-valued projections, with exact
+ * floating-point equality as in Algorithm 2 step 4. */
+int64_t orc_equal_pairs_real(const double *x, const double *z, int64_t p,
+                             int32_t *out, int64_t cap)
+{
+    orc_rpoint *pts = (orc_rpoint *)malloc((size_t)(2 * p) * sizeof(orc_rpoint));
+    for (int64_t j = 0; j < p; j++) {
+        pts[j].v = x[j];
+        pts[j].colour = 0;
+        pts[j].idx = (int32_t)j;
+        pts[p + j].v = z[j];
+        pts[p + j].colour = 1;
+        pts[p + j].idx = (int32_t)j;
+    }
+    qsort(pts, (size_t)(2 * p), sizeof(orc_rpoint), orc_rpoint_cmp);
+    int64_t cnt = 0;
+    int64_t s = 0;
+    while (s < 2 * p) {
+        int64_t e = s;
+        while (e < 2 * p && pts[e].v == pts[s].v)
+            e++;
+        int64_t mid = s;
+        while (mid < e && pts[mid].colour == 0)
+            mid++;
+        for (int64_t a = s; a < mid; a++) {
+            for (int64_t b = mid; b < e; b++) {
+                if (cnt < cap) {
+                    out[2 * cnt + 0] = pts[a].idx;
+                    out[2 * cnt + 1] = pts[b].idx;
+                }
+                cnt++;
+            }
+        }
+        s = e;
+    }
+    free(pts);
+    return cnt;
+}
+
+/* ---------------------------------------------------------------- sets */
+
+typedef struct {
+    int32_t j, k, a;
+} orc_triple;
+
+static int orc_triple_cmp(const void *pa, const void *pb)
+{
+    const orc_triple *a = (const orc_triple *)pa, *b = (const orc_triple *)pb;
+    if (a->j != b->j)
+        return a->j < b->j ? -1 : 1;
+    if (a->k != b->k)
+        return a->k < b->k ? -1 : 1;
+    return 0;
+}
+
+/* Sort triples by (j, k) and keep one per pair; returns the new count. */
+static int64_t orc_sort_unique(orc_triple *t, int64_t cnt)
+{
+    if (cnt == 0)
+        return 0;
+    qsort(t, (size_t)cnt, sizeof(orc_triple), orc_triple_cmp);
+    int64_t u = 1;
+    for (int64_t i = 1; i < cnt; i++) {
+        if (t[i].j != t[u - 1].j || t[i].k != t[u - 1].k)
+            t[u++] = t[i];
+    }
+    return u;
+}
+
+typedef struct {
+    orc_triple *v;
+    int64_t n, cap;
+} orc_vec;
+
+static void orc_vec_push(orc_vec *vec, int32_t j, int32_t k, int32_t a)
+{
+    if (vec->n == vec->cap) {
+        vec->cap = vec->cap ? 2 * vec->cap : 1024;
+        vec->v = (orc_triple *)realloc(vec->v, (size_t)vec->cap * sizeof(orc_triple));
+    }
+    vec->v[vec->n].j = j;
+    vec->v[vec->n].k = k;
+    vec->v[vec->n].a = a;
+    vec->n++;
+}
+
+/* Candidate set E_l of run `run` (Algorithm 2 steps 3-4) as unordered pairs
+ * j < k (reading R4), sorted, each once.  The ordered pairs (j, k) and (k, j)
+ * of the equal-pairs walk name the same unordered pair. */
+static int64_t orc_run_candidates(const int8_t *X, const int8_t *Y, int64_t n,
+                                  int64_t p, int32_t M, uint64_t seed,
+                                  int64_t run, orc_vec *vec)
+{
+    int64_t *rows = (int64_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int64_t));
+    uint64_t *x = (uint64_t *)malloc((size_t)p * sizeof(uint64_t));
+    uint64_t *z = (uint64_t *)malloc((size_t)p * sizeof(uint64_t));
+    orc_draw_rows(seed, run, M, n, rows);
+    orc_keys(X, Y, n, p, rows, M, x, z);
+    int64_t ne = orc_equal_pairs(x, z, p, NULL, 0);
+    int32_t *pairs = (int32_t *)malloc((size_t)(ne > 0 ? ne : 1) * 2 * sizeof(int32_t));
+    orc_equal_pairs(x, z, p, pairs, ne);
+    int64_t first = vec->n;
+    for (int64_t e = 0; e < ne; e++) {
+        int32_t j = pairs[2 * e], k = pairs[2 * e + 1];
+        if (j == k)
+            continue;
+        orc_vec_push(vec, j < k ? j : k, j < k ? k : j, 0);
+    }
+    int64_t added = orc_sort_unique(vec->v + first, vec->n - first);
+    vec->n = first + added;
+    free(pairs);
+    free(z);
+    free(x);
+    free(rows);
+    return added;
+}
+
+/* E_l of one run as unordered pairs (j, k), j < k, sorted by (j, k).
+ * Writes up to `cap` pairs and returns their number. */
+int64_t orc_candidates(const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
+                       int32_t M, uint64_t seed, int64_t run,
+                       int32_t *out, int64_t cap)
+{
+    orc_vec vec = {0, 0, 0};
+    int64_t cnt = orc_run_candidates(X, Y, n, p, M, seed, run, &vec);
+    for (int64_t i = 0; i < cnt && i < cap; i++) {
+        out[2 * i + 0] = vec.v[i].j;
+        out[2 * i + 1] = vec.v[i].k;
+    }
+    free(vec.v);
+    return cnt;
+}
+
+/* Algorithm 2 over runs [l0, l1): for each run draw the rows, build keys,
+ * find E_l, and add to I the pairs of E_l with a_jk >= a_min (R5); return
+ * I sorted by (j, k) with the agreement counts (R6).  Writes up to `cap`
+ * triples (j, k, a) and returns |I|.  The full search is l0 = 0, l1 = L. */
+int64_t orc_xyz_range(const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
+                      int64_t l0, int64_t l1, int32_t M, double kappa,
+                      uint64_t seed, int32_t *out, int64_t cap)
+{
+    int64_t amin = orc_amin(n, kappa);
+    orc_vec found = {0, 0, 0};
+    orc_vec cand = {0, 0, 0};
+    for (int64_t l = l0; l < l1; l++) {
+        cand.n = 0;
+        int64_t ne = orc_run_candidates(X, Y, n, p, M, seed, l, &cand);
+        for (int64_t e = 0; e < ne; e++) {
+            int32_t j = cand.v[e].j, k = cand.v[e].k;
+            int64_t a = orc_agree(X, Y, n, j, k);
+            if (a >= amin)
+                orc_vec_push(&found, j, k, (int32_t)a);
+        }
+    }
+    int64_t u = orc_sort_unique(found.v, found.n);
+    for (int64_t i = 0; i < u && i < cap; i++) {
+        out[3 * i + 0] = found.v[i].j;
+        out[3 * i + 1] = found.v[i].k;
+        out[3 * i + 2] = found.v[i].a;
+    }
+    free(found.v);
+    free(cand.v);
+    return u;
+}
+
+int64_t orc_xyz(const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
+                int32_t L, int32_t M, double kappa, uint64_t seed,
+                int32_t *out, int64_t cap)
+{
+    return orc_xyz_range(X, Y, n, p, 0, L, M, kappa, seed, out, cap);
+}
