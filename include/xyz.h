@@ -1,0 +1,220 @@
+/*
+ * xyz.h -- C ABI of the GB300 binary xyz interaction search.
+ *
+ * The library finds column pairs (j, k) of a +-1 matrix X whose product
+ * X_j o X_k has a large inner product with a +-1 response Y:
+ *
+ *     keep (j, k), j < k, with  Y^T (X_j o X_k) / n  >=  kappa
+ *
+ * (eq. 1 of Thanei, Meinshausen & Shah, "The xyz algorithm for fast
+ * interaction search in high-dimensional data", with the >= of Algorithm 2
+ * step 5), without screening all p(p-1)/2 pairs: it runs the final xyz
+ * algorithm (Algorithm 2, Section 2.2) with minimal subsampling.  Every step
+ * runs in CUDA kernels for sm_103a; the host code only validates, plans and
+ * launches.
+ *
+ * Conventions used by every entry point
+ *   - X is n x p, column-major, int8: X[j*n + i] = X_ij, each entry -1 or +1.
+ *     Y has n int8 entries, each -1 or +1.  Indices are 0-based.
+ *   - "Agreement" a_jk = #{ i : Y_i = X_ij X_ik }  (eq. def_gamma: the
+ *     interaction strength is gamma_jk = a_jk / n and, by eq. equiv,
+ *     Y^T(X_j o X_k)/n = 2 gamma_jk - 1 = (2 a_jk - n) / n).
+ *   - kappa in [-1, 1]; a pair passes when (double)(2a - n) >= kappa * (double)n
+ *     (one IEEE double multiply), i.e. a >= xyz_amin(n, kappa).
+ *   - Row subsets: run l draws M rows i.i.d. uniform on {0..n-1} WITH
+ *     replacement (eq. projR, subsampling class).  Draw number t = l*M + m of
+ *     a search with seed s is u = splitmix64 output t from state s, i.e.
+ *     mix(s + (t+1) * 0x9E3779B97F4A7C15) with the splitmix64 finaliser of
+ *     Steele, Lea & Flood (2014), and the row is floor(u * n / 2^64).
+ *   - A candidate of run l is an unordered pair j != k that agrees on every
+ *     sampled row: X_{s j} = Y_s X_{s k} for all sampled s (Algorithm 2 steps
+ *     3-4; equality of the projections x_j = z_k happens exactly then, see the
+ *     remark on minimal subsampling in Section 2).
+ *   - Results are deterministic: they depend only on (X, Y, M, L, kappa,
+ *     seed), never on tuning, chunking or batching.
+ *
+ * Errors: every int-returning call returns XYZ_OK (0) or one of the codes
+ * below; on error no output is written and xyz_last_error() returns a
+ * message (thread-local, valid until the next call on that thread).
+ *
+ * Ownership: the library copies what it needs from inputs before returning;
+ * callers may free inputs immediately.  Arrays the library returns through
+ * `**` out-parameters are allocated by it and released with xyz_free_pairs()
+ * (or xyz_free() for non-pair arrays).  A context owns its device memory and
+ * its CUDA stream and is not re-entrant: one thread at a time per context.
+ */
+#ifndef XYZ_H
+#define XYZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XYZ_OK 0
+#define XYZ_EINVAL 1      /* bad argument: sizes, null pointer, entry not +-1, M, L, kappa */
+#define XYZ_ENOMEM 2      /* host or device allocation failed, or over a memory budget */
+#define XYZ_ECUDA 3       /* a CUDA call failed (the message names it) */
+#define XYZ_ETIMEDOUT 4   /* a bounded device-side wait gave up */
+#define XYZ_ECANCELED 5   /* a served request was cancelled */
+#define XYZ_EAGAIN 6      /* a served request is not finished yet */
+
+#define XYZ_MAX_M 64      /* keys hold one bit per sampled row */
+
+typedef struct xyz_ctx xyz_ctx;
+
+/* One reported interaction: columns j < k, agreement a_jk and the
+ * kappa-scale strength (2 a_jk - n) / n = Y^T(X_j o X_k)/n (eq. equiv). */
+typedef struct xyz_pair {
+    int32_t j;
+    int32_t k;
+    int32_t agree;
+    float strength;
+} xyz_pair;
+
+/* Counters of the last search on a context (observability only). */
+typedef struct xyz_stats {
+    int64_t runs;             /* runs executed */
+    int64_t chunks;           /* launch groups the runs were split into */
+    int64_t runs_per_chunk;   /* runs sorted together in one launch group */
+    int64_t candidates;       /* sum over runs of |E_l| (unordered pairs) */
+    int64_t buckets;          /* equal-key groups holding >= 1 candidate */
+    int64_t passing;          /* verified pairs before the union over runs */
+    int64_t unique_pairs;     /* |I| returned */
+    int64_t sort_passes;      /* radix passes per launch group */
+    int64_t key_bits;         /* bits sorted per launch group */
+    int64_t gpu_launches;     /* kernels launched by the last call */
+    double ms_keys;           /* device time per stage, summed over launches */
+    double ms_sort;           /*   (filled only when timing is enabled) */
+    double ms_join;
+    double ms_verify;
+    double ms_dedup;
+    double ms_total;          /* device time from first to last kernel */
+    int64_t launches_keys;    /* launches per stage */
+    int64_t launches_sort;
+    int64_t launches_join;
+    int64_t launches_verify;
+    int64_t launches_dedup;
+} xyz_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Algorithm 2 step 1 ("form Z"): copy X and Y to the device and pack them
+ * into bit columns (for verification), bit rows (for key building) and the
+ * response bits; Z is never materialised (its bits are X's bits xor Y's).
+ * X: host pointer, n*p int8, column-major.  Y: host pointer, n int8.
+ * n >= 1, 2 <= p < 2^31, n < 2^31.  Any entry other than -1/+1 gives
+ * XYZ_EINVAL.  On success *out owns all device state. */
+int xyz_create(const int8_t *X, const int8_t *Y, int64_t n, int64_t p, xyz_ctx **out);
+
+/* Same as xyz_create with X and Y already in device memory (e.g. torch
+ * tensors).  `stream` is a cudaStream_t (NULL: the library makes its own);
+ * all later work of the context is ordered on it.  The caller keeps
+ * ownership of dX/dY, which are not referenced after return. */
+int xyz_create_dev(const int8_t *dX, const int8_t *dY, int64_t n, int64_t p, void *stream,
+                   xyz_ctx **out);
+
+/* Replace the response Y (host pointer, n int8) of an existing context,
+ * keeping packed X resident (Section 4 calls xyz repeatedly on one X with
+ * changing responses). */
+int xyz_set_y(xyz_ctx *ctx, const int8_t *Y);
+
+/* xyz_set_y with Y in device memory. */
+int xyz_set_y_dev(xyz_ctx *ctx, const int8_t *dY);
+
+/* Release a context and its device memory.  NULL is ignored. */
+void xyz_destroy(xyz_ctx *ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *xyz_last_error(void);
+
+/* n, p and the device bytes held by the context. */
+int xyz_info(const xyz_ctx *ctx, int64_t *n, int64_t *p, int64_t *device_bytes);
+
+/* ----------------------------------------------------------------- search */
+
+/* Algorithm 2 (final xyz): for runs l = 0..L-1 draw M rows, hash every
+ * column of X and Z to its M sampled bits, group equal keys (Section 2.2,
+ * equal-pairs search by sorting, Figure 2), verify each candidate exactly
+ * and keep it when a_jk >= xyz_amin(n, kappa); return the union over runs.
+ * L >= 1, 0 <= M <= 64, kappa finite in [-1, 1].  M = 0 makes every pair a
+ * candidate (the brute-force search).  *pairs gets *npairs records sorted by
+ * (j, k), each pair once; free with xyz_free_pairs (NULL when *npairs = 0). */
+int xyz_search(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t seed,
+               xyz_pair **pairs, int64_t *npairs);
+
+/* Runs [l0, l1) of the search above (same seed stream), for sharding runs
+ * across devices or processes: the union of the results of disjoint ranges
+ * covering [0, L) equals xyz_search(L).  0 <= l0 < l1. */
+int xyz_search_range(xyz_ctx *ctx, int64_t l0, int64_t l1, int32_t M, double kappa,
+                     uint64_t seed, xyz_pair **pairs, int64_t *npairs);
+
+void xyz_free_pairs(xyz_pair *pairs);
+void xyz_free(void *ptr);
+
+/* Counters (and, with timing on, per-stage device times) of the last search. */
+int xyz_get_stats(const xyz_ctx *ctx, xyz_stats *out);
+
+/* Record CUDA events around every stage of later searches (0 = off). */
+int xyz_set_timing(xyz_ctx *ctx, int enable);
+
+/* Tuning: at most `entries` sorted keys (runs x p) per launch group; one run
+ * per group when entries < p.  Results never depend on it.  Default 2^25. */
+int xyz_set_chunk_entries(xyz_ctx *ctx, int64_t entries);
+
+/* --------------------------------------------------- parity / observability */
+
+/* Keys of run `run` (Algorithm 2 step 3 with the integer reading of the
+ * projection): kx[j] = sum_m bit(X_{s_m j}) 2^m with bit(v) = 1 iff v = -1,
+ * for j < p, and c = sum_m bit(Y_{s_m}) 2^m, so that the Z-key of column k is
+ * kx[k] xor c.  kx: host array of p uint64; c: host pointer. */
+int xyz_run_keys(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, uint64_t *kx, uint64_t *c);
+
+/* Candidate set E_run (Algorithm 2 step 4) as unordered pairs j < k,
+ * sorted; *jk gets 2*count int32 (j0,k0,j1,k1,...), free with xyz_free. */
+int xyz_run_candidates(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, int32_t **jk,
+                       int64_t *count);
+
+/* Exact agreement a_jk (eq. def_gamma) of `count` given pairs, computed on
+ * the device by popcount over the packed columns.  j, k, agree: host arrays
+ * of `count` int32; 0 <= j, k < p. */
+int xyz_agree(xyz_ctx *ctx, const int32_t *j, const int32_t *k, int64_t count, int32_t *agree);
+
+/* Agreement of `count` pairs drawn uniformly among all unordered pairs j != k
+ * (splitmix64 stream of `seed`), for the plug-in estimate of
+ * sum_{j,k} gamma_jk^M in eq. bestM.  j_out, k_out, agree: host arrays. */
+int xyz_sample_agree(xyz_ctx *ctx, int64_t count, uint64_t seed, int32_t *j_out, int32_t *k_out,
+                     int32_t *agree);
+
+/* ---------------------------------------------------- planner (host only) */
+
+/* Least agreement count that passes kappa (n + 1 when none can). */
+int64_t xyz_amin(int64_t n, double kappa);
+
+/* eq. eta: probability that a pair of strength gamma (in [0,1]) is found in
+ * L runs of M rows: 1 - (1 - gamma^M)^L. */
+double xyz_eta(double gamma, int32_t M, int64_t L);
+
+/* eq. L_choice: least L with 1 - (1 - beta)^L >= eta, where beta is the
+ * single-run retention probability (gamma^M for minimal subsampling).
+ * Returns -1 for beta <= 0 or eta outside (0, 1). */
+int64_t xyz_runs_for_recall(double beta, double eta);
+
+/* eq. bestM with the plug-in estimate of Section 2.3: minimise over
+ * M = 1..max_M the cost  -(M p + p log p + n S(M)) / log(1 - gamma^M),
+ * where S(M) = sum_{j != k} gamma_jk^M is estimated as p(p-1) times the mean
+ * of (agree/n)^M over `count` sampled pairs.  Writes the minimiser to *M_out
+ * and the minimum to *cost_out (may be NULL).  gamma in (0, 1). */
+int xyz_best_M(int64_t n, int64_t p, double gamma, const int32_t *agree, int64_t count,
+               int32_t max_M, int32_t *M_out, double *cost_out);
+
+/* M with gamma_0 = p^(-1/M) closest to gamma0 (Section 5.2 sets gamma_0
+ * near 0.55): round(log p / log(1/gamma0)), at least 1. */
+int32_t xyz_M_for_gamma0(int64_t p, double gamma0);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XYZ_H */

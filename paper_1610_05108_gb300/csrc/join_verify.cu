@@ -1,0 +1,339 @@
+// K4 join, K5 verify, K6 unique, K7 pair sampler.
+//
+// Join (Section 2.2, Figure 2): after the sort, the entries of one run with
+// one canonical key form a group; a group with entries on both sides (or,
+// for a run whose response key c is 0, with at least two entries) yields
+// the Cartesian product of its sides as candidates.  One thread per sorted
+// entry detects group heads; a head whose successor is in the same group
+// finds the group end by galloping and the side split by binary search, and
+// appends one bucket with its pair count.  Singleton groups -- almost every
+// entry -- cost three coalesced key reads.
+//
+// Verify (Algorithm 2 step 5): candidate t of the launch group is decoded to
+// (bucket, a, b) through the exclusive scan of the bucket pair counts, so
+// every thread gets one candidate regardless of how skewed the buckets are.
+// The agreement is a_jk = sum_w popc(~(Xc_j[w] ^ Xc_k[w] ^ yb[w])): bit i of
+// the xor is 1 exactly when Y_i != X_ij X_ik, and padding bits contribute 0.
+#include "xyz_internal.cuh"
+
+namespace xyz {
+namespace {
+
+constexpr int JV_THREADS = 256;
+
+template <typename K>
+__device__ __forceinline__ K group_of(K key, int sh) { return key >> sh; }
+
+template <typename K>
+__global__ void __launch_bounds__(JV_THREADS)
+    join_kernel(const K *__restrict__ keys, int64_t N, int M, int rbits,
+                const uint8_t *__restrict__ cnz, Bucket *__restrict__ buckets,
+                uint64_t *__restrict__ pair_counts, uint32_t *__restrict__ nbuckets)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const K ki = keys[i];
+        const int r = rbits > 0 ? (int)(ki >> M) : 0;
+        const int sh = cnz[r] ? 1 : 0;
+        const K gi = group_of(ki, sh);
+        // Entries of other runs never share a group value: the run index sits
+        // above the M >= sh key bits, so equal (key >> sh) implies equal run.
+        if (i > 0 && group_of(keys[i - 1], sh) == gi)
+            continue;                                   // not a head
+        if (i + 1 >= N || group_of(keys[i + 1], sh) != gi)
+            continue;                                   // singleton group
+        int64_t good = i + 1, bad = N, step = 1;
+        while (true) {
+            int64_t probe = good + step;
+            if (probe >= N)
+                break;
+            if (group_of(keys[probe], sh) == gi) {
+                good = probe;
+                step <<= 1;
+            } else {
+                bad = probe;
+                break;
+            }
+        }
+        while (bad - good > 1) {
+            int64_t mid = good + (bad - good) / 2;
+            if (group_of(keys[mid], sh) == gi)
+                good = mid;
+            else
+                bad = mid;
+        }
+        const int64_t end = bad;
+        uint32_t nA, nB;
+        uint64_t pairs;
+        if (sh) {
+            int64_t a = i, b = end;                      // first side-B entry
+            while (a < b) {
+                int64_t mid = a + (b - a) / 2;
+                if (keys[mid] & (K)1)
+                    b = mid;
+                else
+                    a = mid + 1;
+            }
+            nA = (uint32_t)(a - i);
+            nB = (uint32_t)(end - a);
+            if (nA == 0 || nB == 0)
+                continue;
+            pairs = (uint64_t)nA * nB;
+        } else {
+            nA = (uint32_t)(end - i);
+            nB = 0;
+            pairs = (uint64_t)nA * (nA - 1) / 2;
+        }
+        uint32_t b = atomicAdd(nbuckets, 1u);
+        buckets[b] = Bucket{(uint32_t)i, nA, nB, 0u};
+        pair_counts[b] = pairs;
+    }
+}
+
+__device__ __forceinline__ int agree_cols(const uint32_t *__restrict__ Xc, int64_t Wp,
+                                          const uint32_t *__restrict__ yb, int64_t j, int64_t k)
+{
+    const uint4 *cj = reinterpret_cast<const uint4 *>(Xc + j * Wp);
+    const uint4 *ck = reinterpret_cast<const uint4 *>(Xc + k * Wp);
+    const uint4 *y4 = reinterpret_cast<const uint4 *>(yb);
+    int a = 0;
+    const int64_t nq = Wp >> 2;
+    for (int64_t q = 0; q < nq; ++q) {
+        uint4 x = __ldg(cj + q), z = __ldg(ck + q), y = __ldg(y4 + q);
+        a += __popc(~(x.x ^ z.x ^ y.x)) + __popc(~(x.y ^ z.y ^ y.y)) +
+             __popc(~(x.z ^ z.z ^ y.z)) + __popc(~(x.w ^ z.w ^ y.w));
+    }
+    return a;
+}
+
+__global__ void __launch_bounds__(JV_THREADS)
+    verify_kernel(const uint32_t *__restrict__ Xc, int64_t Wp, const uint32_t *__restrict__ yb,
+                  const Bucket *__restrict__ buckets, const uint64_t *__restrict__ pair_off,
+                  const uint32_t *__restrict__ nbuckets, const uint64_t *__restrict__ total_pairs,
+                  const uint32_t *__restrict__ vals, int64_t amin, int kbits,
+                  uint64_t *__restrict__ rec_keys, uint32_t *__restrict__ rec_agree,
+                  uint32_t *__restrict__ nrec, uint32_t rec_cap)
+{
+    const uint32_t nb = *nbuckets;
+    const uint64_t T = *total_pairs;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += stride) {
+        uint32_t lo = 0, hi = nb;      // pair_off[lo] <= t < pair_off[hi], pair_off[nb] = T
+        while (hi - lo > 1) {
+            uint32_t mid = lo + (hi - lo) / 2;
+            if (pair_off[mid] <= t)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const Bucket B = buckets[lo];
+        const uint64_t u = t - pair_off[lo];
+        uint32_t j, k;
+        if (B.nB) {
+            uint64_t ia = u / B.nB, ib = u - ia * B.nB;
+            j = vals[B.start + ia];
+            k = vals[B.start + B.nA + ib];
+        } else {
+            // u -> (x, y), x > y, u = x(x-1)/2 + y
+            uint64_t x = (uint64_t)((1.0 + sqrt(1.0 + 8.0 * (double)u)) * 0.5);
+            while (x * (x - 1) / 2 > u)
+                --x;
+            while ((x + 1) * x / 2 <= u)
+                ++x;
+            uint64_t y = u - x * (x - 1) / 2;
+            j = vals[B.start + x];
+            k = vals[B.start + y];
+        }
+        const int a = agree_cols(Xc, Wp, yb, j, k);
+        if (a >= amin) {
+            uint32_t idx = atomicAdd(nrec, 1u);
+            if (idx < rec_cap) {
+                uint32_t lo_c = j < k ? j : k, hi_c = j < k ? k : j;
+                rec_keys[idx] = ((uint64_t)lo_c << kbits) | hi_c;
+                rec_agree[idx] = (uint32_t)a;
+            }
+        }
+    }
+}
+
+__global__ void unique_flags_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ nrec,
+                                    int64_t cap, uint32_t *__restrict__ flags)
+{
+    int64_t N = *nrec;
+    if (N > cap)
+        N = cap;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+        flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void unique_scatter_kernel(const uint64_t *__restrict__ keys,
+                                      const uint32_t *__restrict__ agree,
+                                      const uint32_t *__restrict__ nrec, int64_t cap,
+                                      const uint32_t *__restrict__ flags,
+                                      const uint32_t *__restrict__ pos, int kbits, int64_t n,
+                                      PairOut *__restrict__ out)
+{
+    int64_t N = *nrec;
+    if (N > cap)
+        N = cap;
+    const uint64_t kmask = (kbits >= 64) ? ~0ULL : ((1ULL << kbits) - 1ULL);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        if (!flags[i])
+            continue;
+        uint64_t key = keys[i];
+        PairOut o;
+        o.j = (int32_t)(key >> kbits);
+        o.k = (int32_t)(key & kmask);
+        o.agree = (int32_t)agree[i];
+        o.strength = (float)((double)(2 * (int64_t)agree[i] - n) / (double)n);
+        out[pos[i]] = o;
+    }
+}
+
+__global__ void agree_pairs_kernel(const uint32_t *__restrict__ Xc, int64_t Wp,
+                                   const uint32_t *__restrict__ yb, const int32_t *__restrict__ j,
+                                   const int32_t *__restrict__ k, int64_t count,
+                                   int32_t *__restrict__ agree)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride)
+        agree[t] = agree_cols(Xc, Wp, yb, j[t], k[t]);
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Pair number t uses splitmix64 outputs 2t and 2t+1 of `seed`: j uniform on
+// [0, p), k uniform on [0, p) \ {j}.
+__global__ void sample_pairs_kernel(const uint32_t *__restrict__ Xc, int64_t Wp,
+                                    const uint32_t *__restrict__ yb, int64_t p, uint64_t seed,
+                                    int64_t count, int32_t *__restrict__ jo,
+                                    int32_t *__restrict__ ko, int32_t *__restrict__ agree)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride) {
+        uint64_t u1 = mix64(seed + (uint64_t)(2 * t + 1) * 0x9E3779B97F4A7C15ULL);
+        uint64_t u2 = mix64(seed + (uint64_t)(2 * t + 2) * 0x9E3779B97F4A7C15ULL);
+        int64_t j = (int64_t)__umul64hi(u1, (uint64_t)p);
+        int64_t k = (int64_t)__umul64hi(u2, (uint64_t)(p - 1));
+        if (k >= j)
+            ++k;
+        jo[t] = (int32_t)j;
+        ko[t] = (int32_t)k;
+        agree[t] = agree_cols(Xc, Wp, yb, j, k);
+    }
+}
+
+unsigned grid_for(int64_t work, int threads, int64_t max_blocks)
+{
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1)
+        b = 1;
+    if (b > max_blocks)
+        b = max_blocks;
+    return (unsigned)b;
+}
+
+int g_sm_count = 0;
+int64_t max_resident_blocks()
+{
+    if (!g_sm_count) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sm_count <= 0)
+            g_sm_count = 152;
+    }
+    return (int64_t)g_sm_count * 8;
+}
+
+template <typename K>
+cudaError_t join_impl(const K *keys, int64_t N, int M, int rbits, const uint8_t *cnz,
+                      Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
+                      int64_t *launches)
+{
+    if (N <= 0)
+        return cudaSuccess;
+    join_kernel<K><<<grid_for(N, JV_THREADS, 1 << 20), JV_THREADS, 0, s>>>(
+        keys, N, M, rbits, cnz, buckets, pair_counts, nbuckets);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_join32(const uint32_t *keys, int64_t N, int M, int rbits, const uint8_t *cnz,
+                          Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
+                          cudaStream_t s, int64_t *launches)
+{
+    return join_impl<uint32_t>(keys, N, M, rbits, cnz, buckets, pair_counts, nbuckets, s, launches);
+}
+
+cudaError_t launch_join64(const uint64_t *keys, int64_t N, int M, int rbits, const uint8_t *cnz,
+                          Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
+                          cudaStream_t s, int64_t *launches)
+{
+    return join_impl<uint64_t>(keys, N, M, rbits, cnz, buckets, pair_counts, nbuckets, s, launches);
+}
+
+cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_t *pair_off,
+                          const uint32_t *nbuckets, const uint64_t *total_pairs,
+                          const uint32_t *vals, int64_t amin, int kbits, uint64_t *rec_keys,
+                          uint32_t *rec_agree, uint32_t *nrec, uint32_t rec_cap, cudaStream_t s,
+                          int64_t *launches)
+{
+    verify_kernel<<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
+        pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits, rec_keys,
+        rec_agree, nrec, rec_cap);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unique(const uint64_t *rec_keys, const uint32_t *rec_agree, const uint32_t *nrec,
+                          int64_t cap, int kbits, int64_t n, uint32_t *flags, uint32_t *pos,
+                          void *scan_temp, PairOut *out, uint32_t *nout, cudaStream_t s,
+                          int64_t *launches)
+{
+    if (cap <= 0)
+        return cudaSuccess;
+    unsigned g = grid_for(cap, JV_THREADS, max_resident_blocks());
+    unique_flags_kernel<<<g, JV_THREADS, 0, s>>>(rec_keys, nrec, cap, flags);
+    *launches += 1;
+    cudaError_t e = scan_u32_dev(flags, pos, nrec, cap, nout, scan_temp, s, launches);
+    if (e != cudaSuccess)
+        return e;
+    unique_scatter_kernel<<<g, JV_THREADS, 0, s>>>(rec_keys, rec_agree, nrec, cap, flags, pos, kbits,
+                                                   n, out);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_agree_pairs(const Packed &pk, const int32_t *j, const int32_t *k, int64_t count,
+                               int32_t *agree, cudaStream_t s, int64_t *launches)
+{
+    if (count <= 0)
+        return cudaSuccess;
+    agree_pairs_kernel<<<grid_for(count, JV_THREADS, max_resident_blocks()), JV_THREADS, 0, s>>>(
+        pk.Xc, pk.Wp, pk.yb, j, k, count, agree);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_pairs(const Packed &pk, int64_t count, uint64_t seed, int32_t *j,
+                                int32_t *k, int32_t *agree, cudaStream_t s, int64_t *launches)
+{
+    if (count <= 0)
+        return cudaSuccess;
+    sample_pairs_kernel<<<grid_for(count, JV_THREADS, max_resident_blocks()), JV_THREADS, 0, s>>>(
+        pk.Xc, pk.Wp, pk.yb, pk.p, seed, count, j, k, agree);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace xyz

@@ -1,0 +1,821 @@
+// C ABI of libxyz: context life cycle, search orchestration, parity hooks.
+//
+// A search over runs [l0, l1) is split into launch groups of R runs.  For
+// each group the device runs: keybuild (K2) -> LSD radix sort of the R*p
+// composite keys (K3) -> join (K4) -> exclusive scan of bucket pair counts
+// -> verify (K5).  Passing (j, k, a) records of all groups accumulate in one
+// device buffer; after the last group they are sorted by (j, k) and made
+// unique (K6), which is the union over runs of Algorithm 2, and copied to
+// the host.  Host work is validation, sizing, and launching; the only
+// synchronisations are the record count read before the final sort and the
+// result copy.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/xyz.h"
+#include "xyz_internal.cuh"
+
+static_assert(sizeof(xyz_pair) == sizeof(xyz::PairOut), "pair layout");
+
+namespace xyz {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int64_t amin_rule(int64_t n, double kappa)
+{
+    // least a in [0, n] with (double)(2a - n) >= kappa * (double)n; the
+    // left side grows with a, so a binary search over a finds it.
+    const double rhs = kappa * (double)n;
+    if ((double)n < rhs)
+        return n + 1;
+    int64_t lo = 0, hi = n;   // hi always passes
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if ((double)(2 * mid - n) >= rhs)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+static int ceil_log2(int64_t x)
+{
+    int b = 0;
+    while (((int64_t)1 << b) < x)
+        ++b;
+    return b;
+}
+
+}  // namespace xyz
+
+using namespace xyz;
+
+// ------------------------------------------------------------------ ctx
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct xyz_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Packed pk;
+    int *d_bad = nullptr;
+    int64_t packed_bytes = 0;
+
+    // workspace, grown on demand
+    DevBuf keysA, keysB, valsA, valsB, radix_tmp, cnz, buckets, pair_counts, pair_off, scan_tmp;
+    DevBuf counters;   // uint32 [0] nbuckets, [1] nrec, [2] nout ; uint64 at +16: total, +24: cand accum
+    DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
+    int64_t rec_cap = 1 << 16;
+    int64_t chunk_entries = (int64_t)1 << 25;
+
+    bool timing = false;
+    xyz_stats stats;
+};
+
+static int ensure(DevBuf &b, size_t bytes)
+{
+    if (b.bytes >= bytes && b.ptr)
+        return XYZ_OK;
+    if (b.ptr)
+        cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&b.ptr, want);
+    if (e != cudaSuccess) {
+        b.ptr = nullptr;
+        cudaGetLastError();
+        return fail(XYZ_ENOMEM, std::string("cudaMalloc of ") + std::to_string(want) +
+                                    " bytes failed: " + cudaGetErrorString(e));
+    }
+    b.bytes = want;
+    return XYZ_OK;
+}
+
+static void release(DevBuf &b)
+{
+    if (b.ptr)
+        cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+static int64_t ws_bytes(const xyz_ctx *c)
+{
+    const DevBuf *all[] = {&c->keysA,   &c->keysB,       &c->valsA,     &c->valsB,
+                           &c->radix_tmp, &c->cnz,       &c->buckets,   &c->pair_counts,
+                           &c->pair_off, &c->scan_tmp,   &c->counters,  &c->rec_keys,
+                           &c->rec_keys_alt, &c->rec_agree, &c->rec_agree_alt, &c->flags,
+                           &c->pos,     &c->out,         &c->dedup_tmp, &c->raw};
+    int64_t s = 0;
+    for (const DevBuf *b : all)
+        s += (int64_t)b->bytes;
+    return s;
+}
+
+// --------------------------------------------------------- stage timing
+
+namespace {
+
+enum Stage { ST_KEYS = 0, ST_SORT, ST_JOIN, ST_VERIFY, ST_DEDUP, ST_N };
+
+struct Timer {
+    bool on;
+    cudaStream_t s;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    cudaEvent_t cur = nullptr;
+    int cur_stage = -1;
+    int64_t launches[ST_N] = {0, 0, 0, 0, 0};
+    int64_t *counter;
+    int64_t at_begin = 0;
+
+    Timer(bool on_, cudaStream_t s_, int64_t *counter_) : on(on_), s(s_), counter(counter_) {}
+    void begin(int st)
+    {
+        cur_stage = st;
+        at_begin = *counter;
+        if (!on)
+            return;
+        cudaEventCreate(&cur);
+        cudaEventRecord(cur, s);
+    }
+    void end()
+    {
+        launches[cur_stage] += *counter - at_begin;
+        if (!on)
+            return;
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        marks.push_back({cur_stage, {cur, e}});
+        cur = nullptr;
+    }
+    // after a stream sync
+    void collect(xyz_stats &st)
+    {
+        double ms[ST_N] = {0, 0, 0, 0, 0};
+        float first_last = 0.f;
+        for (auto &m : marks) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, m.second.first, m.second.second);
+            ms[m.first] += t;
+        }
+        if (!marks.empty())
+            cudaEventElapsedTime(&first_last, marks.front().second.first, marks.back().second.second);
+        st.ms_keys = ms[ST_KEYS];
+        st.ms_sort = ms[ST_SORT];
+        st.ms_join = ms[ST_JOIN];
+        st.ms_verify = ms[ST_VERIFY];
+        st.ms_dedup = ms[ST_DEDUP];
+        st.ms_total = first_last;
+        st.launches_keys = launches[ST_KEYS];
+        st.launches_sort = launches[ST_SORT];
+        st.launches_join = launches[ST_JOIN];
+        st.launches_verify = launches[ST_VERIFY];
+        st.launches_dedup = launches[ST_DEDUP];
+    }
+    ~Timer()
+    {
+        for (auto &m : marks) {
+            cudaEventDestroy(m.second.first);
+            cudaEventDestroy(m.second.second);
+        }
+        if (cur)
+            cudaEventDestroy(cur);
+    }
+};
+
+struct Plan {
+    int64_t R;        // runs per launch group
+    bool k64;         // 64-bit composite keys
+    int kbits;        // bits of a column index (record keys use 2*kbits)
+};
+
+Plan make_plan(const xyz_ctx *c, int64_t runs, int M)
+{
+    Plan pl;
+    const int64_t p = c->pk.p;
+    int64_t rmax = c->chunk_entries / p;
+    if (rmax < 1)
+        rmax = 1;
+    int64_t R = runs < rmax ? runs : rmax;
+    int rb = ceil_log2(R);
+    if (M + rb <= 32) {
+        pl.k64 = false;
+    } else if (M <= 28) {
+        pl.k64 = false;
+        R = (int64_t)1 << (32 - M);
+    } else {
+        pl.k64 = true;
+        if (M + rb > 64)
+            R = (int64_t)1 << (64 - M);   // M = 64 -> one run per group
+    }
+    pl.R = R < 1 ? 1 : R;
+    pl.kbits = ceil_log2(p);
+    if (pl.kbits < 1)
+        pl.kbits = 1;
+    return pl;
+}
+
+int ensure_search_ws(xyz_ctx *c, const Plan &pl)
+{
+    const int64_t N = pl.R * c->pk.p;
+    const size_t ksz = pl.k64 ? 8 : 4;
+    const int64_t bcap = N / 2 + 1;
+    int rc;
+    if ((rc = ensure(c->keysA, N * ksz)) || (rc = ensure(c->keysB, N * ksz)) ||
+        (rc = ensure(c->valsA, N * 4)) || (rc = ensure(c->valsB, N * 4)) ||
+        (rc = ensure(c->radix_tmp, radix_temp_bytes(N))) || (rc = ensure(c->cnz, pl.R)) ||
+        (rc = ensure(c->buckets, bcap * sizeof(Bucket))) ||
+        (rc = ensure(c->pair_counts, bcap * 8)) || (rc = ensure(c->pair_off, bcap * 8)) ||
+        (rc = ensure(c->scan_tmp, scan_temp_bytes(bcap))) || (rc = ensure(c->counters, 64)))
+        return rc;
+    return XYZ_OK;
+}
+
+int ensure_records(xyz_ctx *c)
+{
+    const int64_t cap = c->rec_cap;
+    int rc;
+    if ((rc = ensure(c->rec_keys, cap * 8)) || (rc = ensure(c->rec_keys_alt, cap * 8)) ||
+        (rc = ensure(c->rec_agree, cap * 4)) || (rc = ensure(c->rec_agree_alt, cap * 4)) ||
+        (rc = ensure(c->flags, cap * 4)) || (rc = ensure(c->pos, cap * 4)) ||
+        (rc = ensure(c->out, cap * sizeof(PairOut))) ||
+        (rc = ensure(c->dedup_tmp, radix_temp_bytes(cap) + scan_temp_bytes(cap))))
+        return rc;
+    return XYZ_OK;
+}
+
+uint32_t *ctr_u32(xyz_ctx *c) { return reinterpret_cast<uint32_t *>(c->counters.ptr); }
+uint64_t *ctr_total(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 16); }
+uint64_t *ctr_cand(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 24); }
+
+#define CU(expr)                                                                         \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess)                                                           \
+            return fail(XYZ_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));  \
+    } while (0)
+
+// Runs [l0, l1) with threshold amin; results (sorted, unique) to the device
+// `out` buffer, their count to *nout_host.  Retries once with a larger
+// record buffer when the first attempt overflowed it.
+int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t seed,
+               int64_t *nout_host)
+{
+    const int64_t runs = l1 - l0;
+    const int64_t p = c->pk.p;
+    Plan pl = make_plan(c, runs, M);
+    int rc = ensure_search_ws(c, pl);
+    if (rc)
+        return rc;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if ((rc = ensure_records(c)))
+            return rc;
+        int64_t launches = 0;
+        Timer tm(c->timing, c->stream, &launches);
+        xyz_stats st;
+        std::memset(&st, 0, sizeof(st));
+        CU(cudaMemsetAsync(c->counters.ptr, 0, 64, c->stream));
+        int64_t chunks = 0;
+        int key_bits_max = 0;
+        for (int64_t g0 = l0; g0 < l1; g0 += pl.R) {
+            const int64_t Rc = (l1 - g0) < pl.R ? (l1 - g0) : pl.R;
+            const int64_t Nc = Rc * p;
+            const int rbits = ceil_log2(Rc);
+            const int bits = M + rbits;
+            key_bits_max = bits > key_bits_max ? bits : key_bits_max;
+            ++chunks;
+            CU(cudaMemsetAsync(ctr_u32(c), 0, 4, c->stream));   // nbuckets
+            bool alt = false;
+            tm.begin(ST_KEYS);
+            if (pl.k64)
+                CU(launch_keybuild64(c->pk, M, seed, g0, (int)Rc, rbits, (uint64_t *)c->keysA.ptr,
+                                     (uint32_t *)c->valsA.ptr, (uint8_t *)c->cnz.ptr, nullptr,
+                                     nullptr, c->stream, &launches));
+            else
+                CU(launch_keybuild32(c->pk, M, seed, g0, (int)Rc, rbits, (uint32_t *)c->keysA.ptr,
+                                     (uint32_t *)c->valsA.ptr, (uint8_t *)c->cnz.ptr, nullptr,
+                                     nullptr, c->stream, &launches));
+            tm.end();
+            tm.begin(ST_SORT);
+            if (pl.k64)
+                CU(radix_sort64((uint64_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr,
+                                (uint64_t *)c->keysB.ptr, (uint32_t *)c->valsB.ptr, Nc, bits,
+                                c->radix_tmp.ptr, &alt, c->stream, &launches));
+            else
+                CU(radix_sort32((uint32_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr,
+                                (uint32_t *)c->keysB.ptr, (uint32_t *)c->valsB.ptr, Nc, bits,
+                                c->radix_tmp.ptr, &alt, c->stream, &launches));
+            tm.end();
+            void *ks = alt ? c->keysB.ptr : c->keysA.ptr;
+            uint32_t *vs = (uint32_t *)(alt ? c->valsB.ptr : c->valsA.ptr);
+            const int64_t bcap = Nc / 2 + 1;
+            tm.begin(ST_JOIN);
+            if (pl.k64)
+                CU(launch_join64((const uint64_t *)ks, Nc, M, rbits, (const uint8_t *)c->cnz.ptr,
+                                 (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
+                                 ctr_u32(c), c->stream, &launches));
+            else
+                CU(launch_join32((const uint32_t *)ks, Nc, M, rbits, (const uint8_t *)c->cnz.ptr,
+                                 (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
+                                 ctr_u32(c), c->stream, &launches));
+            CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
+                            ctr_u32(c), bcap, ctr_total(c), ctr_cand(c), c->scan_tmp.ptr, c->stream,
+                            &launches));
+            tm.end();
+            tm.begin(ST_VERIFY);
+            CU(launch_verify(c->pk, (const Bucket *)c->buckets.ptr, (const uint64_t *)c->pair_off.ptr,
+                             ctr_u32(c), ctr_total(c), vs, amin, pl.kbits,
+                             (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
+                             ctr_u32(c) + 1, (uint32_t)c->rec_cap, c->stream, &launches));
+            tm.end();
+        }
+        // record count -> host
+        uint32_t nrec = 0;
+        uint64_t cand = 0;
+        CU(cudaMemcpyAsync(&nrec, ctr_u32(c) + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(&cand, ctr_cand(c), 8, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        if ((int64_t)nrec > c->rec_cap) {
+            if (attempt == 1)
+                return fail(XYZ_ENOMEM, "record buffer overflow after resize");
+            int64_t want = c->rec_cap;
+            while (want < (int64_t)nrec)
+                want *= 2;
+            if (want > (int64_t)0xF0000000LL)
+                return fail(XYZ_ENOMEM, "too many passing pairs for one search");
+            c->rec_cap = want;
+            continue;
+        }
+        tm.begin(ST_DEDUP);
+        bool alt = false;
+        char *dt = (char *)c->dedup_tmp.ptr;
+        size_t rt = radix_temp_bytes(c->rec_cap);
+        CU(radix_sort64((uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
+                        (uint64_t *)c->rec_keys_alt.ptr, (uint32_t *)c->rec_agree_alt.ptr,
+                        (int64_t)nrec, 2 * pl.kbits, dt, &alt, c->stream, &launches));
+        const uint64_t *rk = (const uint64_t *)(alt ? c->rec_keys_alt.ptr : c->rec_keys.ptr);
+        const uint32_t *ra = (const uint32_t *)(alt ? c->rec_agree_alt.ptr : c->rec_agree.ptr);
+        CU(launch_unique(rk, ra, ctr_u32(c) + 1, c->rec_cap, pl.kbits, c->pk.n,
+                         (uint32_t *)c->flags.ptr, (uint32_t *)c->pos.ptr, dt + rt,
+                         (PairOut *)c->out.ptr, ctr_u32(c) + 2, c->stream, &launches));
+        tm.end();
+        uint32_t nout = 0;
+        CU(cudaMemcpyAsync(&nout, ctr_u32(c) + 2, 4, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        if (nrec == 0)
+            nout = 0;
+        st.runs = runs;
+        st.chunks = chunks;
+        st.runs_per_chunk = pl.R;
+        st.candidates = (int64_t)cand;
+        st.passing = nrec;
+        st.unique_pairs = nout;
+        st.key_bits = key_bits_max;
+        st.sort_passes = radix_passes(key_bits_max);
+        st.gpu_launches = launches;
+        tm.collect(st);
+        // buckets of the last group only are visible; report that count
+        uint32_t nb = 0;
+        cudaMemcpy(&nb, ctr_u32(c), 4, cudaMemcpyDeviceToHost);
+        st.buckets = nb;
+        c->stats = st;
+        *nout_host = nout;
+        return XYZ_OK;
+    }
+    return fail(XYZ_ENOMEM, "record buffer overflow");
+}
+
+int check_ctx(const xyz_ctx *c)
+{
+    if (!c)
+        return fail(XYZ_EINVAL, "null context");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess)
+        return fail(XYZ_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    return XYZ_OK;
+}
+
+int check_M(int M)
+{
+    if (M < 0 || M > XYZ_MAX_M)
+        return fail(XYZ_EINVAL, "M must be in [0, 64]");
+    return XYZ_OK;
+}
+
+int check_kappa(double kappa)
+{
+    if (!std::isfinite(kappa) || kappa < -1.0 || kappa > 1.0)
+        return fail(XYZ_EINVAL, "kappa must be finite and in [-1, 1]");
+    return XYZ_OK;
+}
+
+int create_common(const int8_t *dX, const int8_t *dY, int64_t n, int64_t p, cudaStream_t stream,
+                  bool own_stream, xyz_ctx *c)
+{
+    c->stream = stream;
+    c->own_stream = own_stream;
+    Packed &pk = c->pk;
+    pk.n = n;
+    pk.p = p;
+    pk.W = (n + 31) / 32;
+    pk.Wp = (pk.W + 3) / 4 * 4;
+    pk.P = (p + 31) / 32;
+    pk.Pp = (pk.P + 7) / 8 * 8;
+    size_t bXc = (size_t)p * pk.Wp * 4, bXr = (size_t)n * pk.Pp * 4, byb = (size_t)pk.Wp * 4;
+    cudaError_t e;
+    if ((e = cudaMalloc(&pk.Xc, bXc)) != cudaSuccess || (e = cudaMalloc(&pk.Xr, bXr)) != cudaSuccess ||
+        (e = cudaMalloc(&pk.yb, byb)) != cudaSuccess || (e = cudaMalloc(&c->d_bad, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(XYZ_ENOMEM, std::string("cudaMalloc of packed X failed: ") + cudaGetErrorString(e));
+    }
+    c->packed_bytes = (int64_t)(bXc + bXr + byb);
+    CU(cudaMemsetAsync(c->d_bad, 0, 16, stream));
+    int64_t launches = 0;
+    CU(launch_pack(dX, dY, pk, c->d_bad, stream, &launches));
+    int bad = 0;
+    CU(cudaMemcpyAsync(&bad, c->d_bad, 4, cudaMemcpyDeviceToHost, stream));
+    CU(cudaStreamSynchronize(stream));
+    if (bad)
+        return fail(XYZ_EINVAL, "entries of X and Y must be -1 or +1");
+    return XYZ_OK;
+}
+
+void destroy_ctx(xyz_ctx *c)
+{
+    if (!c)
+        return;
+    cudaSetDevice(c->device);
+    if (c->stream)
+        cudaStreamSynchronize(c->stream);
+    cudaFree(c->pk.Xc);
+    cudaFree(c->pk.Xr);
+    cudaFree(c->pk.yb);
+    cudaFree(c->d_bad);
+    DevBuf *all[] = {&c->keysA,   &c->keysB,       &c->valsA,     &c->valsB,    &c->radix_tmp,
+                     &c->cnz,     &c->buckets,     &c->pair_counts, &c->pair_off, &c->scan_tmp,
+                     &c->counters, &c->rec_keys,   &c->rec_keys_alt, &c->rec_agree,
+                     &c->rec_agree_alt, &c->flags, &c->pos,       &c->out,      &c->dedup_tmp,
+                     &c->raw};
+    for (DevBuf *b : all)
+        release(*b);
+    if (c->own_stream && c->stream)
+        cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int check_dims(int64_t n, int64_t p)
+{
+    if (n < 1 || n >= ((int64_t)1 << 31))
+        return fail(XYZ_EINVAL, "n must be in [1, 2^31)");
+    if (p < 2 || p >= ((int64_t)1 << 31))
+        return fail(XYZ_EINVAL, "p must be in [2, 2^31)");
+    return XYZ_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+
+extern "C" {
+
+const char *xyz_last_error(void) { return g_err.c_str(); }
+
+int xyz_create_dev(const int8_t *dX, const int8_t *dY, int64_t n, int64_t p, void *stream,
+                   xyz_ctx **out)
+{
+    if (!dX || !dY || !out)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    int rc = check_dims(n, p);
+    if (rc)
+        return rc;
+    xyz_ctx *c = new (std::nothrow) xyz_ctx();
+    if (!c)
+        return fail(XYZ_ENOMEM, "host allocation failed");
+    std::memset(&c->stats, 0, sizeof(c->stats));
+    cudaGetDevice(&c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    bool own = false;
+    if (!s) {
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(XYZ_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+        }
+        own = true;
+    }
+    rc = create_common(dX, dY, n, p, s, own, c);
+    if (rc) {
+        std::string msg = g_err;
+        destroy_ctx(c);
+        g_err = msg;
+        return rc;
+    }
+    *out = c;
+    g_err.clear();
+    return XYZ_OK;
+}
+
+int xyz_create(const int8_t *X, const int8_t *Y, int64_t n, int64_t p, xyz_ctx **out)
+{
+    if (!X || !Y || !out)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    int rc = check_dims(n, p);
+    if (rc)
+        return rc;
+    int8_t *dX = nullptr, *dY = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&dX, (size_t)n * p)) != cudaSuccess || (e = cudaMalloc(&dY, (size_t)n)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dX);
+        return fail(XYZ_ENOMEM, std::string("cudaMalloc of input staging failed: ") + cudaGetErrorString(e));
+    }
+    if ((e = cudaMemcpy(dX, X, (size_t)n * p, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(dY, Y, (size_t)n, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        cudaFree(dX);
+        cudaFree(dY);
+        return fail(XYZ_ECUDA, std::string("cudaMemcpy of X/Y: ") + cudaGetErrorString(e));
+    }
+    rc = xyz_create_dev(dX, dY, n, p, nullptr, out);
+    cudaFree(dX);
+    cudaFree(dY);
+    return rc;
+}
+
+int xyz_set_y_dev(xyz_ctx *ctx, const int8_t *dY)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!dY)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    // pack into a scratch copy first so a bad Y leaves the context unchanged
+    uint32_t *old = ctx->pk.yb;
+    uint32_t *fresh = nullptr;
+    if (cudaMalloc(&fresh, (size_t)ctx->pk.Wp * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(XYZ_ENOMEM, "cudaMalloc of response bits failed");
+    }
+    Packed tmp = ctx->pk;
+    tmp.yb = fresh;
+    int64_t launches = 0;
+    CU(cudaMemsetAsync(ctx->d_bad, 0, 16, ctx->stream));
+    CU(launch_pack_y(dY, tmp, ctx->d_bad, ctx->stream, &launches));
+    int bad = 0;
+    CU(cudaMemcpyAsync(&bad, ctx->d_bad, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (bad) {
+        cudaFree(fresh);
+        return fail(XYZ_EINVAL, "entries of Y must be -1 or +1");
+    }
+    ctx->pk.yb = fresh;
+    cudaFree(old);
+    return XYZ_OK;
+}
+
+int xyz_set_y(xyz_ctx *ctx, const int8_t *Y)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!Y)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    int8_t *dY = nullptr;
+    if (cudaMalloc(&dY, (size_t)ctx->pk.n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(XYZ_ENOMEM, "cudaMalloc of Y staging failed");
+    }
+    cudaError_t e = cudaMemcpy(dY, Y, (size_t)ctx->pk.n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dY);
+        return fail(XYZ_ECUDA, std::string("cudaMemcpy of Y: ") + cudaGetErrorString(e));
+    }
+    rc = xyz_set_y_dev(ctx, dY);
+    cudaFree(dY);
+    return rc;
+}
+
+void xyz_destroy(xyz_ctx *ctx) { destroy_ctx(ctx); }
+
+int xyz_info(const xyz_ctx *ctx, int64_t *n, int64_t *p, int64_t *device_bytes)
+{
+    if (!ctx)
+        return fail(XYZ_EINVAL, "null context");
+    if (n)
+        *n = ctx->pk.n;
+    if (p)
+        *p = ctx->pk.p;
+    if (device_bytes)
+        *device_bytes = ctx->packed_bytes + ws_bytes(ctx);
+    return XYZ_OK;
+}
+
+int xyz_search_range(xyz_ctx *ctx, int64_t l0, int64_t l1, int32_t M, double kappa, uint64_t seed,
+                     xyz_pair **pairs, int64_t *npairs)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!pairs || !npairs)
+        return fail(XYZ_EINVAL, "null output pointer");
+    if (l0 < 0 || l1 <= l0)
+        return fail(XYZ_EINVAL, "need 0 <= l0 < l1");
+    if ((rc = check_M(M)) || (rc = check_kappa(kappa)))
+        return rc;
+    const int64_t amin = amin_rule(ctx->pk.n, kappa);
+    int64_t nout = 0;
+    if (amin > ctx->pk.n) {
+        std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+        *pairs = nullptr;
+        *npairs = 0;
+        return XYZ_OK;
+    }
+    rc = run_search(ctx, l0, l1, M, amin, seed, &nout);
+    if (rc)
+        return rc;
+    xyz_pair *host = nullptr;
+    if (nout > 0) {
+        host = (xyz_pair *)std::malloc((size_t)nout * sizeof(xyz_pair));
+        if (!host)
+            return fail(XYZ_ENOMEM, "host allocation of results failed");
+        cudaError_t e = cudaMemcpyAsync(host, ctx->out.ptr, (size_t)nout * sizeof(xyz_pair),
+                                        cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            std::free(host);
+            return fail(XYZ_ECUDA, std::string("copy of results: ") + cudaGetErrorString(e));
+        }
+    }
+    *pairs = host;
+    *npairs = nout;
+    return XYZ_OK;
+}
+
+int xyz_search(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t seed, xyz_pair **pairs,
+               int64_t *npairs)
+{
+    if (L < 1)
+        return fail(XYZ_EINVAL, "L must be >= 1");
+    return xyz_search_range(ctx, 0, L, M, kappa, seed, pairs, npairs);
+}
+
+void xyz_free_pairs(xyz_pair *pairs) { std::free(pairs); }
+void xyz_free(void *ptr) { std::free(ptr); }
+
+int xyz_get_stats(const xyz_ctx *ctx, xyz_stats *out)
+{
+    if (!ctx || !out)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    *out = ctx->stats;
+    return XYZ_OK;
+}
+
+int xyz_set_timing(xyz_ctx *ctx, int enable)
+{
+    if (!ctx)
+        return fail(XYZ_EINVAL, "null context");
+    ctx->timing = enable != 0;
+    return XYZ_OK;
+}
+
+int xyz_set_chunk_entries(xyz_ctx *ctx, int64_t entries)
+{
+    if (!ctx)
+        return fail(XYZ_EINVAL, "null context");
+    if (entries < 1)
+        return fail(XYZ_EINVAL, "entries must be >= 1");
+    ctx->chunk_entries = entries;
+    return XYZ_OK;
+}
+
+int xyz_run_keys(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, uint64_t *kx, uint64_t *c)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!kx || !c)
+        return fail(XYZ_EINVAL, "null output pointer");
+    if (run < 0)
+        return fail(XYZ_EINVAL, "run must be >= 0");
+    if ((rc = check_M(M)))
+        return rc;
+    const int64_t p = ctx->pk.p;
+    Plan pl;
+    pl.R = 1;
+    pl.k64 = true;
+    pl.kbits = 1;
+    if ((rc = ensure_search_ws(ctx, pl)) || (rc = ensure(ctx->raw, (size_t)(p + 1) * 8)))
+        return rc;
+    int64_t launches = 0;
+    uint64_t *raw = (uint64_t *)ctx->raw.ptr;
+    CU(launch_keybuild64(ctx->pk, M, seed, run, 1, 0, (uint64_t *)ctx->keysA.ptr,
+                         (uint32_t *)ctx->valsA.ptr, (uint8_t *)ctx->cnz.ptr, raw, raw + p,
+                         ctx->stream, &launches));
+    CU(cudaMemcpyAsync(kx, raw, (size_t)p * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(c, raw + p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return XYZ_OK;
+}
+
+int xyz_run_candidates(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, int32_t **jk,
+                       int64_t *count)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!jk || !count)
+        return fail(XYZ_EINVAL, "null output pointer");
+    if (run < 0)
+        return fail(XYZ_EINVAL, "run must be >= 0");
+    if ((rc = check_M(M)))
+        return rc;
+    int64_t nout = 0;
+    if ((rc = run_search(ctx, run, run + 1, M, 0, seed, &nout)))
+        return rc;
+    int32_t *host = nullptr;
+    if (nout > 0) {
+        std::vector<PairOut> tmp((size_t)nout);
+        CU(cudaMemcpyAsync(tmp.data(), ctx->out.ptr, (size_t)nout * sizeof(PairOut),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        host = (int32_t *)std::malloc((size_t)nout * 2 * sizeof(int32_t));
+        if (!host)
+            return fail(XYZ_ENOMEM, "host allocation failed");
+        for (int64_t i = 0; i < nout; ++i) {
+            host[2 * i] = tmp[i].j;
+            host[2 * i + 1] = tmp[i].k;
+        }
+    }
+    *jk = host;
+    *count = nout;
+    return XYZ_OK;
+}
+
+int xyz_agree(xyz_ctx *ctx, const int32_t *j, const int32_t *k, int64_t count, int32_t *agree)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (count < 0 || (count > 0 && (!j || !k || !agree)))
+        return fail(XYZ_EINVAL, "bad pair arrays");
+    for (int64_t t = 0; t < count; ++t)
+        if (j[t] < 0 || j[t] >= ctx->pk.p || k[t] < 0 || k[t] >= ctx->pk.p)
+            return fail(XYZ_EINVAL, "pair index out of range");
+    if (count == 0)
+        return XYZ_OK;
+    if ((rc = ensure(ctx->raw, (size_t)count * 12)))
+        return rc;
+    int32_t *dj = (int32_t *)ctx->raw.ptr, *dk = dj + count, *da = dk + count;
+    int64_t launches = 0;
+    CU(cudaMemcpyAsync(dj, j, (size_t)count * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(dk, k, (size_t)count * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CU(launch_agree_pairs(ctx->pk, dj, dk, count, da, ctx->stream, &launches));
+    CU(cudaMemcpyAsync(agree, da, (size_t)count * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return XYZ_OK;
+}
+
+int xyz_sample_agree(xyz_ctx *ctx, int64_t count, uint64_t seed, int32_t *j_out, int32_t *k_out,
+                     int32_t *agree)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (count < 0 || (count > 0 && (!j_out || !k_out || !agree)))
+        return fail(XYZ_EINVAL, "bad output arrays");
+    if (count == 0)
+        return XYZ_OK;
+    if ((rc = ensure(ctx->raw, (size_t)count * 12)))
+        return rc;
+    int32_t *dj = (int32_t *)ctx->raw.ptr, *dk = dj + count, *da = dk + count;
+    int64_t launches = 0;
+    CU(launch_sample_pairs(ctx->pk, count, seed, dj, dk, da, ctx->stream, &launches));
+    CU(cudaMemcpyAsync(j_out, dj, (size_t)count * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(k_out, dk, (size_t)count * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(agree, da, (size_t)count * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return XYZ_OK;
+}
+
+int64_t xyz_amin(int64_t n, double kappa) { return amin_rule(n, kappa); }
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal declarations shared by the CUDA translation units of libxyz.
+// Nothing here is part of the public ABI (include/xyz.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace xyz {
+
+// ------------------------------------------------------------ error state
+
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+#define XYZ_CUDA_TRY(expr)                                                         \
+    do {                                                                           \
+        cudaError_t _e = (expr);                                                   \
+        if (_e != cudaSuccess)                                                     \
+            return ::xyz::fail(3, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+// ------------------------------------------------------------- layouts
+//
+// Packed X, resident for the life of a context:
+//   Xc [p][Wp] uint32  column bits, bit i%32 of word i/32 is (X_ij == -1);
+//                      Wp = round_up(ceil(n/32), 4) so a column is whole
+//                      16-byte vectors; padding bits are 0.
+//   yb [Wp]    uint32  response bits (Y_i == -1); padding bits are 1, so a
+//                      padding position never counts as an agreement:
+//                      ~(0 ^ 0 ^ 1) = 0.
+//   Xr [n][Pp] uint32  row bits, bit j%32 of word j/32 is (X_ij == -1);
+//                      Pp = round_up(ceil(p/32), 8) so a row is whole
+//                      32-byte sectors; padding bits are 0.
+
+struct Packed {
+    int64_t n = 0, p = 0;
+    int64_t W = 0, Wp = 0;   // words per column (used, padded)
+    int64_t P = 0, Pp = 0;   // words per row (used, padded)
+    uint32_t *Xc = nullptr;
+    uint32_t *Xr = nullptr;
+    uint32_t *yb = nullptr;
+};
+
+// One group of equal keys that yields candidates.  Entries [start, start+nA)
+// of the sorted arrays are side A, [start+nA, start+nA+nB) side B; nB == 0
+// marks a group of a run whose response key c is 0, where every unordered
+// pair inside the nA entries is a candidate.
+struct Bucket {
+    uint32_t start;
+    uint32_t nA;
+    uint32_t nB;
+    uint32_t pad;
+};
+
+// ------------------------------------------------------ kernel launchers
+// Each returns cudaError_t of its launch(es); `launches` is incremented by
+// the number of kernels launched.
+
+cudaError_t launch_pack(const int8_t *dX, const int8_t *dY, const Packed &pk, int *bad_flag,
+                        cudaStream_t s, int64_t *launches);
+cudaError_t launch_pack_y(const int8_t *dY, const Packed &pk, int *bad_flag, cudaStream_t s,
+                          int64_t *launches);
+
+// Keys of runs [l0, l0+R) into keys[r*p + j] (composite, see keys.cu) and
+// vals[r*p + j] = j; cnz[r] = 1 when the run's response key c != 0.
+// raw_kx/raw_c (nullable) receive the plain keys of run l0 (R must be 1).
+cudaError_t launch_keybuild32(const Packed &pk, int M, uint64_t seed, int64_t l0, int R, int rbits,
+                              uint32_t *keys, uint32_t *vals, uint8_t *cnz, uint64_t *raw_kx,
+                              uint64_t *raw_c, cudaStream_t s, int64_t *launches);
+cudaError_t launch_keybuild64(const Packed &pk, int M, uint64_t seed, int64_t l0, int R, int rbits,
+                              uint64_t *keys, uint32_t *vals, uint8_t *cnz, uint64_t *raw_kx,
+                              uint64_t *raw_c, cudaStream_t s, int64_t *launches);
+
+// LSD radix sort of (key, value) pairs on bits [0, bits).  Ping-pongs
+// between (k0, v0) and (k1, v1); *in_alt is set when the result is in
+// (k1, v1).  temp must hold radix_temp_bytes(N).
+size_t radix_temp_bytes(int64_t N);
+cudaError_t radix_sort32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t N, int bits,
+                         void *temp, bool *in_alt, cudaStream_t s, int64_t *launches);
+cudaError_t radix_sort64(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t N, int bits,
+                         void *temp, bool *in_alt, cudaStream_t s, int64_t *launches);
+int radix_passes(int bits);
+
+// Exclusive scans with the element count read from device memory
+// (count_dev) and at most `cap` elements.
+size_t scan_temp_bytes(int64_t cap);
+cudaError_t scan_u64_dev(const uint64_t *in, uint64_t *out, const uint32_t *count_dev, int64_t cap,
+                         uint64_t *total_out, uint64_t *total_accum, void *temp, cudaStream_t s,
+                         int64_t *launches);
+cudaError_t scan_u32_dev(const uint32_t *in, uint32_t *out, const uint32_t *count_dev, int64_t cap,
+                         uint32_t *total_out, void *temp, cudaStream_t s, int64_t *launches);
+
+// Equal-key groups of a sorted chunk -> buckets + per-bucket pair counts.
+cudaError_t launch_join32(const uint32_t *keys, int64_t N, int M, int rbits, const uint8_t *cnz,
+                          Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
+                          cudaStream_t s, int64_t *launches);
+cudaError_t launch_join64(const uint64_t *keys, int64_t N, int M, int rbits, const uint8_t *cnz,
+                          Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
+                          cudaStream_t s, int64_t *launches);
+
+// Verify every candidate of the buckets; append passing (key, agree)
+// records, key = j * 2^kbits + k with j < k.
+cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_t *pair_off,
+                          const uint32_t *nbuckets, const uint64_t *total_pairs,
+                          const uint32_t *vals, int64_t amin, int kbits, uint64_t *rec_keys,
+                          uint32_t *rec_agree, uint32_t *nrec, uint32_t rec_cap, cudaStream_t s,
+                          int64_t *launches);
+
+// Sorted records -> unique xyz pairs (device array), count in *nout.
+struct PairOut {
+    int32_t j, k, agree;
+    float strength;
+};
+cudaError_t launch_unique(const uint64_t *rec_keys, const uint32_t *rec_agree, const uint32_t *nrec,
+                          int64_t cap, int kbits, int64_t n, uint32_t *flags, uint32_t *pos,
+                          void *scan_temp, PairOut *out, uint32_t *nout, cudaStream_t s,
+                          int64_t *launches);
+
+// Agreement of explicit pairs.
+cudaError_t launch_agree_pairs(const Packed &pk, const int32_t *j, const int32_t *k, int64_t count,
+                               int32_t *agree, cudaStream_t s, int64_t *launches);
+// Agreement of pairs drawn uniformly from the splitmix64 stream of `seed`.
+cudaError_t launch_sample_pairs(const Packed &pk, int64_t count, uint64_t seed, int32_t *j,
+                                int32_t *k, int32_t *agree, cudaStream_t s, int64_t *launches);
+
+// Host-side helpers shared by the API files.
+int64_t amin_rule(int64_t n, double kappa);
+
+}  // namespace xyz

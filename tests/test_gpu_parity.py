@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer work, so the bar is bit-exact: keys of every column, the candidate
+set E_l of a run, the agreement counts, and the final pair list of a
+search.  Sizes span several tiles and ragged tails (n and p not multiples of
+32 or of the 4096-entry sort tile), the degenerate cases (M = 0, c = 0 runs,
+constant columns that make one huge bucket, empty results) and, at the end,
+the full-size SNP-shaped workload the benchmark times, checked on sampled
+runs and on every reported pair.
+"""
+import numpy as np
+import pytest
+
+from paper_1610_05108_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xyz():
+    from paper_1610_05108_gb300 import build, xyz as mod
+    build.build()
+    mod.load()
+    return mod
+
+
+def _rand(n, p, seed):
+    rng = np.random.default_rng(seed)
+    X = np.asfortranarray((rng.integers(0, 2, size=(n, p), dtype=np.int8) * 2 - 1).astype(np.int8))
+    Y = (rng.integers(0, 2, size=n, dtype=np.int8) * 2 - 1).astype(np.int8)
+    return X, Y
+
+
+def _as_set(a):
+    return {tuple(int(v) for v in r) for r in a}
+
+
+def _pairs_array(res):
+    return np.stack([res["j"], res["k"], res["agree"]], axis=1).astype(np.int32) if len(res) else np.zeros((0, 3), np.int32)
+
+
+# ------------------------------------------------------------------ keys
+
+@pytest.mark.parametrize("n,p", [(200, 2000), (97, 333), (33, 65), (1000, 257), (1, 40)])
+@pytest.mark.parametrize("M", [0, 1, 10, 31, 32, 33, 63, 64])
+def test_keys_match_oracle(xyz, orc, n, p, M):
+    X, Y = _rand(n, p, n * 7 + p + M)
+    seed = 0xABCDEF + M
+    with xyz.create(X, Y) as ctx:
+        for run in (0, 1, 17):
+            kx, c = ctx.run_keys(M, seed, run)
+            rows = orc.draw_rows(seed, run, M, n)
+            ox, oz = orc.keys(X, Y, rows)
+            assert np.array_equal(kx, ox)
+            assert np.array_equal(kx ^ np.uint64(c), oz)
+
+
+# ------------------------------------------------------------ candidates
+
+def _cand_cases():
+    d = synth.config_small(1)
+    yield "small_iid", d.X, d.Y, 10, range(3)
+    X, Y = _rand(97, 333, 5)
+    yield "ragged_M4", X, Y, 4, range(3)
+    X, Y = _rand(64, 300, 6)
+    Y[:] = 1                                   # c = 0 in every run
+    yield "c_zero", X, Y, 5, range(3)
+    X, Y = _rand(50, 60, 7)
+    yield "M0_all_pairs", X, Y, 0, range(1)
+    X, Y = _rand(80, 5000, 8)
+    X[:, 100:900] = 1                          # 800 equal columns: one huge bucket
+    X[:, 1000:1300] = -1
+    yield "heavy_bucket", X, Y, 6, range(2)
+    X, Y = _rand(2000, 4100, 9)
+    yield "two_tiles_M12", X, Y, 12, range(2)
+
+
+@pytest.mark.parametrize("case", list(_cand_cases()), ids=lambda c: c[0])
+def test_candidates_match_oracle(xyz, orc, case):
+    name, X, Y, M, runs = case
+    seed = 4242
+    with xyz.create(X, Y) as ctx:
+        for run in runs:
+            got = ctx.run_candidates(M, seed, run)
+            want = orc.candidates(X, Y, M, seed, run)
+            assert got.shape == want.shape, (name, run, got.shape, want.shape)
+            assert np.array_equal(got, want), (name, run)
+
+
+# ---------------------------------------------------------------- agree
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 127, 200, 4001])
+def test_agree_matches_oracle(xyz, orc, n):
+    p = 50
+    X, Y = _rand(n, p, n)
+    rng = np.random.default_rng(n)
+    j = rng.integers(0, p, size=300).astype(np.int32)
+    k = rng.integers(0, p, size=300).astype(np.int32)
+    with xyz.create(X, Y) as ctx:
+        a = ctx.agree(j, k)
+    want = np.array([orc.agree(X, Y, int(a_), int(b_)) for a_, b_ in zip(j, k)])
+    assert np.array_equal(a, want)
+
+
+def test_sample_agree_matches_oracle(xyz, orc):
+    X, Y = _rand(300, 700, 3)
+    with xyz.create(X, Y) as ctx:
+        j, k, a = ctx.sample_agree(5000, 99)
+    assert np.all(j != k) and j.min() >= 0 and k.max() < 700
+    for t in range(0, 5000, 37):
+        assert a[t] == orc.agree(X, Y, int(j[t]), int(k[t]))
+    # every column is drawn (uniform on 700 columns, 10000 draws)
+    assert len(np.unique(np.concatenate([j, k]))) > 650
+
+
+# --------------------------------------------------------------- search
+
+def test_search_small_config_matches_oracle(xyz, orc):
+    d = synth.config_small(1)
+    with xyz.create(d.X, d.Y) as ctx:
+        res = ctx.search(10, 10, 0.5, 2024)
+    want = orc.xyz(d.X, d.Y, 10, 10, 0.5, 2024)
+    got = _pairs_array(res)
+    assert np.array_equal(got, want)
+    assert np.allclose(res["strength"], ((2 * want[:, 2] - d.n) / d.n).astype(np.float32))
+    assert (0, 1) in {(int(a), int(b)) for a, b in want[:, :2]}
+
+
+@pytest.mark.parametrize("n,p,L,M,kappa", [(97, 333, 25, 4, 0.2), (33, 1000, 40, 6, 0.3),
+                                           (500, 4097, 12, 9, 0.25), (64, 200, 7, 3, -0.1)])
+def test_search_ragged_matches_oracle(xyz, orc, n, p, L, M, kappa):
+    X, Y = _rand(n, p, n + p)
+    Y = (X[:, 3] * X[:, p - 2]).astype(np.int8)
+    Y[: n // 8] = -Y[: n // 8]
+    with xyz.create(X, Y) as ctx:
+        got = _pairs_array(ctx.search(L, M, kappa, 31337))
+    want = orc.xyz(X, Y, L, M, kappa, 31337)
+    assert np.array_equal(got, want)
+
+
+def test_search_independent_of_launch_grouping(xyz):
+    X, Y = _rand(120, 900, 11)
+    Y = (X[:, 10] * X[:, 500]).astype(np.int8)
+    Y[:20] = -Y[:20]
+    with xyz.create(X, Y) as ctx:
+        ref = ctx.search(37, 5, 0.1, 5)
+        for entries in (900, 900 * 3, 900 * 8 + 5, 10**9):
+            ctx.set_chunk_entries(entries)
+            got = ctx.search(37, 5, 0.1, 5)
+            assert np.array_equal(got, ref), entries
+            st = ctx.stats()
+            assert st["runs"] == 37
+
+
+def test_search_range_union(xyz):
+    X, Y = _rand(150, 1200, 12)
+    Y = (X[:, 7] * X[:, 8]).astype(np.int8)
+    Y[:30] = -Y[:30]
+    with xyz.create(X, Y) as ctx:
+        whole = ctx.search(30, 6, 0.1, 77)
+        parts = [ctx.search_range(a, b, 6, 0.1, 77) for a, b in ((0, 7), (7, 19), (19, 30))]
+    merged = np.unique(np.concatenate(parts))
+    assert np.array_equal(np.sort(merged, order=["j", "k"]), whole)
+
+
+def test_M0_search_is_brute_force(xyz, orc):
+    X, Y = _rand(150, 300, 13)
+    Y = (X[:, 1] * X[:, 2]).astype(np.int8)
+    with xyz.create(X, Y) as ctx:
+        for kappa in (0.2, 0.0, 1.0):
+            got = _pairs_array(ctx.search(1, 0, kappa, 1))
+            assert np.array_equal(got, orc.brute_force(X, Y, kappa))
+
+
+def test_set_y_then_search(xyz, orc):
+    X, Y = _rand(90, 400, 14)
+    Y2 = (X[:, 5] * X[:, 6]).astype(np.int8)
+    with xyz.create(X, Y) as ctx:
+        ctx.set_y(Y2)
+        got = _pairs_array(ctx.search(8, 5, 0.3, 3))
+    assert np.array_equal(got, orc.xyz(X, Y2, 8, 5, 0.3, 3))
+
+
+def test_empty_result(xyz):
+    X, Y = _rand(200, 300, 15)
+    with xyz.create(X, Y) as ctx:
+        res = ctx.search(5, 8, 0.99, 1)
+        assert len(res) == 0
+
+
+def test_invalid_arguments(xyz):
+    X, Y = _rand(20, 10, 16)
+    Xb = X.copy(order="F")
+    Xb[3, 4] = 0
+    with pytest.raises(xyz.XyzError) as e:
+        xyz.create(Xb, Y)
+    assert e.value.code == xyz.XYZ_EINVAL
+    Yb = Y.copy()
+    Yb[0] = 2
+    with pytest.raises(xyz.XyzError):
+        xyz.create(X, Yb)
+    with xyz.create(X, Y) as ctx:
+        for bad in [dict(L=0, M=3, kappa=0.1), dict(L=1, M=65, kappa=0.1), dict(L=1, M=-1, kappa=0.1),
+                    dict(L=1, M=3, kappa=float("nan")), dict(L=1, M=3, kappa=1.5)]:
+            with pytest.raises(xyz.XyzError) as e:
+                ctx.search(bad["L"], bad["M"], bad["kappa"], 0)
+            assert e.value.code == xyz.XYZ_EINVAL
+        with pytest.raises(xyz.XyzError):
+            ctx.agree(np.array([0]), np.array([10]))
+        with pytest.raises(xyz.XyzError):
+            ctx.set_y(Yb)
+        # a rejected Y leaves the context usable with the old response
+        assert len(ctx.search(2, 2, -1.0, 0)) > 0
+
+
+# --------------------------------------------------- full-size workload
+
+@pytest.fixture(scope="module")
+def gwas_full():
+    return synth.config_gwas(1)
+
+
+def test_full_size_gwas_sampled_parity(xyz, orc, gwas_full):
+    """The SNP-shaped n=2000, p=100000 workload at the benchmark's M: exact
+    E_l on sampled runs, and every reported pair's agreement recomputed one
+    by one by the oracle."""
+    d = gwas_full
+    M, L, kappa, seed = 22, 400, 0.3, 2026
+    with xyz.create(d.X, d.Y) as ctx:
+        for run in (0, 123):
+            got = ctx.run_candidates(M, seed, run)
+            want = orc.candidates(d.X, d.Y, M, seed, run)
+            assert np.array_equal(got, want), run
+        res = ctx.search(L, M, kappa, seed)
+    amin = orc.amin(d.n, kappa)
+    assert np.all(res["agree"] >= amin)
+    assert np.all(res["j"] < res["k"])
+    keys = res["j"].astype(np.int64) * d.p + res["k"]
+    assert np.all(np.diff(keys) > 0)
+    for r in res[:: max(1, len(res) // 200)]:
+        assert r["agree"] == orc.agree(d.X, d.Y, int(r["j"]), int(r["k"]))
+    # every run range result is contained in the whole result
+    with xyz.create(d.X, d.Y) as ctx:
+        part = ctx.search_range(0, 50, M, kappa, seed)
+    assert _as_set(_pairs_array(part)) <= _as_set(_pairs_array(res))
+    want_part = orc.xyz_range(d.X, d.Y, 0, 50, M, kappa, seed)
+    assert np.array_equal(_pairs_array(part), want_part)
