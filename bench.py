@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark: interaction pairs screened per second at >= 95% planted recall.
+
+Workload (default): the SNP-shaped binary problem n = 2000, p = 100000 with
+5 planted pairs (realised strengths ~0.17..0.50) and 10 main effects; kappa =
+0.3, so the planted pairs with strength >= 0.3 are the targets.  M is the
+plug-in minimiser of eq. bestM (gamma = (1 + kappa)/2, sum of gamma_jk^M
+estimated from 10^6 pairs sampled on the GPU) and L is the least number of
+runs that finds the weakest target with probability >= 0.95 (eq. L_choice).
+One step is one complete search (all L runs: keys, grouping, verification,
+union) with its own seed; "pairs screened" is p(p-1)/2 per search.
+
+Timing: inputs are resident in HBM before the timed region; each step is
+bracketed by CUDA events on the library's stream, and a 256 MiB buffer is
+written between steps to flush L2.  The e2e figure repeats the step through
+the public host-pointer API: pinned host X/Y -> xyz_create (copy + pack) ->
+xyz_search -> results to host -> xyz_destroy.
+
+--impl reference times the CPU oracle (plain C, one core) on a bounded
+sample of the same workload and scales it to one search.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "interaction pairs screened/s at >=95% planted recall"
+UNIT = "pairs/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------- workload
+
+def make_workload(name: str):
+    from paper_1610_05108_gb300 import synth
+    if name == "gwas":
+        d = synth.config_gwas(1)
+        kappa = 0.3
+        label = "gwas n=2000 p=100000 (AR(0.6) blocks of 20, MAF U[0.05,0.5], 5 planted pairs + 10 main effects)"
+    elif name == "small":
+        d = synth.config_small(1)
+        kappa = 0.5
+        label = "iid n=200 p=2000, Y = X_0 o X_1 flipped w.p. 0.1"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return d, kappa, label
+
+
+def plan(ctx, d, kappa, xyz, samples=10**6):
+    gamma = (1.0 + kappa) / 2.0
+    _, _, agree = ctx.sample_agree(samples, 0x5EED)
+    M, _ = xyz.best_M(d.n, d.p, gamma, agree)
+    targets = [(pr, s) for pr, s in zip(d.planted, d.strengths) if s >= kappa]
+    g_min = (1.0 + min(s for _, s in targets)) / 2.0
+    L = xyz.runs_for_recall(g_min ** M, 0.95)
+    eta = [xyz.eta((1 + s) / 2, M, L) for _, s in targets]
+    return M, L, targets, eta
+
+
+# --------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- GPU arm
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        d["source"] = "measured"
+        return d
+    return dict(FALLBACK_PEAKS)
+
+
+def load_traffic():
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path))
+        except Exception:
+            return {}
+    return {}
+
+
+# Algorithmic bytes per unit of each stage (one run = p columns):
+#   keys:   read M sampled rows of p bits, write p (key, index) entries.
+#   sort:   one read + one write of the p 8-byte entries.
+#   join:   one read of the p sorted 4-byte keys.
+#   verify: per candidate, 2 columns of W words (first touch only is
+#           algorithmic; we count the 2*4*W column bytes of every candidate,
+#           which is what a cache-less verification reads).
+def algorithmic_bytes(stage: str, n: int, p: int, M: int, runs: int, candidates: int):
+    W = (n + 31) // 32
+    if stage == "keys":
+        return runs * (M * p / 8 + 8 * p)
+    if stage == "sort":
+        return runs * 16 * p
+    if stage == "join":
+        return runs * 4 * p
+    if stage == "verify":
+        return candidates * 8 * W
+    return 0
+
+
+def gpu_arm(args):
+    import torch
+    from paper_1610_05108_gb300 import build as _build
+    from paper_1610_05108_gb300 import xyz
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        if rank == 0:
+            _build.build()
+        dist.barrier()
+    else:
+        _build.build()
+    xyz.load()
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    d, kappa, label = make_workload(args.workload)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        dX = torch.from_numpy(np.ascontiguousarray(d.X.T)).to(dev)     # (p, n) rows = columns of X
+        dY = torch.from_numpy(d.Y).to(dev)
+    stream.synchronize()
+    ctx = xyz.Context.from_device(dX.data_ptr(), dY.data_ptr(), d.n, d.p, stream.cuda_stream)
+    M, L, targets, eta = plan(ctx, d, kappa, xyz)
+    if args.L:
+        L = args.L
+    log(f"[bench] rank {rank}: n={d.n} p={d.p} M={M} L={L} kappa={kappa} targets={targets} eta={eta}")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    pairs_per_search = d.p * (d.p - 1) // 2
+    target_set = {tuple(pr) for pr, _ in targets}
+
+    def hits(res):
+        got = {(int(a), int(b)) for a, b in zip(res["j"], res["k"])}
+        return sum(1 for t in target_set if t in got)
+
+    seed_base = 1_000_003 * (rank + 1)
+    for w in range(args.warmup):
+        ctx.search(L, M, kappa, seed_base + 10_000 + w)
+    ctx.set_timing(True)
+    sampler = ClockSampler(dev.index)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    step_ms, found, stats = [], [], []
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(s & 0xFF)                       # L2 flush, outside the timed window
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = ctx.search(L, M, kappa, seed_base + s)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        found.append(hits(res))
+        stats.append(ctx.stats())
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = pairs_per_search * args.steps * world / (total_ms / 1e3)
+
+    # per-stage device time and the dominant stage's roofline
+    stages = ["keys", "sort", "join", "verify", "dedup"]
+    ms_stage = {st: sum(x[f"ms_{st}"] for x in stats) for st in stages}
+    launches_stage = {st: sum(x[f"launches_{st}"] for x in stats) for st in stages}
+    dom = max(stages, key=lambda st: ms_stage[st])
+    cand = sum(x["candidates"] for x in stats)
+    runs = sum(x["runs"] for x in stats)
+    chunks = sum(x["chunks"] for x in stats)
+    alg = algorithmic_bytes(dom, d.n, d.p, M, runs, cand)
+    achieved_gbs = alg / (ms_stage[dom] / 1e3) / 1e9 if ms_stage[dom] > 0 else 0.0
+    peaks = load_peaks()
+    peak = float(peaks["hbm_gbs"])
+    traffic = load_traffic().get(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved_gbs, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved_gbs / peak, 4),
+                "peak_source": f"{peaks.get('source')} hbm_gbs",
+                "traffic": traffic.get("bytes_per_launch") if traffic else None,
+                "launches": launches_stage[dom], "launch_groups": chunks,
+                "stage_ms": {k: round(v, 3) for k, v in ms_stage.items()},
+                "stage_share": {k: round(v / max(1e-9, sum(ms_stage.values())), 4) for k, v in ms_stage.items()}}
+
+    recall = float(np.mean(found)) / max(1, len(target_set))
+    gpu_launches = sum(x["gpu_launches"] for x in stats)
+    lat = sorted(step_ms)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": label, "n": d.n, "p": d.p, "M": M, "L": L, "kappa": kappa,
+                   "planted_strengths": [round(s, 4) for s in d.strengths],
+                   "targets": [list(pr) for pr, _ in targets], "eta_per_target": [round(e, 4) for e in eta],
+                   "l2": "256 MiB buffer written between steps (L2 flush), outside the timed window",
+                   "parallelism": f"runs of independent searches per GPU x{world}"},
+        "recall": {"measured": round(recall, 4), "expected_min_eta": round(min(eta), 4),
+                   "steps": args.steps},
+        "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                       "p99": round(float(np.percentile(lat, 99)), 3), "n": len(lat)},
+        "roofline": roofline,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e_leg(args, d, kappa, M, L, xyz, torch)
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_leg(d, kappa, M, L, args.cpu_seconds)
+    ctx.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def e2e_leg(args, d, kappa, M, L, xyz, torch):
+    """Same search through the host-pointer API, copies inside the timing."""
+    Xh = torch.from_numpy(np.ascontiguousarray(d.X.T)).pin_memory()
+    Yh = torch.from_numpy(d.Y).pin_memory()
+    Xv = Xh.numpy().T          # column-major view of the pinned buffer
+    Yv = Yh.numpy()
+    times, d2h = [], []
+    steps = max(1, min(args.steps, 5))
+    for s in range(steps + 1):
+        t0 = time.perf_counter()
+        with xyz.Context.from_host(Xv, Yv) as c:
+            res = c.search(L, M, kappa, 7_000_000 + s)
+        t1 = time.perf_counter()
+        if s > 0:                       # first call warms the allocator
+            times.append(t1 - t0)
+            d2h.append(len(res) * 16 + 16)
+    t = float(np.mean(times))
+    return {"value": d.p * (d.p - 1) // 2 / t, "unit": UNIT,
+            "h2d_bytes_per_step": int(d.n * d.p + d.n), "d2h_bytes_per_step": int(np.mean(d2h)),
+            "ms_per_step": round(t * 1e3, 3), "steps": steps,
+            "path": "pinned host X,Y -> xyz_create (H2D + pack) -> xyz_search -> pairs to host -> xyz_destroy"}
+
+
+# --------------------------------------------------------- CPU oracle leg
+
+def cpu_leg(d, kappa, M, L, seconds):
+    """The oracle as it stands, one thread, on a bounded number of runs,
+    scaled linearly to the L runs of one search (runs are i.i.d.)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    runs = 0
+    while True:
+        oracle.xyz_range(d.X, d.Y, runs, runs + 1, M, kappa, 99)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or runs >= L:
+            break
+    per_run = el / runs
+    per_search = per_run * L
+    return {"value": d.p * (d.p - 1) // 2 / per_search, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{runs} of {L} runs timed ({el:.1f} s), scaled to one search of {L} runs"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    d, kappa, label = make_workload(args.workload)
+    # same planning rule as the GPU arm, evaluated on the host oracle's
+    # sampled strengths
+    rng = np.random.default_rng(0x5EED)
+    j = rng.integers(0, d.p, size=20000)
+    k = (j + 1 + rng.integers(0, d.p - 1, size=20000)) % d.p
+    agree = oracle.agree_pairs(d.X, d.Y, j, k)
+    gamma = (1 + kappa) / 2
+    Ms = np.arange(1, 65)
+    means = np.array([np.mean((agree / d.n) ** m) for m in Ms])
+    cost = (Ms * d.p + d.p * np.log(d.p) + d.n * d.p * (d.p - 1) * means) / -np.log1p(-(gamma ** Ms))
+    M = int(Ms[np.argmin(cost)])
+    targets = [s for s in d.strengths if s >= kappa]
+    g_min = (1 + min(targets)) / 2
+    L = int(np.ceil(np.log(0.05) / np.log1p(-(g_min ** M))))
+    per_step = []
+    sample_runs = max(1, int(args.ref_runs))
+    for w in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.xyz_range(d.X, d.Y, w * sample_runs, (w + 1) * sample_runs, M, kappa, 4242)
+        el = time.perf_counter() - t0
+        if w >= args.warmup:
+            per_step.append(el / sample_runs * L)
+    t = float(np.mean(per_step))
+    value = d.p * (d.p - 1) // 2 / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+           "config": {"workload": label, "n": d.n, "p": d.p, "M": M, "L": L, "kappa": kappa},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{sample_runs} runs per step, scaled to {L} runs"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", default="gwas")
+    ap.add_argument("--L", type=int, default=0, help="override the number of runs")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-runs", type=int, default=10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "gb300":
+        log("[bench] warm-up raised to 3 steps")
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

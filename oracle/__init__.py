@@ -54,6 +54,7 @@ def _load():
         "orc_splitmix64_at": (_u64, [_u64, _u64]),
         "orc_draw_rows": (None, [_u64, _i64, _i32, _i64, _p]),
         "orc_agree": (_i64, [_p, _p, _i64, _i64, _i64]),
+        "orc_agree_pairs": (None, [_p, _p, _i64, _p, _p, _i64, _p]),
         "orc_amin": (_i64, [_i64, _dbl]),
         "orc_check_pm1": (ctypes.c_int, [_p, _i64]),
         "orc_brute_force": (_i64, [_p, _p, _i64, _i64, _dbl, _p, _i64]),
@@ -105,6 +106,18 @@ def agree(X, Y, j: int, k: int) -> int:
     """a_jk = sum_i 1{Y_i = X_ij X_ik} (eq. def_gamma)."""
     X, Y, n, p = _check_xy(X, Y)
     return int(_load().orc_agree(_ptr(X), _ptr(Y), n, j, k))
+
+
+def agree_pairs(X, Y, j, k) -> np.ndarray:
+    """a_jk for each given pair (eq. def_gamma), one by one."""
+    X, Y, n, p = _check_xy(X, Y)
+    j = np.ascontiguousarray(j, dtype=np.int32)
+    k = np.ascontiguousarray(k, dtype=np.int32)
+    if j.shape != k.shape or (len(j) and (min(j.min(), k.min()) < 0 or max(j.max(), k.max()) >= p)):
+        raise ValueError("bad pair indices")
+    out = np.zeros(len(j), dtype=np.int32)
+    _load().orc_agree_pairs(_ptr(X), _ptr(Y), n, _ptr(j), _ptr(k), len(j), _ptr(out))
+    return out
 
 
 def amin(n: int, kappa: float) -> int:

@@ -92,6 +92,14 @@ int64_t orc_agree(const int8_t *X, const int8_t *Y, int64_t n,
     return a;
 }
 
+/* a_jk for `count` given pairs (j[t], k[t]), one by one. */
+void orc_agree_pairs(const int8_t *X, const int8_t *Y, int64_t n, const int32_t *j,
+                     const int32_t *k, int64_t count, int32_t *out)
+{
+    for (int64_t t = 0; t < count; t++)
+        out[t] = (int32_t)orc_agree(X, Y, n, j[t], k[t]);
+}
+
 /* Reading R5: least a in [0, n] with (double)(2a - n) >= kappa * (double)n;
  * n + 1 when no a qualifies (then nothing passes). */
 int64_t orc_amin(int64_t n, double kappa)

@@ -292,3 +292,15 @@ def test_rejects_non_pm1(orc):
     X[2, 1] = 0
     with pytest.raises(ValueError):
         orc.brute_force(X, Y, 0.0)
+
+
+def test_agree_pairs_matches_single(orc):
+    rng = np.random.default_rng(17)
+    n, p = 45, 20
+    X = np.asfortranarray(_rand_pm1(rng, n, p))
+    Y = _rand_pm1(rng, n)
+    j = rng.integers(0, p, size=50)
+    k = rng.integers(0, p, size=50)
+    Xf = X.astype(np.int64)
+    want = [int(((Xf[:, a] * Xf[:, b]) == Y).sum()) for a, b in zip(j, k)]
+    assert orc.agree_pairs(X, Y, j, k).tolist() == want
