@@ -213,6 +213,29 @@ int xyz_best_M(int64_t n, int64_t p, double gamma, const int32_t *agree, int64_t
  * near 0.55): round(log p / log(1/gamma0)), at least 1. */
 int32_t xyz_M_for_gamma0(int64_t p, double gamma0);
 
+/* --------------------------------------- allocation-free candidate set */
+
+/* Limits of xyz_run_candidates_noalloc. */
+#define XYZ_NOALLOC_MAX_P 16384      /* columns of X */
+#define XYZ_NOALLOC_MAX_PAIRS 32768  /* candidates of the requested run */
+
+/* The paper has no counterpart to this entry point.  It returns the same
+ * candidate set as xyz_run_candidates, for callers that cannot allocate
+ * device memory at the time they ask (their device memory is owned by another
+ * allocator, or they cannot afford cudaMalloc's device-wide synchronisation).
+ * It allocates nothing: its scratch is a fixed array inside the library of
+ * about 2.3 MB that every GPU which loads the library keeps until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the context's device current), so make the first
+ * call before beginning any stream capture on that device.  Calls share the
+ * array: calls that overlap on the GPU race and must be serialised.
+ * ctx: a context with p <= XYZ_NOALLOC_MAX_P (else XYZ_EINVAL).  jk: host array
+ * of 2*cap int32 that receives the pairs (j0,k0,j1,k1,...), j < k, sorted;
+ * *count gets their number.  A run with more than XYZ_NOALLOC_MAX_PAIRS or
+ * more than cap candidates gives XYZ_ENOMEM and writes nothing. */
+int xyz_run_candidates_noalloc(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, int32_t *jk,
+                               int64_t cap, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

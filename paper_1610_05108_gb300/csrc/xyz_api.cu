@@ -819,3 +819,10 @@ int xyz_sample_agree(xyz_ctx *ctx, int64_t count, uint64_t seed, int32_t *j_out,
 int64_t xyz_amin(int64_t n, double kappa) { return amin_rule(n, kappa); }
 
 }  // extern "C"
+
+// Read-only views of a context for other translation units of the library.
+namespace xyz {
+const Packed *ctx_packed(const xyz_ctx *c) { return &c->pk; }
+cudaStream_t ctx_stream(const xyz_ctx *c) { return c->stream; }
+int ctx_device(const xyz_ctx *c) { return c->device; }
+}  // namespace xyz

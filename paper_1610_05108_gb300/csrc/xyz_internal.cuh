@@ -129,3 +129,12 @@ cudaError_t launch_sample_pairs(const Packed &pk, int64_t count, uint64_t seed, 
 int64_t amin_rule(int64_t n, double kappa);
 
 }  // namespace xyz
+
+struct xyz_ctx;
+
+namespace xyz {
+const Packed *ctx_packed(const xyz_ctx *c);
+cudaStream_t ctx_stream(const xyz_ctx *c);
+int ctx_device(const xyz_ctx *c);
+
+}  // namespace xyz

@@ -72,6 +72,7 @@ SIGNATURES = {
     "xyz_runs_for_recall": (_i64, [_dbl, _dbl]),
     "xyz_best_M": (ctypes.c_int, [_i64, _i64, _dbl, _p, _i64, _i32, _p, _p]),
     "xyz_M_for_gamma0": (_i32, [_i64, _dbl]),
+    "xyz_run_candidates_noalloc": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _i64, _p]),
 }
 
 _lib = None
