@@ -96,6 +96,7 @@ typedef struct xyz_stats {
     int64_t launches_join;
     int64_t launches_verify;
     int64_t launches_dedup;
+    int64_t survivors;        /* entries that reached the sort (all of them without the filter) */
 } xyz_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -162,6 +163,11 @@ int xyz_set_timing(xyz_ctx *ctx, int enable);
 /* Tuning: at most `entries` sorted keys (runs x p) per launch group; one run
  * per group when entries < p.  Results never depend on it.  Default 2^25. */
 int xyz_set_chunk_entries(xyz_ctx *ctx, int64_t entries);
+
+/* Tuning: 1 (default) lets searches with M <= 31 and p <= 262144 drop, per
+ * run, the columns that cannot be in any candidate pair before grouping;
+ * 0 groups every column.  Results never depend on it. */
+int xyz_set_filter(xyz_ctx *ctx, int enable);
 
 /* --------------------------------------------------- parity / observability */
 

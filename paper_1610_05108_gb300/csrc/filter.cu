@@ -1,0 +1,270 @@
+// Per-run survivor filter for the equal-pairs search (Algorithm 2 steps
+// 3-4), used for M <= 31 when p is small enough for a shared-memory filter.
+//
+// In a run whose response key c is non-zero, a column can only be part of a
+// candidate pair if some column on the other side of its canonical group
+// exists (keys.cu: the group of column j is h = min(kx_j, kx_j ^ c), its side
+// is whether kx_j != h).  Almost every column fails that test, so the sort
+// that groups equal keys (radix.cu) only needs the few that pass.  One CTA
+// (1024 threads) handles one run at a time:
+//
+//   pass 1  build the keys of all p columns (each thread: the words of the M
+//           sampled rows, transposed in registers), store kx to the CTA's
+//           L2-resident scratch in bit-major order (coalesced without
+//           staging), and set two bits, at two hashes of h, in the
+//           shared-memory Bloom filter of the column's side;
+//   pass 2  keep the columns whose h may be present on the other side (both
+//           bits set in the other side's filter) and append them, as
+//           (run << M | Kc, j) with the canonical key Kc of keys.cu, to the
+//           CTA's own output segment (warp-aggregated shared-memory cursor,
+//           no global atomics).
+//
+// A small second kernel concatenates the CTA segments for the LSD sort and
+// join of the general path.  A Bloom filter has no false negatives, so every
+// true candidate survives; false positives only cost sort work and are
+// grouped out by the join.  In a run with c == 0 every column survives.
+#include "bits.cuh"
+#include "xyz_internal.cuh"
+
+namespace xyz {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int FL_THREADS = 1024;
+constexpr int FL_LOGB = 19;                       // filter bits per side
+constexpr int FL_WORDS = 1 << (FL_LOGB - 5);      // 16384 words per side
+constexpr uint32_t FL_MASK = (1u << FL_LOGB) - 1u;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int64_t draw_row(uint64_t seed, uint64_t t, int64_t n)
+{
+    uint64_t u = mix64(seed + (t + 1ULL) * 0x9E3779B97F4A7C15ULL);
+    return (int64_t)__umul64hi(u, (uint64_t)n);
+}
+
+// Two filter positions of a canonical group value h.
+__device__ __forceinline__ void bloom_pos(uint32_t h, uint32_t &b1, uint32_t &b2)
+{
+    const uint32_t x = mix32(h);
+    b1 = x & FL_MASK;
+    b2 = (x * 0x9E3779B1u) >> (32 - FL_LOGB);
+}
+
+__device__ __forceinline__ void bloom_set(uint32_t *bm, uint32_t b)
+{
+    const uint32_t bit = 1u << (b & 31);
+    uint32_t *w = bm + (b >> 5);
+    if (!(*(volatile uint32_t *)w & bit))    // heavy groups: skip the atomic once set
+        atomicOr(w, bit);
+}
+
+__device__ __forceinline__ bool bloom_has(const uint32_t *bm, uint32_t b)
+{
+    return (bm[b >> 5] >> (b & 31)) & 1u;
+}
+
+// Survivor i of CTA b goes to seg_keys/vals[b * seg_cap + i]; the CTA's
+// count goes to seg_count[b].  kc_scratch holds, per CTA, the keys of its
+// current run in bit-major order: kx of column 32w + cc at cc * P + w.
+__global__ void __launch_bounds__(FL_THREADS, 1)
+    filter_kernel(const uint32_t *__restrict__ Xr, int64_t Pp, int64_t P,
+                  const uint32_t *__restrict__ yb, int64_t n, int64_t p, int M, uint64_t seed,
+                  int64_t l0, int R, uint32_t *__restrict__ kc_scratch,
+                  uint32_t *__restrict__ seg_keys, uint32_t *__restrict__ seg_vals,
+                  uint32_t *__restrict__ seg_count, uint32_t seg_cap, int *__restrict__ overflow,
+                  uint8_t *__restrict__ cnz)
+{
+    extern __shared__ __align__(16) uint32_t fl_smem[];
+    uint32_t *bmA = fl_smem;                       // [FL_WORDS]
+    uint32_t *bmB = fl_smem + FL_WORDS;            // [FL_WORDS]
+    const int t = threadIdx.x;
+    const int lane = t & 31, wp = t >> 5;
+    __shared__ int64_t rows[32];
+    __shared__ uint32_t c_sh;
+    __shared__ uint32_t cursor;
+    uint32_t *kcs = kc_scratch + (int64_t)blockIdx.x * 32 * P;
+    uint32_t *okeys = seg_keys + (int64_t)blockIdx.x * seg_cap;
+    uint32_t *ovals = seg_vals + (int64_t)blockIdx.x * seg_cap;
+    const unsigned lt = (1u << lane) - 1u;
+    if (t == 0)
+        cursor = 0;
+
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+        for (int i = t; i < 2 * FL_WORDS; i += FL_THREADS)
+            fl_smem[i] = 0;
+        if (wp == 0) {
+            int64_t s = 0;
+            uint32_t ybit = 0;
+            if (lane < M) {
+                s = draw_row(seed, (uint64_t)(l0 + r) * (uint64_t)M + (uint64_t)lane, n);
+                ybit = (yb[s >> 5] >> (s & 31)) & 1u;
+            }
+            rows[lane] = s;
+            const uint32_t c = __ballot_sync(FULL, ybit);
+            if (lane == 0) {
+                c_sh = c;
+                cnz[r] = (c != 0);
+            }
+        }
+        __syncthreads();
+        const uint32_t c = c_sh;
+        const bool nz = c != 0;
+
+        // pass 1: keys to the scratch rows, filter bits of each side
+        for (int64_t w = t; w < P; w += FL_THREADS) {
+            uint32_t A[32];
+#pragma unroll
+            for (int m = 0; m < 32; ++m)
+                A[m] = (m < M) ? __ldg(Xr + rows[m] * Pp + w) : 0u;
+            transpose32(A);
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc) {
+                const uint32_t kx = A[cc];
+                kcs[(int64_t)cc * P + w] = kx;
+                if (nz && 32 * w + cc < p) {
+                    const uint32_t kxc = kx ^ c;
+                    const uint32_t h = kx < kxc ? kx : kxc;
+                    uint32_t b1, b2;
+                    bloom_pos(h, b1, b2);
+                    uint32_t *bm = (kx != h) ? bmB : bmA;
+                    bloom_set(bm, b1);
+                    bloom_set(bm, b2);
+                }
+            }
+        }
+        __syncthreads();
+
+        // pass 2: keep columns whose group may have members on the other
+        // side; write them as (run << M | Kc, j)
+        const int tb = nz ? 31 - __clz(c) : 0;
+        const uint32_t lowmask = nz ? ((1u << tb) - 1u) : 0u;
+        const uint32_t runbits = (uint32_t)r << M;
+        const int64_t steps = (P + FL_THREADS - 1) / FL_THREADS;
+        for (int cc = 0; cc < 32; ++cc) {
+            for (int64_t st = 0; st < steps; ++st) {
+                const int64_t w = st * FL_THREADS + t;
+                const int64_t j = 32 * w + cc;
+                bool keep = false;
+                uint32_t key = 0;
+                if (w < P && j < p) {
+                    const uint32_t kx = kcs[(int64_t)cc * P + w];
+                    if (!nz) {
+                        keep = true;
+                        key = kx;
+                    } else {
+                        const uint32_t kxc = kx ^ c;
+                        const uint32_t h = kx < kxc ? kx : kxc;
+                        const uint32_t side = (kx != h) ? 1u : 0u;
+                        uint32_t b1, b2;
+                        bloom_pos(h, b1, b2);
+                        const uint32_t *other = side ? bmA : bmB;
+                        keep = bloom_has(other, b1) && bloom_has(other, b2);
+                        if (keep) {
+                            const uint32_t above = (h >> (tb + 1)) << tb;
+                            key = ((above | (h & lowmask)) << 1) | side;
+                        }
+                    }
+                }
+                const unsigned bal = __ballot_sync(FULL, keep);
+                if (!bal)
+                    continue;
+                uint32_t wbase = 0;
+                if (lane == 0)
+                    wbase = atomicAdd(&cursor, (uint32_t)__popc(bal));
+                wbase = __shfl_sync(FULL, wbase, 0);
+                if (keep) {
+                    const uint32_t o = wbase + __popc(bal & lt);
+                    if (o < seg_cap) {
+                        okeys[o] = runbits | key;
+                        ovals[o] = (uint32_t)j;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        seg_count[blockIdx.x] = cursor < seg_cap ? cursor : seg_cap;
+        if (cursor > seg_cap)
+            atomicOr(overflow, 1);
+    }
+}
+
+// Concatenate the CTA segments: block b copies segment b to the sum of the
+// counts before it; the last block stores the total.
+__global__ void __launch_bounds__(256)
+    compact_kernel(const uint32_t *__restrict__ seg_keys, const uint32_t *__restrict__ seg_vals,
+                   const uint32_t *__restrict__ seg_count, uint32_t seg_cap, int nseg,
+                   uint32_t *__restrict__ out_keys, uint32_t *__restrict__ out_vals,
+                   uint32_t *__restrict__ total)
+{
+    __shared__ uint32_t base_sh;
+    const int b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int i = 0; i < b; ++i)
+            s += seg_count[i];
+        base_sh = s;
+        if (b == nseg - 1)
+            *total = s + seg_count[b];
+    }
+    __syncthreads();
+    const uint32_t base = base_sh, cnt = seg_count[b];
+    const uint32_t *sk = seg_keys + (int64_t)b * seg_cap;
+    const uint32_t *sv = seg_vals + (int64_t)b * seg_cap;
+    for (uint32_t i = threadIdx.x; i < cnt; i += 256) {
+        out_keys[base + i] = sk[i];
+        out_vals[base + i] = sv[i];
+    }
+}
+
+}  // namespace
+
+bool filter_supported(int64_t p, int M) { return M <= 31 && p <= 262144; }
+
+size_t filter_smem_bytes() { return (size_t)(2 * FL_WORDS) * 4; }
+
+int filter_grid()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 152;
+}
+
+size_t filter_scratch_words(int64_t p) { return (size_t)filter_grid() * 32 * (size_t)((p + 31) / 32); }
+
+cudaError_t launch_filter(const Packed &pk, int M, uint64_t seed, int64_t l0, int R,
+                          uint32_t *kc_scratch, uint32_t *seg_keys, uint32_t *seg_vals,
+                          uint32_t *seg_count, uint32_t seg_cap, int *overflow,
+                          uint32_t *out_keys, uint32_t *out_vals, uint32_t *nsurv, uint8_t *cnz,
+                          cudaStream_t s, int64_t *launches)
+{
+    const size_t smem = filter_smem_bytes();
+    cudaError_t e =
+        cudaFuncSetAttribute(filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    int grid = filter_grid();
+    if (grid > R)
+        grid = R;
+    filter_kernel<<<grid, FL_THREADS, smem, s>>>(pk.Xr, pk.Pp, pk.P, pk.yb, pk.n, pk.p, M, seed, l0, R,
+                                                 kc_scratch, seg_keys, seg_vals, seg_count, seg_cap,
+                                                 overflow, cnz);
+    *launches += 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    compact_kernel<<<grid, 256, 0, s>>>(seg_keys, seg_vals, seg_count, seg_cap, grid, out_keys, out_vals,
+                                        nsurv);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace xyz

@@ -80,10 +80,17 @@ struct xyz_ctx {
 
     // workspace, grown on demand
     DevBuf keysA, keysB, valsA, valsB, radix_tmp, cnz, buckets, pair_counts, pair_off, scan_tmp;
-    DevBuf counters;   // uint32 [0] nbuckets, [1] nrec, [2] nout ; uint64 at +16: total, +24: cand accum
+    DevBuf counters;   // see the ctr_* accessors
+    DevBuf ents, seg, members;   // partitioned grouping
+    DevBuf kc_scratch;           // filter path: one key row per CTA
+    DevBuf seg_keys, seg_vals, seg_count;   // filter path: per-CTA survivor segments
+    int64_t surv_cap = 0;        // filter path: survivor capacity (CTAs x segment)
+    int64_t seg_cap = 0;         // filter path: survivors one CTA may write per group
+    int64_t seg_runs_p = 0;      // filter path: runs-per-CTA x p the segment is sized for
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
     int64_t rec_cap = 1 << 16;
     int64_t chunk_entries = (int64_t)1 << 25;
+    bool use_filter = true;
 
     bool timing = false;
     xyz_stats stats;
@@ -123,7 +130,9 @@ static int64_t ws_bytes(const xyz_ctx *c)
                            &c->radix_tmp, &c->cnz,       &c->buckets,   &c->pair_counts,
                            &c->pair_off, &c->scan_tmp,   &c->counters,  &c->rec_keys,
                            &c->rec_keys_alt, &c->rec_agree, &c->rec_agree_alt, &c->flags,
-                           &c->pos,     &c->out,         &c->dedup_tmp, &c->raw};
+                           &c->pos,     &c->out,         &c->dedup_tmp, &c->raw,
+                           &c->ents, &c->seg, &c->members, &c->kc_scratch,
+                           &c->seg_keys, &c->seg_vals, &c->seg_count};
     int64_t s = 0;
     for (const DevBuf *b : all)
         s += (int64_t)b->bytes;
@@ -204,7 +213,9 @@ struct Timer {
 
 struct Plan {
     int64_t R;        // runs per launch group
-    bool k64;         // 64-bit composite keys
+    bool filter;      // survivor filter + LSD sort of the survivors (M <= 31, moderate p)
+    bool part;        // partitioned grouping (M <= 31, large p)
+    bool k64;         // 64-bit composite keys (LSD path)
     int kbits;        // bits of a column index (record keys use 2*kbits)
 };
 
@@ -212,10 +223,36 @@ Plan make_plan(const xyz_ctx *c, int64_t runs, int M)
 {
     Plan pl;
     const int64_t p = c->pk.p;
-    int64_t rmax = c->chunk_entries / p;
+    int64_t entries = c->chunk_entries < ((int64_t)1 << 31) ? c->chunk_entries : ((int64_t)1 << 31);
+    int64_t rmax = entries / p;
     if (rmax < 1)
         rmax = 1;
+    if (rmax > 65535)
+        rmax = 65535;
     int64_t R = runs < rmax ? runs : rmax;
+    pl.filter = c->use_filter && filter_supported(p, M);
+    pl.part = !pl.filter && part_supported(p, M);
+    pl.k64 = false;
+    pl.kbits = ceil_log2(p);
+    if (pl.kbits < 1)
+        pl.kbits = 1;
+    if (pl.filter) {
+        // survivors carry the run index above the M key bits in 32-bit keys;
+        // only a small share of the entries survive, so a group may span
+        // eight times the entry budget
+        int64_t rf = runs < ((int64_t)1 << (32 - M)) ? runs : ((int64_t)1 << (32 - M));
+        int64_t rb = 8 * entries / p;
+        if (rb < 1)
+            rb = 1;
+        if (rf > rb)
+            rf = rb;
+        pl.R = rf < 1 ? 1 : rf;
+        return pl;
+    }
+    if (pl.part) {
+        pl.R = R < 1 ? 1 : R;
+        return pl;
+    }
     int rb = ceil_log2(R);
     if (M + rb <= 32) {
         pl.k64 = false;
@@ -228,9 +265,6 @@ Plan make_plan(const xyz_ctx *c, int64_t runs, int M)
             R = (int64_t)1 << (64 - M);   // M = 64 -> one run per group
     }
     pl.R = R < 1 ? 1 : R;
-    pl.kbits = ceil_log2(p);
-    if (pl.kbits < 1)
-        pl.kbits = 1;
     return pl;
 }
 
@@ -240,6 +274,40 @@ int ensure_search_ws(xyz_ctx *c, const Plan &pl)
     const size_t ksz = pl.k64 ? 8 : 4;
     const int64_t bcap = N / 2 + 1;
     int rc;
+    if (pl.filter) {
+        // a CTA handles ceil(R / grid) runs of p columns; start its segment
+        // at an eighth of that (plus slack) and grow on overflow
+        const int64_t grid = filter_grid() < pl.R ? filter_grid() : pl.R;
+        const int64_t worst = (pl.R + grid - 1) / grid * c->pk.p;
+        if (c->seg_runs_p != worst) {
+            c->seg_runs_p = worst;
+            c->seg_cap = worst / 8 + 4096 < worst ? worst / 8 + 4096 : worst;
+        }
+        const int64_t seg_cap = c->seg_cap;
+        const int64_t cap = grid * seg_cap;
+        c->surv_cap = cap;
+        const int64_t sb = cap / 2 + 1;
+        if ((rc = ensure(c->kc_scratch, filter_scratch_words(c->pk.p) * 4)) ||
+            (rc = ensure(c->seg_keys, (size_t)cap * 4)) || (rc = ensure(c->seg_vals, (size_t)cap * 4)) ||
+            (rc = ensure(c->seg_count, (size_t)filter_grid() * 4)) ||
+            (rc = ensure(c->keysA, cap * 4)) || (rc = ensure(c->keysB, cap * 4)) ||
+            (rc = ensure(c->valsA, cap * 4)) || (rc = ensure(c->valsB, cap * 4)) ||
+            (rc = ensure(c->radix_tmp, radix_temp_bytes(cap))) || (rc = ensure(c->cnz, pl.R)) ||
+            (rc = ensure(c->buckets, sb * sizeof(Bucket))) || (rc = ensure(c->pair_counts, sb * 8)) ||
+            (rc = ensure(c->pair_off, sb * 8)) || (rc = ensure(c->scan_tmp, scan_temp_bytes(sb))) ||
+            (rc = ensure(c->counters, 64)))
+            return rc;
+        return XYZ_OK;
+    }
+    if (pl.part) {
+        if ((rc = ensure(c->ents, N * 8)) || (rc = ensure(c->members, N * 4)) ||
+            (rc = ensure(c->seg, part_seg_words(c->pk.p, (int)pl.R) * 4)) ||
+            (rc = ensure(c->cnz, pl.R)) || (rc = ensure(c->buckets, bcap * sizeof(Bucket))) ||
+            (rc = ensure(c->pair_counts, bcap * 8)) || (rc = ensure(c->pair_off, bcap * 8)) ||
+            (rc = ensure(c->scan_tmp, scan_temp_bytes(bcap))) || (rc = ensure(c->counters, 64)))
+            return rc;
+        return XYZ_OK;
+    }
     if ((rc = ensure(c->keysA, N * ksz)) || (rc = ensure(c->keysB, N * ksz)) ||
         (rc = ensure(c->valsA, N * 4)) || (rc = ensure(c->valsB, N * 4)) ||
         (rc = ensure(c->radix_tmp, radix_temp_bytes(N))) || (rc = ensure(c->cnz, pl.R)) ||
@@ -263,9 +331,19 @@ int ensure_records(xyz_ctx *c)
     return XYZ_OK;
 }
 
+// Device counters: per launch group (cleared before each group) the bucket
+// and member counts; per search the record and output counts, the error
+// flag, the group's candidate total and the candidate sum over groups.
 uint32_t *ctr_u32(xyz_ctx *c) { return reinterpret_cast<uint32_t *>(c->counters.ptr); }
-uint64_t *ctr_total(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 16); }
-uint64_t *ctr_cand(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 24); }
+uint32_t *ctr_nbuckets(xyz_ctx *c) { return ctr_u32(c) + 0; }
+uint32_t *ctr_members(xyz_ctx *c) { return ctr_u32(c) + 1; }
+uint32_t *ctr_nsurv(xyz_ctx *c) { return ctr_u32(c) + 2; }
+int *ctr_sovf(xyz_ctx *c) { return reinterpret_cast<int *>(ctr_u32(c) + 3); }
+uint32_t *ctr_nrec(xyz_ctx *c) { return ctr_u32(c) + 4; }
+uint32_t *ctr_nout(xyz_ctx *c) { return ctr_u32(c) + 5; }
+int *ctr_err(xyz_ctx *c) { return reinterpret_cast<int *>(ctr_u32(c) + 6); }
+uint64_t *ctr_total(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 32); }
+uint64_t *ctr_cand(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 40); }
 
 #define CU(expr)                                                                         \
     do {                                                                                 \
@@ -295,6 +373,7 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
         std::memset(&st, 0, sizeof(st));
         CU(cudaMemsetAsync(c->counters.ptr, 0, 64, c->stream));
         int64_t chunks = 0;
+        int64_t surv_total = 0;
         int key_bits_max = 0;
         for (int64_t g0 = l0; g0 < l1; g0 += pl.R) {
             const int64_t Rc = (l1 - g0) < pl.R ? (l1 - g0) : pl.R;
@@ -303,7 +382,89 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
             const int bits = M + rbits;
             key_bits_max = bits > key_bits_max ? bits : key_bits_max;
             ++chunks;
-            CU(cudaMemsetAsync(ctr_u32(c), 0, 4, c->stream));   // nbuckets
+            CU(cudaMemsetAsync(ctr_u32(c), 0, 16, c->stream));   // per-group counters
+            const int64_t bcap = Nc / 2 + 1;
+            if (pl.filter) {
+                tm.begin(ST_KEYS);
+                const int64_t seg_cap = c->seg_cap;
+                CU(launch_filter(c->pk, M, seed, g0, (int)Rc, (uint32_t *)c->kc_scratch.ptr,
+                                 (uint32_t *)c->seg_keys.ptr, (uint32_t *)c->seg_vals.ptr,
+                                 (uint32_t *)c->seg_count.ptr, (uint32_t)seg_cap, ctr_sovf(c),
+                                 (uint32_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr, ctr_nsurv(c),
+                                 (uint8_t *)c->cnz.ptr, c->stream, &launches));
+                tm.end();
+                uint32_t ns = 0;
+                int sovf = 0;
+                CU(cudaMemcpyAsync(&ns, ctr_nsurv(c), 4, cudaMemcpyDeviceToHost, c->stream));
+                CU(cudaMemcpyAsync(&sovf, ctr_sovf(c), 4, cudaMemcpyDeviceToHost, c->stream));
+                CU(cudaStreamSynchronize(c->stream));
+                if (sovf) {
+                    // a CTA segment overflowed: grow the segments and redo
+                    // this group (a segment of runs-per-CTA x p never does)
+                    int64_t want = 2 * c->seg_cap;
+                    if (want > c->seg_runs_p)
+                        want = c->seg_runs_p;
+                    if (want <= c->seg_cap)
+                        return fail(XYZ_ENOMEM, "survivor segment cannot grow further");
+                    c->seg_cap = want;
+                    if ((rc = ensure_search_ws(c, pl)))
+                        return rc;
+                    g0 -= pl.R;
+                    --chunks;
+                    continue;
+                }
+                surv_total += ns;
+                bool alt = false;
+                tm.begin(ST_SORT);
+                CU(radix_sort32((uint32_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr,
+                                (uint32_t *)c->keysB.ptr, (uint32_t *)c->valsB.ptr, (int64_t)ns, bits,
+                                c->radix_tmp.ptr, &alt, c->stream, &launches));
+                tm.end();
+                const uint32_t *ks = (const uint32_t *)(alt ? c->keysB.ptr : c->keysA.ptr);
+                const uint32_t *vs = (const uint32_t *)(alt ? c->valsB.ptr : c->valsA.ptr);
+                const int64_t sb = c->surv_cap / 2 + 1;
+                tm.begin(ST_JOIN);
+                CU(launch_join32(ks, (int64_t)ns, M, rbits, (const uint8_t *)c->cnz.ptr,
+                                 (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
+                                 ctr_nbuckets(c), c->stream, &launches));
+                CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
+                                ctr_nbuckets(c), sb, ctr_total(c), ctr_cand(c), c->scan_tmp.ptr,
+                                c->stream, &launches));
+                tm.end();
+                tm.begin(ST_VERIFY);
+                CU(launch_verify(c->pk, (const Bucket *)c->buckets.ptr,
+                                 (const uint64_t *)c->pair_off.ptr, ctr_nbuckets(c), ctr_total(c), vs,
+                                 amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
+                                 (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
+                                 c->stream, &launches));
+                tm.end();
+                continue;
+            }
+            if (pl.part) {
+                tm.begin(ST_KEYS);
+                CU(launch_keybuild_part(c->pk, M, seed, g0, (int)Rc, (uint64_t *)c->ents.ptr,
+                                        (uint32_t *)c->seg.ptr, (uint8_t *)c->cnz.ptr, c->stream,
+                                        &launches));
+                tm.end();
+                tm.begin(ST_JOIN);
+                CU(launch_group(c->pk, (int)Rc, (const uint64_t *)c->ents.ptr,
+                                (const uint32_t *)c->seg.ptr, (const uint8_t *)c->cnz.ptr,
+                                (uint32_t *)c->members.ptr, ctr_members(c), (Bucket *)c->buckets.ptr,
+                                (uint64_t *)c->pair_counts.ptr, ctr_nbuckets(c), ctr_err(c),
+                                c->stream, &launches));
+                CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
+                                ctr_nbuckets(c), bcap, ctr_total(c), ctr_cand(c), c->scan_tmp.ptr,
+                                c->stream, &launches));
+                tm.end();
+                tm.begin(ST_VERIFY);
+                CU(launch_verify(c->pk, (const Bucket *)c->buckets.ptr,
+                                 (const uint64_t *)c->pair_off.ptr, ctr_nbuckets(c), ctr_total(c),
+                                 (const uint32_t *)c->members.ptr, amin, pl.kbits,
+                                 (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
+                                 ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches));
+                tm.end();
+                continue;
+            }
             bool alt = false;
             tm.begin(ST_KEYS);
             if (pl.k64)
@@ -327,33 +488,36 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
             tm.end();
             void *ks = alt ? c->keysB.ptr : c->keysA.ptr;
             uint32_t *vs = (uint32_t *)(alt ? c->valsB.ptr : c->valsA.ptr);
-            const int64_t bcap = Nc / 2 + 1;
             tm.begin(ST_JOIN);
             if (pl.k64)
                 CU(launch_join64((const uint64_t *)ks, Nc, M, rbits, (const uint8_t *)c->cnz.ptr,
                                  (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
-                                 ctr_u32(c), c->stream, &launches));
+                                 ctr_nbuckets(c), c->stream, &launches));
             else
                 CU(launch_join32((const uint32_t *)ks, Nc, M, rbits, (const uint8_t *)c->cnz.ptr,
                                  (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
-                                 ctr_u32(c), c->stream, &launches));
+                                 ctr_nbuckets(c), c->stream, &launches));
             CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
-                            ctr_u32(c), bcap, ctr_total(c), ctr_cand(c), c->scan_tmp.ptr, c->stream,
-                            &launches));
+                            ctr_nbuckets(c), bcap, ctr_total(c), ctr_cand(c), c->scan_tmp.ptr,
+                            c->stream, &launches));
             tm.end();
             tm.begin(ST_VERIFY);
             CU(launch_verify(c->pk, (const Bucket *)c->buckets.ptr, (const uint64_t *)c->pair_off.ptr,
-                             ctr_u32(c), ctr_total(c), vs, amin, pl.kbits,
+                             ctr_nbuckets(c), ctr_total(c), vs, amin, pl.kbits,
                              (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
-                             ctr_u32(c) + 1, (uint32_t)c->rec_cap, c->stream, &launches));
+                             ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches));
             tm.end();
         }
         // record count -> host
         uint32_t nrec = 0;
         uint64_t cand = 0;
-        CU(cudaMemcpyAsync(&nrec, ctr_u32(c) + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+        int err = 0;
+        CU(cudaMemcpyAsync(&nrec, ctr_nrec(c), 4, cudaMemcpyDeviceToHost, c->stream));
         CU(cudaMemcpyAsync(&cand, ctr_cand(c), 8, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(&err, ctr_err(c), 4, cudaMemcpyDeviceToHost, c->stream));
         CU(cudaStreamSynchronize(c->stream));
+        if (err)
+            return fail(XYZ_ECUDA, "grouping table could not separate a partition's keys");
         if ((int64_t)nrec > c->rec_cap) {
             if (attempt == 1)
                 return fail(XYZ_ENOMEM, "record buffer overflow after resize");
@@ -374,12 +538,12 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
                         (int64_t)nrec, 2 * pl.kbits, dt, &alt, c->stream, &launches));
         const uint64_t *rk = (const uint64_t *)(alt ? c->rec_keys_alt.ptr : c->rec_keys.ptr);
         const uint32_t *ra = (const uint32_t *)(alt ? c->rec_agree_alt.ptr : c->rec_agree.ptr);
-        CU(launch_unique(rk, ra, ctr_u32(c) + 1, c->rec_cap, pl.kbits, c->pk.n,
+        CU(launch_unique(rk, ra, ctr_nrec(c), c->rec_cap, pl.kbits, c->pk.n,
                          (uint32_t *)c->flags.ptr, (uint32_t *)c->pos.ptr, dt + rt,
-                         (PairOut *)c->out.ptr, ctr_u32(c) + 2, c->stream, &launches));
+                         (PairOut *)c->out.ptr, ctr_nout(c), c->stream, &launches));
         tm.end();
         uint32_t nout = 0;
-        CU(cudaMemcpyAsync(&nout, ctr_u32(c) + 2, 4, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(&nout, ctr_nout(c), 4, cudaMemcpyDeviceToHost, c->stream));
         CU(cudaStreamSynchronize(c->stream));
         if (nrec == 0)
             nout = 0;
@@ -389,13 +553,14 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
         st.candidates = (int64_t)cand;
         st.passing = nrec;
         st.unique_pairs = nout;
-        st.key_bits = key_bits_max;
-        st.sort_passes = radix_passes(key_bits_max);
+        st.key_bits = pl.part ? M : key_bits_max;
+        st.sort_passes = pl.part ? 0 : radix_passes(key_bits_max);
+        st.survivors = pl.filter ? surv_total : runs * c->pk.p;
         st.gpu_launches = launches;
         tm.collect(st);
         // buckets of the last group only are visible; report that count
         uint32_t nb = 0;
-        cudaMemcpy(&nb, ctr_u32(c), 4, cudaMemcpyDeviceToHost);
+        cudaMemcpy(&nb, ctr_nbuckets(c), 4, cudaMemcpyDeviceToHost);
         st.buckets = nb;
         c->stats = st;
         *nout_host = nout;
@@ -474,7 +639,8 @@ void destroy_ctx(xyz_ctx *c)
                      &c->cnz,     &c->buckets,     &c->pair_counts, &c->pair_off, &c->scan_tmp,
                      &c->counters, &c->rec_keys,   &c->rec_keys_alt, &c->rec_agree,
                      &c->rec_agree_alt, &c->flags, &c->pos,       &c->out,      &c->dedup_tmp,
-                     &c->raw};
+                     &c->raw,     &c->ents,        &c->seg,       &c->members,  &c->kc_scratch,
+                     &c->seg_keys, &c->seg_vals,   &c->seg_count};
     for (DevBuf *b : all)
         release(*b);
     if (c->own_stream && c->stream)
@@ -707,6 +873,14 @@ int xyz_set_chunk_entries(xyz_ctx *ctx, int64_t entries)
     return XYZ_OK;
 }
 
+int xyz_set_filter(xyz_ctx *ctx, int enable)
+{
+    if (!ctx)
+        return fail(XYZ_EINVAL, "null context");
+    ctx->use_filter = enable != 0;
+    return XYZ_OK;
+}
+
 int xyz_run_keys(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, uint64_t *kx, uint64_t *c)
 {
     int rc = check_ctx(ctx);
@@ -721,6 +895,7 @@ int xyz_run_keys(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, uint64_t *
     const int64_t p = ctx->pk.p;
     Plan pl;
     pl.R = 1;
+    pl.part = false;
     pl.k64 = true;
     pl.kbits = 1;
     if ((rc = ensure_search_ws(ctx, pl)) || (rc = ensure(ctx->raw, (size_t)(p + 1) * 8)))

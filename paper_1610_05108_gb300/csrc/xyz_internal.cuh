@@ -125,6 +125,29 @@ cudaError_t launch_agree_pairs(const Packed &pk, const int32_t *j, const int32_t
 cudaError_t launch_sample_pairs(const Packed &pk, int64_t count, uint64_t seed, int32_t *j,
                                 int32_t *k, int32_t *agree, cudaStream_t s, int64_t *launches);
 
+// Partitioned grouping (group.cu), used for M <= 31.
+int part_bits(int64_t p);
+int part_blocks(int64_t p);
+bool part_supported(int64_t p, int M);
+size_t part_seg_words(int64_t p, int R);
+cudaError_t launch_keybuild_part(const Packed &pk, int M, uint64_t seed, int64_t l0, int R,
+                                 uint64_t *ents, uint32_t *seg, uint8_t *cnz, cudaStream_t s,
+                                 int64_t *launches);
+cudaError_t launch_group(const Packed &pk, int R, const uint64_t *ents, const uint32_t *seg,
+                         const uint8_t *cnz, uint32_t *members, uint32_t *members_count,
+                         Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets, int *err,
+                         cudaStream_t s, int64_t *launches);
+
+// Per-run survivor filter (filter.cu), used for M <= 31 and moderate p.
+bool filter_supported(int64_t p, int M);
+int filter_grid();
+size_t filter_scratch_words(int64_t p);
+cudaError_t launch_filter(const Packed &pk, int M, uint64_t seed, int64_t l0, int R,
+                          uint32_t *kc_scratch, uint32_t *seg_keys, uint32_t *seg_vals,
+                          uint32_t *seg_count, uint32_t seg_cap, int *overflow,
+                          uint32_t *out_keys, uint32_t *out_vals, uint32_t *nsurv, uint8_t *cnz,
+                          cudaStream_t s, int64_t *launches);
+
 // Host-side helpers shared by the API files.
 int64_t amin_rule(int64_t n, double kappa);
 

@@ -41,7 +41,8 @@ class Stats(ctypes.Structure):
         [(name, ctypes.c_double) for name in (
             "ms_keys", "ms_sort", "ms_join", "ms_verify", "ms_dedup", "ms_total")] + \
         [(name, ctypes.c_int64) for name in (
-            "launches_keys", "launches_sort", "launches_join", "launches_verify", "launches_dedup")]
+            "launches_keys", "launches_sort", "launches_join", "launches_verify", "launches_dedup",
+            "survivors")]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -63,6 +64,7 @@ SIGNATURES = {
     "xyz_get_stats": (ctypes.c_int, [_p, _p]),
     "xyz_set_timing": (ctypes.c_int, [_p, ctypes.c_int]),
     "xyz_set_chunk_entries": (ctypes.c_int, [_p, _i64]),
+    "xyz_set_filter": (ctypes.c_int, [_p, ctypes.c_int]),
     "xyz_run_keys": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _p]),
     "xyz_run_candidates": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _p]),
     "xyz_agree": (ctypes.c_int, [_p, _p, _p, _i64, _p]),
@@ -230,6 +232,9 @@ class Context:
 
     def set_chunk_entries(self, entries: int):
         _check(load().xyz_set_chunk_entries(self.handle, int(entries)))
+
+    def set_filter(self, on: bool):
+        _check(load().xyz_set_filter(self.handle, 1 if on else 0))
 
     def info(self) -> dict:
         n, p, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

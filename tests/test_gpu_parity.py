@@ -73,6 +73,14 @@ def _cand_cases():
     yield "heavy_bucket", X, Y, 6, range(2)
     X, Y = _rand(2000, 4100, 9)
     yield "two_tiles_M12", X, Y, 12, range(2)
+    X, Y = _rand(300, 9000, 10)
+    yield "three_blocks_M9", X, Y, 9, range(2)
+    X, Y = _rand(70, 3000, 17)
+    X[:, 10:400] = X[:, [5]]                   # 391 equal columns: groups survive M >= 32
+    X[:, 500:520] = X[:, [6]] * Y[:, None]     # X_j = Z_6: partners of column 6 in every run
+    yield "lsd_path_M33", X, Y, 33, range(2)
+    yield "lsd_path_M40", X, Y, 40, range(1)
+    yield "part_path_M31", X, Y, 31, range(2)
 
 
 @pytest.mark.parametrize("case", list(_cand_cases()), ids=lambda c: c[0])
@@ -126,7 +134,8 @@ def test_search_small_config_matches_oracle(xyz, orc):
 
 
 @pytest.mark.parametrize("n,p,L,M,kappa", [(97, 333, 25, 4, 0.2), (33, 1000, 40, 6, 0.3),
-                                           (500, 4097, 12, 9, 0.25), (64, 200, 7, 3, -0.1)])
+                                           (500, 4097, 12, 9, 0.25), (64, 200, 7, 3, -0.1),
+                                           (40, 700, 30, 32, 0.0), (40, 700, 30, 36, 0.0)])
 def test_search_ragged_matches_oracle(xyz, orc, n, p, L, M, kappa):
     X, Y = _rand(n, p, n + p)
     Y = (X[:, 3] * X[:, p - 2]).astype(np.int8)
@@ -149,6 +158,21 @@ def test_search_independent_of_launch_grouping(xyz):
             assert np.array_equal(got, ref), entries
             st = ctx.stats()
             assert st["runs"] == 37
+
+
+@pytest.mark.parametrize("M", [6, 12, 31])
+def test_search_independent_of_filter(xyz, orc, M):
+    d = synth.gwas(400, 6000, 7)
+    with xyz.create(d.X, d.Y) as ctx:
+        on = ctx.search(60, M, 0.2, 9)
+        st_on = ctx.stats()
+        ctx.set_filter(False)
+        off = ctx.search(60, M, 0.2, 9)
+        st_off = ctx.stats()
+    assert np.array_equal(on, off)
+    assert st_on["candidates"] == st_off["candidates"]
+    assert st_on["survivors"] <= st_off["survivors"] == 60 * d.p
+    assert np.array_equal(_pairs_array(on), orc.xyz(d.X, d.Y, 60, M, 0.2, 9))
 
 
 def test_search_range_union(xyz):
