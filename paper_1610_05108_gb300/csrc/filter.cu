@@ -33,7 +33,6 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int FL_THREADS = 1024;
 constexpr int FL_LOGB = 19;                       // filter bits per side
 constexpr int FL_WORDS = 1 << (FL_LOGB - 5);      // 16384 words per side
-constexpr uint32_t FL_MASK = (1u << FL_LOGB) - 1u;
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z)
 {
@@ -48,25 +47,18 @@ __device__ __forceinline__ int64_t draw_row(uint64_t seed, uint64_t t, int64_t n
     return (int64_t)__umul64hi(u, (uint64_t)n);
 }
 
-// Two filter positions of a canonical group value h.
+// Two filter positions of a canonical group value h: the top bits of two
+// multiplicative hashes (Knuth's multiplicative method with two odd
+// constants).
 __device__ __forceinline__ void bloom_pos(uint32_t h, uint32_t &b1, uint32_t &b2)
 {
-    const uint32_t x = mix32(h);
-    b1 = x & FL_MASK;
-    b2 = (x * 0x9E3779B1u) >> (32 - FL_LOGB);
+    b1 = (h * 0x9E3779B1u) >> (32 - FL_LOGB);
+    b2 = (h * 0x7FEB352Du + 0x165667B1u) >> (32 - FL_LOGB);
 }
 
 __device__ __forceinline__ void bloom_set(uint32_t *bm, uint32_t b)
 {
-    const uint32_t bit = 1u << (b & 31);
-    uint32_t *w = bm + (b >> 5);
-    if (!(*(volatile uint32_t *)w & bit))    // heavy groups: skip the atomic once set
-        atomicOr(w, bit);
-}
-
-__device__ __forceinline__ bool bloom_has(const uint32_t *bm, uint32_t b)
-{
-    return (bm[b >> 5] >> (b & 31)) & 1u;
+    atomicOr(bm + (b >> 5), 1u << (b & 31));
 }
 
 // Survivor i of CTA b goes to seg_keys/vals[b * seg_cap + i]; the CTA's
@@ -85,13 +77,12 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     uint32_t *bmB = fl_smem + FL_WORDS;            // [FL_WORDS]
     const int t = threadIdx.x;
     const int lane = t & 31, wp = t >> 5;
-    __shared__ int64_t rows[32];
+    __shared__ int64_t rowoff[32];      // row s_m times the row pitch
     __shared__ uint32_t c_sh;
     __shared__ uint32_t cursor;
     uint32_t *kcs = kc_scratch + (int64_t)blockIdx.x * 32 * P;
     uint32_t *okeys = seg_keys + (int64_t)blockIdx.x * seg_cap;
     uint32_t *ovals = seg_vals + (int64_t)blockIdx.x * seg_cap;
-    const unsigned lt = (1u << lane) - 1u;
     if (t == 0)
         cursor = 0;
 
@@ -105,7 +96,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 s = draw_row(seed, (uint64_t)(l0 + r) * (uint64_t)M + (uint64_t)lane, n);
                 ybit = (yb[s >> 5] >> (s & 31)) & 1u;
             }
-            rows[lane] = s;
+            rowoff[lane] = s * Pp;
             const uint32_t c = __ballot_sync(FULL, ybit);
             if (lane == 0) {
                 c_sh = c;
@@ -117,17 +108,18 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         const bool nz = c != 0;
 
         // pass 1: keys to the scratch rows, filter bits of each side
-        for (int64_t w = t; w < P; w += FL_THREADS) {
+        const uint32_t P32 = (uint32_t)P, p32 = (uint32_t)p;
+        for (uint32_t w = t; w < P32; w += FL_THREADS) {
             uint32_t A[32];
 #pragma unroll
             for (int m = 0; m < 32; ++m)
-                A[m] = (m < M) ? __ldg(Xr + rows[m] * Pp + w) : 0u;
+                A[m] = (m < M) ? __ldg(Xr + rowoff[m] + w) : 0u;
             transpose32(A);
 #pragma unroll
             for (int cc = 0; cc < 32; ++cc) {
                 const uint32_t kx = A[cc];
-                kcs[(int64_t)cc * P + w] = kx;
-                if (nz && 32 * w + cc < p) {
+                kcs[cc * P32 + w] = kx;
+                if (nz && 32 * w + cc < p32) {
                     const uint32_t kxc = kx ^ c;
                     const uint32_t h = kx < kxc ? kx : kxc;
                     uint32_t b1, b2;
@@ -145,46 +137,68 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         const int tb = nz ? 31 - __clz(c) : 0;
         const uint32_t lowmask = nz ? ((1u << tb) - 1u) : 0u;
         const uint32_t runbits = (uint32_t)r << M;
-        const int64_t steps = (P + FL_THREADS - 1) / FL_THREADS;
-        for (int cc = 0; cc < 32; ++cc) {
-            for (int64_t st = 0; st < steps; ++st) {
-                const int64_t w = st * FL_THREADS + t;
-                const int64_t j = 32 * w + cc;
-                bool keep = false;
-                uint32_t key = 0;
-                if (w < P && j < p) {
-                    const uint32_t kx = kcs[(int64_t)cc * P + w];
-                    if (!nz) {
-                        keep = true;
-                        key = kx;
-                    } else {
+        const uint32_t steps = (P32 + FL_THREADS - 1) / FL_THREADS;
+        for (uint32_t st = 0; st < steps; ++st) {
+            const uint32_t w = st * FL_THREADS + t;
+            uint32_t kv[32];
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc)
+                kv[cc] = (w < P32) ? kcs[cc * P32 + w] : 0u;
+            // bit cc of `keep`: column 32w + cc survives
+            uint32_t keep = 0;
+            if (w < P32) {
+                const uint32_t valid = (32 * w + 32 <= p32) ? 0xFFFFFFFFu
+                                                            : ((1u << (p32 - 32 * w)) - 1u);
+                if (!nz) {
+                    keep = valid;
+                } else {
+#pragma unroll
+                    for (int cc = 0; cc < 32; ++cc) {
+                        const uint32_t kx = kv[cc];
                         const uint32_t kxc = kx ^ c;
                         const uint32_t h = kx < kxc ? kx : kxc;
-                        const uint32_t side = (kx != h) ? 1u : 0u;
                         uint32_t b1, b2;
                         bloom_pos(h, b1, b2);
-                        const uint32_t *other = side ? bmA : bmB;
-                        keep = bloom_has(other, b1) && bloom_has(other, b2);
-                        if (keep) {
-                            const uint32_t above = (h >> (tb + 1)) << tb;
-                            key = ((above | (h & lowmask)) << 1) | side;
-                        }
+                        const uint32_t *other = (kx != h) ? bmA : bmB;
+                        const uint32_t hit = (other[b1 >> 5] >> (b1 & 31)) & (other[b2 >> 5] >> (b2 & 31)) & 1u;
+                        keep |= hit << cc;
                     }
+                    keep &= valid;
                 }
-                const unsigned bal = __ballot_sync(FULL, keep);
-                if (!bal)
-                    continue;
-                uint32_t wbase = 0;
-                if (lane == 0)
-                    wbase = atomicAdd(&cursor, (uint32_t)__popc(bal));
-                wbase = __shfl_sync(FULL, wbase, 0);
-                if (keep) {
-                    const uint32_t o = wbase + __popc(bal & lt);
-                    if (o < seg_cap) {
-                        okeys[o] = runbits | key;
-                        ovals[o] = (uint32_t)j;
-                    }
+            }
+            // one cursor step per warp
+            const uint32_t cnt = __popc(keep);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            const uint32_t wtot = __shfl_sync(FULL, incl, 31);
+            if (wtot == 0)
+                continue;
+            uint32_t wbase = 0;
+            if (lane == 31)
+                wbase = atomicAdd(&cursor, wtot);
+            wbase = __shfl_sync(FULL, wbase, 31);
+            uint32_t o = wbase + incl - cnt;
+            while (keep) {
+                const int cc = __ffs(keep) - 1;
+                keep &= keep - 1;
+                const uint32_t kx = kcs[cc * P32 + w];   // survivors only: re-read, cache-hot
+                uint32_t key = kx;
+                if (nz) {
+                    const uint32_t kxc = kx ^ c;
+                    const uint32_t h = kx < kxc ? kx : kxc;
+                    const uint32_t above = (h >> (tb + 1)) << tb;
+                    key = ((above | (h & lowmask)) << 1) | ((kx != h) ? 1u : 0u);
                 }
+                if (o < seg_cap) {
+                    okeys[o] = runbits | key;
+                    ovals[o] = 32 * w + cc;
+                }
+                ++o;
             }
         }
         __syncthreads();

@@ -106,6 +106,14 @@ __device__ __forceinline__ int agree_cols(const uint32_t *__restrict__ Xc, int64
     return a;
 }
 
+// Verification with eight lanes per candidate: each warp decodes 32
+// consecutive candidates (one per lane), then in eight steps handles four of
+// them at a time, the eight lanes of a group reading consecutive 16-byte
+// pieces of the two columns (fully used 128-byte segments) and summing their
+// popcounts with shuffles.  Each lane keeps its pieces of the response bits
+// in registers across the steps.
+constexpr int VQ = 4;   // response pieces per lane held in registers (columns up to 4096 rows)
+
 __global__ void __launch_bounds__(JV_THREADS)
     verify_kernel(const uint32_t *__restrict__ Xc, int64_t Wp, const uint32_t *__restrict__ yb,
                   const Bucket *__restrict__ buckets, const uint64_t *__restrict__ pair_off,
@@ -116,41 +124,103 @@ __global__ void __launch_bounds__(JV_THREADS)
 {
     const uint32_t nb = *nbuckets;
     const uint64_t T = *total_pairs;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & 7;
+    const int nq = (int)(Wp >> 2);
+    const uint4 *y4 = reinterpret_cast<const uint4 *>(yb);
+    uint4 yr[VQ];
+#pragma unroll
+    for (int i = 0; i < VQ; ++i) {
+        const int q = sub + 8 * i;
+        yr[i] = q < nq ? __ldg(y4 + q) : make_uint4(0, 0, 0, 0);
+    }
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += stride) {
-        uint32_t lo = 0, hi = nb;      // pair_off[lo] <= t < pair_off[hi], pair_off[nb] = T
-        while (hi - lo > 1) {
-            uint32_t mid = lo + (hi - lo) / 2;
-            if (pair_off[mid] <= t)
-                lo = mid;
-            else
-                hi = mid;
+    // Each warp takes 32 consecutive candidates.  Lane 0 finds the bucket of
+    // the first by binary search; 32 consecutive candidates span at most 32
+    // buckets (each holds >= 1), so every lane then searches only that window.
+    for (uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < T; t0 += stride) {
+        uint32_t base = 0;
+        if (lane == 0) {
+            uint32_t lo = 0, hi = nb;      // pair_off[lo] <= t0 < pair_off[hi], pair_off[nb] = T
+            while (hi - lo > 1) {
+                uint32_t mid = lo + (hi - lo) / 2;
+                if (pair_off[mid] <= t0)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            base = lo;
         }
-        const Bucket B = buckets[lo];
-        const uint64_t u = t - pair_off[lo];
-        uint32_t j, k;
-        if (B.nB) {
-            uint64_t ia = u / B.nB, ib = u - ia * B.nB;
-            j = vals[B.start + ia];
-            k = vals[B.start + B.nA + ib];
-        } else {
-            // u -> (x, y), x > y, u = x(x-1)/2 + y
-            uint64_t x = (uint64_t)((1.0 + sqrt(1.0 + 8.0 * (double)u)) * 0.5);
-            while (x * (x - 1) / 2 > u)
-                --x;
-            while ((x + 1) * x / 2 <= u)
-                ++x;
-            uint64_t y = u - x * (x - 1) / 2;
-            j = vals[B.start + x];
-            k = vals[B.start + y];
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const uint64_t t = t0 + lane;
+        const bool valid = t < T;
+        uint32_t j = 0, k = 0;
+        if (valid) {
+            uint32_t lo = base, hi = (nb - base > 33u) ? base + 33u : nb;
+            while (hi - lo > 1) {
+                uint32_t mid = lo + (hi - lo) / 2;
+                if (pair_off[mid] <= t)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            const Bucket B = buckets[lo];
+            const uint64_t u = t - pair_off[lo];
+            if (B.nB) {
+                uint64_t ia = u / B.nB, ib = u - ia * B.nB;
+                j = vals[B.start + ia];
+                k = vals[B.start + B.nA + ib];
+            } else {
+                // u -> (x, y), x > y, u = x(x-1)/2 + y
+                uint64_t x = (uint64_t)((1.0 + sqrt(1.0 + 8.0 * (double)u)) * 0.5);
+                while (x * (x - 1) / 2 > u)
+                    --x;
+                while ((x + 1) * x / 2 <= u)
+                    ++x;
+                uint64_t y = u - x * (x - 1) / 2;
+                j = vals[B.start + x];
+                k = vals[B.start + y];
+            }
         }
-        const int a = agree_cols(Xc, Wp, yb, j, k);
-        if (a >= amin) {
+        int agree = 0;
+#pragma unroll
+        for (int st = 0; st < 8; ++st) {
+            const int cidx = 4 * st + (lane >> 3);           // candidate of this lane's group
+            const uint32_t jj = __shfl_sync(0xffffffffu, j, cidx);
+            const uint32_t kk = __shfl_sync(0xffffffffu, k, cidx);
+            const bool vv = __shfl_sync(0xffffffffu, (int)valid, cidx) != 0;
+            int part = 0;
+            if (vv) {
+                const uint4 *cj = reinterpret_cast<const uint4 *>(Xc + (int64_t)jj * Wp);
+                const uint4 *ck = reinterpret_cast<const uint4 *>(Xc + (int64_t)kk * Wp);
+#pragma unroll
+                for (int i = 0; i < VQ; ++i) {
+                    const int q = sub + 8 * i;
+                    if (q < nq) {
+                        const uint4 x = __ldg(cj + q), z = __ldg(ck + q), y = yr[i];
+                        part += __popc(~(x.x ^ z.x ^ y.x)) + __popc(~(x.y ^ z.y ^ y.y)) +
+                                __popc(~(x.z ^ z.z ^ y.z)) + __popc(~(x.w ^ z.w ^ y.w));
+                    }
+                }
+                for (int q = sub + 8 * VQ; q < nq; q += 8) {
+                    const uint4 x = __ldg(cj + q), z = __ldg(ck + q), y = __ldg(y4 + q);
+                    part += __popc(~(x.x ^ z.x ^ y.x)) + __popc(~(x.y ^ z.y ^ y.y)) +
+                            __popc(~(x.z ^ z.z ^ y.z)) + __popc(~(x.w ^ z.w ^ y.w));
+                }
+            }
+            part += __shfl_xor_sync(0xffffffffu, part, 4);
+            part += __shfl_xor_sync(0xffffffffu, part, 2);
+            part += __shfl_xor_sync(0xffffffffu, part, 1);
+            const int got = __shfl_sync(0xffffffffu, part, 8 * (lane & 3));
+            if ((lane >> 2) == st)
+                agree = got;
+        }
+        if (valid && agree >= amin) {
             uint32_t idx = atomicAdd(nrec, 1u);
             if (idx < rec_cap) {
                 uint32_t lo_c = j < k ? j : k, hi_c = j < k ? k : j;
                 rec_keys[idx] = ((uint64_t)lo_c << kbits) | hi_c;
-                rec_agree[idx] = (uint32_t)a;
+                rec_agree[idx] = (uint32_t)agree;
             }
         }
     }
