@@ -19,10 +19,13 @@
 //           CTA's own output segment (warp-aggregated shared-memory cursor,
 //           no global atomics).
 //
-// A small second kernel concatenates the CTA segments for the LSD sort and
-// join of the general path.  A Bloom filter has no false negatives, so every
-// true candidate survives; false positives only cost sort work and are
-// grouped out by the join.  In a run with c == 0 every column survives.
+// The survivors of a run (a few percent of its columns) are then grouped on
+// chip into buckets and members, ready for verification; a run with too
+// many survivors for the chip goes to the CTA's global segment instead, and
+// a small second kernel concatenates the segments for the LSD sort and join
+// of the general path.  A Bloom filter has no false negatives, so every true
+// candidate survives; false positives are single-sided groups that never
+// become buckets.  In a run with c == 0 every column survives.
 #include "bits.cuh"
 #include "xyz_internal.cuh"
 
@@ -61,25 +64,47 @@ __device__ __forceinline__ void bloom_set(uint32_t *bm, uint32_t b)
     atomicOr(bm + (b >> 5), 1u << (b & 31));
 }
 
-// Survivor i of CTA b goes to seg_keys/vals[b * seg_cap + i]; the CTA's
-// count goes to seg_count[b].  kc_scratch holds, per CTA, the keys of its
-// current run in bit-major order: kx of column 32w + cc at cc * P + w.
+constexpr int FL_SMAX = 6144;                    // survivors of one run grouped on chip
+constexpr int FL_LOGT = 13;
+constexpr int FL_T = 1 << FL_LOGT;                // table slots, in the filter's memory
+constexpr uint32_t FL_EMPTY = 0xFFFFFFFFu;
+
+// One CTA per run at a time.  Passes 1-2 as described at the top of the
+// file; then, when the run has at most FL_SMAX survivors, they are grouped
+// on chip: the 128 KB that held the two filters becomes a hash table of
+// FL_T group keys with side counts, each group with candidates becomes a
+// bucket (bucket and member space reserved with one global atomic pair per
+// run) and its members are written side A first.  A run with more survivors
+// (for example every column of a run whose c is 0) re-runs pass 2 into the
+// CTA's global segment instead, as (run << M | Kc, j), for the general sort
+// and join.  kc_scratch holds, per CTA, the keys of its current run in
+// bit-major order: kx of column 32w + cc at cc * P + w.
 __global__ void __launch_bounds__(FL_THREADS, 1)
     filter_kernel(const uint32_t *__restrict__ Xr, int64_t Pp, int64_t P,
                   const uint32_t *__restrict__ yb, int64_t n, int64_t p, int M, uint64_t seed,
                   int64_t l0, int R, uint32_t *__restrict__ kc_scratch,
                   uint32_t *__restrict__ seg_keys, uint32_t *__restrict__ seg_vals,
                   uint32_t *__restrict__ seg_count, uint32_t seg_cap, int *__restrict__ overflow,
-                  uint8_t *__restrict__ cnz)
+                  uint8_t *__restrict__ cnz, uint32_t *__restrict__ members,
+                  uint32_t *__restrict__ members_count, Bucket *__restrict__ buckets,
+                  uint64_t *__restrict__ pair_counts, uint32_t *__restrict__ nbuckets)
 {
     extern __shared__ __align__(16) uint32_t fl_smem[];
-    uint32_t *bmA = fl_smem;                       // [FL_WORDS]
+    uint32_t *bmA = fl_smem;                       // [FL_WORDS]   (passes 1-2)
     uint32_t *bmB = fl_smem + FL_WORDS;            // [FL_WORDS]
+    uint32_t *tkey = fl_smem;                      // [FL_T]       (grouping)
+    uint32_t *cA = fl_smem + FL_T;                 // [FL_T]
+    uint32_t *cB = fl_smem + 2 * FL_T;             // [FL_T]
+    uint32_t *tok = fl_smem + 3 * FL_T;            // [FL_T] 1 = group has a bucket
+    uint64_t *sv = reinterpret_cast<uint64_t *>(fl_smem + 2 * FL_WORDS);   // [FL_SMAX]
     const int t = threadIdx.x;
     const int lane = t & 31, wp = t >> 5;
     __shared__ int64_t rowoff[32];      // row s_m times the row pitch
     __shared__ uint32_t c_sh;
-    __shared__ uint32_t cursor;
+    __shared__ uint32_t cursor;         // global segment fill
+    __shared__ uint32_t ns;             // survivors of the current run
+    __shared__ uint32_t wsum[FL_THREADS / 32];
+    __shared__ uint32_t mbase_sh, bbase_sh;
     uint32_t *kcs = kc_scratch + (int64_t)blockIdx.x * 32 * P;
     uint32_t *okeys = seg_keys + (int64_t)blockIdx.x * seg_cap;
     uint32_t *ovals = seg_vals + (int64_t)blockIdx.x * seg_cap;
@@ -100,15 +125,19 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             const uint32_t c = __ballot_sync(FULL, ybit);
             if (lane == 0) {
                 c_sh = c;
+                ns = 0;
                 cnz[r] = (c != 0);
             }
         }
         __syncthreads();
         const uint32_t c = c_sh;
         const bool nz = c != 0;
+        const int tb = nz ? 31 - __clz(c) : 0;
+        const uint32_t lowmask = nz ? ((1u << tb) - 1u) : 0u;
+        const uint32_t P32 = (uint32_t)P, p32 = (uint32_t)p;
+        const uint32_t steps = (P32 + FL_THREADS - 1) / FL_THREADS;
 
         // pass 1: keys to the scratch rows, filter bits of each side
-        const uint32_t P32 = (uint32_t)P, p32 = (uint32_t)p;
         for (uint32_t w = t; w < P32; w += FL_THREADS) {
             uint32_t A[32];
 #pragma unroll
@@ -132,74 +161,179 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         }
         __syncthreads();
 
-        // pass 2: keep columns whose group may have members on the other
-        // side; write them as (run << M | Kc, j)
-        const int tb = nz ? 31 - __clz(c) : 0;
-        const uint32_t lowmask = nz ? ((1u << tb) - 1u) : 0u;
-        const uint32_t runbits = (uint32_t)r << M;
-        const uint32_t steps = (P32 + FL_THREADS - 1) / FL_THREADS;
-        for (uint32_t st = 0; st < steps; ++st) {
-            const uint32_t w = st * FL_THREADS + t;
-            uint32_t kv[32];
+        // pass 2: the survivors of the run.  to_global = false: into the
+        // shared survivor array (only counted past FL_SMAX); true: into the
+        // CTA's global segment as (run << M | Kc, j).
+        auto pass2 = [&](bool to_global) {
+            const uint32_t runbits = (uint32_t)r << M;
+            for (uint32_t st = 0; st < steps; ++st) {
+                const uint32_t w = st * FL_THREADS + t;
+                uint32_t kv[32];
 #pragma unroll
-            for (int cc = 0; cc < 32; ++cc)
-                kv[cc] = (w < P32) ? kcs[cc * P32 + w] : 0u;
-            // bit cc of `keep`: column 32w + cc survives
-            uint32_t keep = 0;
-            if (w < P32) {
-                const uint32_t valid = (32 * w + 32 <= p32) ? 0xFFFFFFFFu
-                                                            : ((1u << (p32 - 32 * w)) - 1u);
-                if (!nz) {
-                    keep = valid;
-                } else {
+                for (int cc = 0; cc < 32; ++cc)
+                    kv[cc] = (w < P32) ? kcs[cc * P32 + w] : 0u;
+                uint32_t keep = 0;     // bit cc: column 32w + cc survives
+                if (w < P32) {
+                    const uint32_t valid = (32 * w + 32 <= p32) ? 0xFFFFFFFFu
+                                                                : ((1u << (p32 - 32 * w)) - 1u);
+                    if (!nz) {
+                        keep = valid;
+                    } else {
 #pragma unroll
-                    for (int cc = 0; cc < 32; ++cc) {
-                        const uint32_t kx = kv[cc];
+                        for (int cc = 0; cc < 32; ++cc) {
+                            const uint32_t kx = kv[cc];
+                            const uint32_t kxc = kx ^ c;
+                            const uint32_t h = kx < kxc ? kx : kxc;
+                            uint32_t b1, b2;
+                            bloom_pos(h, b1, b2);
+                            const uint32_t *other = (kx != h) ? bmA : bmB;
+                            const uint32_t hit =
+                                (other[b1 >> 5] >> (b1 & 31)) & (other[b2 >> 5] >> (b2 & 31)) & 1u;
+                            keep |= hit << cc;
+                        }
+                        keep &= valid;
+                    }
+                }
+                const uint32_t cnt = __popc(keep);
+                uint32_t incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o)
+                        incl += y;
+                }
+                const uint32_t wtot = __shfl_sync(FULL, incl, 31);
+                if (wtot == 0)
+                    continue;
+                uint32_t wbase = 0;
+                if (lane == 31)
+                    wbase = atomicAdd(to_global ? &cursor : &ns, wtot);
+                wbase = __shfl_sync(FULL, wbase, 31);
+                uint32_t o = wbase + incl - cnt;
+                while (keep) {
+                    const int cc = __ffs(keep) - 1;
+                    keep &= keep - 1;
+                    const uint32_t kx = kcs[cc * P32 + w];   // survivors only: re-read, cache-hot
+                    uint32_t key = kx;
+                    if (nz) {
                         const uint32_t kxc = kx ^ c;
                         const uint32_t h = kx < kxc ? kx : kxc;
-                        uint32_t b1, b2;
-                        bloom_pos(h, b1, b2);
-                        const uint32_t *other = (kx != h) ? bmA : bmB;
-                        const uint32_t hit = (other[b1 >> 5] >> (b1 & 31)) & (other[b2 >> 5] >> (b2 & 31)) & 1u;
-                        keep |= hit << cc;
+                        const uint32_t above = (h >> (tb + 1)) << tb;
+                        key = ((above | (h & lowmask)) << 1) | ((kx != h) ? 1u : 0u);
                     }
-                    keep &= valid;
+                    if (to_global) {
+                        if (o < seg_cap) {
+                            okeys[o] = runbits | key;
+                            ovals[o] = 32 * w + cc;
+                        }
+                    } else if (o < FL_SMAX) {
+                        sv[o] = ((uint64_t)key << 32) | (32 * w + cc);
+                    }
+                    ++o;
                 }
             }
-            // one cursor step per warp
-            const uint32_t cnt = __popc(keep);
-            uint32_t incl = cnt;
+        };
+        pass2(false);
+        __syncthreads();
+        const uint32_t s = ns;
+        if (s > FL_SMAX) {
+            pass2(true);            // too many for the chip: the general path groups them
+            __syncthreads();
+            continue;
+        }
+
+        // grouping on chip; the filters are dead, their memory is the table
+        for (int i = t; i < FL_T; i += FL_THREADS) {
+            tkey[i] = FL_EMPTY;
+            cA[i] = 0;
+            cB[i] = 0;
+        }
+        __syncthreads();
+        // phase I: insert group keys, count sides; keep (side, slot, j)
+        for (uint32_t i = t; i < s; i += FL_THREADS) {
+            const uint64_t e = sv[i];
+            const uint32_t Kc = (uint32_t)(e >> 32);
+            const uint32_t g = nz ? (Kc >> 1) : Kc;
+            const uint32_t side = nz ? (Kc & 1u) : 0u;
+            uint32_t slot = (g * 0x9E3779B1u) >> (32 - FL_LOGT);
+            for (int probe = 0; probe < FL_T; ++probe) {     // s < FL_T: always ends
+                const uint32_t old = atomicCAS(&tkey[slot], FL_EMPTY, g);
+                if (old == FL_EMPTY || old == g)
+                    break;
+                slot = (slot + 1) & (FL_T - 1);
+            }
+            atomicAdd(side ? &cB[slot] : &cA[slot], 1u);
+            sv[i] = ((uint64_t)((side << 31) | slot) << 32) | (uint32_t)e;
+        }
+        __syncthreads();
+        // phase II: groups with candidates -> buckets; one global atomic
+        // pair per run reserves their space
+        {
+            constexpr int PER = FL_T / FL_THREADS;
+            uint32_t packed[PER];          // members << 16 | buckets of each slot
+            uint32_t mysum = 0;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int slot = t * PER + q;
+                uint32_t v = 0;
+                if (tkey[slot] != FL_EMPTY) {
+                    const uint32_t nA = cA[slot], nB = cB[slot];
+                    const bool ok = nz ? (nA > 0 && nB > 0) : (nA > 1);
+                    if (ok)
+                        v = ((nA + nB) << 16) | 1u;
+                }
+                packed[q] = v;
+                mysum += v;
+            }
+            uint32_t incl = mysum;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(FULL, incl, o);
                 if (lane >= o)
                     incl += y;
             }
-            const uint32_t wtot = __shfl_sync(FULL, incl, 31);
-            if (wtot == 0)
-                continue;
-            uint32_t wbase = 0;
             if (lane == 31)
-                wbase = atomicAdd(&cursor, wtot);
-            wbase = __shfl_sync(FULL, wbase, 31);
-            uint32_t o = wbase + incl - cnt;
-            while (keep) {
-                const int cc = __ffs(keep) - 1;
-                keep &= keep - 1;
-                const uint32_t kx = kcs[cc * P32 + w];   // survivors only: re-read, cache-hot
-                uint32_t key = kx;
-                if (nz) {
-                    const uint32_t kxc = kx ^ c;
-                    const uint32_t h = kx < kxc ? kx : kxc;
-                    const uint32_t above = (h >> (tb + 1)) << tb;
-                    key = ((above | (h & lowmask)) << 1) | ((kx != h) ? 1u : 0u);
-                }
-                if (o < seg_cap) {
-                    okeys[o] = runbits | key;
-                    ovals[o] = 32 * w + cc;
-                }
-                ++o;
+                wsum[wp] = incl;
+            __syncthreads();
+            uint32_t before = 0, total = 0;
+            for (int i = 0; i < FL_THREADS / 32; ++i) {
+                before += (i < wp) ? wsum[i] : 0u;
+                total += wsum[i];
             }
+            if (t == 0) {
+                const uint32_t mt = total >> 16, bt = total & 0xFFFFu;
+                mbase_sh = bt ? atomicAdd(members_count, mt) : 0u;
+                bbase_sh = bt ? atomicAdd(nbuckets, bt) : 0u;
+            }
+            __syncthreads();
+            uint32_t run_off = before + incl - mysum;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int slot = t * PER + q;
+                const uint32_t v = packed[q];
+                tok[slot] = v ? 1u : 0u;
+                if (v) {
+                    const uint32_t nA = cA[slot], nB = cB[slot];
+                    const uint32_t base = mbase_sh + (run_off >> 16);
+                    const uint32_t bi = bbase_sh + (run_off & 0xFFFFu);
+                    buckets[bi] = Bucket{base, nA, nz ? nB : 0u, 0u};
+                    pair_counts[bi] = nz ? (uint64_t)nA * nB : (uint64_t)nA * (nA - 1) / 2;
+                    cA[slot] = base + nA;          // end of side A: cursor counts down
+                    cB[slot] = base + nA + nB;     // end of side B
+                }
+                run_off += v;
+            }
+        }
+        __syncthreads();
+        // phase III: members, side A first
+        for (uint32_t i = t; i < s; i += FL_THREADS) {
+            const uint64_t e = sv[i];
+            const uint32_t hi = (uint32_t)(e >> 32);
+            const uint32_t slot = hi & 0x7FFFFFFFu;
+            if (!tok[slot])
+                continue;
+            const uint32_t pos = atomicSub((hi >> 31) ? &cB[slot] : &cA[slot], 1u) - 1u;
+            members[pos] = (uint32_t)e;
         }
         __syncthreads();
     }
@@ -242,7 +376,9 @@ __global__ void __launch_bounds__(256)
 
 bool filter_supported(int64_t p, int M) { return M <= 31 && p <= 262144; }
 
-size_t filter_smem_bytes() { return (size_t)(2 * FL_WORDS) * 4; }
+size_t filter_smem_bytes() { return (size_t)(2 * FL_WORDS) * 4 + (size_t)FL_SMAX * 8; }
+
+int64_t filter_run_cap() { return FL_SMAX; }
 
 int filter_grid()
 {
@@ -258,7 +394,9 @@ cudaError_t launch_filter(const Packed &pk, int M, uint64_t seed, int64_t l0, in
                           uint32_t *kc_scratch, uint32_t *seg_keys, uint32_t *seg_vals,
                           uint32_t *seg_count, uint32_t seg_cap, int *overflow,
                           uint32_t *out_keys, uint32_t *out_vals, uint32_t *nsurv, uint8_t *cnz,
-                          cudaStream_t s, int64_t *launches)
+                          uint32_t *members, uint32_t *members_count, Bucket *buckets,
+                          uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
+                          int64_t *launches)
 {
     const size_t smem = filter_smem_bytes();
     cudaError_t e =
@@ -270,7 +408,8 @@ cudaError_t launch_filter(const Packed &pk, int M, uint64_t seed, int64_t l0, in
         grid = R;
     filter_kernel<<<grid, FL_THREADS, smem, s>>>(pk.Xr, pk.Pp, pk.P, pk.yb, pk.n, pk.p, M, seed, l0, R,
                                                  kc_scratch, seg_keys, seg_vals, seg_count, seg_cap,
-                                                 overflow, cnz);
+                                                 overflow, cnz, members, members_count, buckets,
+                                                 pair_counts, nbuckets);
     *launches += 1;
     e = cudaGetLastError();
     if (e != cudaSuccess)

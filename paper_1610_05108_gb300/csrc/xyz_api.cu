@@ -84,6 +84,7 @@ struct xyz_ctx {
     DevBuf ents, seg, members;   // partitioned grouping
     DevBuf kc_scratch;           // filter path: one key row per CTA
     DevBuf seg_keys, seg_vals, seg_count;   // filter path: per-CTA survivor segments
+    DevBuf buckets2, pair_counts2, pair_off2, scan_tmp2;   // filter path: spilled runs
     int64_t surv_cap = 0;        // filter path: survivor capacity (CTAs x segment)
     int64_t seg_cap = 0;         // filter path: survivors one CTA may write per group
     int64_t seg_runs_p = 0;      // filter path: runs-per-CTA x p the segment is sized for
@@ -132,7 +133,8 @@ static int64_t ws_bytes(const xyz_ctx *c)
                            &c->rec_keys_alt, &c->rec_agree, &c->rec_agree_alt, &c->flags,
                            &c->pos,     &c->out,         &c->dedup_tmp, &c->raw,
                            &c->ents, &c->seg, &c->members, &c->kc_scratch,
-                           &c->seg_keys, &c->seg_vals, &c->seg_count};
+                           &c->seg_keys, &c->seg_vals, &c->seg_count,
+                           &c->buckets2, &c->pair_counts2, &c->pair_off2, &c->scan_tmp2};
     int64_t s = 0;
     for (const DevBuf *b : all)
         s += (int64_t)b->bytes;
@@ -280,21 +282,27 @@ int ensure_search_ws(xyz_ctx *c, const Plan &pl)
         const int64_t grid = filter_grid() < pl.R ? filter_grid() : pl.R;
         const int64_t worst = (pl.R + grid - 1) / grid * c->pk.p;
         if (c->seg_runs_p != worst) {
+            // spilled runs are rare: room for about one per CTA, grown on overflow
             c->seg_runs_p = worst;
-            c->seg_cap = worst / 8 + 4096 < worst ? worst / 8 + 4096 : worst;
+            c->seg_cap = c->pk.p + 4096 < worst ? c->pk.p + 4096 : worst;
         }
         const int64_t seg_cap = c->seg_cap;
         const int64_t cap = grid * seg_cap;
         c->surv_cap = cap;
         const int64_t sb = cap / 2 + 1;
+        const int64_t mcap = pl.R * filter_run_cap();   // members grouped on chip
+        const int64_t mb = mcap / 2 + 1;
         if ((rc = ensure(c->kc_scratch, filter_scratch_words(c->pk.p) * 4)) ||
             (rc = ensure(c->seg_keys, (size_t)cap * 4)) || (rc = ensure(c->seg_vals, (size_t)cap * 4)) ||
             (rc = ensure(c->seg_count, (size_t)filter_grid() * 4)) ||
             (rc = ensure(c->keysA, cap * 4)) || (rc = ensure(c->keysB, cap * 4)) ||
             (rc = ensure(c->valsA, cap * 4)) || (rc = ensure(c->valsB, cap * 4)) ||
             (rc = ensure(c->radix_tmp, radix_temp_bytes(cap))) || (rc = ensure(c->cnz, pl.R)) ||
-            (rc = ensure(c->buckets, sb * sizeof(Bucket))) || (rc = ensure(c->pair_counts, sb * 8)) ||
-            (rc = ensure(c->pair_off, sb * 8)) || (rc = ensure(c->scan_tmp, scan_temp_bytes(sb))) ||
+            (rc = ensure(c->members, mcap * 4)) || (rc = ensure(c->buckets, mb * sizeof(Bucket))) ||
+            (rc = ensure(c->pair_counts, mb * 8)) || (rc = ensure(c->pair_off, mb * 8)) ||
+            (rc = ensure(c->scan_tmp, scan_temp_bytes(mb))) ||
+            (rc = ensure(c->buckets2, sb * sizeof(Bucket))) || (rc = ensure(c->pair_counts2, sb * 8)) ||
+            (rc = ensure(c->pair_off2, sb * 8)) || (rc = ensure(c->scan_tmp2, scan_temp_bytes(sb))) ||
             (rc = ensure(c->counters, 64)))
             return rc;
         return XYZ_OK;
@@ -339,11 +347,13 @@ uint32_t *ctr_nbuckets(xyz_ctx *c) { return ctr_u32(c) + 0; }
 uint32_t *ctr_members(xyz_ctx *c) { return ctr_u32(c) + 1; }
 uint32_t *ctr_nsurv(xyz_ctx *c) { return ctr_u32(c) + 2; }
 int *ctr_sovf(xyz_ctx *c) { return reinterpret_cast<int *>(ctr_u32(c) + 3); }
-uint32_t *ctr_nrec(xyz_ctx *c) { return ctr_u32(c) + 4; }
-uint32_t *ctr_nout(xyz_ctx *c) { return ctr_u32(c) + 5; }
-int *ctr_err(xyz_ctx *c) { return reinterpret_cast<int *>(ctr_u32(c) + 6); }
+uint32_t *ctr_nbuckets2(xyz_ctx *c) { return ctr_u32(c) + 4; }
+uint32_t *ctr_nrec(xyz_ctx *c) { return ctr_u32(c) + 5; }
+uint32_t *ctr_nout(xyz_ctx *c) { return ctr_u32(c) + 6; }
+int *ctr_err(xyz_ctx *c) { return reinterpret_cast<int *>(ctr_u32(c) + 7); }
 uint64_t *ctr_total(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 32); }
 uint64_t *ctr_cand(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 40); }
+uint64_t *ctr_total2(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 48); }
 
 #define CU(expr)                                                                         \
     do {                                                                                 \
@@ -382,16 +392,31 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
             const int bits = M + rbits;
             key_bits_max = bits > key_bits_max ? bits : key_bits_max;
             ++chunks;
-            CU(cudaMemsetAsync(ctr_u32(c), 0, 16, c->stream));   // per-group counters
+            CU(cudaMemsetAsync(ctr_u32(c), 0, 20, c->stream));   // per-group counters
             const int64_t bcap = Nc / 2 + 1;
             if (pl.filter) {
-                tm.begin(ST_KEYS);
                 const int64_t seg_cap = c->seg_cap;
+                const int64_t mb = pl.R * filter_run_cap() / 2 + 1;
+                tm.begin(ST_KEYS);
                 CU(launch_filter(c->pk, M, seed, g0, (int)Rc, (uint32_t *)c->kc_scratch.ptr,
                                  (uint32_t *)c->seg_keys.ptr, (uint32_t *)c->seg_vals.ptr,
                                  (uint32_t *)c->seg_count.ptr, (uint32_t)seg_cap, ctr_sovf(c),
                                  (uint32_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr, ctr_nsurv(c),
-                                 (uint8_t *)c->cnz.ptr, c->stream, &launches));
+                                 (uint8_t *)c->cnz.ptr, (uint32_t *)c->members.ptr, ctr_members(c),
+                                 (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
+                                 ctr_nbuckets(c), c->stream, &launches));
+                tm.end();
+                tm.begin(ST_JOIN);
+                CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
+                                ctr_nbuckets(c), mb, ctr_total(c), ctr_cand(c), c->scan_tmp.ptr,
+                                c->stream, &launches));
+                tm.end();
+                tm.begin(ST_VERIFY);
+                CU(launch_verify(c->pk, (const Bucket *)c->buckets.ptr,
+                                 (const uint64_t *)c->pair_off.ptr, ctr_nbuckets(c), ctr_total(c),
+                                 (const uint32_t *)c->members.ptr, amin, pl.kbits,
+                                 (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
+                                 ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches));
                 tm.end();
                 uint32_t ns = 0;
                 int sovf = 0;
@@ -399,8 +424,10 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
                 CU(cudaMemcpyAsync(&sovf, ctr_sovf(c), 4, cudaMemcpyDeviceToHost, c->stream));
                 CU(cudaStreamSynchronize(c->stream));
                 if (sovf) {
-                    // a CTA segment overflowed: grow the segments and redo
-                    // this group (a segment of runs-per-CTA x p never does)
+                    // a CTA segment of spilled runs overflowed: grow the segments
+                    // and redo this group (records found twice are merged by the
+                    // final deduplication; a segment of runs-per-CTA x p never
+                    // overflows)
                     int64_t want = 2 * c->seg_cap;
                     if (want > c->seg_runs_p)
                         want = c->seg_runs_p;
@@ -413,6 +440,9 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
                     --chunks;
                     continue;
                 }
+                if (ns == 0)
+                    continue;
+                // runs with too many survivors for the chip: general path
                 surv_total += ns;
                 bool alt = false;
                 tm.begin(ST_SORT);
@@ -425,15 +455,15 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
                 const int64_t sb = c->surv_cap / 2 + 1;
                 tm.begin(ST_JOIN);
                 CU(launch_join32(ks, (int64_t)ns, M, rbits, (const uint8_t *)c->cnz.ptr,
-                                 (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
-                                 ctr_nbuckets(c), c->stream, &launches));
-                CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
-                                ctr_nbuckets(c), sb, ctr_total(c), ctr_cand(c), c->scan_tmp.ptr,
+                                 (Bucket *)c->buckets2.ptr, (uint64_t *)c->pair_counts2.ptr,
+                                 ctr_nbuckets2(c), c->stream, &launches));
+                CU(scan_u64_dev((const uint64_t *)c->pair_counts2.ptr, (uint64_t *)c->pair_off2.ptr,
+                                ctr_nbuckets2(c), sb, ctr_total2(c), ctr_cand(c), c->scan_tmp2.ptr,
                                 c->stream, &launches));
                 tm.end();
                 tm.begin(ST_VERIFY);
-                CU(launch_verify(c->pk, (const Bucket *)c->buckets.ptr,
-                                 (const uint64_t *)c->pair_off.ptr, ctr_nbuckets(c), ctr_total(c), vs,
+                CU(launch_verify(c->pk, (const Bucket *)c->buckets2.ptr,
+                                 (const uint64_t *)c->pair_off2.ptr, ctr_nbuckets2(c), ctr_total2(c), vs,
                                  amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
                                  (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
                                  c->stream, &launches));
@@ -640,7 +670,8 @@ void destroy_ctx(xyz_ctx *c)
                      &c->counters, &c->rec_keys,   &c->rec_keys_alt, &c->rec_agree,
                      &c->rec_agree_alt, &c->flags, &c->pos,       &c->out,      &c->dedup_tmp,
                      &c->raw,     &c->ents,        &c->seg,       &c->members,  &c->kc_scratch,
-                     &c->seg_keys, &c->seg_vals,   &c->seg_count};
+                     &c->seg_keys, &c->seg_vals,   &c->seg_count, &c->buckets2, &c->pair_counts2,
+                     &c->pair_off2, &c->scan_tmp2};
     for (DevBuf *b : all)
         release(*b);
     if (c->own_stream && c->stream)

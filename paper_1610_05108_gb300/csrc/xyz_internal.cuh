@@ -142,11 +142,14 @@ cudaError_t launch_group(const Packed &pk, int R, const uint64_t *ents, const ui
 bool filter_supported(int64_t p, int M);
 int filter_grid();
 size_t filter_scratch_words(int64_t p);
+int64_t filter_run_cap();
 cudaError_t launch_filter(const Packed &pk, int M, uint64_t seed, int64_t l0, int R,
                           uint32_t *kc_scratch, uint32_t *seg_keys, uint32_t *seg_vals,
                           uint32_t *seg_count, uint32_t seg_cap, int *overflow,
                           uint32_t *out_keys, uint32_t *out_vals, uint32_t *nsurv, uint8_t *cnz,
-                          cudaStream_t s, int64_t *launches);
+                          uint32_t *members, uint32_t *members_count, Bucket *buckets,
+                          uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
+                          int64_t *launches);
 
 // Host-side helpers shared by the API files.
 int64_t amin_rule(int64_t n, double kappa);

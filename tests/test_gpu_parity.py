@@ -81,6 +81,9 @@ def _cand_cases():
     yield "lsd_path_M33", X, Y, 33, range(2)
     yield "lsd_path_M40", X, Y, 40, range(1)
     yield "part_path_M31", X, Y, 31, range(2)
+    X, Y = _rand(90, 7000, 18)
+    Y[:] = 1                                   # c = 0: all 7000 columns survive -> spill path
+    yield "spill_c_zero", X, Y, 13, range(2)
 
 
 @pytest.mark.parametrize("case", list(_cand_cases()), ids=lambda c: c[0])
@@ -173,6 +176,21 @@ def test_search_independent_of_filter(xyz, orc, M):
     assert st_on["candidates"] == st_off["candidates"]
     assert st_on["survivors"] <= st_off["survivors"] == 60 * d.p
     assert np.array_equal(_pairs_array(on), orc.xyz(d.X, d.Y, 60, M, 0.2, 9))
+
+
+def test_search_mixing_spilled_and_on_chip_runs(xyz, orc):
+    # Y mostly +1: with M = 4 most runs draw only +1 rows (c = 0, every
+    # column survives, p > 6144 -> general sort path), the others are grouped
+    # on chip; both feed one result.
+    X, Y = _rand(120, 6500, 19)
+    Y[:] = 1
+    Y[:6] = -1
+    Y = Y * (X[:, 2] * X[:, 3]) * (X[:, 2] * X[:, 3])     # keep +-1, no change
+    with xyz.create(X, Y) as ctx:
+        got = _pairs_array(ctx.search(12, 4, 0.9, 5))
+        st = ctx.stats()
+    assert st["survivors"] > 0
+    assert np.array_equal(got, orc.xyz(X, Y, 12, 4, 0.9, 5))
 
 
 def test_search_range_union(xyz):
