@@ -11,10 +11,11 @@
 //   pass 1  build the keys of all p columns (each thread: the words of the M
 //           sampled rows, transposed in registers), store kx to the CTA's
 //           L2-resident scratch in bit-major order (coalesced without
-//           staging), and set two bits, at two hashes of h, in the
-//           shared-memory Bloom filter of the column's side;
+//           staging), and set two bits
+//           of one word, chosen by hashes of h, in the shared-memory
+//           blocked Bloom filter of the column's side;
 //   pass 2  keep the columns whose h may be present on the other side (both
-//           bits set in the other side's filter) and append them, as
+//           bits set in the other side's filter word) and append them, as
 //           (run << M | Kc, j) with the canonical key Kc of keys.cu, to the
 //           CTA's own output segment (warp-aggregated shared-memory cursor,
 //           no global atomics).
@@ -50,18 +51,15 @@ __device__ __forceinline__ int64_t draw_row(uint64_t seed, uint64_t t, int64_t n
     return (int64_t)__umul64hi(u, (uint64_t)n);
 }
 
-// Two filter positions of a canonical group value h: the top bits of two
-// multiplicative hashes (Knuth's multiplicative method with two odd
-// constants).
-__device__ __forceinline__ void bloom_pos(uint32_t h, uint32_t &b1, uint32_t &b2)
+// Blocked Bloom filter: a group value h selects one 32-bit word of its
+// side's filter and two bits inside it, all from multiplicative hashes
+// (Knuth's method with two odd constants, top bits).  Setting is one shared
+// atomic OR, testing one shared load.
+__device__ __forceinline__ void bloom_pos(uint32_t h, uint32_t &word, uint32_t &mask)
 {
-    b1 = (h * 0x9E3779B1u) >> (32 - FL_LOGB);
-    b2 = (h * 0x7FEB352Du + 0x165667B1u) >> (32 - FL_LOGB);
-}
-
-__device__ __forceinline__ void bloom_set(uint32_t *bm, uint32_t b)
-{
-    atomicOr(bm + (b >> 5), 1u << (b & 31));
+    word = (h * 0x9E3779B1u) >> (32 - (FL_LOGB - 5));
+    const uint32_t y = h * 0x7FEB352Du + 0x165667B1u;
+    mask = (1u << (y >> 27)) | (1u << ((y >> 22) & 31u));
 }
 
 constexpr int FL_SMAX = 6144;                    // survivors of one run grouped on chip
@@ -79,6 +77,7 @@ constexpr uint32_t FL_EMPTY = 0xFFFFFFFFu;
 // CTA's global segment instead, as (run << M | Kc, j), for the general sort
 // and join.  kc_scratch holds, per CTA, the keys of its current run in
 // bit-major order: kx of column 32w + cc at cc * P + w.
+template <int MB>
 __global__ void __launch_bounds__(FL_THREADS, 1)
     filter_kernel(const uint32_t *__restrict__ Xr, int64_t Pp, int64_t P,
                   const uint32_t *__restrict__ yb, int64_t n, int64_t p, int M, uint64_t seed,
@@ -137,25 +136,29 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         const uint32_t P32 = (uint32_t)P, p32 = (uint32_t)p;
         const uint32_t steps = (P32 + FL_THREADS - 1) / FL_THREADS;
 
-        // pass 1: keys to the scratch rows, filter bits of each side
+        // pass 1: keys to the scratch rows, filter bits of each side.  Rows
+        // at or past MB are zero at compile time, which trims the transpose.
         for (uint32_t w = t; w < P32; w += FL_THREADS) {
             uint32_t A[32];
 #pragma unroll
             for (int m = 0; m < 32; ++m)
-                A[m] = (m < M) ? __ldg(Xr + rowoff[m] + w) : 0u;
+                A[m] = (m < MB && m < M) ? __ldg(Xr + rowoff[m] + w) : 0u;
             transpose32(A);
 #pragma unroll
-            for (int cc = 0; cc < 32; ++cc) {
-                const uint32_t kx = A[cc];
-                kcs[cc * P32 + w] = kx;
-                if (nz && 32 * w + cc < p32) {
-                    const uint32_t kxc = kx ^ c;
-                    const uint32_t h = kx < kxc ? kx : kxc;
-                    uint32_t b1, b2;
-                    bloom_pos(h, b1, b2);
-                    uint32_t *bm = (kx != h) ? bmB : bmA;
-                    bloom_set(bm, b1);
-                    bloom_set(bm, b2);
+            for (int cc = 0; cc < 32; ++cc)
+                kcs[cc * P32 + w] = A[cc];         // bit-major: coalesced across the warp
+            if (nz) {
+                const uint32_t ncol = (32 * w + 32 <= p32) ? 32u : p32 - 32 * w;
+#pragma unroll
+                for (int cc = 0; cc < 32; ++cc) {
+                    if ((uint32_t)cc < ncol) {
+                        const uint32_t kx = A[cc];
+                        const uint32_t kxc = kx ^ c;
+                        const uint32_t h = kx < kxc ? kx : kxc;
+                        uint32_t word, mask;
+                        bloom_pos(h, word, mask);
+                        atomicOr(((kx != h) ? bmB : bmA) + word, mask);
+                    }
                 }
             }
         }
@@ -184,12 +187,10 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                             const uint32_t kx = kv[cc];
                             const uint32_t kxc = kx ^ c;
                             const uint32_t h = kx < kxc ? kx : kxc;
-                            uint32_t b1, b2;
-                            bloom_pos(h, b1, b2);
-                            const uint32_t *other = (kx != h) ? bmA : bmB;
-                            const uint32_t hit =
-                                (other[b1 >> 5] >> (b1 & 31)) & (other[b2 >> 5] >> (b2 & 31)) & 1u;
-                            keep |= hit << cc;
+                            uint32_t word, mask;
+                            bloom_pos(h, word, mask);
+                            const uint32_t have = ((kx != h) ? bmA : bmB)[word];
+                            keep |= ((have & mask) == mask ? 1u : 0u) << cc;
                         }
                         keep &= valid;
                     }
@@ -399,14 +400,15 @@ cudaError_t launch_filter(const Packed &pk, int M, uint64_t seed, int64_t l0, in
                           int64_t *launches)
 {
     const size_t smem = filter_smem_bytes();
-    cudaError_t e =
-        cudaFuncSetAttribute(filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = M <= 8 ? filter_kernel<8> : M <= 16 ? filter_kernel<16> : M <= 24 ? filter_kernel<24>
+                                                                                 : filter_kernel<32>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     int grid = filter_grid();
     if (grid > R)
         grid = R;
-    filter_kernel<<<grid, FL_THREADS, smem, s>>>(pk.Xr, pk.Pp, pk.P, pk.yb, pk.n, pk.p, M, seed, l0, R,
+    kern<<<grid, FL_THREADS, smem, s>>>(pk.Xr, pk.Pp, pk.P, pk.yb, pk.n, pk.p, M, seed, l0, R,
                                                  kc_scratch, seg_keys, seg_vals, seg_count, seg_cap,
                                                  overflow, cnz, members, members_count, buckets,
                                                  pair_counts, nbuckets);
