@@ -136,33 +136,57 @@ def load_peaks():
 
 
 def load_traffic():
+    """ncu DRAM bytes per launch recorded under profiles/ (null when the
+    kernel source changed since the capture)."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(path):
-        try:
-            return json.load(open(path))
-        except Exception:
-            return {}
-    return {}
+    if not os.path.exists(path):
+        return {}
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return {}
+    out = {}
+    for stage, v in rec.items():
+        src = os.path.join(ROOT, v.get("source", ""))
+        if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == v.get("sha"):
+            out[stage] = v
+    return out
 
 
-# Algorithmic bytes per unit of each stage (one run = p columns):
-#   keys:   read M sampled rows of p bits, write p (key, index) entries.
-#   sort:   one read + one write of the p 8-byte entries.
-#   join:   one read of the p sorted 4-byte keys.
-#   verify: per candidate, 2 columns of W words (first touch only is
-#           algorithmic; we count the 2*4*W column bytes of every candidate,
-#           which is what a cache-less verification reads).
-def algorithmic_bytes(stage: str, n: int, p: int, M: int, runs: int, candidates: int):
+# Work per unit of each stage (one run = p columns), stated in DESIGN.md:
+#   keys (survivor filter, ALU-bound): 30 integer operations per column and
+#       run -- 12.5 for the 32 x 32 bit transpose that forms the M-bit keys
+#       (400 ops per 32 columns), 3 for the canonical group value, 6 to
+#       insert it into the blocked Bloom filter, 8 to test the other side.
+#   sort (HBM): one read + one write of each 8-byte entry that reaches it.
+#   join (HBM): one read of each 4-byte sorted key.
+#   verify (HBM/L2): 2 columns of 4W bytes per candidate.
+FILTER_OPS_PER_COLUMN = 30
+INT32_LANES_PER_SM = 128
+
+
+def int_peak_tops():
+    """Peak 32-bit integer operations per second from the unit counts and the
+    maximum SM clock: SMs x 128 INT32 lanes x f_max."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peaks = load_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return sms * INT32_LANES_PER_SM * mhz * 1e6 / 1e12, sms, mhz
+
+
+def stage_work(stage: str, n: int, p: int, M: int, runs: int, candidates: int, survivors: int):
     W = (n + 31) // 32
     if stage == "keys":
-        return runs * (M * p / 8 + 8 * p)
+        return runs * p * FILTER_OPS_PER_COLUMN, "ops"
     if stage == "sort":
-        return runs * 16 * p
+        return survivors * 16, "bytes"
     if stage == "join":
-        return runs * 4 * p
+        return survivors * 4, "bytes"
     if stage == "verify":
-        return candidates * 8 * W
-    return 0
+        return candidates * 8 * W, "bytes"
+    return 0, "bytes"
 
 
 def gpu_arm(args):
@@ -244,18 +268,30 @@ def gpu_arm(args):
     cand = sum(x["candidates"] for x in stats)
     runs = sum(x["runs"] for x in stats)
     chunks = sum(x["chunks"] for x in stats)
-    alg = algorithmic_bytes(dom, d.n, d.p, M, runs, cand)
-    achieved_gbs = alg / (ms_stage[dom] / 1e3) / 1e9 if ms_stage[dom] > 0 else 0.0
+    surv = sum(x["survivors"] for x in stats)
+    work, kind = stage_work(dom, d.n, d.p, M, runs, cand, surv)
+    secs = ms_stage[dom] / 1e3
     peaks = load_peaks()
-    peak = float(peaks["hbm_gbs"])
     traffic = load_traffic().get(dom)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved_gbs, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved_gbs / peak, 4),
-                "peak_source": f"{peaks.get('source')} hbm_gbs",
-                "traffic": traffic.get("bytes_per_launch") if traffic else None,
-                "launches": launches_stage[dom], "launch_groups": chunks,
-                "stage_ms": {k: round(v, 3) for k, v in ms_stage.items()},
-                "stage_share": {k: round(v / max(1e-9, sum(ms_stage.values())), 4) for k, v in ms_stage.items()}}
+    if kind == "ops":
+        peak, sms, mhz = int_peak_tops()
+        achieved = work / secs / 1e12 if secs > 0 else 0.0
+        roofline = {"bound": "alu", "kernel": "filter_kernel", "achieved": round(achieved, 3),
+                    "peak": round(peak, 3), "unit": "TOPS (int32)", "frac": round(achieved / peak, 4),
+                    "peak_source": f"derived: {sms} SMs x {INT32_LANES_PER_SM} INT32 lanes x {mhz:.0f} MHz",
+                    "work_per_unit": f"{FILTER_OPS_PER_COLUMN} int ops per column per run"}
+    else:
+        peak = float(peaks["hbm_gbs"])
+        achieved = work / secs / 1e9 if secs > 0 else 0.0
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "peak_source": f"{peaks.get('source')} hbm_gbs"}
+    roofline.update({
+        "traffic": traffic.get("bytes_per_launch") if traffic else None,
+        "traffic_note": traffic.get("note") if traffic else "no ncu capture of the current kernel source",
+        "launches": launches_stage[dom], "launch_groups": chunks,
+        "stage_ms": {k: round(v, 3) for k, v in ms_stage.items()},
+        "stage_share": {k: round(v / max(1e-9, sum(ms_stage.values())), 4) for k, v in ms_stage.items()}})
 
     recall = float(np.mean(found)) / max(1, len(target_set))
     gpu_launches = sum(x["gpu_launches"] for x in stats)

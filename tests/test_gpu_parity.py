@@ -285,3 +285,19 @@ def test_full_size_gwas_sampled_parity(xyz, orc, gwas_full):
     assert _as_set(_pairs_array(part)) <= _as_set(_pairs_array(res))
     want_part = orc.xyz_range(d.X, d.Y, 0, 50, M, kappa, seed)
     assert np.array_equal(_pairs_array(part), want_part)
+
+
+def test_sharded_search_through_library(xyz):
+    # run-range sharding as the multi-GPU path does it, ranks simulated in
+    # turn on one device; the merged result equals the whole search
+    from paper_1610_05108_gb300 import shard
+    X, Y = _rand(200, 3000, 20)
+    Y = (X[:, 11] * X[:, 1500]).astype(np.int8)
+    Y[:25] = -Y[:25]
+    L, M, kappa, seed = 50, 8, 0.2, 99
+    with xyz.create(X, Y) as ctx:
+        whole = _pairs_array(ctx.search(L, M, kappa, seed))
+        world = 3
+        parts = [ctx.search_range(a, b, M, kappa, seed) for a, b in shard.run_ranges(L, world)]
+    merged = shard.merge_pairs(parts)
+    assert np.array_equal(merged, whole.astype(np.int64))
