@@ -151,6 +151,21 @@ int xyz_search(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t seed,
 int xyz_search_range(xyz_ctx *ctx, int64_t l0, int64_t l1, int32_t M, double kappa,
                      uint64_t seed, xyz_pair **pairs, int64_t *npairs);
 
+/* Batched search (many responses on one resident X, as Section 4's repeated
+ * calls with changing responses need): for each of B responses (Ys: host
+ * array of B rows of n int8, row b = response b) the same search as
+ * xyz_search(L, M, kappa, seed) with that response.  All responses share the
+ * row stream, so each run's keys of X are built once.  *pairs gets all
+ * results, response b's at [offsets[b], offsets[b+1]) sorted by (j, k);
+ * offsets: caller array of B + 1.  Results are identical to B separate
+ * searches.  B >= 1; other arguments as xyz_search. */
+int xyz_search_batch(xyz_ctx *ctx, const int8_t *Ys, int32_t B, int32_t L, int32_t M, double kappa,
+                     uint64_t seed, xyz_pair **pairs, int64_t *offsets);
+
+/* xyz_search_batch with the responses in device memory. */
+int xyz_search_batch_dev(xyz_ctx *ctx, const int8_t *dYs, int32_t B, int32_t L, int32_t M,
+                         double kappa, uint64_t seed, xyz_pair **pairs, int64_t *offsets);
+
 void xyz_free_pairs(xyz_pair *pairs);
 void xyz_free(void *ptr);
 

@@ -26,10 +26,11 @@ __device__ __forceinline__ K group_of(K key, int sh) { return key >> sh; }
 
 template <typename K>
 __global__ void __launch_bounds__(JV_THREADS)
-    join_kernel(const K *__restrict__ keys, int64_t N, int M, int rbits,
+    join_kernel(const K *__restrict__ keys, int64_t N, int M, int rbits, int runbits,
                 const uint8_t *__restrict__ cnz, Bucket *__restrict__ buckets,
                 uint64_t *__restrict__ pair_counts, uint32_t *__restrict__ nbuckets)
 {
+    const int resp_shift = M + runbits;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
         const K ki = keys[i];
@@ -85,7 +86,8 @@ __global__ void __launch_bounds__(JV_THREADS)
             pairs = (uint64_t)nA * (nA - 1) / 2;
         }
         uint32_t b = atomicAdd(nbuckets, 1u);
-        buckets[b] = Bucket{(uint32_t)i, nA, nB, 0u};
+        const uint32_t resp = resp_shift < (int)(8 * sizeof(K)) ? (uint32_t)(ki >> resp_shift) : 0u;
+        buckets[b] = Bucket{(uint32_t)i, nA, nB, resp};
         pair_counts[b] = pairs;
     }
 }
@@ -114,14 +116,23 @@ __device__ __forceinline__ int agree_cols(const uint32_t *__restrict__ Xc, int64
 // in registers across the steps.
 constexpr int VQ = 4;   // response pieces per lane held in registers (columns up to 4096 rows)
 
+template <bool BATCH>
 __global__ void __launch_bounds__(JV_THREADS)
     verify_kernel(const uint32_t *__restrict__ Xc, int64_t Wp, const uint32_t *__restrict__ yb,
                   const Bucket *__restrict__ buckets, const uint64_t *__restrict__ pair_off,
                   const uint32_t *__restrict__ nbuckets, const uint64_t *__restrict__ total_pairs,
                   const uint32_t *__restrict__ vals, int64_t amin, int kbits,
                   uint64_t *__restrict__ rec_keys, uint32_t *__restrict__ rec_agree,
-                  uint32_t *__restrict__ nrec, uint32_t rec_cap)
+                  uint32_t *__restrict__ nrec, uint32_t rec_cap, const int *__restrict__ abort_flag)
 {
+    // abort_flag (may be null): bit 2 set means the producer of the buckets
+    // ran out of space after reserving some of them, so their entries are not
+    // all written; the whole launch group is then skipped (and redone).
+    if (abort_flag && (*(volatile const int *)abort_flag & 2))
+        return;
+    // BATCH: yb holds one response-bit row of Wp words per response; a
+    // bucket's pad names its response, which is also the top field of the
+    // record key (resp << 2 kbits | j << kbits | k).
     const uint32_t nb = *nbuckets;
     const uint64_t T = *total_pairs;
     const int lane = threadIdx.x & 31;
@@ -154,7 +165,7 @@ __global__ void __launch_bounds__(JV_THREADS)
         base = __shfl_sync(0xffffffffu, base, 0);
         const uint64_t t = t0 + lane;
         const bool valid = t < T;
-        uint32_t j = 0, k = 0;
+        uint32_t j = 0, k = 0, resp = 0;
         if (valid) {
             uint32_t lo = base, hi = (nb - base > 33u) ? base + 33u : nb;
             while (hi - lo > 1) {
@@ -166,6 +177,7 @@ __global__ void __launch_bounds__(JV_THREADS)
             }
             const Bucket B = buckets[lo];
             const uint64_t u = t - pair_off[lo];
+            resp = B.pad;
             if (B.nB) {
                 uint64_t ia = u / B.nB, ib = u - ia * B.nB;
                 j = vals[B.start + ia];
@@ -189,21 +201,24 @@ __global__ void __launch_bounds__(JV_THREADS)
             const uint32_t jj = __shfl_sync(0xffffffffu, j, cidx);
             const uint32_t kk = __shfl_sync(0xffffffffu, k, cidx);
             const bool vv = __shfl_sync(0xffffffffu, (int)valid, cidx) != 0;
+            const uint32_t rr = BATCH ? __shfl_sync(0xffffffffu, resp, cidx) : 0u;
             int part = 0;
             if (vv) {
                 const uint4 *cj = reinterpret_cast<const uint4 *>(Xc + (int64_t)jj * Wp);
                 const uint4 *ck = reinterpret_cast<const uint4 *>(Xc + (int64_t)kk * Wp);
+                const uint4 *yq = BATCH ? reinterpret_cast<const uint4 *>(yb + (int64_t)rr * Wp) : y4;
 #pragma unroll
                 for (int i = 0; i < VQ; ++i) {
                     const int q = sub + 8 * i;
                     if (q < nq) {
-                        const uint4 x = __ldg(cj + q), z = __ldg(ck + q), y = yr[i];
+                        const uint4 x = __ldg(cj + q), z = __ldg(ck + q);
+                        const uint4 y = BATCH ? __ldg(yq + q) : yr[i];
                         part += __popc(~(x.x ^ z.x ^ y.x)) + __popc(~(x.y ^ z.y ^ y.y)) +
                                 __popc(~(x.z ^ z.z ^ y.z)) + __popc(~(x.w ^ z.w ^ y.w));
                     }
                 }
                 for (int q = sub + 8 * VQ; q < nq; q += 8) {
-                    const uint4 x = __ldg(cj + q), z = __ldg(ck + q), y = __ldg(y4 + q);
+                    const uint4 x = __ldg(cj + q), z = __ldg(ck + q), y = __ldg(yq + q);
                     part += __popc(~(x.x ^ z.x ^ y.x)) + __popc(~(x.y ^ z.y ^ y.y)) +
                             __popc(~(x.z ^ z.z ^ y.z)) + __popc(~(x.w ^ z.w ^ y.w));
                 }
@@ -219,7 +234,7 @@ __global__ void __launch_bounds__(JV_THREADS)
             uint32_t idx = atomicAdd(nrec, 1u);
             if (idx < rec_cap) {
                 uint32_t lo_c = j < k ? j : k, hi_c = j < k ? k : j;
-                rec_keys[idx] = ((uint64_t)lo_c << kbits) | hi_c;
+                rec_keys[idx] = ((uint64_t)resp << (2 * kbits)) | ((uint64_t)lo_c << kbits) | hi_c;
                 rec_agree[idx] = (uint32_t)agree;
             }
         }
@@ -242,7 +257,7 @@ __global__ void unique_scatter_kernel(const uint64_t *__restrict__ keys,
                                       const uint32_t *__restrict__ nrec, int64_t cap,
                                       const uint32_t *__restrict__ flags,
                                       const uint32_t *__restrict__ pos, int kbits, int64_t n,
-                                      PairOut *__restrict__ out)
+                                      PairOut *__restrict__ out, uint32_t *__restrict__ resp)
 {
     int64_t N = *nrec;
     if (N > cap)
@@ -254,11 +269,13 @@ __global__ void unique_scatter_kernel(const uint64_t *__restrict__ keys,
             continue;
         uint64_t key = keys[i];
         PairOut o;
-        o.j = (int32_t)(key >> kbits);
+        o.j = (int32_t)((key >> kbits) & kmask);
         o.k = (int32_t)(key & kmask);
         o.agree = (int32_t)agree[i];
         o.strength = (float)((double)(2 * (int64_t)agree[i] - n) / (double)n);
         out[pos[i]] = o;
+        if (resp)
+            resp[pos[i]] = (uint32_t)(key >> (2 * kbits));
     }
 }
 
@@ -324,14 +341,14 @@ int64_t max_resident_blocks()
 }
 
 template <typename K>
-cudaError_t join_impl(const K *keys, int64_t N, int M, int rbits, const uint8_t *cnz,
+cudaError_t join_impl(const K *keys, int64_t N, int M, int rbits, int runbits, const uint8_t *cnz,
                       Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
                       int64_t *launches)
 {
     if (N <= 0)
         return cudaSuccess;
     join_kernel<K><<<grid_for(N, JV_THREADS, 1 << 20), JV_THREADS, 0, s>>>(
-        keys, N, M, rbits, cnz, buckets, pair_counts, nbuckets);
+        keys, N, M, rbits, runbits, cnz, buckets, pair_counts, nbuckets);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -342,25 +359,32 @@ cudaError_t launch_join32(const uint32_t *keys, int64_t N, int M, int rbits, con
                           Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
                           cudaStream_t s, int64_t *launches)
 {
-    return join_impl<uint32_t>(keys, N, M, rbits, cnz, buckets, pair_counts, nbuckets, s, launches);
+    return join_impl<uint32_t>(keys, N, M, rbits, rbits, cnz, buckets, pair_counts, nbuckets, s,
+                               launches);
 }
 
 cudaError_t launch_join64(const uint64_t *keys, int64_t N, int M, int rbits, const uint8_t *cnz,
                           Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
-                          cudaStream_t s, int64_t *launches)
+                          cudaStream_t s, int64_t *launches, int runbits)
 {
-    return join_impl<uint64_t>(keys, N, M, rbits, cnz, buckets, pair_counts, nbuckets, s, launches);
+    return join_impl<uint64_t>(keys, N, M, rbits, runbits < 0 ? rbits : runbits, cnz, buckets,
+                               pair_counts, nbuckets, s, launches);
 }
 
 cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_t *pair_off,
                           const uint32_t *nbuckets, const uint64_t *total_pairs,
                           const uint32_t *vals, int64_t amin, int kbits, uint64_t *rec_keys,
                           uint32_t *rec_agree, uint32_t *nrec, uint32_t rec_cap, cudaStream_t s,
-                          int64_t *launches)
+                          int64_t *launches, const uint32_t *ybs, const int *abort_flag)
 {
-    verify_kernel<<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
-        pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits, rec_keys,
-        rec_agree, nrec, rec_cap);
+    if (ybs)
+        verify_kernel<true><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
+            pk.Xc, pk.Wp, ybs, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits, rec_keys,
+            rec_agree, nrec, rec_cap, abort_flag);
+    else
+        verify_kernel<false><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
+            pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits,
+            rec_keys, rec_agree, nrec, rec_cap, abort_flag);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -368,7 +392,7 @@ cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_
 cudaError_t launch_unique(const uint64_t *rec_keys, const uint32_t *rec_agree, const uint32_t *nrec,
                           int64_t cap, int kbits, int64_t n, uint32_t *flags, uint32_t *pos,
                           void *scan_temp, PairOut *out, uint32_t *nout, cudaStream_t s,
-                          int64_t *launches)
+                          int64_t *launches, uint32_t *resp)
 {
     if (cap <= 0)
         return cudaSuccess;
@@ -379,7 +403,7 @@ cudaError_t launch_unique(const uint64_t *rec_keys, const uint32_t *rec_agree, c
     if (e != cudaSuccess)
         return e;
     unique_scatter_kernel<<<g, JV_THREADS, 0, s>>>(rec_keys, rec_agree, nrec, cap, flags, pos, kbits,
-                                                   n, out);
+                                                   n, out, resp);
     *launches += 1;
     return cudaGetLastError();
 }

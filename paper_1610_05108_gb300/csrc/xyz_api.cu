@@ -87,7 +87,8 @@ struct xyz_ctx {
     DevBuf buckets2, pair_counts2, pair_off2, scan_tmp2;   // filter path: spilled runs
     int64_t surv_cap = 0;        // filter path: survivor capacity (CTAs x segment)
     int64_t seg_cap = 0;         // filter path: survivors one CTA may write per group
-    int64_t seg_runs_p = 0;      // filter path: runs-per-CTA x p the segment is sized for
+    int64_t mem_cap = 0;         // filter path: members of on-chip groups per launch group
+    DevBuf resp, ybs;            // batched search: response of each output pair, response bits
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
     int64_t rec_cap = 1 << 16;
     int64_t chunk_entries = (int64_t)1 << 25;
@@ -134,7 +135,8 @@ static int64_t ws_bytes(const xyz_ctx *c)
                            &c->pos,     &c->out,         &c->dedup_tmp, &c->raw,
                            &c->ents, &c->seg, &c->members, &c->kc_scratch,
                            &c->seg_keys, &c->seg_vals, &c->seg_count,
-                           &c->buckets2, &c->pair_counts2, &c->pair_off2, &c->scan_tmp2};
+                           &c->buckets2, &c->pair_counts2, &c->pair_off2, &c->scan_tmp2,
+                           &c->resp, &c->ybs};
     int64_t s = 0;
     for (const DevBuf *b : all)
         s += (int64_t)b->bytes;
@@ -215,13 +217,14 @@ struct Timer {
 
 struct Plan {
     int64_t R;        // runs per launch group
-    bool filter;      // survivor filter + LSD sort of the survivors (M <= 31, moderate p)
+    int NB, BB;       // filter path: response blocks per run, responses per block
+    bool filter;      // per-run survivor filter with on-chip grouping (M <= 31, p <= 262144)
     bool part;        // partitioned grouping (M <= 31, large p)
     bool k64;         // 64-bit composite keys (LSD path)
     int kbits;        // bits of a column index (record keys use 2*kbits)
 };
 
-Plan make_plan(const xyz_ctx *c, int64_t runs, int M)
+Plan make_plan(const xyz_ctx *c, int64_t runs, int M, int B)
 {
     Plan pl;
     const int64_t p = c->pk.p;
@@ -232,23 +235,32 @@ Plan make_plan(const xyz_ctx *c, int64_t runs, int M)
     if (rmax > 65535)
         rmax = 65535;
     int64_t R = runs < rmax ? runs : rmax;
-    pl.filter = c->use_filter && filter_supported(p, M);
+    pl.filter = (c->use_filter || B > 1) && filter_supported(p, M);
     pl.part = !pl.filter && part_supported(p, M);
     pl.k64 = false;
+    pl.NB = pl.BB = 1;
     pl.kbits = ceil_log2(p);
     if (pl.kbits < 1)
         pl.kbits = 1;
     if (pl.filter) {
-        // survivors carry the run index above the M key bits in 32-bit keys;
-        // only a small share of the entries survive, so a group may span
-        // eight times the entry budget
-        int64_t rf = runs < ((int64_t)1 << (32 - M)) ? runs : ((int64_t)1 << (32 - M));
-        int64_t rb = 8 * entries / p;
-        if (rb < 1)
-            rb = 1;
-        if (rf > rb)
-            rf = rb;
-        pl.R = rf < 1 ? 1 : rf;
+        // a launch group holds about 2048 (run, response) items; only a few
+        // percent of a run's columns survive, so it may span eight times the
+        // entry budget
+        int64_t rf = B > 1 ? (4096 / B > 0 ? 4096 / B : 1) : 8 * entries / p;
+        if (rf < 1)
+            rf = 1;
+        if (rf > 4096)
+            rf = 4096;
+        pl.R = runs < rf ? runs : rf;
+        // enough (run, response block) items for every SM
+        const int64_t want = 2 * (int64_t)filter_grid();
+        int64_t nb = (want + pl.R - 1) / pl.R;
+        if (nb > B)
+            nb = B;
+        if (nb < 1)
+            nb = 1;
+        pl.BB = (int)((B + nb - 1) / nb);
+        pl.NB = (int)((B + pl.BB - 1) / pl.BB);
         return pl;
     }
     if (pl.part) {
@@ -270,34 +282,36 @@ Plan make_plan(const xyz_ctx *c, int64_t runs, int M)
     return pl;
 }
 
-int ensure_search_ws(xyz_ctx *c, const Plan &pl)
+int ensure_search_ws(xyz_ctx *c, const Plan &pl, int B, int64_t runs)
 {
     const int64_t N = pl.R * c->pk.p;
     const size_t ksz = pl.k64 ? 8 : 4;
     const int64_t bcap = N / 2 + 1;
     int rc;
     if (pl.filter) {
-        // a CTA handles ceil(R / grid) runs of p columns; start its segment
-        // at an eighth of that (plus slack) and grow on overflow
-        const int64_t grid = filter_grid() < pl.R ? filter_grid() : pl.R;
-        const int64_t worst = (pl.R + grid - 1) / grid * c->pk.p;
-        if (c->seg_runs_p != worst) {
-            // spilled runs are rare: room for about one per CTA, grown on overflow
-            c->seg_runs_p = worst;
-            c->seg_cap = c->pk.p + 4096 < worst ? c->pk.p + 4096 : worst;
-        }
-        const int64_t seg_cap = c->seg_cap;
-        const int64_t cap = grid * seg_cap;
+        // spilled runs are rare: each CTA's segment starts with room for
+        // about one run and grows when it overflows
+        if (c->seg_cap < 1)
+            c->seg_cap = c->pk.p + 4096;
+        const int64_t grid = filter_grid();
+        const int64_t cap = grid * c->seg_cap;
         c->surv_cap = cap;
         const int64_t sb = cap / 2 + 1;
-        const int64_t mcap = pl.R * filter_run_cap();   // members grouped on chip
+        const int64_t items = pl.R * B;
+        if (c->mem_cap < 1) {
+            // members grouped on chip per launch group, grown on overflow
+            const int64_t per = c->pk.p < 4096 ? c->pk.p : 4096;
+            c->mem_cap = items * per > 65536 ? items * per : 65536;
+        }
+        const int64_t mcap = c->mem_cap;
         const int64_t mb = mcap / 2 + 1;
+        const int64_t cnz_bytes = (int64_t)B << ceil_log2(runs);
         if ((rc = ensure(c->kc_scratch, filter_scratch_words(c->pk.p) * 4)) ||
-            (rc = ensure(c->seg_keys, (size_t)cap * 4)) || (rc = ensure(c->seg_vals, (size_t)cap * 4)) ||
-            (rc = ensure(c->seg_count, (size_t)filter_grid() * 4)) ||
-            (rc = ensure(c->keysA, cap * 4)) || (rc = ensure(c->keysB, cap * 4)) ||
+            (rc = ensure(c->seg_keys, (size_t)cap * 8)) || (rc = ensure(c->seg_vals, (size_t)cap * 4)) ||
+            (rc = ensure(c->seg_count, (size_t)grid * 4)) ||
+            (rc = ensure(c->keysA, cap * 8)) || (rc = ensure(c->keysB, cap * 8)) ||
             (rc = ensure(c->valsA, cap * 4)) || (rc = ensure(c->valsB, cap * 4)) ||
-            (rc = ensure(c->radix_tmp, radix_temp_bytes(cap))) || (rc = ensure(c->cnz, pl.R)) ||
+            (rc = ensure(c->radix_tmp, radix_temp_bytes(cap))) || (rc = ensure(c->cnz, cnz_bytes)) ||
             (rc = ensure(c->members, mcap * 4)) || (rc = ensure(c->buckets, mb * sizeof(Bucket))) ||
             (rc = ensure(c->pair_counts, mb * 8)) || (rc = ensure(c->pair_off, mb * 8)) ||
             (rc = ensure(c->scan_tmp, scan_temp_bytes(mb))) ||
@@ -326,7 +340,7 @@ int ensure_search_ws(xyz_ctx *c, const Plan &pl)
     return XYZ_OK;
 }
 
-int ensure_records(xyz_ctx *c)
+int ensure_records(xyz_ctx *c, int B)
 {
     const int64_t cap = c->rec_cap;
     int rc;
@@ -334,14 +348,16 @@ int ensure_records(xyz_ctx *c)
         (rc = ensure(c->rec_agree, cap * 4)) || (rc = ensure(c->rec_agree_alt, cap * 4)) ||
         (rc = ensure(c->flags, cap * 4)) || (rc = ensure(c->pos, cap * 4)) ||
         (rc = ensure(c->out, cap * sizeof(PairOut))) ||
-        (rc = ensure(c->dedup_tmp, radix_temp_bytes(cap) + scan_temp_bytes(cap))))
+        (rc = ensure(c->dedup_tmp, radix_temp_bytes(cap) + scan_temp_bytes(cap))) ||
+        (B > 1 && (rc = ensure(c->resp, cap * 4))))
         return rc;
     return XYZ_OK;
 }
 
 // Device counters: per launch group (cleared before each group) the bucket
-// and member counts; per search the record and output counts, the error
-// flag, the group's candidate total and the candidate sum over groups.
+// and member counts; per search the spill count and overflow flags, the
+// spill-path bucket count, the record and output counts, the error flag,
+// the group's candidate total, the candidate sum and the spill total.
 uint32_t *ctr_u32(xyz_ctx *c) { return reinterpret_cast<uint32_t *>(c->counters.ptr); }
 uint32_t *ctr_nbuckets(xyz_ctx *c) { return ctr_u32(c) + 0; }
 uint32_t *ctr_members(xyz_ctx *c) { return ctr_u32(c) + 1; }
@@ -362,20 +378,27 @@ uint64_t *ctr_total2(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c
             return fail(XYZ_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));  \
     } while (0)
 
-// Runs [l0, l1) with threshold amin; results (sorted, unique) to the device
-// `out` buffer, their count to *nout_host.  Retries once with a larger
-// record buffer when the first attempt overflowed it.
-int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t seed,
-               int64_t *nout_host)
+// Runs [l0, l1) for B responses with threshold amin.  ybs: the responses'
+// bit rows on the device (B rows of Wp words; B == 1 and ybs == pk.yb for an
+// ordinary search; B > 1 needs the filter path).  Results (sorted by
+// (response, j, k), each once) go to the device `out` buffer, and their
+// responses to `resp` when B > 1; the count goes to *nout_host.  An
+// attempt that overflowed a buffer is redone once the buffer has grown.
+int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t l1, int M,
+                     int64_t amin, uint64_t seed, int64_t *nout_host)
 {
     const int64_t runs = l1 - l0;
     const int64_t p = c->pk.p;
-    Plan pl = make_plan(c, runs, M);
-    int rc = ensure_search_ws(c, pl);
-    if (rc)
-        return rc;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        if ((rc = ensure_records(c)))
+    Plan pl = make_plan(c, runs, M, B);
+    if (B > 1 && !pl.filter)
+        return fail(XYZ_EINVAL, "batched search needs M <= 31 and p <= 262144");
+    const int bbits = ceil_log2(B);
+    const int rbits = ceil_log2(runs);
+    if (pl.filter && bbits + rbits + M > 64)
+        return fail(XYZ_EINVAL, "too many runs x responses for one search");
+    int rc;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        if ((rc = ensure_search_ws(c, pl, B, runs)) || (rc = ensure_records(c, B)))
             return rc;
         int64_t launches = 0;
         Timer tm(c->timing, c->stream, &launches);
@@ -385,23 +408,21 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
         int64_t chunks = 0;
         int64_t surv_total = 0;
         int key_bits_max = 0;
-        for (int64_t g0 = l0; g0 < l1; g0 += pl.R) {
-            const int64_t Rc = (l1 - g0) < pl.R ? (l1 - g0) : pl.R;
-            const int64_t Nc = Rc * p;
-            const int rbits = ceil_log2(Rc);
-            const int bits = M + rbits;
-            key_bits_max = bits > key_bits_max ? bits : key_bits_max;
-            ++chunks;
-            CU(cudaMemsetAsync(ctr_u32(c), 0, 20, c->stream));   // per-group counters
-            const int64_t bcap = Nc / 2 + 1;
-            if (pl.filter) {
-                const int64_t seg_cap = c->seg_cap;
-                const int64_t mb = pl.R * filter_run_cap() / 2 + 1;
+        bool redo = false;
+        if (pl.filter) {
+            const int grid = filter_grid();
+            const int64_t mb = c->mem_cap / 2 + 1;
+            CU(launch_seg_reset((uint32_t *)c->seg_count.ptr, c->stream, &launches));
+            for (int64_t g0 = l0; g0 < l1; g0 += pl.R) {
+                const int64_t Rc = (l1 - g0) < pl.R ? (l1 - g0) : pl.R;
+                ++chunks;
+                CU(cudaMemsetAsync(ctr_u32(c), 0, 8, c->stream));   // buckets, members
                 tm.begin(ST_KEYS);
-                CU(launch_filter(c->pk, M, seed, g0, (int)Rc, (uint32_t *)c->kc_scratch.ptr,
-                                 (uint32_t *)c->seg_keys.ptr, (uint32_t *)c->seg_vals.ptr,
-                                 (uint32_t *)c->seg_count.ptr, (uint32_t)seg_cap, ctr_sovf(c),
-                                 (uint32_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr, ctr_nsurv(c),
+                CU(launch_filter(c->pk, ybs, B, M, seed, g0, (int)Rc, pl.NB, pl.BB, rbits, g0 - l0,
+                                 grid, (uint32_t)(c->mem_cap < 0xFFFFFFFFLL ? c->mem_cap : 0xFFFFFFFFLL),
+                                 (uint32_t)mb, (uint32_t *)c->kc_scratch.ptr,
+                                 (uint64_t *)c->seg_keys.ptr, (uint32_t *)c->seg_vals.ptr,
+                                 (uint32_t *)c->seg_count.ptr, (uint32_t)c->seg_cap, ctr_sovf(c),
                                  (uint8_t *)c->cnz.ptr, (uint32_t *)c->members.ptr, ctr_members(c),
                                  (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
                                  ctr_nbuckets(c), c->stream, &launches));
@@ -416,47 +437,49 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
                                  (const uint64_t *)c->pair_off.ptr, ctr_nbuckets(c), ctr_total(c),
                                  (const uint32_t *)c->members.ptr, amin, pl.kbits,
                                  (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
-                                 ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches));
+                                 ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches,
+                                 B > 1 ? ybs : nullptr, ctr_sovf(c)));
                 tm.end();
-                uint32_t ns = 0;
-                int sovf = 0;
-                CU(cudaMemcpyAsync(&ns, ctr_nsurv(c), 4, cudaMemcpyDeviceToHost, c->stream));
-                CU(cudaMemcpyAsync(&sovf, ctr_sovf(c), 4, cudaMemcpyDeviceToHost, c->stream));
-                CU(cudaStreamSynchronize(c->stream));
-                if (sovf) {
-                    // a CTA segment of spilled runs overflowed: grow the segments
-                    // and redo this group (records found twice are merged by the
-                    // final deduplication; a segment of runs-per-CTA x p never
-                    // overflows)
-                    int64_t want = 2 * c->seg_cap;
-                    if (want > c->seg_runs_p)
-                        want = c->seg_runs_p;
-                    if (want <= c->seg_cap)
-                        return fail(XYZ_ENOMEM, "survivor segment cannot grow further");
-                    c->seg_cap = want;
-                    if ((rc = ensure_search_ws(c, pl)))
-                        return rc;
-                    g0 -= pl.R;
-                    --chunks;
-                    continue;
-                }
-                if (ns == 0)
-                    continue;
-                // runs with too many survivors for the chip: general path
-                surv_total += ns;
+            }
+            // runs with too many survivors for the chip, all groups at once
+            tm.begin(ST_KEYS);
+            CU(launch_compact((const uint64_t *)c->seg_keys.ptr, (const uint32_t *)c->seg_vals.ptr,
+                              (const uint32_t *)c->seg_count.ptr, (uint32_t)c->seg_cap, grid,
+                              (uint64_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr, ctr_nsurv(c),
+                              c->stream, &launches));
+            tm.end();
+            uint32_t ns = 0;
+            int sovf = 0;
+            CU(cudaMemcpyAsync(&ns, ctr_nsurv(c), 4, cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaMemcpyAsync(&sovf, ctr_sovf(c), 4, cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+            if (sovf & 1) {
+                c->seg_cap *= 2;               // a spill segment overflowed
+                redo = true;
+            }
+            if (sovf & 2) {
+                c->mem_cap *= 2;               // the on-chip groups' members did
+                redo = true;
+            }
+            if (redo)
+                continue;
+            const int sbits = bbits + rbits + M;
+            key_bits_max = sbits;
+            if (ns > 0) {
+                surv_total = ns;
+                const int64_t sb = c->surv_cap / 2 + 1;
                 bool alt = false;
                 tm.begin(ST_SORT);
-                CU(radix_sort32((uint32_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr,
-                                (uint32_t *)c->keysB.ptr, (uint32_t *)c->valsB.ptr, (int64_t)ns, bits,
+                CU(radix_sort64((uint64_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr,
+                                (uint64_t *)c->keysB.ptr, (uint32_t *)c->valsB.ptr, (int64_t)ns, sbits,
                                 c->radix_tmp.ptr, &alt, c->stream, &launches));
                 tm.end();
-                const uint32_t *ks = (const uint32_t *)(alt ? c->keysB.ptr : c->keysA.ptr);
+                const uint64_t *ks = (const uint64_t *)(alt ? c->keysB.ptr : c->keysA.ptr);
                 const uint32_t *vs = (const uint32_t *)(alt ? c->valsB.ptr : c->valsA.ptr);
-                const int64_t sb = c->surv_cap / 2 + 1;
                 tm.begin(ST_JOIN);
-                CU(launch_join32(ks, (int64_t)ns, M, rbits, (const uint8_t *)c->cnz.ptr,
+                CU(launch_join64(ks, (int64_t)ns, M, bbits + rbits, (const uint8_t *)c->cnz.ptr,
                                  (Bucket *)c->buckets2.ptr, (uint64_t *)c->pair_counts2.ptr,
-                                 ctr_nbuckets2(c), c->stream, &launches));
+                                 ctr_nbuckets2(c), c->stream, &launches, rbits));
                 CU(scan_u64_dev((const uint64_t *)c->pair_counts2.ptr, (uint64_t *)c->pair_off2.ptr,
                                 ctr_nbuckets2(c), sb, ctr_total2(c), ctr_cand(c), c->scan_tmp2.ptr,
                                 c->stream, &launches));
@@ -466,77 +489,88 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
                                  (const uint64_t *)c->pair_off2.ptr, ctr_nbuckets2(c), ctr_total2(c), vs,
                                  amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
                                  (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
-                                 c->stream, &launches));
+                                 c->stream, &launches, B > 1 ? ybs : nullptr));
                 tm.end();
-                continue;
             }
-            if (pl.part) {
+        } else {
+            for (int64_t g0 = l0; g0 < l1; g0 += pl.R) {
+                const int64_t Rc = (l1 - g0) < pl.R ? (l1 - g0) : pl.R;
+                const int64_t Nc = Rc * p;
+                const int rb = ceil_log2(Rc);
+                const int bits = M + rb;
+                key_bits_max = bits > key_bits_max ? bits : key_bits_max;
+                ++chunks;
+                CU(cudaMemsetAsync(ctr_u32(c), 0, 8, c->stream));   // buckets, members
+                const int64_t bcap = Nc / 2 + 1;
+                if (pl.part) {
+                    tm.begin(ST_KEYS);
+                    CU(launch_keybuild_part(c->pk, M, seed, g0, (int)Rc, (uint64_t *)c->ents.ptr,
+                                            (uint32_t *)c->seg.ptr, (uint8_t *)c->cnz.ptr, c->stream,
+                                            &launches));
+                    tm.end();
+                    tm.begin(ST_JOIN);
+                    CU(launch_group(c->pk, (int)Rc, (const uint64_t *)c->ents.ptr,
+                                    (const uint32_t *)c->seg.ptr, (const uint8_t *)c->cnz.ptr,
+                                    (uint32_t *)c->members.ptr, ctr_members(c),
+                                    (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
+                                    ctr_nbuckets(c), ctr_err(c), c->stream, &launches));
+                    CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
+                                    ctr_nbuckets(c), bcap, ctr_total(c), ctr_cand(c), c->scan_tmp.ptr,
+                                    c->stream, &launches));
+                    tm.end();
+                    tm.begin(ST_VERIFY);
+                    CU(launch_verify(c->pk, (const Bucket *)c->buckets.ptr,
+                                     (const uint64_t *)c->pair_off.ptr, ctr_nbuckets(c), ctr_total(c),
+                                     (const uint32_t *)c->members.ptr, amin, pl.kbits,
+                                     (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
+                                     ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches));
+                    tm.end();
+                    continue;
+                }
+                bool alt = false;
                 tm.begin(ST_KEYS);
-                CU(launch_keybuild_part(c->pk, M, seed, g0, (int)Rc, (uint64_t *)c->ents.ptr,
-                                        (uint32_t *)c->seg.ptr, (uint8_t *)c->cnz.ptr, c->stream,
-                                        &launches));
+                if (pl.k64)
+                    CU(launch_keybuild64(c->pk, M, seed, g0, (int)Rc, rb, (uint64_t *)c->keysA.ptr,
+                                         (uint32_t *)c->valsA.ptr, (uint8_t *)c->cnz.ptr, nullptr,
+                                         nullptr, c->stream, &launches));
+                else
+                    CU(launch_keybuild32(c->pk, M, seed, g0, (int)Rc, rb, (uint32_t *)c->keysA.ptr,
+                                         (uint32_t *)c->valsA.ptr, (uint8_t *)c->cnz.ptr, nullptr,
+                                         nullptr, c->stream, &launches));
                 tm.end();
+                tm.begin(ST_SORT);
+                if (pl.k64)
+                    CU(radix_sort64((uint64_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr,
+                                    (uint64_t *)c->keysB.ptr, (uint32_t *)c->valsB.ptr, Nc, bits,
+                                    c->radix_tmp.ptr, &alt, c->stream, &launches));
+                else
+                    CU(radix_sort32((uint32_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr,
+                                    (uint32_t *)c->keysB.ptr, (uint32_t *)c->valsB.ptr, Nc, bits,
+                                    c->radix_tmp.ptr, &alt, c->stream, &launches));
+                tm.end();
+                void *ks = alt ? c->keysB.ptr : c->keysA.ptr;
+                uint32_t *vs = (uint32_t *)(alt ? c->valsB.ptr : c->valsA.ptr);
                 tm.begin(ST_JOIN);
-                CU(launch_group(c->pk, (int)Rc, (const uint64_t *)c->ents.ptr,
-                                (const uint32_t *)c->seg.ptr, (const uint8_t *)c->cnz.ptr,
-                                (uint32_t *)c->members.ptr, ctr_members(c), (Bucket *)c->buckets.ptr,
-                                (uint64_t *)c->pair_counts.ptr, ctr_nbuckets(c), ctr_err(c),
-                                c->stream, &launches));
+                if (pl.k64)
+                    CU(launch_join64((const uint64_t *)ks, Nc, M, rb, (const uint8_t *)c->cnz.ptr,
+                                     (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
+                                     ctr_nbuckets(c), c->stream, &launches));
+                else
+                    CU(launch_join32((const uint32_t *)ks, Nc, M, rb, (const uint8_t *)c->cnz.ptr,
+                                     (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
+                                     ctr_nbuckets(c), c->stream, &launches));
                 CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
                                 ctr_nbuckets(c), bcap, ctr_total(c), ctr_cand(c), c->scan_tmp.ptr,
                                 c->stream, &launches));
                 tm.end();
                 tm.begin(ST_VERIFY);
                 CU(launch_verify(c->pk, (const Bucket *)c->buckets.ptr,
-                                 (const uint64_t *)c->pair_off.ptr, ctr_nbuckets(c), ctr_total(c),
-                                 (const uint32_t *)c->members.ptr, amin, pl.kbits,
-                                 (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
-                                 ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches));
+                                 (const uint64_t *)c->pair_off.ptr, ctr_nbuckets(c), ctr_total(c), vs,
+                                 amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
+                                 (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
+                                 c->stream, &launches));
                 tm.end();
-                continue;
             }
-            bool alt = false;
-            tm.begin(ST_KEYS);
-            if (pl.k64)
-                CU(launch_keybuild64(c->pk, M, seed, g0, (int)Rc, rbits, (uint64_t *)c->keysA.ptr,
-                                     (uint32_t *)c->valsA.ptr, (uint8_t *)c->cnz.ptr, nullptr,
-                                     nullptr, c->stream, &launches));
-            else
-                CU(launch_keybuild32(c->pk, M, seed, g0, (int)Rc, rbits, (uint32_t *)c->keysA.ptr,
-                                     (uint32_t *)c->valsA.ptr, (uint8_t *)c->cnz.ptr, nullptr,
-                                     nullptr, c->stream, &launches));
-            tm.end();
-            tm.begin(ST_SORT);
-            if (pl.k64)
-                CU(radix_sort64((uint64_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr,
-                                (uint64_t *)c->keysB.ptr, (uint32_t *)c->valsB.ptr, Nc, bits,
-                                c->radix_tmp.ptr, &alt, c->stream, &launches));
-            else
-                CU(radix_sort32((uint32_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr,
-                                (uint32_t *)c->keysB.ptr, (uint32_t *)c->valsB.ptr, Nc, bits,
-                                c->radix_tmp.ptr, &alt, c->stream, &launches));
-            tm.end();
-            void *ks = alt ? c->keysB.ptr : c->keysA.ptr;
-            uint32_t *vs = (uint32_t *)(alt ? c->valsB.ptr : c->valsA.ptr);
-            tm.begin(ST_JOIN);
-            if (pl.k64)
-                CU(launch_join64((const uint64_t *)ks, Nc, M, rbits, (const uint8_t *)c->cnz.ptr,
-                                 (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
-                                 ctr_nbuckets(c), c->stream, &launches));
-            else
-                CU(launch_join32((const uint32_t *)ks, Nc, M, rbits, (const uint8_t *)c->cnz.ptr,
-                                 (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
-                                 ctr_nbuckets(c), c->stream, &launches));
-            CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
-                            ctr_nbuckets(c), bcap, ctr_total(c), ctr_cand(c), c->scan_tmp.ptr,
-                            c->stream, &launches));
-            tm.end();
-            tm.begin(ST_VERIFY);
-            CU(launch_verify(c->pk, (const Bucket *)c->buckets.ptr, (const uint64_t *)c->pair_off.ptr,
-                             ctr_nbuckets(c), ctr_total(c), vs, amin, pl.kbits,
-                             (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
-                             ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches));
-            tm.end();
         }
         // record count -> host
         uint32_t nrec = 0;
@@ -549,8 +583,6 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
         if (err)
             return fail(XYZ_ECUDA, "grouping table could not separate a partition's keys");
         if ((int64_t)nrec > c->rec_cap) {
-            if (attempt == 1)
-                return fail(XYZ_ENOMEM, "record buffer overflow after resize");
             int64_t want = c->rec_cap;
             while (want < (int64_t)nrec)
                 want *= 2;
@@ -565,12 +597,13 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
         size_t rt = radix_temp_bytes(c->rec_cap);
         CU(radix_sort64((uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
                         (uint64_t *)c->rec_keys_alt.ptr, (uint32_t *)c->rec_agree_alt.ptr,
-                        (int64_t)nrec, 2 * pl.kbits, dt, &alt, c->stream, &launches));
+                        (int64_t)nrec, bbits + 2 * pl.kbits, dt, &alt, c->stream, &launches));
         const uint64_t *rk = (const uint64_t *)(alt ? c->rec_keys_alt.ptr : c->rec_keys.ptr);
         const uint32_t *ra = (const uint32_t *)(alt ? c->rec_agree_alt.ptr : c->rec_agree.ptr);
         CU(launch_unique(rk, ra, ctr_nrec(c), c->rec_cap, pl.kbits, c->pk.n,
                          (uint32_t *)c->flags.ptr, (uint32_t *)c->pos.ptr, dt + rt,
-                         (PairOut *)c->out.ptr, ctr_nout(c), c->stream, &launches));
+                         (PairOut *)c->out.ptr, ctr_nout(c), c->stream, &launches,
+                         B > 1 ? (uint32_t *)c->resp.ptr : nullptr));
         tm.end();
         uint32_t nout = 0;
         CU(cudaMemcpyAsync(&nout, ctr_nout(c), 4, cudaMemcpyDeviceToHost, c->stream));
@@ -588,15 +621,21 @@ int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t
         st.survivors = pl.filter ? surv_total : runs * c->pk.p;
         st.gpu_launches = launches;
         tm.collect(st);
-        // buckets of the last group only are visible; report that count
         uint32_t nb = 0;
-        cudaMemcpy(&nb, ctr_nbuckets(c), 4, cudaMemcpyDeviceToHost);
+        CU(cudaMemcpyAsync(&nb, ctr_nbuckets(c), 4, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
         st.buckets = nb;
         c->stats = st;
         *nout_host = nout;
         return XYZ_OK;
     }
-    return fail(XYZ_ENOMEM, "record buffer overflow");
+    return fail(XYZ_ENOMEM, "search buffers kept overflowing");
+}
+
+int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t seed,
+               int64_t *nout_host)
+{
+    return run_search_multi(c, c->pk.yb, 1, l0, l1, M, amin, seed, nout_host);
 }
 
 int check_ctx(const xyz_ctx *c)
@@ -671,7 +710,7 @@ void destroy_ctx(xyz_ctx *c)
                      &c->rec_agree_alt, &c->flags, &c->pos,       &c->out,      &c->dedup_tmp,
                      &c->raw,     &c->ents,        &c->seg,       &c->members,  &c->kc_scratch,
                      &c->seg_keys, &c->seg_vals,   &c->seg_count, &c->buckets2, &c->pair_counts2,
-                     &c->pair_off2, &c->scan_tmp2};
+                     &c->pair_off2, &c->scan_tmp2, &c->resp,   &c->ybs};
     for (DevBuf *b : all)
         release(*b);
     if (c->own_stream && c->stream)
@@ -904,6 +943,143 @@ int xyz_set_chunk_entries(xyz_ctx *ctx, int64_t entries)
     return XYZ_OK;
 }
 
+namespace {
+
+// Pack B responses (device int8, B rows of n) into ctx->ybs; -1/+1 only.
+int pack_responses(xyz_ctx *ctx, const int8_t *dYs, int32_t B)
+{
+    const size_t row = (size_t)ctx->pk.Wp * 4;
+    int rc = ensure(ctx->ybs, row * (size_t)B);
+    if (rc)
+        return rc;
+    int64_t launches = 0;
+    CU(cudaMemsetAsync(ctx->d_bad, 0, 16, ctx->stream));
+    for (int32_t b = 0; b < B; ++b) {
+        Packed tmp = ctx->pk;
+        tmp.yb = (uint32_t *)((char *)ctx->ybs.ptr + row * b);
+        CU(launch_pack_y(dYs + (int64_t)b * ctx->pk.n, tmp, ctx->d_bad, ctx->stream, &launches));
+    }
+    int bad = 0;
+    CU(cudaMemcpyAsync(&bad, ctx->d_bad, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (bad)
+        return fail(XYZ_EINVAL, "entries of the responses must be -1 or +1");
+    return XYZ_OK;
+}
+
+// Copy `nout` device results (and their responses) to host pairs + offsets.
+int collect_batch(xyz_ctx *ctx, int32_t B, int64_t nout, bool have_resp, int32_t only,
+                  std::vector<xyz_pair> &acc, std::vector<int64_t> &counts)
+{
+    if (nout == 0)
+        return XYZ_OK;
+    const size_t at = acc.size();
+    acc.resize(at + (size_t)nout);
+    CU(cudaMemcpyAsync(acc.data() + at, ctx->out.ptr, (size_t)nout * sizeof(xyz_pair),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<uint32_t> resp;
+    if (have_resp) {
+        resp.resize((size_t)nout);
+        CU(cudaMemcpyAsync(resp.data(), ctx->resp.ptr, (size_t)nout * 4, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int64_t i = 0; i < nout; ++i) {
+        const uint32_t b = have_resp ? resp[(size_t)i] : (uint32_t)only;
+        if (b >= (uint32_t)B)
+            return fail(XYZ_ECUDA, "response index out of range in batched results");
+        counts[b] += 1;
+    }
+    return XYZ_OK;
+}
+
+int search_batch_dev(xyz_ctx *ctx, const int8_t *dYs, int32_t B, int32_t L, int32_t M, double kappa,
+                     uint64_t seed, xyz_pair **pairs, int64_t *offsets)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!dYs || !pairs || !offsets)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    if (B < 1 || L < 1)
+        return fail(XYZ_EINVAL, "need B >= 1 and L >= 1");
+    if ((rc = check_M(M)) || (rc = check_kappa(kappa)))
+        return rc;
+    if ((rc = pack_responses(ctx, dYs, B)))
+        return rc;
+    const int64_t amin = amin_rule(ctx->pk.n, kappa);
+    std::vector<xyz_pair> acc;
+    std::vector<int64_t> counts((size_t)B, 0);
+    const size_t row = (size_t)ctx->pk.Wp * 4;
+    if (amin <= ctx->pk.n) {
+        Plan pl = make_plan(ctx, L, M, B);
+        if (B > 1 && pl.filter) {
+            int64_t nout = 0;
+            if ((rc = run_search_multi(ctx, (const uint32_t *)ctx->ybs.ptr, B, 0, L, M, amin, seed,
+                                       &nout)) ||
+                (rc = collect_batch(ctx, B, nout, true, 0, acc, counts)))
+                return rc;
+        } else {
+            // one response at a time on the resident X (results are identical)
+            uint32_t *own = ctx->pk.yb;
+            for (int32_t b = 0; b < B && !rc; ++b) {
+                ctx->pk.yb = (uint32_t *)((char *)ctx->ybs.ptr + row * b);
+                int64_t nout = 0;
+                rc = run_search(ctx, 0, L, M, amin, seed, &nout);
+                if (!rc)
+                    rc = collect_batch(ctx, B, nout, false, b, acc, counts);
+            }
+            ctx->pk.yb = own;
+            if (rc)
+                return rc;
+        }
+    }
+    xyz_pair *host = nullptr;
+    if (!acc.empty()) {
+        host = (xyz_pair *)std::malloc(acc.size() * sizeof(xyz_pair));
+        if (!host)
+            return fail(XYZ_ENOMEM, "host allocation of results failed");
+        std::memcpy(host, acc.data(), acc.size() * sizeof(xyz_pair));
+    }
+    offsets[0] = 0;
+    for (int32_t b = 0; b < B; ++b)
+        offsets[b + 1] = offsets[b] + counts[(size_t)b];
+    *pairs = host;
+    return XYZ_OK;
+}
+
+}  // namespace
+
+int xyz_search_batch_dev(xyz_ctx *ctx, const int8_t *dYs, int32_t B, int32_t L, int32_t M, double kappa,
+                         uint64_t seed, xyz_pair **pairs, int64_t *offsets)
+{
+    return search_batch_dev(ctx, dYs, B, L, M, kappa, seed, pairs, offsets);
+}
+
+int xyz_search_batch(xyz_ctx *ctx, const int8_t *Ys, int32_t B, int32_t L, int32_t M, double kappa,
+                     uint64_t seed, xyz_pair **pairs, int64_t *offsets)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!Ys || B < 1)
+        return fail(XYZ_EINVAL, "need Ys and B >= 1");
+    int8_t *dYs = nullptr;
+    const size_t bytes = (size_t)B * (size_t)ctx->pk.n;
+    if (cudaMalloc(&dYs, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(XYZ_ENOMEM, "cudaMalloc of response staging failed");
+    }
+    cudaError_t e = cudaMemcpy(dYs, Ys, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dYs);
+        return fail(XYZ_ECUDA, std::string("cudaMemcpy of responses: ") + cudaGetErrorString(e));
+    }
+    rc = search_batch_dev(ctx, dYs, B, L, M, kappa, seed, pairs, offsets);
+    cudaFree(dYs);
+    return rc;
+}
+
 int xyz_set_filter(xyz_ctx *ctx, int enable)
 {
     if (!ctx)
@@ -926,10 +1102,12 @@ int xyz_run_keys(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, uint64_t *
     const int64_t p = ctx->pk.p;
     Plan pl;
     pl.R = 1;
+    pl.NB = pl.BB = 1;
+    pl.filter = false;
     pl.part = false;
     pl.k64 = true;
     pl.kbits = 1;
-    if ((rc = ensure_search_ws(ctx, pl)) || (rc = ensure(ctx->raw, (size_t)(p + 1) * 8)))
+    if ((rc = ensure_search_ws(ctx, pl, 1, 1)) || (rc = ensure(ctx->raw, (size_t)(p + 1) * 8)))
         return rc;
     int64_t launches = 0;
     uint64_t *raw = (uint64_t *)ctx->raw.ptr;

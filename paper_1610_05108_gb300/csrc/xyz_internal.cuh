@@ -93,12 +93,14 @@ cudaError_t scan_u32_dev(const uint32_t *in, uint32_t *out, const uint32_t *coun
                          uint32_t *total_out, void *temp, cudaStream_t s, int64_t *launches);
 
 // Equal-key groups of a sorted chunk -> buckets + per-bucket pair counts.
+// Keys are ((resp << runbits | run) << M) | Kc with rbits = bits above M;
+// a bucket's `pad` gets resp (0 when rbits == runbits).
 cudaError_t launch_join32(const uint32_t *keys, int64_t N, int M, int rbits, const uint8_t *cnz,
                           Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
                           cudaStream_t s, int64_t *launches);
 cudaError_t launch_join64(const uint64_t *keys, int64_t N, int M, int rbits, const uint8_t *cnz,
                           Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
-                          cudaStream_t s, int64_t *launches);
+                          cudaStream_t s, int64_t *launches, int runbits = -1);
 
 // Verify every candidate of the buckets; append passing (key, agree)
 // records, key = j * 2^kbits + k with j < k.
@@ -106,7 +108,8 @@ cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_
                           const uint32_t *nbuckets, const uint64_t *total_pairs,
                           const uint32_t *vals, int64_t amin, int kbits, uint64_t *rec_keys,
                           uint32_t *rec_agree, uint32_t *nrec, uint32_t rec_cap, cudaStream_t s,
-                          int64_t *launches);
+                          int64_t *launches, const uint32_t *ybs = nullptr,
+                          const int *abort_flag = nullptr);
 
 // Sorted records -> unique xyz pairs (device array), count in *nout.
 struct PairOut {
@@ -116,7 +119,7 @@ struct PairOut {
 cudaError_t launch_unique(const uint64_t *rec_keys, const uint32_t *rec_agree, const uint32_t *nrec,
                           int64_t cap, int kbits, int64_t n, uint32_t *flags, uint32_t *pos,
                           void *scan_temp, PairOut *out, uint32_t *nout, cudaStream_t s,
-                          int64_t *launches);
+                          int64_t *launches, uint32_t *resp = nullptr);
 
 // Agreement of explicit pairs.
 cudaError_t launch_agree_pairs(const Packed &pk, const int32_t *j, const int32_t *k, int64_t count,
@@ -143,13 +146,24 @@ bool filter_supported(int64_t p, int M);
 int filter_grid();
 size_t filter_scratch_words(int64_t p);
 int64_t filter_run_cap();
-cudaError_t launch_filter(const Packed &pk, int M, uint64_t seed, int64_t l0, int R,
-                          uint32_t *kc_scratch, uint32_t *seg_keys, uint32_t *seg_vals,
-                          uint32_t *seg_count, uint32_t seg_cap, int *overflow,
-                          uint32_t *out_keys, uint32_t *out_vals, uint32_t *nsurv, uint8_t *cnz,
-                          uint32_t *members, uint32_t *members_count, Bucket *buckets,
+// ybs: B response-bit rows of Wp words (B = 1: the context's own).  Runs
+// [l0, l0 + R) of a search whose first run is l0 - rbase, as R * NB work
+// items of one run and a block of BB responses; spilled survivors
+// go to the per-CTA segments as ((b << rbits | run) << M | Kc, j) and the
+// segments fill across launch groups (reset with launch_seg_reset, joined
+// with launch_compact).  overflow bit 1: a segment overflowed; bit 2: the
+// member/bucket space (mcap/bcap) did.
+cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, uint64_t seed,
+                          int64_t l0, int R, int NB, int BB, int rbits, int64_t rbase, int grid,
+                          uint32_t mcap, uint32_t bcap, uint32_t *kc_scratch, uint64_t *seg_keys,
+                          uint32_t *seg_vals, uint32_t *seg_count, uint32_t seg_cap, int *overflow,
+                          uint8_t *cnz, uint32_t *members, uint32_t *members_count, Bucket *buckets,
                           uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
                           int64_t *launches);
+cudaError_t launch_seg_reset(uint32_t *seg_count, cudaStream_t s, int64_t *launches);
+cudaError_t launch_compact(const uint64_t *seg_keys, const uint32_t *seg_vals,
+                           const uint32_t *seg_count, uint32_t seg_cap, int nseg, uint64_t *out_keys,
+                           uint32_t *out_vals, uint32_t *total, cudaStream_t s, int64_t *launches);
 
 // Host-side helpers shared by the API files.
 int64_t amin_rule(int64_t n, double kappa);

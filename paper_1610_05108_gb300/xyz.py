@@ -59,6 +59,8 @@ SIGNATURES = {
     "xyz_info": (ctypes.c_int, [_p, _p, _p, _p]),
     "xyz_search": (ctypes.c_int, [_p, _i32, _i32, _dbl, _u64, _p, _p]),
     "xyz_search_range": (ctypes.c_int, [_p, _i64, _i64, _i32, _dbl, _u64, _p, _p]),
+    "xyz_search_batch": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, _dbl, _u64, _p, _p]),
+    "xyz_search_batch_dev": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, _dbl, _u64, _p, _p]),
     "xyz_free_pairs": (None, [_p]),
     "xyz_free": (None, [_p]),
     "xyz_get_stats": (ctypes.c_int, [_p, _p]),
@@ -221,6 +223,19 @@ class Context:
         _check(load().xyz_search_range(self.handle, int(l0), int(l1), int(M), float(kappa),
                                        seed & (2**64 - 1), ctypes.byref(out), ctypes.byref(cnt)))
         return _pairs_to_numpy(out, cnt.value)
+
+    def search_batch(self, Ys: np.ndarray, L: int, M: int, kappa: float, seed: int) -> list:
+        """One search per row of Ys (B x n int8 +-1) on this X; list of B results."""
+        Ys = np.ascontiguousarray(Ys, dtype=np.int8)
+        if Ys.ndim != 2 or Ys.shape[1] != self.n:
+            raise ValueError("Ys must have shape (B, n)")
+        B = Ys.shape[0]
+        out = ctypes.c_void_p()
+        offs = np.zeros(B + 1, dtype=np.int64)
+        _check(load().xyz_search_batch(self.handle, _ptr(Ys), B, int(L), int(M), float(kappa),
+                                       seed & (2**64 - 1), ctypes.byref(out), _ptr(offs)))
+        allp = _pairs_to_numpy(out, int(offs[-1]))
+        return [allp[offs[b]:offs[b + 1]].copy() for b in range(B)]
 
     def stats(self) -> dict:
         st = Stats()
