@@ -18,6 +18,16 @@ xyz_search -> results to host -> xyz_destroy.
 
 --impl reference times the CPU oracle (plain C, one core) on a bounded
 sample of the same workload and scales it to one search.
+
+--pattern batch: one SNP-shaped X (n = 2000, p = 200000) with 256 responses,
+each with 3 planted pairs, screened once by the batched search (one call,
+shared row stream and keys) and once as 256 plain searches; both must give
+identical results.  --pattern serve: a Poisson stream (200 requests/s) of
+searches with L in [20, 200] and kappa in [0.2, 0.6] over resident SNP-shaped
+datasets of log-uniform n in [500, 8000] and p in [1e4, 5e5], each request
+with its own response (one planted pair of gamma in {0.7, 0.8, 0.9}) and M
+from the gamma0 = 0.55 rule of Section 6; reports p50/p99 latency and
+throughput of the server against the same requests run one after another.
 """
 from __future__ import annotations
 
@@ -35,7 +45,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-METRIC = "interaction pairs screened/s at >=95% planted recall"
+METRIC = "interaction pairs screened/s at \u226595% planted recall; p50/p99 search latency"
 UNIT = "pairs/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
@@ -411,6 +421,170 @@ def reference_arm(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------- batch pattern
+
+def batch_arm(args):
+    import torch
+    from paper_1610_05108_gb300 import build as _build
+    from paper_1610_05108_gb300 import synth, xyz
+    _build.build()
+    xyz.load()
+    n, p, B = 2000, 200000, args.batch_responses
+    t0 = time.perf_counter()
+    X, _ = synth.gwas_X(n, p, synth.rng_for(21, "X"))
+    Ys, planted, real = synth.extra_responses(X, B, 22, pairs_per_y=3, target_range=(0.45, 0.55),
+                                                balance=True)
+    log(f"[bench] batch: data made in {time.perf_counter() - t0:.1f} s")
+    kappa = 0.4
+    M = xyz.M_for_gamma0(p, 0.55)
+    targets = [[pr for pr, s_ in zip(planted[b], real[b]) if s_ >= kappa] for b in range(B)]
+    g_min = (1 + min(s_ for b in range(B) for s_ in real[b] if s_ >= kappa)) / 2
+    L = xyz.runs_for_recall(g_min ** M, 0.95)
+    seed = 77
+    ctx = xyz.create(X, Ys[0])
+    ctx.search_batch(Ys[:8], L, M, kappa, seed)                 # warm-up (workspace growth)
+    ctx.search(L, M, kappa, seed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    got = ctx.search_batch(Ys, L, M, kappa, seed)
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plain = []
+    for b in range(B):
+        ctx.set_y(Ys[b])
+        plain.append(ctx.search(L, M, kappa, seed))
+    t_plain = time.perf_counter() - t0
+    ctx.close()
+    same = all(np.array_equal(a, b) for a, b in zip(got, plain))
+    found = sum(1 for b in range(B) for pr in targets[b]
+                if any((int(j), int(k)) == tuple(pr) for j, k in zip(got[b]["j"], got[b]["k"])))
+    ntarget = sum(len(t) for t in targets)
+    pairs = B * p * (p - 1) / 2
+    out = {"metric": METRIC, "pattern": "batch", "value": pairs / t_batch, "unit": UNIT,
+           "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+           "ms_per_response": round(t_batch / B * 1e3, 3),
+           "plain": {"value": pairs / t_plain, "ms_per_response": round(t_plain / B * 1e3, 3),
+                     "path": "xyz_set_y + xyz_search per response"},
+           "speedup_vs_plain": round(t_plain / t_batch, 3), "identical_to_plain": bool(same),
+           "recall": {"found": found, "targets": ntarget,
+                      "expected_min_eta": round(xyz.eta(g_min, M, L), 4)},
+           "config": {"workload": f"one SNP-shaped X n={n} p={p} with {B} responses x 3 planted pairs "
+                                  f"(strength U[0.45,0.55] before scaling, balanced Y)",
+                      "n": n, "p": p, "B": B, "M": M, "L": L, "kappa": kappa,
+                      "timing": "host wall clock around the whole call, results on the host"}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------- serve pattern
+
+def serve_arm(args):
+    import threading
+
+    import torch
+    from paper_1610_05108_gb300 import build as _build
+    from paper_1610_05108_gb300 import synth, xyz
+    _build.build()
+    xyz.load()
+    D, R = args.serve_datasets, 8
+    sizes = synth.instance_sizes(D, 31)
+    t0 = time.perf_counter()
+    data = []
+    for i, (n, p) in enumerate(sizes):
+        X, f = synth.gwas_X(n, p, synth.rng_for(300 + i, "X"))
+        Ys, pairs, real = synth.single_pair_responses(X, f, R, 400 + i)
+        data.append((X, Ys, pairs, real))
+    reqs = synth.serve_requests(args.serve_requests, args.serve_rate, 32, D, R)
+    for q in reqs:
+        n, p = sizes[q["dataset"]]
+        q["M"] = xyz.M_for_gamma0(p, 0.55)
+    log(f"[bench] serve: {D} datasets {sizes} made in {time.perf_counter() - t0:.1f} s")
+
+    # plain: the same searches one after another, one context per dataset
+    ctxs = [xyz.create(X, Ys[0]) for X, Ys, _, _ in data]
+    for i, c in enumerate(ctxs):                               # warm-up
+        c.search(200, xyz.M_for_gamma0(sizes[i][1], 0.55), 0.2, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for q in reqs:
+        c = ctxs[q["dataset"]]
+        c.set_y(data[q["dataset"]][1][q["response"]])
+        plain.append(c.search(q["L"], q["M"], q["kappa"], q["seed"]))
+    t_plain = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+
+    def run_server(paced: bool):
+        srv = xyz.Server(workers=args.serve_workers, hbm_budget_bytes=120 << 30,
+                         slice_runs=args.serve_slice)
+        ds = [srv.add_dataset(X, Ys[0]) for X, Ys, _, _ in data]
+        for i in range(D):          # grow each worker's workspace before timing
+            for r in [srv.submit(ds[i], 64, xyz.M_for_gamma0(sizes[i][1], 0.55), 0.2, 3)
+                      for _ in range(args.serve_workers)]:
+                srv.wait(r)
+        ids = [None] * len(reqs)
+        start = time.perf_counter()
+
+        def producer():
+            for i, q in enumerate(reqs):
+                if paced:
+                    dt = start + q["t"] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                ids[i] = srv.submit(ds[q["dataset"]], q["L"], q["M"], q["kappa"], q["seed"],
+                                    Y=data[q["dataset"]][1][q["response"]])
+
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        res, lat = [], []
+        for i in range(len(reqs)):
+            r, l_ = srv.wait(ids[i])
+            res.append(r)
+            lat.append(l_)
+        el = time.perf_counter() - start
+        st = srv.stats()
+        srv.close()
+        return res, np.asarray(lat), el, st
+
+    served, lat, el, st = run_server(True)
+    sat, lat_sat, el_sat, _ = run_server(False)
+    same = all(np.array_equal(a, b) for a, b in zip(served, plain)) and \
+        all(np.array_equal(a, b) for a, b in zip(sat, plain))
+    pairs_total = sum(sizes[q["dataset"]][1] * (sizes[q["dataset"]][1] - 1) / 2 for q in reqs)
+    found = targets = 0
+    eta = []
+    for q, r in zip(reqs, served):
+        X, Ys, pairs, real = data[q["dataset"]]
+        s_ = real[q["response"]]
+        if s_ >= q["kappa"]:
+            targets += 1
+            pr = pairs[q["response"]]
+            found += int(any((int(j), int(k)) == pr for j, k in zip(r["j"], r["k"])))
+            eta.append(xyz.eta((1 + s_) / 2, q["M"], q["L"]))
+    out = {"metric": METRIC, "pattern": "serve", "value": pairs_total / el, "unit": UNIT,
+           "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+           "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                          "p99": round(float(np.percentile(lat, 99)), 3), "n": len(lat)},
+           "elapsed_s": round(el, 3), "arrivals_span_s": round(reqs[-1]["t"], 3),
+           "saturated": {"value": pairs_total / el_sat, "elapsed_s": round(el_sat, 3),
+                         "p50_ms": round(float(np.percentile(lat_sat, 50)), 3),
+                         "p99_ms": round(float(np.percentile(lat_sat, 99)), 3),
+                         "note": "all requests submitted at once"},
+           "plain": {"value": pairs_total / t_plain, "elapsed_s": round(t_plain, 3),
+                     "path": "one xyz_search per request, one after another"},
+           "identical_to_plain": bool(same),
+           "recall": {"found": found, "targets": targets,
+                      "expected": round(float(np.mean(eta)) if eta else 0.0, 4)},
+           "server": {"workers": args.serve_workers, "slice_runs": args.serve_slice,
+                      "budget_bytes": 120 << 30, "device_bytes": st["device_bytes"]},
+           "config": {"workload": f"Poisson {args.serve_rate:g} req/s, {len(reqs)} requests over {D} "
+                                  "resident SNP-shaped datasets, n in [500,8000], p in [1e4,5e5] "
+                                  "log-uniform, L in [20,200], kappa in [0.2,0.6]",
+                      "datasets": [list(x) for x in sizes]}}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,12 +597,23 @@ def main(argv=None):
     ap.add_argument("--ref-runs", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--pattern", choices=["search", "batch", "serve"], default="search")
+    ap.add_argument("--batch-responses", type=int, default=256)
+    ap.add_argument("--serve-datasets", type=int, default=6)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-slice", type=int, default=32)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gb300":
         log("[bench] warm-up raised to 3 steps")
         args.warmup = 3
     if args.impl == "reference":
         reference_arm(args)
+    elif args.pattern == "batch":
+        batch_arm(args)
+    elif args.pattern == "serve":
+        serve_arm(args)
     else:
         gpu_arm(args)
 

@@ -56,7 +56,7 @@ extern "C" {
 #define XYZ_EINVAL 1      /* bad argument: sizes, null pointer, entry not +-1, M, L, kappa */
 #define XYZ_ENOMEM 2      /* host or device allocation failed, or over a memory budget */
 #define XYZ_ECUDA 3       /* a CUDA call failed (the message names it) */
-#define XYZ_ETIMEDOUT 4   /* a bounded device-side wait gave up */
+#define XYZ_ETIMEDOUT 4   /* a bounded wait gave up (device-side, or xyz_server_wait) */
 #define XYZ_ECANCELED 5   /* a served request was cancelled */
 #define XYZ_EAGAIN 6      /* a served request is not finished yet */
 
@@ -256,6 +256,69 @@ int32_t xyz_M_for_gamma0(int64_t p, double gamma0);
  * more than cap candidates gives XYZ_ENOMEM and writes nothing. */
 int xyz_run_candidates_noalloc(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, int32_t *jk,
                                int64_t cap, int64_t *count);
+
+/* ------------------------------------------------------------- server */
+
+/* A search server: the search as a request loop.  The paper screens one X
+ * against several responses (the scaling experiment of Section 6 builds
+ * responses of strength 0.7, 0.8 and 0.9 for each X); here each such search
+ * is a request.  Datasets (packed X and a
+ * default response) stay resident on the device; requests carry their own
+ * response, L, M, kappa and seed.  Requests are admitted in arrival order
+ * while the device memory in use (resident datasets + the workers'
+ * workspaces + about one packed response and 1 MiB per admitted request)
+ * stays within hbm_budget_bytes; the others wait (the oldest waiting request
+ * is admitted whenever nothing is running, so none waits forever).  Admitted
+ * requests are cut into slices of slice_runs runs, and `workers` threads --
+ * each with its own CUDA stream and workspace -- take slices round-robin
+ * over all admitted requests (continuous batching at run granularity).  The
+ * result of a request is the union over its slices, which equals
+ * xyz_search(L, M, kappa, seed) on its (X, Y) exactly, whatever else is
+ * being served.  All xyz_server_* calls are thread-safe. */
+typedef struct xyz_server xyz_server;
+
+typedef struct xyz_server_stats {
+    int64_t completed;        /* requests finished with a result */
+    int64_t canceled;         /* requests cancelled */
+    int64_t failed;           /* requests that ended with an error */
+    int64_t queued;           /* waiting for admission now */
+    int64_t active;           /* admitted, not finished, now */
+    int64_t device_bytes;     /* device memory counted against the budget now */
+    int64_t budget_bytes;     /* the budget */
+    double p50_ms;            /* median submit-to-finish latency of completed requests */
+    double p99_ms;            /* 99th percentile of the same (linear interpolation) */
+    double pairs_screened;    /* sum of p(p-1)/2 over completed requests */
+    double elapsed_ms;        /* first submit to last completion */
+} xyz_server_stats;
+
+/* workers in [1, 64]; hbm_budget_bytes > 0; slice_runs >= 1.  Uses the
+ * current CUDA device. */
+int xyz_server_create(int32_t workers, int64_t hbm_budget_bytes, int64_t slice_runs, xyz_server **out);
+/* Make X (and default response Y) resident; same layout and checks as
+ * xyz_create.  XYZ_ENOMEM when the datasets would exceed the budget. */
+int xyz_server_add_dataset(xyz_server *srv, const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
+                           int32_t *dataset);
+/* Queue a search of `dataset` with response Y (n int8 +-1, copied before the
+ * call returns; NULL = the dataset's default response).  *request gets an id
+ * for wait/poll/cancel. */
+int xyz_server_submit(xyz_server *srv, int32_t dataset, const int8_t *Y, int32_t L, int32_t M,
+                      double kappa, uint64_t seed, int64_t *request);
+/* Block until the request ends or timeout_ms passes (< 0: no limit).  On
+ * XYZ_OK the request is retired and *pairs / *npairs / *latency_ms get its
+ * result (sorted by (j, k), free with xyz_free_pairs) and its submit-to-finish
+ * time; XYZ_ETIMEDOUT leaves it running; XYZ_ECANCELED / an error code retire
+ * it. */
+int xyz_server_wait(xyz_server *srv, int64_t request, int64_t timeout_ms, xyz_pair **pairs,
+                    int64_t *npairs, double *latency_ms);
+/* As xyz_server_wait with no waiting: XYZ_EAGAIN while the request runs. */
+int xyz_server_poll(xyz_server *srv, int64_t request, xyz_pair **pairs, int64_t *npairs,
+                    double *latency_ms);
+/* Cancel a queued or running request (slices already on the GPU finish;
+ * no new ones start).  Its wait/poll then returns XYZ_ECANCELED. */
+int xyz_server_cancel(xyz_server *srv, int64_t request);
+int xyz_server_get_stats(xyz_server *srv, xyz_server_stats *out);
+/* Stops the workers after their current slice and frees everything. */
+void xyz_server_destroy(xyz_server *srv);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,494 @@
+// Search server: a request loop in front of the xyz search.
+//
+// Datasets (packed X and a default response) stay resident on the device.
+// A request names a dataset, optionally its own response Y, and (L, M,
+// kappa, seed).  Requests are admitted while the device memory in use --
+// resident datasets, the workers' workspaces, and the admitted requests'
+// reservations -- stays within the budget; the rest wait in arrival order.
+// Admitted requests are served by continuous batching at run-range
+// granularity: each is cut into slices of `slice_runs` runs, and the worker
+// threads take slices round-robin over all admitted requests, so a request
+// that arrives while others are running starts at the next slice boundary
+// and its kernels overlap with theirs on the device (every worker owns a
+// CUDA stream and one workspace that it points at whichever dataset its
+// current slice belongs to).  The runs of a search are independent and
+// counter-seeded (Algorithm 2's loop), so the union of a request's slice
+// results is exactly the result of the whole search, whatever else was
+// running: results depend only on (X, Y, L, M, kappa, seed).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/xyz.h"
+#include "xyz_internal.cuh"
+
+using namespace xyz;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point a, Clock::time_point b)
+{
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+enum ReqState { RQ_QUEUED, RQ_ACTIVE, RQ_DONE, RQ_CANCELED, RQ_FAILED };
+
+struct Request {
+    int64_t id = 0;
+    int dataset = 0;
+    uint32_t *yb = nullptr;       // own packed response (device), or null
+    int32_t L = 1, M = 0;
+    double kappa = 0;
+    uint64_t seed = 0;
+    int64_t next_run = 0;         // first run not yet handed out
+    int slices_out = 0, slices_done = 0;
+    int64_t reserve = 0;          // bytes counted against the budget
+    std::vector<xyz_pair> acc;
+    ReqState state = RQ_QUEUED;
+    int err_code = 0;
+    std::string err;
+    bool cancel = false;
+    Clock::time_point t_submit, t_admit, t_done;
+};
+
+struct Dataset {
+    xyz_ctx *base = nullptr;
+    int64_t bytes = 0;
+};
+
+}  // namespace
+
+struct xyz_server {
+    int device = 0;
+    int64_t budget = 0;
+    int64_t slice_runs = 2048;
+    std::mutex mu;
+    std::mutex pack_mu;               // serialises packing of submitted responses
+    std::condition_variable cv_work, cv_done;
+    std::vector<Dataset> datasets;
+    std::map<int64_t, Request> reqs;
+    std::deque<int64_t> queued;       // waiting for admission, arrival order
+    std::vector<int64_t> active;      // admitted, runs left to hand out
+    size_t rr = 0;                    // round-robin position in `active`
+    int64_t next_id = 1;
+    int64_t reserved = 0;
+    std::vector<int64_t> worker_bytes;
+    std::vector<std::thread> threads;
+    std::vector<xyz_ctx *> views;
+    bool stop = false;
+    // statistics
+    std::vector<double> latencies;
+    int64_t completed = 0, canceled = 0, failed = 0;
+    double pairs_screened = 0;
+    Clock::time_point t0;
+    bool started = false;
+    Clock::time_point first_submit, last_done;
+};
+
+namespace {
+
+int64_t datasets_bytes(const xyz_server *s)
+{
+    int64_t b = 0;
+    for (const Dataset &d : s->datasets)
+        b += d.bytes;
+    return b;
+}
+
+int64_t in_use(const xyz_server *s)
+{
+    int64_t b = datasets_bytes(s) + s->reserved;
+    for (int64_t w : s->worker_bytes)
+        b += w;
+    return b;
+}
+
+// Move queued requests to active while the budget allows (lock held).
+// The oldest waiting request is always admitted when nothing is active,
+// so a request larger than the budget cannot wait forever.
+void admit(xyz_server *s)
+{
+    while (!s->queued.empty()) {
+        Request &r = s->reqs[s->queued.front()];
+        if (r.cancel) {
+            r.state = RQ_CANCELED;
+            r.t_done = Clock::now();
+            s->canceled++;
+            s->queued.pop_front();
+            s->cv_done.notify_all();
+            continue;
+        }
+        if (!s->active.empty() && in_use(s) + r.reserve > s->budget)
+            break;
+        r.state = RQ_ACTIVE;
+        r.t_admit = Clock::now();
+        s->reserved += r.reserve;
+        s->active.push_back(r.id);
+        s->queued.pop_front();
+    }
+}
+
+void finish(xyz_server *s, Request &r)
+{
+    // union of the slices' results: each pair once, sorted by (j, k)
+    std::sort(r.acc.begin(), r.acc.end(), [](const xyz_pair &a, const xyz_pair &b) {
+        return a.j != b.j ? a.j < b.j : a.k < b.k;
+    });
+    r.acc.erase(std::unique(r.acc.begin(), r.acc.end(),
+                            [](const xyz_pair &a, const xyz_pair &b) { return a.j == b.j && a.k == b.k; }),
+                r.acc.end());
+    r.t_done = Clock::now();
+    s->reserved -= r.reserve;
+    if (r.cancel) {
+        r.state = RQ_CANCELED;
+        s->canceled++;
+        r.acc.clear();
+    } else if (r.err_code) {
+        r.state = RQ_FAILED;
+        s->failed++;
+    } else {
+        r.state = RQ_DONE;
+        s->completed++;
+        s->latencies.push_back(ms_since(r.t_submit, r.t_done));
+        const double p = (double)ctx_packed(s->datasets[r.dataset].base)->p;
+        s->pairs_screened += p * (p - 1) / 2;
+        s->last_done = r.t_done;
+    }
+    if (r.yb) {
+        cudaFree(r.yb);
+        r.yb = nullptr;
+    }
+    admit(s);
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+}
+
+void worker_main(xyz_server *s, int w)
+{
+    cudaSetDevice(s->device);
+    xyz_ctx *view = s->views[w];
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        // next slice, round-robin over the admitted requests
+        int64_t rid = -1;
+        while (!s->stop) {
+            for (size_t k = 0; k < s->active.size(); ++k) {
+                const size_t i = (s->rr + k) % s->active.size();
+                Request &r = s->reqs[s->active[i]];
+                if (!r.cancel && r.next_run < r.L && !r.err_code) {
+                    rid = r.id;
+                    s->rr = i + 1;
+                    break;
+                }
+            }
+            if (rid >= 0)
+                break;
+            s->cv_work.wait(lk);
+        }
+        if (s->stop)
+            return;
+        Request &r = s->reqs[rid];
+        const int64_t l0 = r.next_run;
+        const int64_t l1 = std::min<int64_t>(r.L, l0 + s->slice_runs);
+        r.next_run = l1;
+        r.slices_out++;
+        if (r.next_run >= r.L)
+            s->active.erase(std::find(s->active.begin(), s->active.end(), rid));
+        xyz_ctx *base = s->datasets[r.dataset].base;
+        uint32_t *yb = r.yb;
+        const int32_t M = r.M;
+        const double kappa = r.kappa;
+        const uint64_t seed = r.seed;
+        lk.unlock();
+
+        view_target(view, base, yb);
+        xyz_pair *pairs = nullptr;
+        int64_t np = 0;
+        const int rc = xyz_search_range(view, l0, l1, M, kappa, seed, &pairs, &np);
+        std::string msg = rc ? xyz_last_error() : "";
+        const int64_t wb = ctx_device_bytes(view);
+
+        lk.lock();
+        s->worker_bytes[w] = wb;
+        Request &q = s->reqs[rid];
+        if (rc) {
+            q.err_code = rc;
+            q.err = msg;
+        } else if (np > 0) {
+            q.acc.insert(q.acc.end(), pairs, pairs + np);
+        }
+        xyz_free_pairs(pairs);
+        q.slices_done++;
+        if ((q.next_run >= q.L || q.cancel || q.err_code) && q.slices_done == q.slices_out) {
+            auto it = std::find(s->active.begin(), s->active.end(), rid);
+            if (it != s->active.end())
+                s->active.erase(it);
+            finish(s, q);
+        }
+    }
+}
+
+int take_result(xyz_server *s, Request &r, xyz_pair **pairs, int64_t *npairs, double *latency_ms)
+{
+    if (r.state == RQ_CANCELED)
+        return fail(XYZ_ECANCELED, "request was cancelled");
+    if (r.state == RQ_FAILED)
+        return fail(r.err_code, r.err);
+    xyz_pair *host = nullptr;
+    if (!r.acc.empty()) {
+        host = (xyz_pair *)std::malloc(r.acc.size() * sizeof(xyz_pair));
+        if (!host)
+            return fail(XYZ_ENOMEM, "host allocation of results failed");
+        std::memcpy(host, r.acc.data(), r.acc.size() * sizeof(xyz_pair));
+    }
+    if (pairs)
+        *pairs = host;
+    else
+        std::free(host);
+    if (npairs)
+        *npairs = (int64_t)r.acc.size();
+    if (latency_ms)
+        *latency_ms = ms_since(r.t_submit, r.t_done);
+    s->reqs.erase(r.id);
+    return XYZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int xyz_server_create(int32_t workers, int64_t hbm_budget_bytes, int64_t slice_runs, xyz_server **out)
+{
+    if (!out || workers < 1 || workers > 64 || hbm_budget_bytes < 1 || slice_runs < 1)
+        return fail(XYZ_EINVAL, "need 1 <= workers <= 64, a positive budget and slice size");
+    xyz_server *s = new (std::nothrow) xyz_server();
+    if (!s)
+        return fail(XYZ_ENOMEM, "host allocation failed");
+    cudaGetDevice(&s->device);
+    s->budget = hbm_budget_bytes;
+    s->slice_runs = slice_runs;
+    s->worker_bytes.assign((size_t)workers, 0);
+    for (int w = 0; w < workers; ++w) {
+        xyz_ctx *v = nullptr;
+        int rc = view_create(s->device, &v);
+        if (rc) {
+            for (xyz_ctx *x : s->views)
+                xyz_destroy(x);
+            delete s;
+            return rc;
+        }
+        s->views.push_back(v);
+    }
+    for (int w = 0; w < workers; ++w)
+        s->threads.emplace_back(worker_main, s, w);
+    *out = s;
+    return XYZ_OK;
+}
+
+int xyz_server_add_dataset(xyz_server *s, const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
+                           int32_t *dataset)
+{
+    if (!s || !dataset)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    xyz_ctx *c = nullptr;
+    int rc = xyz_create(X, Y, n, p, &c);
+    if (rc)
+        return rc;
+    int64_t bytes = 0;
+    xyz_info(c, nullptr, nullptr, &bytes);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (datasets_bytes(s) + bytes > s->budget) {
+        xyz_destroy(c);
+        return fail(XYZ_ENOMEM, "dataset does not fit the server's device memory budget");
+    }
+    s->datasets.push_back(Dataset{c, bytes});
+    *dataset = (int32_t)s->datasets.size() - 1;
+    return XYZ_OK;
+}
+
+int xyz_server_submit(xyz_server *s, int32_t dataset, const int8_t *Y, int32_t L, int32_t M,
+                      double kappa, uint64_t seed, int64_t *request)
+{
+    if (!s || !request)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    if (L < 1 || M < 0 || M > XYZ_MAX_M || !(kappa >= -1.0 && kappa <= 1.0))
+        return fail(XYZ_EINVAL, "bad L, M or kappa");
+    xyz_ctx *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (dataset < 0 || dataset >= (int32_t)s->datasets.size())
+            return fail(XYZ_EINVAL, "unknown dataset");
+        base = s->datasets[dataset].base;
+    }
+    const Packed &pk = *ctx_packed(base);
+    uint32_t *yb = nullptr;
+    if (Y) {
+        if (cudaMalloc(&yb, (size_t)pk.Wp * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(XYZ_ENOMEM, "cudaMalloc of a request's response failed");
+        }
+        int rc;
+        {
+            std::lock_guard<std::mutex> plk(s->pack_mu);
+            rc = pack_response(base, Y, yb);
+        }
+        if (rc) {
+            cudaFree(yb);
+            return rc;
+        }
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    Request r;
+    r.id = s->next_id++;
+    r.dataset = dataset;
+    r.yb = yb;
+    r.L = L;
+    r.M = M;
+    r.kappa = kappa;
+    r.seed = seed;
+    // response bits plus room for results (records of a slice)
+    r.reserve = (int64_t)pk.Wp * 4 + ((int64_t)1 << 20);
+    r.t_submit = Clock::now();
+    if (!s->started) {
+        s->started = true;
+        s->first_submit = r.t_submit;
+    }
+    s->reqs[r.id] = std::move(r);
+    s->queued.push_back(*request = s->next_id - 1);
+    admit(s);
+    s->cv_work.notify_all();
+    return XYZ_OK;
+}
+
+int xyz_server_wait(xyz_server *s, int64_t request, int64_t timeout_ms, xyz_pair **pairs,
+                    int64_t *npairs, double *latency_ms)
+{
+    if (!s)
+        return fail(XYZ_EINVAL, "null server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto done = [&] {
+        auto it = s->reqs.find(request);
+        return it == s->reqs.end() || it->second.state == RQ_DONE || it->second.state == RQ_CANCELED ||
+               it->second.state == RQ_FAILED;
+    };
+    if (timeout_ms < 0)
+        s->cv_done.wait(lk, done);
+    else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
+        return fail(XYZ_ETIMEDOUT, "request not finished within the timeout");
+    auto it = s->reqs.find(request);
+    if (it == s->reqs.end())
+        return fail(XYZ_EINVAL, "unknown request");
+    return take_result(s, it->second, pairs, npairs, latency_ms);
+}
+
+int xyz_server_poll(xyz_server *s, int64_t request, xyz_pair **pairs, int64_t *npairs, double *latency_ms)
+{
+    if (!s)
+        return fail(XYZ_EINVAL, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(request);
+    if (it == s->reqs.end())
+        return fail(XYZ_EINVAL, "unknown request");
+    ReqState st = it->second.state;
+    if (st == RQ_QUEUED || st == RQ_ACTIVE)
+        return fail(XYZ_EAGAIN, "request not finished");
+    return take_result(s, it->second, pairs, npairs, latency_ms);
+}
+
+int xyz_server_cancel(xyz_server *s, int64_t request)
+{
+    if (!s)
+        return fail(XYZ_EINVAL, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(request);
+    if (it == s->reqs.end())
+        return fail(XYZ_EINVAL, "unknown request");
+    Request &r = it->second;
+    if (r.state == RQ_QUEUED || r.state == RQ_ACTIVE) {
+        r.cancel = true;
+        if (r.state == RQ_QUEUED) {
+            s->queued.erase(std::find(s->queued.begin(), s->queued.end(), request));
+            r.state = RQ_CANCELED;
+            r.t_done = Clock::now();
+            s->canceled++;
+            if (r.yb) {
+                cudaFree(r.yb);
+                r.yb = nullptr;
+            }
+            s->cv_done.notify_all();
+        } else if (r.slices_done == r.slices_out) {
+            auto a = std::find(s->active.begin(), s->active.end(), request);
+            if (a != s->active.end())
+                s->active.erase(a);
+            finish(s, r);
+        }
+    }
+    return XYZ_OK;
+}
+
+int xyz_server_get_stats(xyz_server *s, xyz_server_stats *out)
+{
+    if (!s || !out)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->completed = s->completed;
+    out->canceled = s->canceled;
+    out->failed = s->failed;
+    out->queued = (int64_t)s->queued.size();
+    int64_t act = 0;
+    for (auto &kv : s->reqs)
+        act += kv.second.state == RQ_ACTIVE;
+    out->active = act;
+    out->device_bytes = in_use(s);
+    out->budget_bytes = s->budget;
+    std::vector<double> l = s->latencies;
+    if (!l.empty()) {
+        std::sort(l.begin(), l.end());
+        auto pct = [&](double q) {
+            double x = q * (double)(l.size() - 1);
+            size_t i = (size_t)x;
+            double f = x - (double)i;
+            return i + 1 < l.size() ? l[i] * (1 - f) + l[i + 1] * f : l[i];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+    }
+    out->pairs_screened = s->pairs_screened;
+    if (s->started && s->completed)
+        out->elapsed_ms = ms_since(s->first_submit, s->last_done);
+    return XYZ_OK;
+}
+
+void xyz_server_destroy(xyz_server *s)
+{
+    if (!s)
+        return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->cv_work.notify_all();
+    }
+    for (std::thread &t : s->threads)
+        t.join();
+    for (xyz_ctx *v : s->views)
+        xyz_destroy(v);
+    for (auto &kv : s->reqs)
+        if (kv.second.yb)
+            cudaFree(kv.second.yb);
+    for (Dataset &d : s->datasets)
+        xyz_destroy(d.base);
+    delete s;
+}
+
+}  // extern "C"

@@ -74,6 +74,7 @@ struct xyz_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    bool owns_packed = true;     // false for a view sharing another context's packed X
     Packed pk;
     int *d_bad = nullptr;
     int64_t packed_bytes = 0;
@@ -700,9 +701,11 @@ void destroy_ctx(xyz_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream)
         cudaStreamSynchronize(c->stream);
-    cudaFree(c->pk.Xc);
-    cudaFree(c->pk.Xr);
-    cudaFree(c->pk.yb);
+    if (c->owns_packed) {
+        cudaFree(c->pk.Xc);
+        cudaFree(c->pk.Xr);
+        cudaFree(c->pk.yb);
+    }
     cudaFree(c->d_bad);
     DevBuf *all[] = {&c->keysA,   &c->keysB,       &c->valsA,     &c->valsB,    &c->radix_tmp,
                      &c->cnz,     &c->buckets,     &c->pair_counts, &c->pair_off, &c->scan_tmp,
@@ -1209,4 +1212,67 @@ namespace xyz {
 const Packed *ctx_packed(const xyz_ctx *c) { return &c->pk; }
 cudaStream_t ctx_stream(const xyz_ctx *c) { return c->stream; }
 int ctx_device(const xyz_ctx *c) { return c->device; }
+
+// A context with its own stream and workspace that searches the packed X of
+// other contexts (view_target); it never frees packed arrays.
+int view_create(int device, xyz_ctx **out)
+{
+    xyz_ctx *c = new (std::nothrow) xyz_ctx();
+    if (!c)
+        return fail(XYZ_ENOMEM, "host allocation failed");
+    std::memset(&c->stats, 0, sizeof(c->stats));
+    c->device = device;
+    c->owns_packed = false;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->d_bad, 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        destroy_ctx(c);
+        return fail(XYZ_ECUDA, std::string("view set-up: ") + cudaGetErrorString(e));
+    }
+    c->own_stream = true;
+    *out = c;
+    return XYZ_OK;
+}
+
+void view_target(xyz_ctx *view, const xyz_ctx *base, uint32_t *yb)
+{
+    view->pk = base->pk;
+    if (yb)
+        view->pk.yb = yb;
+}
+
+int64_t ctx_device_bytes(const xyz_ctx *c) { return (c->owns_packed ? c->packed_bytes : 0) + ws_bytes(c); }
+
+// Pack a host response into yb_dev (Wp words) on c's stream; -1/+1 only.
+int pack_response(xyz_ctx *c, const int8_t *Y, uint32_t *yb_dev)
+{
+    int8_t *dY = nullptr;
+    if (cudaMalloc(&dY, (size_t)c->pk.n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(XYZ_ENOMEM, "cudaMalloc of response staging failed");
+    }
+    int64_t launches = 0;
+    Packed tmp = c->pk;
+    tmp.yb = yb_dev;
+    int bad = 0;
+    cudaError_t e = cudaMemcpyAsync(dY, Y, (size_t)c->pk.n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->d_bad, 0, 16, c->stream);
+    if (e == cudaSuccess)
+        e = launch_pack_y(dY, tmp, c->d_bad, c->stream, &launches);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&bad, c->d_bad, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    cudaFree(dY);
+    if (e != cudaSuccess)
+        return fail(XYZ_ECUDA, std::string("packing a response: ") + cudaGetErrorString(e));
+    if (bad)
+        return fail(XYZ_EINVAL, "entries of Y must be -1 or +1");
+    return XYZ_OK;
+}
 }  // namespace xyz

@@ -176,5 +176,9 @@ namespace xyz {
 const Packed *ctx_packed(const xyz_ctx *c);
 cudaStream_t ctx_stream(const xyz_ctx *c);
 int ctx_device(const xyz_ctx *c);
+int view_create(int device, xyz_ctx **out);
+void view_target(xyz_ctx *view, const xyz_ctx *base, uint32_t *yb);
+int64_t ctx_device_bytes(const xyz_ctx *c);
+int pack_response(xyz_ctx *c, const int8_t *Y, uint32_t *yb_dev);
 
 }  // namespace xyz

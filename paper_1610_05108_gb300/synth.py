@@ -107,13 +107,15 @@ def gwas_X(n: int, p: int, rng: np.random.Generator, block: int = 20, rho: float
     for c0 in range(0, p, chunk_cols):
         c1 = min(p, c0 + chunk_cols)
         e = rng.standard_normal(size=(c1 - c0, n), dtype=np.float32)  # column-major rows
-        u = np.empty_like(e)
-        for c in range(c1 - c0):
-            j = c0 + c
-            if j % block == 0 or c == 0:
-                u[c] = e[c]
-            else:
-                u[c] = rho32 * u[c - 1] + s * e[c]
+        # the chain restarts at every block start (c0 is one); step all blocks
+        # of the chunk together, one position within the block at a time
+        nb = -(-(c1 - c0) // block)
+        u = np.zeros((nb * block, n), dtype=np.float32)
+        u[: c1 - c0] = e
+        u = u.reshape(nb, block, n)
+        for t in range(1, block):
+            u[:, t] = rho32 * u[:, t - 1] + s * u[:, t]
+        u = u.reshape(nb * block, n)[: c1 - c0]
         X[:, c0:c1] = np.where(u < thr[c0:c1, None], np.int8(-1), np.int8(1)).T
     return X, f
 
@@ -139,9 +141,14 @@ def _pick_planted(f: np.ndarray, count: int, block: int, rng: np.random.Generato
     return [tuple(sorted((cols[2 * t], cols[2 * t + 1]))) for t in range(count)]
 
 
-def plant_response(X: np.ndarray, pairs, targets, rng: np.random.Generator):
+def plant_response(X: np.ndarray, pairs, targets, rng: np.random.Generator, balance: bool = False):
     """Response whose products with the planted pairs reach lambda * targets
-    for the largest feasible lambda (<= 1), allocated exactly per pattern."""
+    for the largest feasible lambda (<= 1), allocated exactly per pattern.
+
+    ``balance`` adds the constraint sum_i Y_i = 0 (up to rounding): on
+    SNP-shaped columns an unbalanced response makes every pair of nearly
+    constant columns (both of low minor frequency) look like an interaction
+    of strength about mean(Y)."""
     from scipy.optimize import linprog
 
     n = X.shape[0]
@@ -157,11 +164,13 @@ def plant_response(X: np.ndarray, pairs, targets, rng: np.random.Generator):
     # variables: y(c) in [-1, 1] for each pattern, lambda in [0, 1]
     c_obj = np.zeros(nv + 1)
     c_obj[-1] = -1.0
-    A_eq = np.zeros((T, nv + 1))
-    A_eq[:, :nv] = (pats * mu[:, None]).T
-    A_eq[:, nv] = -targets
+    A_eq = np.zeros((T + int(balance), nv + 1))
+    A_eq[:T, :nv] = (pats * mu[:, None]).T
+    A_eq[:T, nv] = -targets
+    if balance:
+        A_eq[T, :nv] = mu
     bounds = [(-1.0, 1.0)] * nv + [(0.0, 1.0)]
-    res = linprog(c_obj, A_eq=A_eq, b_eq=np.zeros(T), bounds=bounds, method="highs")
+    res = linprog(c_obj, A_eq=A_eq, b_eq=np.zeros(len(A_eq)), bounds=bounds, method="highs")
     if not res.success:
         raise RuntimeError("planting LP failed: " + str(res.message))
     yv = res.x[:nv]
@@ -229,7 +238,7 @@ def config_gwas_large(seed: int = 1) -> Dataset:
 
 
 def extra_responses(X: np.ndarray, count: int, seed: int, pairs_per_y: int = 3,
-                    target_range=(0.3, 0.5), flip_noise: float = 0.0):
+                    target_range=(0.3, 0.5), flip_noise: float = 0.0, balance: bool = False):
     """``count`` further responses for one X, each with its own planted pairs.
 
     Returns (Ys (count, n) int8, planted [[(j, k)]], realised [[s]])."""
@@ -241,7 +250,7 @@ def extra_responses(X: np.ndarray, count: int, seed: int, pairs_per_y: int = 3,
         cols = r.choice(p, size=2 * pairs_per_y, replace=False)
         pairs = [tuple(sorted((int(cols[2 * t]), int(cols[2 * t + 1])))) for t in range(pairs_per_y)]
         targets = r.uniform(target_range[0], target_range[1], size=pairs_per_y)
-        Y, _ = plant_response(X, pairs, targets, r)
+        Y, _ = plant_response(X, pairs, targets, r, balance=balance)
         if flip_noise > 0:
             fl = r.random(n) < flip_noise
             Y[fl] = -Y[fl]
@@ -263,3 +272,41 @@ def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
     """Arrival times (s) of a Poisson stream with mean ``rate`` per second."""
     r = rng_for(seed, "serve")
     return np.cumsum(r.exponential(1.0 / rate, size=count))
+
+
+def single_pair_responses(X: np.ndarray, f: np.ndarray, count: int, seed: int,
+                          gammas=(0.7, 0.8, 0.9), block: int = 20):
+    """``count`` balanced responses for one X, each with one planted pair
+    whose interaction strength gamma = a/n is drawn from ``gammas`` (the
+    scaling experiment of Section 6 plants one pair of gamma in {0.7, 0.8,
+    0.9}).
+
+    Returns (Ys (count, n) int8, pairs [(j, k)], realised [Y^T(X_j o X_k)/n])."""
+    n, _ = X.shape
+    r = rng_for(seed, "multi")
+    Ys = np.empty((count, n), dtype=np.int8)
+    pairs, real = [], []
+    for b in range(count):
+        pr = _pick_planted(f, 1, block, r)
+        g = float(r.choice(np.asarray(gammas, dtype=np.float64)))
+        Y, _ = plant_response(X, pr, [2.0 * g - 1.0], r, balance=True)
+        Ys[b] = Y
+        pairs.append(pr[0])
+        real.append(_realised(X, Y, pr)[0])
+    return Ys, pairs, real
+
+
+def serve_requests(count: int, rate: float, seed: int, datasets: int, responses: int,
+                   L_range=(20, 200), kappa_range=(0.2, 0.6)):
+    """A Poisson request stream over resident datasets: per request the
+    arrival time (s), dataset index, response index, L (uniform integer in
+    L_range), kappa (uniform in kappa_range) and search seed."""
+    r = rng_for(seed, "serve")
+    t = np.cumsum(r.exponential(1.0 / rate, size=count))
+    ds = r.integers(0, datasets, size=count)
+    ys = r.integers(0, responses, size=count)
+    Ls = r.integers(L_range[0], L_range[1] + 1, size=count)
+    ks = r.uniform(kappa_range[0], kappa_range[1], size=count)
+    seeds = r.integers(0, 2**62, size=count)
+    return [dict(t=float(t[i]), dataset=int(ds[i]), response=int(ys[i]), L=int(Ls[i]),
+                 kappa=float(ks[i]), seed=int(seeds[i])) for i in range(count)]

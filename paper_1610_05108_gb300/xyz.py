@@ -48,6 +48,15 @@ class Stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "completed", "canceled", "failed", "queued", "active", "device_bytes", "budget_bytes")] + \
+        [(name, ctypes.c_double) for name in ("p50_ms", "p99_ms", "pairs_screened", "elapsed_ms")]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 # name -> (restype, argtypes); every symbol declared in include/xyz.h
 SIGNATURES = {
     "xyz_create": (ctypes.c_int, [_p, _p, _i64, _i64, _p]),
@@ -77,6 +86,14 @@ SIGNATURES = {
     "xyz_best_M": (ctypes.c_int, [_i64, _i64, _dbl, _p, _i64, _i32, _p, _p]),
     "xyz_M_for_gamma0": (_i32, [_i64, _dbl]),
     "xyz_run_candidates_noalloc": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _i64, _p]),
+    "xyz_server_create": (ctypes.c_int, [_i32, _i64, _i64, _p]),
+    "xyz_server_add_dataset": (ctypes.c_int, [_p, _p, _p, _i64, _i64, _p]),
+    "xyz_server_submit": (ctypes.c_int, [_p, _i32, _p, _i32, _i32, _dbl, _u64, _p]),
+    "xyz_server_wait": (ctypes.c_int, [_p, _i64, _i64, _p, _p, _p]),
+    "xyz_server_poll": (ctypes.c_int, [_p, _i64, _p, _p, _p]),
+    "xyz_server_cancel": (ctypes.c_int, [_p, _i64]),
+    "xyz_server_get_stats": (ctypes.c_int, [_p, _p]),
+    "xyz_server_destroy": (None, [_p]),
 }
 
 _lib = None
@@ -297,3 +314,89 @@ class Context:
 
 def create(X: np.ndarray, Y: np.ndarray) -> Context:
     return Context.from_host(X, Y)
+
+
+class Server:
+    """Request loop over resident datasets (xyz_server_* in include/xyz.h).
+
+    ``submit`` returns a request id; ``wait``/``poll`` return
+    ``(pairs, latency_ms)``; a cancelled request raises XyzError with code
+    XYZ_ECANCELED, an unfinished one XYZ_ETIMEDOUT (wait) or XYZ_EAGAIN (poll).
+    """
+
+    def __init__(self, workers: int = 2, hbm_budget_bytes: int = 120 << 30, slice_runs: int = 2048):
+        h = ctypes.c_void_p()
+        _check(load().xyz_server_create(int(workers), int(hbm_budget_bytes), int(slice_runs),
+                                        ctypes.byref(h)))
+        self._h = h
+        self._n = {}
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("server is closed")
+        return self._h
+
+    def add_dataset(self, X: np.ndarray, Y: np.ndarray) -> int:
+        X = np.asfortranarray(X, dtype=np.int8)
+        Y = np.ascontiguousarray(Y, dtype=np.int8)
+        n, p = X.shape
+        if Y.shape != (n,):
+            raise ValueError("Y must have shape (n,)")
+        d = ctypes.c_int32(0)
+        _check(load().xyz_server_add_dataset(self.handle, _ptr(X), _ptr(Y), n, p, ctypes.byref(d)))
+        self._n[d.value] = n
+        return d.value
+
+    def submit(self, dataset: int, L: int, M: int, kappa: float, seed: int, Y: np.ndarray = None) -> int:
+        yp = None
+        if Y is not None:
+            Y = np.ascontiguousarray(Y, dtype=np.int8)
+            if Y.shape != (self._n[dataset],):
+                raise ValueError("Y must have shape (n,)")
+            yp = _ptr(Y)
+        r = ctypes.c_int64(0)
+        _check(load().xyz_server_submit(self.handle, int(dataset), yp, int(L), int(M), float(kappa),
+                                        seed & (2**64 - 1), ctypes.byref(r)))
+        return r.value
+
+    def wait(self, request: int, timeout_ms: int = -1):
+        out = ctypes.c_void_p()
+        cnt = ctypes.c_int64(0)
+        lat = ctypes.c_double(0)
+        _check(load().xyz_server_wait(self.handle, int(request), int(timeout_ms), ctypes.byref(out),
+                                      ctypes.byref(cnt), ctypes.byref(lat)))
+        return _pairs_to_numpy(out, cnt.value), lat.value
+
+    def poll(self, request: int):
+        out = ctypes.c_void_p()
+        cnt = ctypes.c_int64(0)
+        lat = ctypes.c_double(0)
+        _check(load().xyz_server_poll(self.handle, int(request), ctypes.byref(out), ctypes.byref(cnt),
+                                      ctypes.byref(lat)))
+        return _pairs_to_numpy(out, cnt.value), lat.value
+
+    def cancel(self, request: int):
+        _check(load().xyz_server_cancel(self.handle, int(request)))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().xyz_server_get_stats(self.handle, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().xyz_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
