@@ -19,10 +19,11 @@ xyz_search -> results to host -> xyz_destroy.
 --impl reference times the CPU oracle (plain C, one core) on a bounded
 sample of the same workload and scales it to one search.
 
---pattern batch: one SNP-shaped X (n = 2000, p = 200000) with 256 responses,
-each with 3 planted pairs, screened once by the batched search (one call,
-shared row stream and keys) and once as 256 plain searches; both must give
-identical results.  --pattern serve: a Poisson stream (200 requests/s) of
+--pattern batch: one SNP-shaped X (n = 2000, p = 200000) with 256 balanced
+responses, each with 3 planted pairs, kappa = 0.4, M by eq. bestM and L for
+95% recall of the weakest target, screened once by the batched search (one
+call, shared row stream and keys) and once as 256 plain searches; both must
+give identical results.  --pattern serve: a Poisson stream (200 requests/s) of
 searches with L in [20, 200] and kappa in [0.2, 0.6] over resident SNP-shaped
 datasets of log-uniform n in [500, 8000] and p in [1e4, 5e5], each request
 with its own response (one planted pair of gamma in {0.7, 0.8, 0.9}) and M
@@ -436,12 +437,13 @@ def batch_arm(args):
                                                 balance=True)
     log(f"[bench] batch: data made in {time.perf_counter() - t0:.1f} s")
     kappa = 0.4
-    M = xyz.M_for_gamma0(p, 0.55)
     targets = [[pr for pr, s_ in zip(planted[b], real[b]) if s_ >= kappa] for b in range(B)]
     g_min = (1 + min(s_ for b in range(B) for s_ in real[b] if s_ >= kappa)) / 2
-    L = xyz.runs_for_recall(g_min ** M, 0.95)
     seed = 77
     ctx = xyz.create(X, Ys[0])
+    _, _, agree = ctx.sample_agree(10**6, 0x5EED)             # plug-in M of eq. bestM
+    M, _ = xyz.best_M(n, p, (1 + kappa) / 2, agree)
+    L = xyz.runs_for_recall(g_min ** M, 0.95)
     ctx.search_batch(Ys[:8], L, M, kappa, seed)                 # warm-up (workspace growth)
     ctx.search(L, M, kappa, seed)
     torch.cuda.synchronize()

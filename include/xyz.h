@@ -184,6 +184,12 @@ int xyz_set_chunk_entries(xyz_ctx *ctx, int64_t entries);
  * 0 groups every column.  Results never depend on it. */
 int xyz_set_filter(xyz_ctx *ctx, int enable);
 
+/* Tuning (filter path): runs whose survivors do not fit on chip are grouped
+ * through a sort, once per `groups` launch groups (0, the default: once per
+ * search; the library lowers it by itself when the spill buffers would pass
+ * about 2^27 entries).  groups >= 0.  Results never depend on it. */
+int xyz_set_spill_flush(xyz_ctx *ctx, int64_t groups);
+
 /* --------------------------------------------------- parity / observability */
 
 /* Keys of run `run` (Algorithm 2 step 3 with the integer reading of the

@@ -1,32 +1,32 @@
 // Per-run survivor filter for the equal-pairs search (Algorithm 2 steps
 // 3-4), used for M <= 31 when p is small enough for a shared-memory filter.
 //
-// In a run whose response key c is non-zero, a column can only be part of a
-// candidate pair if some column on the other side of its canonical group
-// exists (keys.cu: the group of column j is h = min(kx_j, kx_j ^ c), its side
-// is whether kx_j != h).  Almost every column fails that test, so the sort
-// that groups equal keys (radix.cu) only needs the few that pass.  One CTA
-// (1024 threads) handles one run at a time:
+// In run l with response key c, columns j and k form a candidate exactly
+// when kx_j ^ kx_k = c (keys.cu: X_j and Z_k agree on the sampled rows).  A
+// column can therefore only be part of a candidate pair if the key kx_j ^ c
+// is present among the run's column keys.  Almost every column fails that
+// test, so the grouping of equal canonical keys only needs the few that
+// pass.  One CTA (1024 threads) handles one run at a time:
 //
 //   pass 1  build the keys of all p columns (each thread: the words of the M
 //           sampled rows, transposed in registers), store kx to the CTA's
 //           L2-resident scratch in bit-major order (coalesced without
-//           staging), and set two bits
-//           of one word, chosen by hashes of h, in the shared-memory
-//           blocked Bloom filter of the column's side;
-//   pass 2  keep the columns whose h may be present on the other side (both
-//           bits set in the other side's filter word) and append them, as
-//           (run << M | Kc, j) with the canonical key Kc of keys.cu, to the
-//           CTA's own output segment (warp-aggregated shared-memory cursor,
-//           no global atomics).
+//           staging), and set two bits of one word, chosen by hashes of kx,
+//           in the shared-memory blocked Bloom filter F of the run;
+//   pass 2  keep the columns whose kx ^ c may be in F (both bits set) and
+//           append them, as (Kc, j) with the canonical key Kc of keys.cu, to
+//           the shared survivor array (warp-aggregated cursor).
 //
-// The survivors of a run (a few percent of its columns) are then grouped on
-// chip into buckets and members, ready for verification; a run with too
-// many survivors for the chip goes to the CTA's global segment instead, and
-// a small second kernel concatenates the segments for the LSD sort and join
-// of the general path.  A Bloom filter has no false negatives, so every true
-// candidate survives; false positives are single-sided groups that never
-// become buckets.  In a run with c == 0 every column survives.
+// A Bloom filter has no false negatives, and when kx_j ^ c = kx_k both j and
+// k pass (kx_k ^ c = kx_j), so every column of every candidate pair
+// survives; false positives are groups with one side only, which yield no
+// bucket.  When a run keeps more columns than the chip can group, the
+// survivors are filtered again with a fresh filter built from the survivors
+// alone (refinement: a candidate pair's columns are both survivors, so
+// they still find each other), and only what remains after a few rounds is
+// spilled to the CTA's global segment for the general sort and join.  The
+// survivors of a run are grouped on chip into buckets and members, ready
+// for verification.  In a run with c == 0 every column survives.
 #include <type_traits>
 
 #include "bits.cuh"
@@ -37,8 +37,33 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int FL_THREADS = 1024;
-constexpr int FL_LOGB = 19;                       // filter bits per side
-constexpr int FL_WORDS = 1 << (FL_LOGB - 5);      // 16384 words per side
+constexpr int FL_LOGF = 20;                       // bits of the run filter F
+constexpr int FL_FWORDS = 1 << (FL_LOGF - 5);     // 32768 words (128 KB)
+constexpr int FL_LOGR = 13;
+constexpr int FL_RWORDS = 1 << FL_LOGR;           // refinement filter, in the survivor array
+constexpr int FL_KWORDS = 262144 / 32;            // keep-mask words: p <= 262144
+constexpr int FL_LOGT = 13;
+constexpr int FL_T = 1 << FL_LOGT;                // grouping table slots (key + packed counts)
+constexpr int FL_ROUNDS = 3;                      // refinement rounds at most
+constexpr uint32_t FL_EMPTY = 0xFFFFFFFFu;
+
+// Shared-memory layout, in 32-bit words.  One response per run: the filter
+// F is dead once the survivors are known, so the grouping table takes its
+// place and the survivor array can hold 6144 entries.  Several responses per
+// run: F must outlive every response's grouping, so the table has its own
+// region (where the keep mask also lives) and the survivor array holds 4096.
+template <bool BATCH>
+struct FlLayout {
+    static constexpr int SMAX = BATCH ? 4096 : 6144;           // survivors grouped on chip
+    static constexpr int OFF_SV = FL_FWORDS;                   // [SMAX] u64 | refinement filter
+    static constexpr int OFF_KM = OFF_SV + 2 * SMAX;           // [FL_KWORDS] keep mask
+    static constexpr int OFF_TAB = BATCH ? OFF_KM : 0;         // [FL_T] keys, [FL_T] counts
+    static constexpr int WORDS = BATCH ? OFF_TAB + 2 * FL_T : OFF_KM + FL_KWORDS;
+    static_assert(2 * SMAX >= FL_RWORDS, "the refinement filter fits the survivor array");
+    static_assert(!BATCH || 2 * FL_T >= FL_KWORDS, "the keep mask lies inside the table");
+    static_assert(BATCH || 2 * FL_T <= FL_FWORDS, "the table fits the filter's memory");
+    static_assert(SMAX < FL_T, "the table has a free slot for every survivor");
+};
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z)
 {
@@ -53,39 +78,46 @@ __device__ __forceinline__ int64_t draw_row(uint64_t seed, uint64_t t, int64_t n
     return (int64_t)__umul64hi(u, (uint64_t)n);
 }
 
-// Blocked Bloom filter: a group value h selects one 32-bit word of its
-// side's filter and two bits inside it, all from multiplicative hashes
-// (Knuth's method with two odd constants, top bits).  Setting is one shared
-// atomic OR, testing one shared load.
+// Blocked Bloom filter of 2^LOGW words: a key selects one 32-bit word and
+// two bits inside it, all from multiplicative hashes (Knuth's method with
+// two odd constants, top bits).  Setting is one shared atomic OR, testing
+// one shared load.
+template <int LOGW>
 __device__ __forceinline__ void bloom_pos(uint32_t h, uint32_t &word, uint32_t &mask)
 {
-    word = (h * 0x9E3779B1u) >> (32 - (FL_LOGB - 5));
+    word = (h * 0x9E3779B1u) >> (32 - LOGW);
     const uint32_t y = h * 0x7FEB352Du + 0x165667B1u;
     mask = (1u << (y >> 27)) | (1u << ((y >> 22) & 31u));
 }
 
-constexpr int FL_SMAX = 6144;                    // survivors of one run grouped on chip
-constexpr int FL_LOGT = 13;
-constexpr int FL_T = 1 << FL_LOGT;                // table slots, in the filter's memory
-constexpr uint32_t FL_EMPTY = 0xFFFFFFFFu;
+// Canonical key of a surviving column (keys.cu): group h = min(kx, kx ^ c)
+// with bit tb = msb(c) removed, shifted left, side bit kx != h at the bottom.
+__device__ __forceinline__ uint32_t canon(uint32_t kx, uint32_t c, int tb, uint32_t lowmask)
+{
+    if (c == 0)
+        return kx;
+    const uint32_t kxc = kx ^ c;
+    const uint32_t h = kx < kxc ? kx : kxc;
+    const uint32_t above = (h >> (tb + 1)) << tb;
+    return ((above | (h & lowmask)) << 1) | ((kx != h) ? 1u : 0u);
+}
 
-// One CTA per run at a time.  Passes 1-2 as described at the top of the
-// file; then, when the run has at most FL_SMAX survivors, they are grouped
-// on chip: the 128 KB that held the two filters becomes a hash table of
-// FL_T group keys with side counts, each group with candidates becomes a
-// bucket (bucket and member space reserved with one global atomic pair per
-// run) and its members are written side A first.  A run with more survivors
-// (for example every column of a run whose c is 0) re-runs pass 2 into the
-// CTA's global segment instead, as (run << M | Kc, j), for the general sort
-// and join.  Spilled survivors carry ((b << rbits | run) << M) | Kc in 64-bit
-// keys, run counted from the start of the search, and the per-CTA segments
-// fill across launch groups: the search sorts all of them once at its end.
-// kc_scratch holds, per CTA, the keys of its current run in bit-major
-// order: kx of column 32w + cc at cc * P + w.
+// One CTA per run at a time (passes 1-2 as described at the top of the
+// file).  When the run keeps at most FL_SMAX columns they are grouped on
+// chip: a hash table of FL_T group keys with packed side counts, each group
+// with candidates becomes a bucket (bucket and member space reserved with
+// one global atomic pair per run) and its members are written side A first.
+// A run that keeps more, after refinement (for example every column of a run
+// whose c is 0), goes to the CTA's global segment instead, for the general
+// sort and join.  Spilled survivors carry ((b << rbits | run) << M) | Kc in
+// 64-bit keys, run counted from the start of the search, and the per-CTA
+// segments fill across launch groups until the host sorts them.  kc_scratch
+// holds, per CTA, the keys of its current run in bit-major order: kx of
+// column 32w + cc at cc * P + w.
 //
-// BATCH: B responses share X and the row stream.  The keys of a run are
-// built once; the filter, survivors and grouping then run once per response
-// b (its response key c_b, its filters) and buckets carry b in their `pad`
+// BATCH: B responses share X and the row stream.  The keys of a run and its
+// filter F are built once; pass 2, refinement and grouping then run once per
+// response b (its response key c_b), and buckets carry b in their `pad`
 // field.  cnz is indexed (b << rbits) | run.
 template <int MB, bool BATCH>
 __global__ void __launch_bounds__(FL_THREADS, 1)
@@ -101,13 +133,14 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
 {
     using SegKey = uint64_t;
     extern __shared__ __align__(16) uint32_t fl_smem[];
-    uint32_t *bmA = fl_smem;                       // [FL_WORDS]   (passes 1-2)
-    uint32_t *bmB = fl_smem + FL_WORDS;            // [FL_WORDS]
-    uint32_t *tkey = fl_smem;                      // [FL_T]       (grouping)
-    uint32_t *cA = fl_smem + FL_T;                 // [FL_T]
-    uint32_t *cB = fl_smem + 2 * FL_T;             // [FL_T]
-    uint32_t *tok = fl_smem + 3 * FL_T;            // [FL_T] 1 = group has a bucket
-    uint64_t *sv = reinterpret_cast<uint64_t *>(fl_smem + 2 * FL_WORDS);   // [FL_SMAX]
+    using Lay = FlLayout<BATCH>;
+    constexpr int FL_SMAX = Lay::SMAX;
+    uint32_t *F = fl_smem;                                                   // [FL_FWORDS]
+    uint64_t *sv = reinterpret_cast<uint64_t *>(fl_smem + Lay::OFF_SV);      // [FL_SMAX]
+    uint32_t *rf = fl_smem + Lay::OFF_SV;                                    // [FL_RWORDS]
+    uint32_t *kmask = fl_smem + Lay::OFF_KM;                                 // [FL_KWORDS]
+    uint32_t *tkey = fl_smem + Lay::OFF_TAB;                                 // [FL_T]
+    uint32_t *tcnt = fl_smem + Lay::OFF_TAB + FL_T;                          // [FL_T]
     const int t = threadIdx.x;
     const int lane = t & 31, wp = t >> 5;
     __shared__ int64_t rowoff[32];      // row s_m times the row pitch
@@ -115,6 +148,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     __shared__ uint32_t c_sh;
     __shared__ uint32_t cursor;         // global segment fill
     __shared__ uint32_t ns;             // survivors of the current (run, response)
+    __shared__ uint32_t scur;           // survivor array fill after refinement
     __shared__ uint32_t wsum[FL_THREADS / 32];
     __shared__ uint32_t mbase_sh, bbase_sh;
     uint32_t *kcs = kc_scratch + (int64_t)blockIdx.x * 32 * P;
@@ -126,15 +160,14 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         cursor = seg_count[blockIdx.x];     // segments fill across launch groups
 
     // work item = (run r, block of responses [b0, b1)); the keys of the run
-    // are built once per item
+    // and its filter are built once per item
     for (int item = blockIdx.x; item < R * NB; item += gridDim.x) {
         const int r = item / NB;
         const int b0 = (item - r * NB) * BB;
         const int b1 = (b0 + BB < B) ? b0 + BB : B;
         const uint64_t rl = (uint64_t)(rbase + r);   // run index within the search
-        if (!BATCH)
-            for (int i = t; i < 2 * FL_WORDS; i += FL_THREADS)
-                fl_smem[i] = 0;
+        for (int i = t; i < FL_FWORDS; i += FL_THREADS)
+            F[i] = 0;
         if (wp == 0) {
             int64_t s = 0;
             if (lane < M)
@@ -146,18 +179,16 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 const uint32_t c = __ballot_sync(FULL, ybit);
                 if (lane == 0) {
                     c_sh = c;
-                    ns = 0;
                     cnz[rl] = (c != 0);
                 }
             }
         }
         __syncthreads();
 
-        // pass 1: keys to the scratch rows (and, for one response, the filter
-        // bits of each side).  Rows at or past MB are zero at compile time.
+        // pass 1: keys to the scratch rows and the filter.  Rows at or past
+        // MB are zero at compile time.
         {
-            const uint32_t c = BATCH ? 0u : c_sh;
-            const bool nz = c != 0;
+            const bool need = BATCH || c_sh != 0;    // c == 0 keeps every column
             for (uint32_t w = t; w < P32; w += FL_THREADS) {
                 uint32_t A[32];
 #pragma unroll
@@ -167,17 +198,14 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
 #pragma unroll
                 for (int cc = 0; cc < 32; ++cc)
                     kcs[cc * P32 + w] = A[cc];         // bit-major: coalesced across the warp
-                if (!BATCH && nz) {
+                if (need) {
                     const uint32_t ncol = (32 * w + 32 <= p32) ? 32u : p32 - 32 * w;
 #pragma unroll
                     for (int cc = 0; cc < 32; ++cc) {
                         if ((uint32_t)cc < ncol) {
-                            const uint32_t kx = A[cc];
-                            const uint32_t kxc = kx ^ c;
-                            const uint32_t h = kx < kxc ? kx : kxc;
                             uint32_t word, mask;
-                            bloom_pos(h, word, mask);
-                            atomicOr(((kx != h) ? bmB : bmA) + word, mask);
+                            bloom_pos<FL_LOGF - 5>(A[cc], word, mask);
+                            atomicOr(F + word, mask);
                         }
                     }
                 }
@@ -187,9 +215,6 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
 
         for (int b = b0; b < b1; ++b) {
             if (BATCH) {
-                // this response's key c_b and filters
-                for (int i = t; i < 2 * FL_WORDS; i += FL_THREADS)
-                    fl_smem[i] = 0;
                 if (wp == 0) {
                     const int64_t s = rowidx[lane];
                     const uint32_t *ybb = ybs + (int64_t)b * Wp;
@@ -197,63 +222,123 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                     const uint32_t c = __ballot_sync(FULL, ybit);
                     if (lane == 0) {
                         c_sh = c;
-                        ns = 0;
                         cnz[((uint64_t)b << rbits) | rl] = (c != 0);
                     }
                 }
-                __syncthreads();
-                const uint32_t c = c_sh;
-                if (c != 0) {
-                    for (uint32_t cc = 0; cc < 32; ++cc)
-                    for (uint32_t w = t; w < P32; w += FL_THREADS) {
-                        if (32 * w + cc >= p32)
-                            continue;
-                        const uint32_t kx = kcs[cc * P32 + w];
-                        const uint32_t kxc = kx ^ c;
-                        const uint32_t h = kx < kxc ? kx : kxc;
-                        uint32_t word, mask;
-                        bloom_pos(h, word, mask);
-                        atomicOr(((kx != h) ? bmB : bmA) + word, mask);
-                    }
-                }
-                __syncthreads();
             }
+            if (t == 0)
+                ns = 0;
+            __syncthreads();
             const uint32_t c = c_sh;
             const bool nz = c != 0;
             const int tb = nz ? 31 - __clz(c) : 0;
             const uint32_t lowmask = nz ? ((1u << tb) - 1u) : 0u;
+            const SegKey runbits = (SegKey)((((uint64_t)b << rbits) | rl) << M);
 
-            // pass 2: the survivors.  to_global = false: into the shared
-            // survivor array (only counted past FL_SMAX); true: into the
-            // CTA's global segment with the composite key.
-            auto pass2 = [&](bool to_global) {
-                const SegKey runbits = (SegKey)((((uint64_t)b << rbits) | rl) << M);
-                for (uint32_t st = 0; st < steps; ++st) {
-                    const uint32_t w = st * FL_THREADS + t;
-                    uint32_t kv[32];
+            // pass 2: test every column; keep bits of column word w to
+            // kmask[w], and the survivors, while they fit, to the shared array
+            for (uint32_t st = 0; st < steps; ++st) {
+                const uint32_t w = st * FL_THREADS + t;
+                uint32_t keep = 0;     // bit cc: column 32w + cc survives
+                if (w < P32) {
+                    const uint32_t valid = (32 * w + 32 <= p32) ? 0xFFFFFFFFu
+                                                                : ((1u << (p32 - 32 * w)) - 1u);
+                    if (!nz) {
+                        keep = valid;
+                    } else {
 #pragma unroll
-                    for (int cc = 0; cc < 32; ++cc)
-                        kv[cc] = (w < P32) ? kcs[cc * P32 + w] : 0u;
-                    uint32_t keep = 0;     // bit cc: column 32w + cc survives
-                    if (w < P32) {
-                        const uint32_t valid = (32 * w + 32 <= p32) ? 0xFFFFFFFFu
-                                                                    : ((1u << (p32 - 32 * w)) - 1u);
-                        if (!nz) {
-                            keep = valid;
-                        } else {
+                        for (int cc = 0; cc < 32; ++cc) {
+                            uint32_t word, mask;
+                            bloom_pos<FL_LOGF - 5>(kcs[cc * P32 + w] ^ c, word, mask);
+                            keep |= ((F[word] & mask) == mask ? 1u : 0u) << cc;
+                        }
+                        keep &= valid;
+                    }
+                    kmask[w] = keep;
+                }
+                const uint32_t cnt = __popc(keep);
+                uint32_t incl = cnt;
 #pragma unroll
-                            for (int cc = 0; cc < 32; ++cc) {
-                                const uint32_t kx = kv[cc];
-                                const uint32_t kxc = kx ^ c;
-                                const uint32_t h = kx < kxc ? kx : kxc;
-                                uint32_t word, mask;
-                                bloom_pos(h, word, mask);
-                                const uint32_t have = ((kx != h) ? bmA : bmB)[word];
-                                keep |= ((have & mask) == mask ? 1u : 0u) << cc;
-                            }
-                            keep &= valid;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o)
+                        incl += y;
+                }
+                const uint32_t wtot = __shfl_sync(FULL, incl, 31);
+                if (wtot == 0)
+                    continue;
+                uint32_t wbase = 0;
+                if (lane == 31)
+                    wbase = atomicAdd(&ns, wtot);
+                wbase = __shfl_sync(FULL, wbase, 31);
+                uint32_t o = wbase + incl - cnt;
+                while (keep && o < (uint32_t)FL_SMAX) {
+                    const int cc = __ffs(keep) - 1;
+                    keep &= keep - 1;
+                    const uint32_t kx = kcs[cc * P32 + w];   // survivors only: re-read, cache-hot
+                    sv[o] = ((uint64_t)canon(kx, c, tb, lowmask) << 32) | (32 * w + cc);
+                    ++o;
+                }
+            }
+            __syncthreads();
+            uint32_t s = ns;
+
+            if (s > (uint32_t)FL_SMAX) {
+                // refinement: a fresh filter of the survivors' keys (in the
+                // survivor array's memory) with new hashes, tested again
+                for (int round = 1; nz && round <= FL_ROUNDS; ++round) {
+                    __syncthreads();                   // every thread has read ns
+                    for (int i = t; i < FL_RWORDS; i += FL_THREADS)
+                        rf[i] = 0;
+                    if (t == 0)
+                        ns = 0;
+                    __syncthreads();
+                    const uint32_t salt = 0x9E3779B9u * (uint32_t)round;
+                    for (uint32_t w = t; w < P32; w += FL_THREADS) {
+                        uint32_t keep = kmask[w];
+                        while (keep) {
+                            const int cc = __ffs(keep) - 1;
+                            keep &= keep - 1;
+                            uint32_t word, mask;
+                            bloom_pos<FL_LOGR>(mix32(kcs[cc * P32 + w] ^ salt), word, mask);
+                            atomicOr(rf + word, mask);
                         }
                     }
+                    __syncthreads();
+                    for (uint32_t st = 0; st < steps; ++st) {
+                        const uint32_t w = st * FL_THREADS + t;
+                        uint32_t keep = w < P32 ? kmask[w] : 0u;
+                        uint32_t left = keep;
+                        while (left) {
+                            const int cc = __ffs(left) - 1;
+                            left &= left - 1;
+                            uint32_t word, mask;
+                            bloom_pos<FL_LOGR>(mix32((kcs[cc * P32 + w] ^ c) ^ salt), word, mask);
+                            if ((rf[word] & mask) != mask)
+                                keep &= ~(1u << cc);
+                        }
+                        if (w < P32)
+                            kmask[w] = keep;
+                        const uint32_t wtot = __reduce_add_sync(FULL, (uint32_t)__popc(keep));
+                        if (lane == 0 && wtot)
+                            atomicAdd(&ns, wtot);
+                    }
+                    __syncthreads();
+                    const uint32_t s_new = ns;
+                    const bool done = s_new <= (uint32_t)FL_SMAX || s_new > s - s / 8;
+                    s = s_new;
+                    if (done)
+                        break;
+                }
+                // emit what is left: to the survivor array when it fits, else
+                // to the CTA's global segment with the composite key
+                const bool to_global = s > (uint32_t)FL_SMAX;
+                if (t == 0)
+                    scur = 0;
+                __syncthreads();
+                for (uint32_t st = 0; st < steps; ++st) {
+                    const uint32_t w = st * FL_THREADS + t;
+                    uint32_t keep = w < P32 ? kmask[w] : 0u;
                     const uint32_t cnt = __popc(keep);
                     uint32_t incl = cnt;
 #pragma unroll
@@ -267,49 +352,38 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                         continue;
                     uint32_t wbase = 0;
                     if (lane == 31)
-                        wbase = atomicAdd(to_global ? &cursor : &ns, wtot);
+                        wbase = atomicAdd(to_global ? &cursor : &scur, wtot);
                     wbase = __shfl_sync(FULL, wbase, 31);
                     uint32_t o = wbase + incl - cnt;
                     while (keep) {
                         const int cc = __ffs(keep) - 1;
                         keep &= keep - 1;
-                        const uint32_t kx = kcs[cc * P32 + w];   // survivors only: re-read, cache-hot
-                        uint32_t key = kx;
-                        if (nz) {
-                            const uint32_t kxc = kx ^ c;
-                            const uint32_t h = kx < kxc ? kx : kxc;
-                            const uint32_t above = (h >> (tb + 1)) << tb;
-                            key = ((above | (h & lowmask)) << 1) | ((kx != h) ? 1u : 0u);
-                        }
+                        const uint32_t key = canon(kcs[cc * P32 + w], c, tb, lowmask);
                         if (to_global) {
                             if (o < seg_cap) {
                                 okeys[o] = runbits | (SegKey)key;
                                 ovals[o] = 32 * w + cc;
                             }
-                        } else if (o < FL_SMAX) {
+                        } else if (o < (uint32_t)FL_SMAX) {
                             sv[o] = ((uint64_t)key << 32) | (32 * w + cc);
                         }
                         ++o;
                     }
                 }
-            };
-            pass2(false);
-            __syncthreads();
-            const uint32_t s = ns;
-            if (s > FL_SMAX) {
-                pass2(true);            // too many for the chip: the general path groups them
                 __syncthreads();
-                continue;
+                if (to_global)
+                    continue;               // the general path groups this run
             }
 
-            // grouping on chip; the filters are dead, their memory is the table
+            // grouping on chip in the table (the keep mask and, for one
+            // response, the filter are dead)
             for (int i = t; i < FL_T; i += FL_THREADS) {
                 tkey[i] = FL_EMPTY;
-                cA[i] = 0;
-                cB[i] = 0;
+                tcnt[i] = 0;
             }
             __syncthreads();
-            // phase I: insert group keys, count sides; keep (side, slot, j)
+            // phase I: insert group keys, count sides (A high half, B low
+            // half); keep (side, slot, j)
             for (uint32_t i = t; i < s; i += FL_THREADS) {
                 const uint64_t e = sv[i];
                 const uint32_t Kc = (uint32_t)(e >> 32);
@@ -322,12 +396,14 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                         break;
                     slot = (slot + 1) & (FL_T - 1);
                 }
-                atomicAdd(side ? &cB[slot] : &cA[slot], 1u);
+                atomicAdd(&tcnt[slot], side ? 1u : 0x10000u);
                 sv[i] = ((uint64_t)((side << 31) | slot) << 32) | (uint32_t)e;
             }
             __syncthreads();
             // phase II: groups with candidates -> buckets; one global atomic
-            // pair per (run, response) reserves their space
+            // pair per (run, response) reserves their space.  Afterwards
+            // tkey / tcnt of a bucket's slot are the end cursors of its sides
+            // A / B, and tcnt is FL_EMPTY for a slot without a bucket.
             {
                 constexpr int PER = FL_T / FL_THREADS;
                 uint32_t packed[PER];          // members << 16 | buckets of each slot
@@ -337,7 +413,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                     const int slot = t * PER + q;
                     uint32_t v = 0;
                     if (tkey[slot] != FL_EMPTY) {
-                        const uint32_t nA = cA[slot], nB = cB[slot];
+                        const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
                         const bool ok = nz ? (nA > 0 && nB > 0) : (nA > 1);
                         if (ok)
                             v = ((nA + nB) << 16) | 1u;
@@ -377,15 +453,16 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 for (int q = 0; q < PER; ++q) {
                     const int slot = t * PER + q;
                     const uint32_t v = packed[q];
-                    tok[slot] = v ? 1u : 0u;
                     if (v) {
-                        const uint32_t nA = cA[slot], nB = cB[slot];
+                        const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
                         const uint32_t base = mbase_sh + (run_off >> 16);
                         const uint32_t bi = bbase_sh + (run_off & 0xFFFFu);
                         buckets[bi] = Bucket{base, nA, nz ? nB : 0u, (uint32_t)b};
                         pair_counts[bi] = nz ? (uint64_t)nA * nB : (uint64_t)nA * (nA - 1) / 2;
-                        cA[slot] = base + nA;          // end of side A: cursor counts down
-                        cB[slot] = base + nA + nB;     // end of side B
+                        tkey[slot] = base + nA;          // end of side A: cursor counts down
+                        tcnt[slot] = base + nA + nB;     // end of side B
+                    } else {
+                        tcnt[slot] = FL_EMPTY;
                     }
                     run_off += v;
                 }
@@ -396,9 +473,9 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 const uint64_t e = sv[i];
                 const uint32_t hi = (uint32_t)(e >> 32);
                 const uint32_t slot = hi & 0x7FFFFFFFu;
-                if (!tok[slot])
+                if (tcnt[slot] == FL_EMPTY)
                     continue;
-                const uint32_t pos = atomicSub((hi >> 31) ? &cB[slot] : &cA[slot], 1u) - 1u;
+                const uint32_t pos = atomicSub((hi >> 31) ? &tcnt[slot] : &tkey[slot], 1u) - 1u;
                 members[pos] = (uint32_t)e;
             }
             __syncthreads();
@@ -451,9 +528,12 @@ __global__ void __launch_bounds__(256)
 
 bool filter_supported(int64_t p, int M) { return M <= 31 && p <= 262144; }
 
-size_t filter_smem_bytes() { return (size_t)(2 * FL_WORDS) * 4 + (size_t)FL_SMAX * 8; }
+size_t filter_smem_bytes(bool batch)
+{
+    return (size_t)(batch ? FlLayout<true>::WORDS : FlLayout<false>::WORDS) * 4;
+}
 
-int64_t filter_run_cap() { return FL_SMAX; }
+int64_t filter_run_cap() { return FlLayout<false>::SMAX; }
 
 int filter_grid()
 {
@@ -490,8 +570,8 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
                           uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
                           int64_t *launches)
 {
-    const size_t smem = filter_smem_bytes();
     const bool batch = B > 1;
+    const size_t smem = filter_smem_bytes(batch);
     using KernT = void (*)(const uint32_t *, int64_t, int64_t, const uint32_t *, int64_t, int, int64_t,
                            int64_t, int, uint64_t, int64_t, int, int, int, int, int64_t, uint32_t, uint32_t,
                            uint32_t *, void *, uint32_t *, uint32_t *, uint32_t, int *, uint8_t *,

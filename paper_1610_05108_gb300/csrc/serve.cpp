@@ -85,6 +85,8 @@ struct xyz_server {
     std::vector<int64_t> worker_bytes;
     std::vector<std::thread> threads;
     std::vector<xyz_ctx *> views;
+    // device buffers for requests' packed responses, reused across requests
+    std::vector<std::pair<size_t, uint32_t *>> yb_free;
     bool stop = false;
     // statistics
     std::vector<double> latencies;
@@ -110,7 +112,39 @@ int64_t in_use(const xyz_server *s)
     int64_t b = datasets_bytes(s) + s->reserved;
     for (int64_t w : s->worker_bytes)
         b += w;
+    for (const auto &f : s->yb_free)
+        b += (int64_t)f.first;
     return b;
+}
+
+// Return a request's response buffer to the server's free list (lock held).
+void release_yb(xyz_server *s, Request &r)
+{
+    if (r.yb) {
+        const Packed &pk = *ctx_packed(s->datasets[r.dataset].base);
+        s->yb_free.emplace_back((size_t)pk.Wp * 4, r.yb);
+        r.yb = nullptr;
+    }
+}
+
+// A free response buffer of at least `bytes`, or a new one (lock held).
+uint32_t *take_yb(xyz_server *s, size_t bytes)
+{
+    size_t best = s->yb_free.size();
+    for (size_t i = 0; i < s->yb_free.size(); ++i)
+        if (s->yb_free[i].first >= bytes && (best == s->yb_free.size() || s->yb_free[i].first < s->yb_free[best].first))
+            best = i;
+    if (best < s->yb_free.size()) {
+        uint32_t *p = s->yb_free[best].second;
+        s->yb_free.erase(s->yb_free.begin() + (ptrdiff_t)best);
+        return p;
+    }
+    uint32_t *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
 }
 
 // Move queued requests to active while the budget allows (lock held).
@@ -124,6 +158,7 @@ void admit(xyz_server *s)
             r.state = RQ_CANCELED;
             r.t_done = Clock::now();
             s->canceled++;
+            release_yb(s, r);
             s->queued.pop_front();
             s->cv_done.notify_all();
             continue;
@@ -164,10 +199,7 @@ void finish(xyz_server *s, Request &r)
         s->pairs_screened += p * (p - 1) / 2;
         s->last_done = r.t_done;
     }
-    if (r.yb) {
-        cudaFree(r.yb);
-        r.yb = nullptr;
-    }
+    release_yb(s, r);
     admit(s);
     s->cv_done.notify_all();
     s->cv_work.notify_all();
@@ -333,17 +365,20 @@ int xyz_server_submit(xyz_server *s, int32_t dataset, const int8_t *Y, int32_t L
     const Packed &pk = *ctx_packed(base);
     uint32_t *yb = nullptr;
     if (Y) {
-        if (cudaMalloc(&yb, (size_t)pk.Wp * 4) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(XYZ_ENOMEM, "cudaMalloc of a request's response failed");
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            yb = take_yb(s, (size_t)pk.Wp * 4);
         }
+        if (!yb)
+            return fail(XYZ_ENOMEM, "cudaMalloc of a request's response failed");
         int rc;
         {
             std::lock_guard<std::mutex> plk(s->pack_mu);
             rc = pack_response(base, Y, yb);
         }
         if (rc) {
-            cudaFree(yb);
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->yb_free.emplace_back((size_t)pk.Wp * 4, yb);
             return rc;
         }
     }
@@ -421,10 +456,7 @@ int xyz_server_cancel(xyz_server *s, int64_t request)
             r.state = RQ_CANCELED;
             r.t_done = Clock::now();
             s->canceled++;
-            if (r.yb) {
-                cudaFree(r.yb);
-                r.yb = nullptr;
-            }
+            release_yb(s, r);
             s->cv_done.notify_all();
         } else if (r.slices_done == r.slices_out) {
             auto a = std::find(s->active.begin(), s->active.end(), request);
@@ -486,6 +518,8 @@ void xyz_server_destroy(xyz_server *s)
     for (auto &kv : s->reqs)
         if (kv.second.yb)
             cudaFree(kv.second.yb);
+    for (auto &f : s->yb_free)
+        cudaFree(f.second);
     for (Dataset &d : s->datasets)
         xyz_destroy(d.base);
     delete s;

@@ -89,7 +89,9 @@ struct xyz_ctx {
     int64_t surv_cap = 0;        // filter path: survivor capacity (CTAs x segment)
     int64_t seg_cap = 0;         // filter path: survivors one CTA may write per group
     int64_t mem_cap = 0;         // filter path: members of on-chip groups per launch group
+    int64_t spill_flush = 0;     // filter path: launch groups per spill flush (0: one per search)
     DevBuf resp, ybs;            // batched search: response of each output pair, response bits
+    DevBuf y_alt, y_stage;       // response updates: packed copy checked before use, host staging
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
     int64_t rec_cap = 1 << 16;
     int64_t chunk_entries = (int64_t)1 << 25;
@@ -137,7 +139,7 @@ static int64_t ws_bytes(const xyz_ctx *c)
                            &c->ents, &c->seg, &c->members, &c->kc_scratch,
                            &c->seg_keys, &c->seg_vals, &c->seg_count,
                            &c->buckets2, &c->pair_counts2, &c->pair_off2, &c->scan_tmp2,
-                           &c->resp, &c->ybs};
+                           &c->resp, &c->ybs, &c->y_alt, &c->y_stage};
     int64_t s = 0;
     for (const DevBuf *b : all)
         s += (int64_t)b->bytes;
@@ -413,14 +415,78 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
         if (pl.filter) {
             const int grid = filter_grid();
             const int64_t mb = c->mem_cap / 2 + 1;
+            const int sbits = bbits + rbits + M;
+            key_bits_max = sbits;
+            // Runs with too many survivors for the chip spill to per-CTA
+            // segments; the spills of `flush` launch groups (all of them when
+            // flush == 0) are sorted, joined and verified together.
+            auto flush_spills = [&]() -> int {
+                tm.begin(ST_KEYS);
+                CU(launch_compact((const uint64_t *)c->seg_keys.ptr, (const uint32_t *)c->seg_vals.ptr,
+                                  (const uint32_t *)c->seg_count.ptr, (uint32_t)c->seg_cap, grid,
+                                  (uint64_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr, ctr_nsurv(c),
+                                  c->stream, &launches));
+                tm.end();
+                uint32_t ns = 0;
+                int sovf = 0;
+                CU(cudaMemcpyAsync(&ns, ctr_nsurv(c), 4, cudaMemcpyDeviceToHost, c->stream));
+                CU(cudaMemcpyAsync(&sovf, ctr_sovf(c), 4, cudaMemcpyDeviceToHost, c->stream));
+                CU(cudaStreamSynchronize(c->stream));
+                if (sovf & 1) {
+                    // a spill segment overflowed: larger segments up to a
+                    // bound, then more frequent flushes
+                    const int64_t seg_limit = ((int64_t)1 << 27) / grid;
+                    if (c->seg_cap * 2 <= seg_limit || c->spill_flush == 1)
+                        c->seg_cap *= 2;
+                    else
+                        c->spill_flush = c->spill_flush ? (c->spill_flush + 1) / 2
+                                                        : ((l1 - l0 + pl.R - 1) / pl.R + 1) / 2;
+                    redo = true;
+                }
+                if (sovf & 2) {
+                    c->mem_cap *= 2;               // the on-chip groups' members did
+                    redo = true;
+                }
+                if (redo || ns == 0)
+                    return XYZ_OK;
+                surv_total += ns;
+                const int64_t sb = c->surv_cap / 2 + 1;
+                bool alt = false;
+                tm.begin(ST_SORT);
+                CU(radix_sort64((uint64_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr,
+                                (uint64_t *)c->keysB.ptr, (uint32_t *)c->valsB.ptr, (int64_t)ns, sbits,
+                                c->radix_tmp.ptr, &alt, c->stream, &launches));
+                tm.end();
+                const uint64_t *ks = (const uint64_t *)(alt ? c->keysB.ptr : c->keysA.ptr);
+                const uint32_t *vs = (const uint32_t *)(alt ? c->valsB.ptr : c->valsA.ptr);
+                tm.begin(ST_JOIN);
+                CU(cudaMemsetAsync(ctr_nbuckets2(c), 0, 4, c->stream));
+                CU(launch_join64(ks, (int64_t)ns, M, bbits + rbits, (const uint8_t *)c->cnz.ptr,
+                                 (Bucket *)c->buckets2.ptr, (uint64_t *)c->pair_counts2.ptr,
+                                 ctr_nbuckets2(c), c->stream, &launches, rbits));
+                CU(scan_u64_dev((const uint64_t *)c->pair_counts2.ptr, (uint64_t *)c->pair_off2.ptr,
+                                ctr_nbuckets2(c), sb, ctr_total2(c), ctr_cand(c), c->scan_tmp2.ptr,
+                                c->stream, &launches));
+                tm.end();
+                tm.begin(ST_VERIFY);
+                CU(launch_verify(c->pk, (const Bucket *)c->buckets2.ptr,
+                                 (const uint64_t *)c->pair_off2.ptr, ctr_nbuckets2(c), ctr_total2(c), vs,
+                                 amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
+                                 (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
+                                 c->stream, &launches, B > 1 ? ybs : nullptr));
+                tm.end();
+                CU(launch_seg_reset((uint32_t *)c->seg_count.ptr, c->stream, &launches));
+                return XYZ_OK;
+            };
             CU(launch_seg_reset((uint32_t *)c->seg_count.ptr, c->stream, &launches));
-            for (int64_t g0 = l0; g0 < l1; g0 += pl.R) {
+            int64_t since_flush = 0;
+            for (int64_t g0 = l0; g0 < l1 && !redo; g0 += pl.R) {
                 const int64_t Rc = (l1 - g0) < pl.R ? (l1 - g0) : pl.R;
                 ++chunks;
                 CU(cudaMemsetAsync(ctr_u32(c), 0, 8, c->stream));   // buckets, members
                 tm.begin(ST_KEYS);
                 CU(launch_filter(c->pk, ybs, B, M, seed, g0, (int)Rc, pl.NB, pl.BB, rbits, g0 - l0,
-                                 grid, (uint32_t)(c->mem_cap < 0xFFFFFFFFLL ? c->mem_cap : 0xFFFFFFFFLL),
+                                 grid, (uint32_t)(c->mem_cap < 0xFFFFFFFELL ? c->mem_cap : 0xFFFFFFFELL),
                                  (uint32_t)mb, (uint32_t *)c->kc_scratch.ptr,
                                  (uint64_t *)c->seg_keys.ptr, (uint32_t *)c->seg_vals.ptr,
                                  (uint32_t *)c->seg_count.ptr, (uint32_t)c->seg_cap, ctr_sovf(c),
@@ -441,58 +507,18 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches,
                                  B > 1 ? ybs : nullptr, ctr_sovf(c)));
                 tm.end();
-            }
-            // runs with too many survivors for the chip, all groups at once
-            tm.begin(ST_KEYS);
-            CU(launch_compact((const uint64_t *)c->seg_keys.ptr, (const uint32_t *)c->seg_vals.ptr,
-                              (const uint32_t *)c->seg_count.ptr, (uint32_t)c->seg_cap, grid,
-                              (uint64_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr, ctr_nsurv(c),
-                              c->stream, &launches));
-            tm.end();
-            uint32_t ns = 0;
-            int sovf = 0;
-            CU(cudaMemcpyAsync(&ns, ctr_nsurv(c), 4, cudaMemcpyDeviceToHost, c->stream));
-            CU(cudaMemcpyAsync(&sovf, ctr_sovf(c), 4, cudaMemcpyDeviceToHost, c->stream));
-            CU(cudaStreamSynchronize(c->stream));
-            if (sovf & 1) {
-                c->seg_cap *= 2;               // a spill segment overflowed
-                redo = true;
-            }
-            if (sovf & 2) {
-                c->mem_cap *= 2;               // the on-chip groups' members did
-                redo = true;
+                if (c->spill_flush && ++since_flush == c->spill_flush && g0 + pl.R < l1) {
+                    since_flush = 0;
+                    if ((rc = flush_spills()))
+                        return rc;
+                }
             }
             if (redo)
                 continue;
-            const int sbits = bbits + rbits + M;
-            key_bits_max = sbits;
-            if (ns > 0) {
-                surv_total = ns;
-                const int64_t sb = c->surv_cap / 2 + 1;
-                bool alt = false;
-                tm.begin(ST_SORT);
-                CU(radix_sort64((uint64_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr,
-                                (uint64_t *)c->keysB.ptr, (uint32_t *)c->valsB.ptr, (int64_t)ns, sbits,
-                                c->radix_tmp.ptr, &alt, c->stream, &launches));
-                tm.end();
-                const uint64_t *ks = (const uint64_t *)(alt ? c->keysB.ptr : c->keysA.ptr);
-                const uint32_t *vs = (const uint32_t *)(alt ? c->valsB.ptr : c->valsA.ptr);
-                tm.begin(ST_JOIN);
-                CU(launch_join64(ks, (int64_t)ns, M, bbits + rbits, (const uint8_t *)c->cnz.ptr,
-                                 (Bucket *)c->buckets2.ptr, (uint64_t *)c->pair_counts2.ptr,
-                                 ctr_nbuckets2(c), c->stream, &launches, rbits));
-                CU(scan_u64_dev((const uint64_t *)c->pair_counts2.ptr, (uint64_t *)c->pair_off2.ptr,
-                                ctr_nbuckets2(c), sb, ctr_total2(c), ctr_cand(c), c->scan_tmp2.ptr,
-                                c->stream, &launches));
-                tm.end();
-                tm.begin(ST_VERIFY);
-                CU(launch_verify(c->pk, (const Bucket *)c->buckets2.ptr,
-                                 (const uint64_t *)c->pair_off2.ptr, ctr_nbuckets2(c), ctr_total2(c), vs,
-                                 amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
-                                 (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
-                                 c->stream, &launches, B > 1 ? ybs : nullptr));
-                tm.end();
-            }
+            if ((rc = flush_spills()))
+                return rc;
+            if (redo)
+                continue;
         } else {
             for (int64_t g0 = l0; g0 < l1; g0 += pl.R) {
                 const int64_t Rc = (l1 - g0) < pl.R ? (l1 - g0) : pl.R;
@@ -713,7 +739,7 @@ void destroy_ctx(xyz_ctx *c)
                      &c->rec_agree_alt, &c->flags, &c->pos,       &c->out,      &c->dedup_tmp,
                      &c->raw,     &c->ents,        &c->seg,       &c->members,  &c->kc_scratch,
                      &c->seg_keys, &c->seg_vals,   &c->seg_count, &c->buckets2, &c->pair_counts2,
-                     &c->pair_off2, &c->scan_tmp2, &c->resp,   &c->ybs};
+                     &c->pair_off2, &c->scan_tmp2, &c->resp,   &c->ybs, &c->y_alt, &c->y_stage};
     for (DevBuf *b : all)
         release(*b);
     if (c->own_stream && c->stream)
@@ -806,27 +832,22 @@ int xyz_set_y_dev(xyz_ctx *ctx, const int8_t *dY)
         return rc;
     if (!dY)
         return fail(XYZ_EINVAL, "null pointer argument");
-    // pack into a scratch copy first so a bad Y leaves the context unchanged
-    uint32_t *old = ctx->pk.yb;
-    uint32_t *fresh = nullptr;
-    if (cudaMalloc(&fresh, (size_t)ctx->pk.Wp * 4) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(XYZ_ENOMEM, "cudaMalloc of response bits failed");
-    }
+    // pack into a second buffer first so a bad Y leaves the context unchanged
+    const size_t bytes = (size_t)ctx->pk.Wp * 4;
+    if ((rc = ensure(ctx->y_alt, bytes)))
+        return rc;
     Packed tmp = ctx->pk;
-    tmp.yb = fresh;
+    tmp.yb = (uint32_t *)ctx->y_alt.ptr;
     int64_t launches = 0;
     CU(cudaMemsetAsync(ctx->d_bad, 0, 16, ctx->stream));
     CU(launch_pack_y(dY, tmp, ctx->d_bad, ctx->stream, &launches));
     int bad = 0;
     CU(cudaMemcpyAsync(&bad, ctx->d_bad, 4, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    if (bad) {
-        cudaFree(fresh);
+    if (bad)
         return fail(XYZ_EINVAL, "entries of Y must be -1 or +1");
-    }
-    ctx->pk.yb = fresh;
-    cudaFree(old);
+    CU(cudaMemcpyAsync(ctx->pk.yb, ctx->y_alt.ptr, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
     return XYZ_OK;
 }
 
@@ -837,19 +858,10 @@ int xyz_set_y(xyz_ctx *ctx, const int8_t *Y)
         return rc;
     if (!Y)
         return fail(XYZ_EINVAL, "null pointer argument");
-    int8_t *dY = nullptr;
-    if (cudaMalloc(&dY, (size_t)ctx->pk.n) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(XYZ_ENOMEM, "cudaMalloc of Y staging failed");
-    }
-    cudaError_t e = cudaMemcpy(dY, Y, (size_t)ctx->pk.n, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        cudaFree(dY);
-        return fail(XYZ_ECUDA, std::string("cudaMemcpy of Y: ") + cudaGetErrorString(e));
-    }
-    rc = xyz_set_y_dev(ctx, dY);
-    cudaFree(dY);
-    return rc;
+    if ((rc = ensure(ctx->y_stage, (size_t)ctx->pk.n)))
+        return rc;
+    CU(cudaMemcpyAsync(ctx->y_stage.ptr, Y, (size_t)ctx->pk.n, cudaMemcpyHostToDevice, ctx->stream));
+    return xyz_set_y_dev(ctx, (const int8_t *)ctx->y_stage.ptr);
 }
 
 void xyz_destroy(xyz_ctx *ctx) { destroy_ctx(ctx); }
@@ -1091,6 +1103,14 @@ int xyz_set_filter(xyz_ctx *ctx, int enable)
     return XYZ_OK;
 }
 
+int xyz_set_spill_flush(xyz_ctx *ctx, int64_t groups)
+{
+    if (!ctx || groups < 0)
+        return fail(XYZ_EINVAL, "need a context and groups >= 0");
+    ctx->spill_flush = groups;
+    return XYZ_OK;
+}
+
 int xyz_run_keys(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, uint64_t *kx, uint64_t *c)
 {
     int rc = check_ctx(ctx);
@@ -1248,29 +1268,21 @@ void view_target(xyz_ctx *view, const xyz_ctx *base, uint32_t *yb)
 int64_t ctx_device_bytes(const xyz_ctx *c) { return (c->owns_packed ? c->packed_bytes : 0) + ws_bytes(c); }
 
 // Pack a host response into yb_dev (Wp words) on c's stream; -1/+1 only.
+// Uses c's staging buffer: calls on one context must not overlap.
 int pack_response(xyz_ctx *c, const int8_t *Y, uint32_t *yb_dev)
 {
-    int8_t *dY = nullptr;
-    if (cudaMalloc(&dY, (size_t)c->pk.n) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(XYZ_ENOMEM, "cudaMalloc of response staging failed");
-    }
+    int rc = ensure(c->y_stage, (size_t)c->pk.n);
+    if (rc)
+        return rc;
     int64_t launches = 0;
     Packed tmp = c->pk;
     tmp.yb = yb_dev;
     int bad = 0;
-    cudaError_t e = cudaMemcpyAsync(dY, Y, (size_t)c->pk.n, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(c->d_bad, 0, 16, c->stream);
-    if (e == cudaSuccess)
-        e = launch_pack_y(dY, tmp, c->d_bad, c->stream, &launches);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&bad, c->d_bad, 4, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(c->stream);
-    cudaFree(dY);
-    if (e != cudaSuccess)
-        return fail(XYZ_ECUDA, std::string("packing a response: ") + cudaGetErrorString(e));
+    CU(cudaMemcpyAsync(c->y_stage.ptr, Y, (size_t)c->pk.n, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->d_bad, 0, 16, c->stream));
+    CU(launch_pack_y((const int8_t *)c->y_stage.ptr, tmp, c->d_bad, c->stream, &launches));
+    CU(cudaMemcpyAsync(&bad, c->d_bad, 4, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
     if (bad)
         return fail(XYZ_EINVAL, "entries of Y must be -1 or +1");
     return XYZ_OK;

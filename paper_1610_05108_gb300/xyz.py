@@ -76,6 +76,7 @@ SIGNATURES = {
     "xyz_set_timing": (ctypes.c_int, [_p, ctypes.c_int]),
     "xyz_set_chunk_entries": (ctypes.c_int, [_p, _i64]),
     "xyz_set_filter": (ctypes.c_int, [_p, ctypes.c_int]),
+    "xyz_set_spill_flush": (ctypes.c_int, [_p, _i64]),
     "xyz_run_keys": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _p]),
     "xyz_run_candidates": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _p]),
     "xyz_agree": (ctypes.c_int, [_p, _p, _p, _i64, _p]),
@@ -267,6 +268,9 @@ class Context:
 
     def set_filter(self, on: bool):
         _check(load().xyz_set_filter(self.handle, 1 if on else 0))
+
+    def set_spill_flush(self, groups: int):
+        _check(load().xyz_set_spill_flush(self.handle, int(groups)))
 
     def info(self) -> dict:
         n, p, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

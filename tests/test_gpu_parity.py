@@ -193,6 +193,25 @@ def test_search_mixing_spilled_and_on_chip_runs(xyz, orc):
     assert np.array_equal(got, orc.xyz(X, Y, 12, 4, 0.9, 5))
 
 
+def test_spill_flush_windows_do_not_change_results(xyz, orc):
+    # spilled runs grouped through the sort once per search, after every
+    # launch group, and after every third one: one result
+    X, Y = _rand(120, 6500, 19)
+    Y[:] = 1
+    Y[:6] = -1
+    want = orc.xyz(X, Y, 12, 4, 0.9, 5)
+    with xyz.create(X, Y) as ctx:
+        ctx.set_chunk_entries(6500 // 8)          # one run per launch group
+        for flush in (0, 1, 3):
+            ctx.set_spill_flush(flush)
+            got = _pairs_array(ctx.search(12, 4, 0.9, 5))
+            st = ctx.stats()
+            assert st["chunks"] == 12 and st["survivors"] > 0, flush
+            assert np.array_equal(got, want), flush
+        with pytest.raises(xyz.XyzError):
+            ctx.set_spill_flush(-1)
+
+
 def test_search_range_union(xyz):
     X, Y = _rand(150, 1200, 12)
     Y = (X[:, 7] * X[:, 8]).astype(np.int8)
