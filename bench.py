@@ -27,7 +27,7 @@ give identical results.  --pattern serve: a Poisson stream (200 requests/s) of
 searches with L in [20, 200] and kappa in [0.2, 0.6] over resident SNP-shaped
 datasets of log-uniform n in [500, 8000] and p in [1e4, 5e5], each request
 with its own response (one planted pair of gamma in {0.7, 0.8, 0.9}) and M
-from the gamma0 = 0.55 rule of Section 6; reports p50/p99 latency and
+from the gamma0 = 0.55 rule of Section 5.2; reports p50/p99 latency and
 throughput of the server against the same requests run one after another.
 """
 from __future__ import annotations
@@ -166,14 +166,15 @@ def load_traffic():
 
 
 # Work per unit of each stage (one run = p columns), stated in the design doc:
-#   keys (survivor filter, ALU-bound): 30 integer operations per column and
+#   keys (survivor filter, ALU-bound): 28 integer operations per column and
 #       run -- 12.5 for the 32 x 32 bit transpose that forms the M-bit keys
-#       (400 ops per 32 columns), 3 for the canonical group value, 6 to
-#       insert it into the blocked Bloom filter, 8 to test the other side.
+#       (400 ops per 32 columns), 6 to insert kx into the blocked Bloom
+#       filter (hash, word, two bits, OR), 9.5 to test kx ^ c (xor, hash,
+#       word, bits, load, compare, keep bit).
 #   sort (HBM): one read + one write of each 8-byte entry that reaches it.
 #   join (HBM): one read of each 4-byte sorted key.
 #   verify (HBM/L2): 2 columns of 4W bytes per candidate.
-FILTER_OPS_PER_COLUMN = 30
+FILTER_OPS_PER_COLUMN = 28
 INT32_LANES_PER_SM = 128
 
 
@@ -604,8 +605,8 @@ def main(argv=None):
     ap.add_argument("--serve-datasets", type=int, default=6)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-workers", type=int, default=4)
-    ap.add_argument("--serve-slice", type=int, default=32)
+    ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--serve-slice", type=int, default=128)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gb300":
         log("[bench] warm-up raised to 3 steps")

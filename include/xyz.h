@@ -266,7 +266,7 @@ int xyz_run_candidates_noalloc(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t r
 /* ------------------------------------------------------------- server */
 
 /* A search server: the search as a request loop.  The paper screens one X
- * against several responses (the scaling experiment of Section 6 builds
+ * against several responses (the scaling experiment of Section 5.2 builds
  * responses of strength 0.7, 0.8 and 0.9 for each X); here each such search
  * is a request.  Datasets (packed X and a
  * default response) stay resident on the device; requests carry their own

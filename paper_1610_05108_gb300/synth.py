@@ -278,7 +278,7 @@ def single_pair_responses(X: np.ndarray, f: np.ndarray, count: int, seed: int,
                           gammas=(0.7, 0.8, 0.9), block: int = 20):
     """``count`` balanced responses for one X, each with one planted pair
     whose interaction strength gamma = a/n is drawn from ``gammas`` (the
-    scaling experiment of Section 6 plants one pair of gamma in {0.7, 0.8,
+    scaling experiment of Section 5.2 plants one pair of gamma in {0.7, 0.8,
     0.9}).
 
     Returns (Ys (count, n) int8, pairs [(j, k)], realised [Y^T(X_j o X_k)/n])."""
