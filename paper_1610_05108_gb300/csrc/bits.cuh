@@ -28,8 +28,27 @@ XYZ_HD void transpose32(uint32_t (&A)[32])
             A[k + (J)] ^= t;                                           \
         }                                                              \
     }
+#ifdef __CUDA_ARCH__
+    // rounds 16 and 8 move whole half-words and bytes: one byte permutation
+    // per output word instead of the shift/xor/mask sequence (same result)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const uint32_t a = A[k], b = A[k + 16];
+        A[k] = __byte_perm(a, b, 0x5410);        // low halves of a, b
+        A[k + 16] = __byte_perm(a, b, 0x7632);   // high halves of a, b
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        if ((k & 8) == 0) {
+            const uint32_t a = A[k], b = A[k + 8];
+            A[k] = __byte_perm(a, b, 0x6240);        // even bytes of a, b interleaved
+            A[k + 8] = __byte_perm(a, b, 0x7351);    // odd bytes
+        }
+    }
+#else
     XYZ_TR_ROUND(16, 0x0000FFFFu)
     XYZ_TR_ROUND(8, 0x00FF00FFu)
+#endif
     XYZ_TR_ROUND(4, 0x0F0F0F0Fu)
     XYZ_TR_ROUND(2, 0x33333333u)
     XYZ_TR_ROUND(1, 0x55555555u)

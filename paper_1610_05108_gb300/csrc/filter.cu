@@ -78,14 +78,13 @@ __device__ __forceinline__ int64_t draw_row(uint64_t seed, uint64_t t, int64_t n
     return (int64_t)__umul64hi(u, (uint64_t)n);
 }
 
-// Blocked Bloom filter of 2^LOGW words: a key selects one 32-bit word and
+// Blocked Bloom filter of 2^k words: a key selects one 32-bit word and
 // two bits inside it, all from multiplicative hashes (Knuth's method with
 // two odd constants, top bits).  Setting is one shared atomic OR, testing
 // one shared load.
-template <int LOGW>
-__device__ __forceinline__ void bloom_pos(uint32_t h, uint32_t &word, uint32_t &mask)
+__device__ __forceinline__ void bloom_pos(uint32_t h, int shift, uint32_t &word, uint32_t &mask)
 {
-    word = (h * 0x9E3779B1u) >> (32 - LOGW);
+    word = (h * 0x9E3779B1u) >> shift;          // shift = 32 - log2(filter words)
     const uint32_t y = h * 0x7FEB352Du + 0x165667B1u;
     mask = (1u << (y >> 27)) | (1u << ((y >> 22) & 31u));
 }
@@ -150,12 +149,21 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     __shared__ uint32_t ns;             // survivors of the current (run, response)
     __shared__ uint32_t scur;           // survivor array fill after refinement
     __shared__ uint32_t wsum[FL_THREADS / 32];
+    const int T = (int)blockDim.x;      // a multiple of 32, at most FL_THREADS
+    const int nwarps = T >> 5;
     __shared__ uint32_t mbase_sh, bbase_sh;
     uint32_t *kcs = kc_scratch + (int64_t)blockIdx.x * 32 * P;
     SegKey *okeys = reinterpret_cast<SegKey *>(seg_keys_v) + (int64_t)blockIdx.x * seg_cap;
     uint32_t *ovals = seg_vals + (int64_t)blockIdx.x * seg_cap;
     const uint32_t P32 = (uint32_t)P, p32 = (uint32_t)p;
-    const uint32_t steps = (P32 + FL_THREADS - 1) / FL_THREADS;
+    const uint32_t steps = (P32 + T - 1) / T;
+    // filter F: about 16 bits per column (2^20 at most), so the load, and
+    // with it the false-positive rate, does not depend on p
+    int flog = 10;
+    while (flog < FL_LOGF && ((int64_t)1 << flog) < 16 * p)
+        ++flog;
+    const int fwords = 1 << (flog - 5);
+    const int fshift = 32 - (flog - 5);
     if (t == 0)
         cursor = seg_count[blockIdx.x];     // segments fill across launch groups
 
@@ -166,7 +174,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         const int b0 = (item - r * NB) * BB;
         const int b1 = (b0 + BB < B) ? b0 + BB : B;
         const uint64_t rl = (uint64_t)(rbase + r);   // run index within the search
-        for (int i = t; i < FL_FWORDS; i += FL_THREADS)
+        for (int i = t; i < fwords; i += T)
             F[i] = 0;
         if (wp == 0) {
             int64_t s = 0;
@@ -189,7 +197,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         // MB are zero at compile time.
         {
             const bool need = BATCH || c_sh != 0;    // c == 0 keeps every column
-            for (uint32_t w = t; w < P32; w += FL_THREADS) {
+            for (uint32_t w = t; w < P32; w += T) {
                 uint32_t A[32];
 #pragma unroll
                 for (int m = 0; m < 32; ++m)
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                     for (int cc = 0; cc < 32; ++cc) {
                         if ((uint32_t)cc < ncol) {
                             uint32_t word, mask;
-                            bloom_pos<FL_LOGF - 5>(A[cc], word, mask);
+                            bloom_pos(A[cc], fshift, word, mask);
                             atomicOr(F + word, mask);
                         }
                     }
@@ -238,7 +246,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             // pass 2: test every column; keep bits of column word w to
             // kmask[w], and the survivors, while they fit, to the shared array
             for (uint32_t st = 0; st < steps; ++st) {
-                const uint32_t w = st * FL_THREADS + t;
+                const uint32_t w = st * T + t;
                 uint32_t keep = 0;     // bit cc: column 32w + cc survives
                 if (w < P32) {
                     const uint32_t valid = (32 * w + 32 <= p32) ? 0xFFFFFFFFu
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
 #pragma unroll
                         for (int cc = 0; cc < 32; ++cc) {
                             uint32_t word, mask;
-                            bloom_pos<FL_LOGF - 5>(kcs[cc * P32 + w] ^ c, word, mask);
+                            bloom_pos(kcs[cc * P32 + w] ^ c, fshift, word, mask);
                             keep |= ((F[word] & mask) == mask ? 1u : 0u) << cc;
                         }
                         keep &= valid;
@@ -288,32 +296,32 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 // survivor array's memory) with new hashes, tested again
                 for (int round = 1; nz && round <= FL_ROUNDS; ++round) {
                     __syncthreads();                   // every thread has read ns
-                    for (int i = t; i < FL_RWORDS; i += FL_THREADS)
+                    for (int i = t; i < FL_RWORDS; i += T)
                         rf[i] = 0;
                     if (t == 0)
                         ns = 0;
                     __syncthreads();
                     const uint32_t salt = 0x9E3779B9u * (uint32_t)round;
-                    for (uint32_t w = t; w < P32; w += FL_THREADS) {
+                    for (uint32_t w = t; w < P32; w += T) {
                         uint32_t keep = kmask[w];
                         while (keep) {
                             const int cc = __ffs(keep) - 1;
                             keep &= keep - 1;
                             uint32_t word, mask;
-                            bloom_pos<FL_LOGR>(mix32(kcs[cc * P32 + w] ^ salt), word, mask);
+                            bloom_pos(mix32(kcs[cc * P32 + w] ^ salt), 32 - FL_LOGR, word, mask);
                             atomicOr(rf + word, mask);
                         }
                     }
                     __syncthreads();
                     for (uint32_t st = 0; st < steps; ++st) {
-                        const uint32_t w = st * FL_THREADS + t;
+                        const uint32_t w = st * T + t;
                         uint32_t keep = w < P32 ? kmask[w] : 0u;
                         uint32_t left = keep;
                         while (left) {
                             const int cc = __ffs(left) - 1;
                             left &= left - 1;
                             uint32_t word, mask;
-                            bloom_pos<FL_LOGR>(mix32((kcs[cc * P32 + w] ^ c) ^ salt), word, mask);
+                            bloom_pos(mix32((kcs[cc * P32 + w] ^ c) ^ salt), 32 - FL_LOGR, word, mask);
                             if ((rf[word] & mask) != mask)
                                 keep &= ~(1u << cc);
                         }
@@ -337,7 +345,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                     scur = 0;
                 __syncthreads();
                 for (uint32_t st = 0; st < steps; ++st) {
-                    const uint32_t w = st * FL_THREADS + t;
+                    const uint32_t w = st * T + t;
                     uint32_t keep = w < P32 ? kmask[w] : 0u;
                     const uint32_t cnt = __popc(keep);
                     uint32_t incl = cnt;
@@ -377,24 +385,29 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
 
             // grouping on chip in the table (the keep mask and, for one
             // response, the filter are dead)
-            for (int i = t; i < FL_T; i += FL_THREADS) {
+            // table of 2^tlog slots, at least twice the survivors
+            int tlog = 8;
+            while (tlog < FL_LOGT && (1u << tlog) < 2 * s)
+                ++tlog;
+            const int tsize = 1 << tlog;
+            for (int i = t; i < tsize; i += T) {
                 tkey[i] = FL_EMPTY;
                 tcnt[i] = 0;
             }
             __syncthreads();
             // phase I: insert group keys, count sides (A high half, B low
             // half); keep (side, slot, j)
-            for (uint32_t i = t; i < s; i += FL_THREADS) {
+            for (uint32_t i = t; i < s; i += T) {
                 const uint64_t e = sv[i];
                 const uint32_t Kc = (uint32_t)(e >> 32);
                 const uint32_t g = nz ? (Kc >> 1) : Kc;
                 const uint32_t side = nz ? (Kc & 1u) : 0u;
-                uint32_t slot = (g * 0x9E3779B1u) >> (32 - FL_LOGT);
-                for (int probe = 0; probe < FL_T; ++probe) {     // s < FL_T: always ends
+                uint32_t slot = (g * 0x9E3779B1u) >> (32 - tlog);
+                for (int probe = 0; probe < tsize; ++probe) {    // s < tsize: always ends
                     const uint32_t old = atomicCAS(&tkey[slot], FL_EMPTY, g);
                     if (old == FL_EMPTY || old == g)
                         break;
-                    slot = (slot + 1) & (FL_T - 1);
+                    slot = (slot + 1) & (tsize - 1);
                 }
                 atomicAdd(&tcnt[slot], side ? 1u : 0x10000u);
                 sv[i] = ((uint64_t)((side << 31) | slot) << 32) | (uint32_t)e;
@@ -405,22 +418,21 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             // tkey / tcnt of a bucket's slot are the end cursors of its sides
             // A / B, and tcnt is FL_EMPTY for a slot without a bucket.
             {
-                constexpr int PER = FL_T / FL_THREADS;
-                uint32_t packed[PER];          // members << 16 | buckets of each slot
+                // each thread owns a contiguous range of slots; the value of
+                // a slot is members << 16 | 1 when its group yields a bucket
+                const int per = (tsize + T - 1) / T;
+                const int s0 = t * per < tsize ? t * per : tsize;
+                const int s1 = s0 + per < tsize ? s0 + per : tsize;
+                auto slot_value = [&](int slot) -> uint32_t {
+                    if (tkey[slot] == FL_EMPTY)
+                        return 0u;
+                    const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
+                    const bool ok = nz ? (nA > 0 && nB > 0) : (nA > 1);
+                    return ok ? ((nA + nB) << 16) | 1u : 0u;
+                };
                 uint32_t mysum = 0;
-#pragma unroll
-                for (int q = 0; q < PER; ++q) {
-                    const int slot = t * PER + q;
-                    uint32_t v = 0;
-                    if (tkey[slot] != FL_EMPTY) {
-                        const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
-                        const bool ok = nz ? (nA > 0 && nB > 0) : (nA > 1);
-                        if (ok)
-                            v = ((nA + nB) << 16) | 1u;
-                    }
-                    packed[q] = v;
-                    mysum += v;
-                }
+                for (int slot = s0; slot < s1; ++slot)
+                    mysum += slot_value(slot);
                 uint32_t incl = mysum;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -432,7 +444,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                     wsum[wp] = incl;
                 __syncthreads();
                 uint32_t before = 0, total = 0;
-                for (int i = 0; i < FL_THREADS / 32; ++i) {
+                for (int i = 0; i < nwarps; ++i) {
                     before += (i < wp) ? wsum[i] : 0u;
                     total += wsum[i];
                 }
@@ -449,10 +461,8 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 if (mbase_sh == 0xFFFFFFFFu)
                     continue;
                 uint32_t run_off = before + incl - mysum;
-#pragma unroll
-                for (int q = 0; q < PER; ++q) {
-                    const int slot = t * PER + q;
-                    const uint32_t v = packed[q];
+                for (int slot = s0; slot < s1; ++slot) {
+                    const uint32_t v = slot_value(slot);
                     if (v) {
                         const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
                         const uint32_t base = mbase_sh + (run_off >> 16);
@@ -469,7 +479,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             }
             __syncthreads();
             // phase III: members, side A first
-            for (uint32_t i = t; i < s; i += FL_THREADS) {
+            for (uint32_t i = t; i < s; i += T) {
                 const uint64_t e = sv[i];
                 const uint32_t hi = (uint32_t)(e >> 32);
                 const uint32_t slot = hi & 0x7FFFFFFFu;
@@ -535,6 +545,24 @@ size_t filter_smem_bytes(bool batch)
 
 int64_t filter_run_cap() { return FlLayout<false>::SMAX; }
 
+// Threads per filter CTA: the passes give each thread whole 32-column words,
+// so a multiple of 32 between 640 and 1024 that wastes the fewest thread
+// slots in the last round over the P words (the largest among near ties).
+int filter_threads(int64_t P)
+{
+    int best = FL_THREADS;
+    double best_eff = 0.0;
+    for (int T = FL_THREADS; T >= 640; T -= 32) {
+        const int64_t rounds = (P + T - 1) / T;
+        const double eff = (double)P / (double)(rounds * T);
+        if (eff > best_eff + 0.01) {
+            best_eff = eff;
+            best = T;
+        }
+    }
+    return best;
+}
+
 int filter_grid()
 {
     int dev = 0, sms = 0;
@@ -586,7 +614,7 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    kern<<<grid, FL_THREADS, smem, s>>>(pk.Xr, pk.Pp, pk.P, ybs, pk.Wp, B, pk.n, pk.p, M, seed, l0, R,
+    kern<<<grid, filter_threads(pk.P), smem, s>>>(pk.Xr, pk.Pp, pk.P, ybs, pk.Wp, B, pk.n, pk.p, M, seed, l0, R,
                                         NB, BB, rbits, rbase, mcap, bcap, kc_scratch, seg_keys, seg_vals,
                                         seg_count, seg_cap, overflow, cnz, members, members_count,
                                         buckets, pair_counts, nbuckets);
