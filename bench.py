@@ -23,7 +23,9 @@ sample of the same workload and scales it to one search.
 responses, each with 3 planted pairs, kappa = 0.4, M by eq. bestM and L for
 95% recall of the weakest target, screened once by the batched search (one
 call, shared row stream and keys) and once as 256 plain searches; both must
-give identical results.  --pattern serve: a Poisson stream (200 requests/s) of
+give identical results.  --pattern scaling: Section 5.2's experiment (time to discover one planted
+pair of gamma in {0.7, 0.8, 0.9} against p, M from gamma0 = 0.55) with the
+exhaustive GPU screen beside it.  --pattern serve: a Poisson stream (200 requests/s) of
 searches with L in [20, 200] and kappa in [0.2, 0.6] over resident SNP-shaped
 datasets of log-uniform n in [500, 8000] and p in [1e4, 5e5], each request
 with its own response (one planted pair of gamma in {0.7, 0.8, 0.9}) and M
@@ -588,6 +590,79 @@ def serve_arm(args):
     print(json.dumps(out), flush=True)
 
 
+# -------------------------------------------------------- scaling pattern
+
+def scaling_arm(args):
+    """Section 5.2: time for xyz to discover the one strong pair (0, 1) of
+    strength gamma in {0.7, 0.8, 0.9} on i.i.d. +-1 data, against p, with M
+    from gamma0 = p^(-1/M) ~ 0.55; the exhaustive GPU screen timed beside it.
+    Theory (Theorem on minimal subsampling): time ~ n p^(1 + log gamma / log
+    gamma0)."""
+    import torch
+    from paper_1610_05108_gb300 import build as _build
+    from paper_1610_05108_gb300 import xyz
+    _build.build()
+    xyz.load()
+    n = args.scaling_n
+    ps = [int(v) for v in args.scaling_p.split(",")]
+    gammas = (0.7, 0.8, 0.9)
+    reps = args.scaling_reps
+    rows = []
+    rng = np.random.default_rng(1610)
+    for p in ps:
+        X = np.asfortranarray((rng.integers(0, 2, size=(n, p), dtype=np.int8) * 2 - 1).astype(np.int8))
+        M = xyz.M_for_gamma0(p, 0.55)
+        for g in gammas:
+            Y = (X[:, 0] * X[:, 1]).astype(np.int8)
+            flips = rng.choice(n, size=int(round((1 - g) * n)), replace=False)
+            Y[flips] = -Y[flips]
+            a12 = int(np.sum(Y == X[:, 0] * X[:, 1]))
+            kappa = (2.0 * a12 - n) / n - 1e-9
+            with xyz.create(X, Y) as ctx:
+                expect = 1.0 / (a12 / n) ** M                  # mean runs to discovery
+                step = max(1, int(expect / 4))
+                ctx.search_range(0, step, M, kappa, 1)          # warm-up
+                times, runs = [], []
+                for r in range(reps):
+                    seed = 1000 + r
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    l0 = 0
+                    while True:
+                        res = ctx.search_range(l0, l0 + step, M, kappa, seed)
+                        l0 += step
+                        if any(int(j) == 0 and int(k) == 1 for j, k in zip(res["j"], res["k"])):
+                            break
+                        if l0 > 200 * expect:
+                            break
+                    times.append(time.perf_counter() - t0)
+                    runs.append(l0)
+                ctx.brute_force(kappa)                          # warm-up
+                t0 = time.perf_counter()
+                bf = ctx.brute_force(kappa)
+                t_bf = time.perf_counter() - t0
+            found_bf = [(int(j), int(k)) for j, k in zip(bf["j"], bf["k"])] == [(0, 1)]
+            rows.append({"p": p, "gamma": round(a12 / n, 4), "M": M, "runs_mean": float(np.mean(runs)),
+                         "runs_expected": round(expect, 1), "xyz_ms": round(1e3 * float(np.mean(times)), 3),
+                         "brute_ms": round(1e3 * t_bf, 3), "brute_found_only_pair": found_bf})
+            log(f"[bench] scaling p={p} gamma={g} M={M} xyz {rows[-1]['xyz_ms']} ms brute {rows[-1]['brute_ms']} ms")
+    fit = {}
+    for g in gammas:
+        rr = [r for r in rows if abs(r["gamma"] - g) < 0.01]
+        big = [r for r in rr if r["p"] >= 10000]
+        if len(big) >= 2:
+            slope = float(np.polyfit(np.log([r["p"] for r in big]), np.log([r["xyz_ms"] for r in big]), 1)[0])
+            fit[str(g)] = {"slope_p_ge_1e4": round(slope, 3),
+                           "theory": round(1 + np.log(g) / np.log(0.55), 3)}
+    out = {"metric": METRIC, "pattern": "scaling", "unit": "ms", "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": f"iid +-1 X, n={n}, one planted pair (0,1) of gamma in {{0.7,0.8,0.9}}, "
+                                  "M from gamma0=0.55, time to discovery (runs in slices of a quarter of "
+                                  "the expected count) vs the exhaustive GPU screen",
+                      "reps": reps},
+           "rows": rows, "fit": fit}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -600,13 +675,16 @@ def main(argv=None):
     ap.add_argument("--ref-runs", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--pattern", choices=["search", "batch", "serve"], default="search")
+    ap.add_argument("--pattern", choices=["search", "batch", "serve", "scaling"], default="search")
     ap.add_argument("--batch-responses", type=int, default=256)
     ap.add_argument("--serve-datasets", type=int, default=6)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-slice", type=int, default=128)
+    ap.add_argument("--scaling-n", type=int, default=1000)
+    ap.add_argument("--scaling-p", default="1000,3000,10000,30000,100000,250000")
+    ap.add_argument("--scaling-reps", type=int, default=5)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gb300":
         log("[bench] warm-up raised to 3 steps")
@@ -617,6 +695,8 @@ def main(argv=None):
         batch_arm(args)
     elif args.pattern == "serve":
         serve_arm(args)
+    elif args.pattern == "scaling":
+        scaling_arm(args)
     else:
         gpu_arm(args)
 

@@ -166,6 +166,13 @@ int xyz_search_batch(xyz_ctx *ctx, const int8_t *Ys, int32_t B, int32_t L, int32
 int xyz_search_batch_dev(xyz_ctx *ctx, const int8_t *dYs, int32_t B, int32_t L, int32_t M,
                          double kappa, uint64_t seed, xyz_pair **pairs, int64_t *offsets);
 
+/* Exhaustive screen: every pair j < k with (2a - n) >= kappa*n, i.e. I* of
+ * eq. 1 under the >= reading -- the comparator the search is measured
+ * against and the M = 0 case of Algorithm 2 (one empty key, every pair a
+ * candidate).  O(p^2 n / 32) word operations on the GPU (a tiled popcount
+ * over the packed columns); output as xyz_search. */
+int xyz_brute_force(xyz_ctx *ctx, double kappa, xyz_pair **pairs, int64_t *npairs);
+
 void xyz_free_pairs(xyz_pair *pairs);
 void xyz_free(void *ptr);
 

@@ -921,6 +921,84 @@ int xyz_search_range(xyz_ctx *ctx, int64_t l0, int64_t l1, int32_t M, double kap
     return XYZ_OK;
 }
 
+int xyz_brute_force(xyz_ctx *ctx, double kappa, xyz_pair **pairs, int64_t *npairs)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!pairs || !npairs)
+        return fail(XYZ_EINVAL, "null output pointer");
+    if ((rc = check_kappa(kappa)))
+        return rc;
+    xyz_ctx *c = ctx;
+    const int64_t amin = amin_rule(c->pk.n, kappa);
+    std::memset(&c->stats, 0, sizeof(c->stats));
+    *pairs = nullptr;
+    *npairs = 0;
+    if (amin > c->pk.n)
+        return XYZ_OK;
+    const int kbits = ceil_log2(c->pk.p) < 1 ? 1 : ceil_log2(c->pk.p);
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        if ((rc = ensure_records(c, 1)) || (rc = ensure(c->counters, 64)))
+            return rc;
+        int64_t launches = 0;
+        CU(cudaMemsetAsync(c->counters.ptr, 0, 64, c->stream));
+        CU(launch_brute(c->pk, amin, kbits, (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
+                        ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches));
+        uint32_t nrec = 0;
+        CU(cudaMemcpyAsync(&nrec, ctr_nrec(c), 4, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        if ((int64_t)nrec > c->rec_cap) {
+            int64_t want = c->rec_cap;
+            while (want < (int64_t)nrec)
+                want *= 2;
+            if (want > (int64_t)0xF0000000LL)
+                return fail(XYZ_ENOMEM, "too many passing pairs");
+            c->rec_cap = want;
+            continue;
+        }
+        uint32_t nout = 0;
+        if (nrec > 0) {
+            // order the passing pairs by (j, k)
+            bool alt = false;
+            char *dt = (char *)c->dedup_tmp.ptr;
+            size_t rt = radix_temp_bytes(c->rec_cap);
+            CU(radix_sort64((uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
+                            (uint64_t *)c->rec_keys_alt.ptr, (uint32_t *)c->rec_agree_alt.ptr, (int64_t)nrec,
+                            2 * kbits, dt, &alt, c->stream, &launches));
+            const uint64_t *rk = (const uint64_t *)(alt ? c->rec_keys_alt.ptr : c->rec_keys.ptr);
+            const uint32_t *ra = (const uint32_t *)(alt ? c->rec_agree_alt.ptr : c->rec_agree.ptr);
+            CU(launch_unique(rk, ra, ctr_nrec(c), c->rec_cap, kbits, c->pk.n, (uint32_t *)c->flags.ptr,
+                             (uint32_t *)c->pos.ptr, dt + rt, (PairOut *)c->out.ptr, ctr_nout(c), c->stream,
+                             &launches));
+            CU(cudaMemcpyAsync(&nout, ctr_nout(c), 4, cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+        }
+        xyz_pair *host = nullptr;
+        if (nout > 0) {
+            host = (xyz_pair *)std::malloc((size_t)nout * sizeof(xyz_pair));
+            if (!host)
+                return fail(XYZ_ENOMEM, "host allocation of results failed");
+            cudaError_t e = cudaMemcpyAsync(host, c->out.ptr, (size_t)nout * sizeof(xyz_pair),
+                                            cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) {
+                std::free(host);
+                return fail(XYZ_ECUDA, std::string("copy of results: ") + cudaGetErrorString(e));
+            }
+        }
+        c->stats.candidates = c->pk.p * (c->pk.p - 1) / 2;
+        c->stats.passing = nrec;
+        c->stats.unique_pairs = nout;
+        c->stats.gpu_launches = launches;
+        *pairs = host;
+        *npairs = nout;
+        return XYZ_OK;
+    }
+    return fail(XYZ_ENOMEM, "result buffers kept overflowing");
+}
+
 int xyz_search(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t seed, xyz_pair **pairs,
                int64_t *npairs)
 {

@@ -168,6 +168,13 @@ cudaError_t launch_compact(const uint64_t *seg_keys, const uint32_t *seg_vals,
 // Host-side helpers shared by the API files.
 int64_t amin_rule(int64_t n, double kappa);
 
+// Exhaustive screen (brute.cu): records (j << kbits | k, a) of every pair
+// j < k with a >= amin; blocks = brute_tiles(p).
+int64_t brute_tiles(int64_t p);
+cudaError_t launch_brute(const Packed &pk, int64_t amin, int kbits, uint64_t *rec_keys,
+                         uint32_t *rec_agree, uint32_t *nrec, uint32_t rec_cap, cudaStream_t s,
+                         int64_t *launches);
+
 }  // namespace xyz
 
 struct xyz_ctx;

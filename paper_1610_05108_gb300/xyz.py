@@ -70,6 +70,7 @@ SIGNATURES = {
     "xyz_search_range": (ctypes.c_int, [_p, _i64, _i64, _i32, _dbl, _u64, _p, _p]),
     "xyz_search_batch": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, _dbl, _u64, _p, _p]),
     "xyz_search_batch_dev": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, _dbl, _u64, _p, _p]),
+    "xyz_brute_force": (ctypes.c_int, [_p, _dbl, _p, _p]),
     "xyz_free_pairs": (None, [_p]),
     "xyz_free": (None, [_p]),
     "xyz_get_stats": (ctypes.c_int, [_p, _p]),
@@ -240,6 +241,13 @@ class Context:
         cnt = ctypes.c_int64(0)
         _check(load().xyz_search_range(self.handle, int(l0), int(l1), int(M), float(kappa),
                                        seed & (2**64 - 1), ctypes.byref(out), ctypes.byref(cnt)))
+        return _pairs_to_numpy(out, cnt.value)
+
+    def brute_force(self, kappa: float) -> np.ndarray:
+        """Every pair j < k with strength >= kappa (exhaustive GPU screen)."""
+        out = ctypes.c_void_p()
+        cnt = ctypes.c_int64(0)
+        _check(load().xyz_brute_force(self.handle, float(kappa), ctypes.byref(out), ctypes.byref(cnt)))
         return _pairs_to_numpy(out, cnt.value)
 
     def search_batch(self, Ys: np.ndarray, L: int, M: int, kappa: float, seed: int) -> list:
