@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
     ):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.run(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC],
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
             check=True,
         )
         os.replace(tmp, _LIB_PATH)
@@ -65,6 +65,12 @@ def _load():
         "orc_candidates": (_i64, [_p, _p, _i64, _i64, _i32, _u64, _i64, _p, _i64]),
         "orc_xyz_range": (_i64, [_p, _p, _i64, _i64, _i64, _i64, _i32, _dbl, _u64, _p, _i64]),
         "orc_xyz": (_i64, [_p, _p, _i64, _i64, _i32, _i32, _dbl, _u64, _p, _i64]),
+        "orc_quantize_y": (ctypes.c_int, [_p, _i64, _p, _p]),
+        "orc_draw_rows_weighted": (None, [_p, _i64, _u64, _i64, _i32, _p]),
+        "orc_weighted_agree": (_i64, [_p, _p, _p, _i64, _i64, _i64, _p]),
+        "orc_xyz_weighted_range": (_i64, [_p, _p, _i64, _i64, _i64, _i64, _i32, _dbl, _u64, _p, _p,
+                                          _i64]),
+        "orc_brute_force_weighted": (_i64, [_p, _p, _i64, _i64, _dbl, _p, _p, _i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -205,3 +211,75 @@ def xyz_range(X, Y, l0: int, l1: int, M: int, kappa: float, seed: int) -> np.nda
 def xyz(X, Y, L: int, M: int, kappa: float, seed: int) -> np.ndarray:
     """Algorithm 2 (final xyz): union over L runs of verified candidates."""
     return xyz_range(X, Y, 0, L, M, kappa, seed)
+
+
+# ------------------------------------------------------ continuous response
+# Section 3.1 with readings R9-R11 of xyz_oracle.c.
+
+
+def _check_x_real(X: np.ndarray, Y: np.ndarray):
+    X = np.asfortranarray(X, dtype=np.int8)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    n, p = X.shape
+    if Y.shape != (n,):
+        raise ValueError("Y must have shape (n,)")
+    if not _load().orc_check_pm1(_ptr(X), X.size):
+        raise ValueError("entries of X must be -1 or +1")
+    return X, Y, n, p
+
+
+def quantize_y(Y) -> tuple:
+    """Fixed-point weights q and signs of a real response (R9)."""
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    q = np.zeros(len(Y), dtype=np.int64)
+    sgn = np.zeros(len(Y), dtype=np.int8)
+    if _load().orc_quantize_y(_ptr(Y), len(Y), _ptr(q), _ptr(sgn)) != 0:
+        raise ValueError("Y must be finite and not all zero")
+    return q, sgn
+
+
+def draw_rows_weighted(q, seed: int, run: int, M: int) -> np.ndarray:
+    """Rows of one run drawn with probability q_i / sum q (R10)."""
+    q = np.ascontiguousarray(q, dtype=np.int64)
+    rows = np.zeros(max(M, 1), dtype=np.int64)
+    _load().orc_draw_rows_weighted(_ptr(q), len(q), seed & (2**64 - 1), run, M, _ptr(rows))
+    return rows[:M]
+
+
+def weighted_agree(X, Y, j: int, k: int) -> tuple:
+    """(count of sign-agreeing rows, their weight sum S_jk) under R9."""
+    X, Y, n, p = _check_x_real(X, Y)
+    q, sgn = quantize_y(Y)
+    S = ctypes.c_int64(0)
+    a = _load().orc_weighted_agree(_ptr(X), _ptr(sgn), _ptr(q), n, j, k, ctypes.byref(S))
+    return int(a), int(S.value)
+
+
+def _weighted_call(fn, X, Y, *args):
+    X, Y, n, p = _check_x_real(X, Y)
+    cap = 4096
+    while True:
+        out = np.zeros((cap, 3), dtype=np.int32)
+        ws = np.zeros(cap, dtype=np.int64)
+        cnt = fn(_ptr(X), _ptr(Y), n, p, *args, _ptr(out), _ptr(ws), cap)
+        if cnt < 0:
+            raise ValueError("Y must be finite and not all zero")
+        if cnt <= cap:
+            return out[:cnt], ws[:cnt]
+        cap = cnt
+
+
+def xyz_weighted_range(X, Y, l0: int, l1: int, M: int, kappa: float, seed: int) -> tuple:
+    """Algorithm 2 with the continuous-Y modifications of Section 3.1 over
+    runs [l0, l1): sorted (j, k, a) triples and their weight sums S."""
+    return _weighted_call(_load().orc_xyz_weighted_range, X, Y, l0, l1, M, float(kappa),
+                          seed & (2**64 - 1))
+
+
+def xyz_weighted(X, Y, L: int, M: int, kappa: float, seed: int) -> tuple:
+    return xyz_weighted_range(X, Y, 0, L, M, kappa, seed)
+
+
+def brute_force_weighted(X, Y, kappa: float) -> tuple:
+    """Every pair passing R11 by the naive loop over all pairs."""
+    return _weighted_call(_load().orc_brute_force_weighted, X, Y, float(kappa))

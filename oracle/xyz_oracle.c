@@ -43,6 +43,7 @@
  * outputs is a project convention; it is pinned only by agreement with the
  * CUDA path.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -362,14 +363,12 @@ static void orc_vec_push(orc_vec *vec, int32_t j, int32_t k, int32_t a)
 /* Candidate set E_l of run `run` (Algorithm 2 steps 3-4) as unordered pairs
  * j < k (reading R4), sorted, each once.  The ordered pairs (j, k) and (k, j)
  * of the equal-pairs walk name the same unordered pair. */
-static int64_t orc_run_candidates(const int8_t *X, const int8_t *Y, int64_t n,
-                                  int64_t p, int32_t M, uint64_t seed,
-                                  int64_t run, orc_vec *vec)
+static int64_t orc_rows_candidates(const int8_t *X, const int8_t *Y, int64_t n,
+                                   int64_t p, const int64_t *rows, int32_t M,
+                                   orc_vec *vec)
 {
-    int64_t *rows = (int64_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int64_t));
     uint64_t *x = (uint64_t *)malloc((size_t)p * sizeof(uint64_t));
     uint64_t *z = (uint64_t *)malloc((size_t)p * sizeof(uint64_t));
-    orc_draw_rows(seed, run, M, n, rows);
     orc_keys(X, Y, n, p, rows, M, x, z);
     int64_t ne = orc_equal_pairs(x, z, p, NULL, 0);
     int32_t *pairs = (int32_t *)malloc((size_t)(ne > 0 ? ne : 1) * 2 * sizeof(int32_t));
@@ -386,6 +385,16 @@ static int64_t orc_run_candidates(const int8_t *X, const int8_t *Y, int64_t n,
     free(pairs);
     free(z);
     free(x);
+    return added;
+}
+
+static int64_t orc_run_candidates(const int8_t *X, const int8_t *Y, int64_t n,
+                                  int64_t p, int32_t M, uint64_t seed,
+                                  int64_t run, orc_vec *vec)
+{
+    int64_t *rows = (int64_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int64_t));
+    orc_draw_rows(seed, run, M, n, rows);
+    int64_t added = orc_rows_candidates(X, Y, n, p, rows, M, vec);
     free(rows);
     return added;
 }
@@ -443,4 +452,171 @@ int64_t orc_xyz(const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
                 int32_t *out, int64_t cap)
 {
     return orc_xyz_range(X, Y, n, p, 0, L, M, kappa, seed, out, cap);
+}
+
+/* ------------------------------------------------- continuous response */
+
+/* Section 3.1, continuous Y with binary X.  Z_ij = sgn(Y_i) X_ij, the rows of
+ * a run are drawn i.i.d. with P(i) proportional to |Y_i|, and the strength of
+ * (j, k) is the weighted agreement sum_{i : sgn(Y_i) = X_ij X_ik} |Y_i| over
+ * ||Y||_1; in kappa form Y^T(X_j o X_k) / ||Y||_1 = 2 gamma~_jk - 1.
+ *
+ * Readings taken here:
+ *   R9   the weights are used in fixed point.  With m = max_i |Y_i| written
+ *        m = f 2^e, f in [0.5, 1), q_i = floor(|Y_i| 2^(24 - e) + 1/2), an
+ *        integer in [0, 2^24]; Q = sum_i q_i.  sgn(0) = +1 (such a row has
+ *        weight 0 and is never drawn).  The relative error of any weighted
+ *        sum is below 2^-24 max|Y| / mean|Y|.
+ *   R10  the weighted draw t of a search with seed s: u = splitmix64 output t
+ *        (R2), r = floor(u Q / 2^64), and the row is the least i with
+ *        q_0 + ... + q_i > r.  With equal weights this is the draw of R2.
+ *   R11  a candidate passes when (double)(2 S_jk - Q) >= kappa (double)Q,
+ *        S_jk = sum_{i : sgn(Y_i) = X_ij X_ik} q_i (one IEEE multiply, as R5).
+ */
+
+/* R9: fixed-point weights q and signs (+1 / -1) of a real response.  Returns
+ * 0, or -1 when an entry is not finite or every entry is 0. */
+int orc_quantize_y(const double *Y, int64_t n, int64_t *q, int8_t *sgn)
+{
+    double m = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        if (!isfinite(Y[i]))
+            return -1;
+        double a = fabs(Y[i]);
+        if (a > m)
+            m = a;
+    }
+    if (m == 0.0)
+        return -1;
+    int e = 0;
+    frexp(m, &e);
+    for (int64_t i = 0; i < n; i++) {
+        q[i] = (int64_t)floor(ldexp(fabs(Y[i]), 24 - e) + 0.5);
+        sgn[i] = Y[i] < 0.0 ? (int8_t)-1 : (int8_t)1;
+    }
+    return 0;
+}
+
+/* R10: the M rows of run `run`, drawn with probability q_i / Q. */
+void orc_draw_rows_weighted(const int64_t *q, int64_t n, uint64_t seed,
+                            int64_t run, int32_t M, int64_t *rows)
+{
+    uint64_t Q = 0;
+    for (int64_t i = 0; i < n; i++)
+        Q += (uint64_t)q[i];
+    for (int32_t m = 0; m < M; m++) {
+        uint64_t u = orc_splitmix64_at(seed, (uint64_t)run * (uint64_t)M + (uint64_t)m);
+        uint64_t r = (uint64_t)(((unsigned __int128)u * (unsigned __int128)Q) >> 64);
+        uint64_t c = 0;
+        int64_t row = n - 1;
+        for (int64_t i = 0; i < n; i++) {
+            c += (uint64_t)q[i];
+            if (c > r) {
+                row = i;
+                break;
+            }
+        }
+        rows[m] = row;
+    }
+}
+
+/* Weighted agreement of (j, k): returns the count of rows with
+ * sgn(Y_i) = X_ij X_ik and writes their weight sum S_jk. */
+int64_t orc_weighted_agree(const int8_t *X, const int8_t *sgn, const int64_t *q,
+                           int64_t n, int64_t j, int64_t k, int64_t *S)
+{
+    int64_t a = 0, w = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if ((int)X[j * n + i] * (int)X[k * n + i] == (int)sgn[i]) {
+            a++;
+            w += q[i];
+        }
+    }
+    *S = w;
+    return a;
+}
+
+/* Algorithm 2 with the modifications of Section 3.1 over runs [l0, l1):
+ * weighted rows (R10), keys of X and Z = sgn(Y) o X, candidates as in the
+ * binary search, kept by R11.  Writes up to `cap` triples (j, k, a) and
+ * their S to `wsum`, sorted by (j, k), each pair once; returns the count.
+ * -1 when Y is not usable (R9). */
+int64_t orc_xyz_weighted_range(const int8_t *X, const double *Y, int64_t n, int64_t p,
+                               int64_t l0, int64_t l1, int32_t M, double kappa,
+                               uint64_t seed, int32_t *out, int64_t *wsum, int64_t cap)
+{
+    int64_t *q = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int8_t *sgn = (int8_t *)malloc((size_t)n);
+    if (orc_quantize_y(Y, n, q, sgn) != 0) {
+        free(q);
+        free(sgn);
+        return -1;
+    }
+    int64_t Q = 0;
+    for (int64_t i = 0; i < n; i++)
+        Q += q[i];
+    int64_t *rows = (int64_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int64_t));
+    orc_vec found = {0, 0, 0};
+    orc_vec cand = {0, 0, 0};
+    for (int64_t l = l0; l < l1; l++) {
+        cand.n = 0;
+        orc_draw_rows_weighted(q, n, seed, l, M, rows);
+        int64_t ne = orc_rows_candidates(X, sgn, n, p, rows, M, &cand);
+        for (int64_t e = 0; e < ne; e++) {
+            int32_t j = cand.v[e].j, k = cand.v[e].k;
+            int64_t S = 0;
+            int64_t a = orc_weighted_agree(X, sgn, q, n, j, k, &S);
+            if ((double)(2 * S - Q) >= kappa * (double)Q)
+                orc_vec_push(&found, j, k, (int32_t)a);
+        }
+    }
+    int64_t u = orc_sort_unique(found.v, found.n);
+    for (int64_t i = 0; i < u && i < cap; i++) {
+        out[3 * i + 0] = found.v[i].j;
+        out[3 * i + 1] = found.v[i].k;
+        out[3 * i + 2] = found.v[i].a;
+        orc_weighted_agree(X, sgn, q, n, found.v[i].j, found.v[i].k, &wsum[i]);
+    }
+    free(found.v);
+    free(cand.v);
+    free(rows);
+    free(sgn);
+    free(q);
+    return u;
+}
+
+/* Every pair j < k passing R11, by looping over all pairs (the exhaustive
+ * screen with the weighted strength).  Output as orc_xyz_weighted_range. */
+int64_t orc_brute_force_weighted(const int8_t *X, const double *Y, int64_t n, int64_t p,
+                                 double kappa, int32_t *out, int64_t *wsum, int64_t cap)
+{
+    int64_t *q = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int8_t *sgn = (int8_t *)malloc((size_t)n);
+    if (orc_quantize_y(Y, n, q, sgn) != 0) {
+        free(q);
+        free(sgn);
+        return -1;
+    }
+    int64_t Q = 0;
+    for (int64_t i = 0; i < n; i++)
+        Q += q[i];
+    int64_t cnt = 0;
+    for (int64_t j = 0; j < p; j++) {
+        for (int64_t k = j + 1; k < p; k++) {
+            int64_t S = 0;
+            int64_t a = orc_weighted_agree(X, sgn, q, n, j, k, &S);
+            if ((double)(2 * S - Q) >= kappa * (double)Q) {
+                if (cnt < cap) {
+                    out[3 * cnt + 0] = (int32_t)j;
+                    out[3 * cnt + 1] = (int32_t)k;
+                    out[3 * cnt + 2] = (int32_t)a;
+                    wsum[cnt] = S;
+                }
+                cnt++;
+            }
+        }
+    }
+    free(sgn);
+    free(q);
+    return cnt;
 }
