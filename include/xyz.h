@@ -125,6 +125,23 @@ int xyz_set_y(xyz_ctx *ctx, const int8_t *Y);
 int xyz_set_y_dev(xyz_ctx *ctx, const int8_t *dY);
 
 /* Release a context and its device memory.  NULL is ignored. */
+/* Real-valued response (Section 3.1, continuous Y with binary X): the rows
+ * of a run are drawn with probability |Y_i| / ||Y||_1, Z = sgn(Y) o X
+ * (sgn(0) = +1), and a candidate passes when Y^T(X_j o X_k) >= kappa ||Y||_1,
+ * i.e. its |Y|-weighted agreement gamma~_jk >= (1 + kappa)/2.  The weights
+ * are used in fixed point, exactly on every step: with max|Y_i| = f 2^e
+ * (f in [0.5, 1)), q_i = floor(|Y_i| 2^(24-e) + 1/2) and Q = sum q_i; the
+ * weighted draw t is the least i with q_0 + ... + q_i > floor(u Q / 2^64),
+ * u the splitmix64 output t; a pair passes when (double)(2 S - Q) >=
+ * kappa * (double)Q with S the weight sum of the rows where
+ * sgn(Y_i) = X_ij X_ik.  Results report agree = the count of those rows and
+ * strength = (2 S - Q) / Q.  Y: n doubles, finite, not all zero (else
+ * XYZ_EINVAL, context unchanged).  The context stays in this mode until the
+ * next xyz_set_y(_dev).  Batched search and the exhaustive screen take
+ * binary responses only (XYZ_EINVAL in this mode). */
+int xyz_set_y_real(xyz_ctx *ctx, const double *Y);
+int xyz_set_y_real_dev(xyz_ctx *ctx, const double *dY);
+
 void xyz_destroy(xyz_ctx *ctx);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -30,6 +30,7 @@
 #include <type_traits>
 
 #include "bits.cuh"
+#include "rows.cuh"
 #include "xyz_internal.cuh"
 
 namespace xyz {
@@ -64,19 +65,6 @@ struct FlLayout {
     static_assert(BATCH || 2 * FL_T <= FL_FWORDS, "the table fits the filter's memory");
     static_assert(SMAX < FL_T, "the table has a free slot for every survivor");
 };
-
-__device__ __forceinline__ uint64_t mix64(uint64_t z)
-{
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ int64_t draw_row(uint64_t seed, uint64_t t, int64_t n)
-{
-    uint64_t u = mix64(seed + (t + 1ULL) * 0x9E3779B97F4A7C15ULL);
-    return (int64_t)__umul64hi(u, (uint64_t)n);
-}
 
 // Blocked Bloom filter of 2^k words: a key selects one 32-bit word and
 // two bits inside it, all from multiplicative hashes (Knuth's method with
@@ -128,7 +116,8 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                   uint32_t *__restrict__ seg_count, uint32_t seg_cap, int *__restrict__ overflow,
                   uint8_t *__restrict__ cnz, uint32_t *__restrict__ members,
                   uint32_t *__restrict__ members_count, Bucket *__restrict__ buckets,
-                  uint64_t *__restrict__ pair_counts, uint32_t *__restrict__ nbuckets)
+                  uint64_t *__restrict__ pair_counts, uint32_t *__restrict__ nbuckets,
+                  const uint64_t *__restrict__ cdf, uint64_t wtot)
 {
     using SegKey = uint64_t;
     extern __shared__ __align__(16) uint32_t fl_smem[];
@@ -179,7 +168,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         if (wp == 0) {
             int64_t s = 0;
             if (lane < M)
-                s = draw_row(seed, (uint64_t)(l0 + r) * (uint64_t)M + (uint64_t)lane, n);
+                s = draw_row(seed, (uint64_t)(l0 + r) * (uint64_t)M + (uint64_t)lane, n, cdf, wtot);
             rowoff[lane] = s * Pp;
             rowidx[lane] = s;
             if (!BATCH) {
@@ -603,7 +592,8 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
     using KernT = void (*)(const uint32_t *, int64_t, int64_t, const uint32_t *, int64_t, int, int64_t,
                            int64_t, int, uint64_t, int64_t, int, int, int, int, int64_t, uint32_t, uint32_t,
                            uint32_t *, void *, uint32_t *, uint32_t *, uint32_t, int *, uint8_t *,
-                           uint32_t *, uint32_t *, Bucket *, uint64_t *, uint32_t *);
+                           uint32_t *, uint32_t *, Bucket *, uint64_t *, uint32_t *, const uint64_t *,
+                           uint64_t);
     KernT kern;
     if (batch)
         kern = M <= 8 ? filter_kernel<8, true> : M <= 16 ? filter_kernel<16, true>
@@ -617,7 +607,7 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
     kern<<<grid, filter_threads(pk.P), smem, s>>>(pk.Xr, pk.Pp, pk.P, ybs, pk.Wp, B, pk.n, pk.p, M, seed, l0, R,
                                         NB, BB, rbits, rbase, mcap, bcap, kc_scratch, seg_keys, seg_vals,
                                         seg_count, seg_cap, overflow, cnz, members, members_count,
-                                        buckets, pair_counts, nbuckets);
+                                        buckets, pair_counts, nbuckets, pk.cdf, pk.wtotal);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -23,6 +23,7 @@
 // same hash and handles the halves one after the other; equal keys never
 // split, so a heavy group costs one table slot however large it is.
 #include "bits.cuh"
+#include "rows.cuh"
 #include "xyz_internal.cuh"
 
 namespace xyz {
@@ -39,19 +40,6 @@ constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 constexpr int GR_STACK = 64;
 constexpr int GR_CACHE = 8;                  // entries per thread kept in registers
 
-__device__ __forceinline__ uint64_t mix64(uint64_t z)
-{
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ int64_t draw_row(uint64_t seed, uint64_t t, int64_t n)
-{
-    uint64_t u = mix64(seed + (t + 1ULL) * 0x9E3779B97F4A7C15ULL);
-    return (int64_t)__umul64hi(u, (uint64_t)n);
-}
-
 __device__ __forceinline__ uint32_t group_key(uint32_t Kc, bool nz) { return nz ? (Kc >> 1) : Kc; }
 
 __device__ __forceinline__ uint32_t part_of(uint32_t g, int d)
@@ -63,7 +51,8 @@ __global__ void __launch_bounds__(KP_THREADS)
     keybuild_part_kernel(const uint32_t *__restrict__ Xr, int64_t Pp, int64_t P,
                          const uint32_t *__restrict__ yb, int64_t n, int64_t p, int M,
                          uint64_t seed, int64_t l0, int d, int nblk, uint64_t *__restrict__ ents,
-                         uint32_t *__restrict__ seg, uint8_t *__restrict__ cnz)
+                         uint32_t *__restrict__ seg, uint8_t *__restrict__ cnz,
+                         const uint64_t *__restrict__ cdf, uint64_t wtot)
 {
     extern __shared__ __align__(16) unsigned char kp_smem[];
     uint64_t *ent = reinterpret_cast<uint64_t *>(kp_smem);                 // [KP_COLS]
@@ -85,7 +74,7 @@ __global__ void __launch_bounds__(KP_THREADS)
         int64_t s = 0;
         uint32_t ybit = 0;
         if (t < M) {
-            s = draw_row(seed, (uint64_t)run * (uint64_t)M + (uint64_t)t, n);
+            s = draw_row(seed, (uint64_t)run * (uint64_t)M + (uint64_t)t, n, cdf, wtot);
             ybit = (yb[s >> 5] >> (s & 31)) & 1u;
         }
         rows[t] = s;
@@ -747,7 +736,8 @@ cudaError_t launch_keybuild_part(const Packed &pk, int M, uint64_t seed, int64_t
         return ae;
     dim3 grid((unsigned)nblk, (unsigned)R);
     keybuild_part_kernel<<<grid, KP_THREADS, smem, s>>>(pk.Xr, pk.Pp, pk.P, pk.yb, pk.n, pk.p, M,
-                                                        seed, l0, d, nblk, ents, seg, cnz);
+                                                        seed, l0, d, nblk, ents, seg, cnz, pk.cdf,
+                                                        pk.wtotal);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -116,15 +116,32 @@ __device__ __forceinline__ int agree_cols(const uint32_t *__restrict__ Xc, int64
 // in registers across the steps.
 constexpr int VQ = 4;   // response pieces per lane held in registers (columns up to 4096 rows)
 
-template <bool BATCH>
+// Weighted agreement of one 32-row word (Section 3.1): sum over the agreeing
+// rows of their fixed-point weights, from the weights' bit planes of that
+// word (plane b holds bit b of q_i for the word's 32 rows).
+__device__ __forceinline__ int32_t word_weight(const uint32_t *__restrict__ planes, int64_t w, uint32_t g)
+{
+    const uint32_t *pl = planes + w * XYZ_WPLANES;
+    int32_t s = 0;
+#pragma unroll
+    for (int b = 0; b < XYZ_WPLANES; ++b)
+        s += __popc(g & __ldg(pl + b)) << b;
+    return s;                     // <= 32 (2^25 - 1) < 2^31
+}
+
+template <bool BATCH, bool WEIGHTED>
 __global__ void __launch_bounds__(JV_THREADS)
     verify_kernel(const uint32_t *__restrict__ Xc, int64_t Wp, const uint32_t *__restrict__ yb,
                   const Bucket *__restrict__ buckets, const uint64_t *__restrict__ pair_off,
                   const uint32_t *__restrict__ nbuckets, const uint64_t *__restrict__ total_pairs,
                   const uint32_t *__restrict__ vals, int64_t amin, int kbits,
                   uint64_t *__restrict__ rec_keys, uint32_t *__restrict__ rec_agree,
-                  uint32_t *__restrict__ nrec, uint32_t rec_cap, const int *__restrict__ abort_flag)
+                  uint32_t *__restrict__ nrec, uint32_t rec_cap, const int *__restrict__ abort_flag,
+                  const uint32_t *__restrict__ planes, int64_t wQ, double kq)
 {
+    // WEIGHTED (real response, Section 3.1): yb holds the signs of Y; a
+    // candidate passes when (double)(2 S - Q) >= kappa * Q, S the weight sum
+    // of its agreeing rows (the records still carry the agreement count).
     // abort_flag (may be null): bit 2 set means the producer of the buckets
     // ran out of space after reserving some of them, so their entries are not
     // all written; the whole launch group is then skipped (and redone).
@@ -195,6 +212,7 @@ __global__ void __launch_bounds__(JV_THREADS)
             }
         }
         int agree = 0;
+        int64_t wsum = 0;
 #pragma unroll
         for (int st = 0; st < 8; ++st) {
             const int cidx = 4 * st + (lane >> 3);           // candidate of this lane's group
@@ -203,6 +221,7 @@ __global__ void __launch_bounds__(JV_THREADS)
             const bool vv = __shfl_sync(0xffffffffu, (int)valid, cidx) != 0;
             const uint32_t rr = BATCH ? __shfl_sync(0xffffffffu, resp, cidx) : 0u;
             int part = 0;
+            int64_t wpart = 0;
             if (vv) {
                 const uint4 *cj = reinterpret_cast<const uint4 *>(Xc + (int64_t)jj * Wp);
                 const uint4 *ck = reinterpret_cast<const uint4 *>(Xc + (int64_t)kk * Wp);
@@ -213,14 +232,22 @@ __global__ void __launch_bounds__(JV_THREADS)
                     if (q < nq) {
                         const uint4 x = __ldg(cj + q), z = __ldg(ck + q);
                         const uint4 y = BATCH ? __ldg(yq + q) : yr[i];
-                        part += __popc(~(x.x ^ z.x ^ y.x)) + __popc(~(x.y ^ z.y ^ y.y)) +
-                                __popc(~(x.z ^ z.z ^ y.z)) + __popc(~(x.w ^ z.w ^ y.w));
+                        const uint32_t g0 = ~(x.x ^ z.x ^ y.x), g1 = ~(x.y ^ z.y ^ y.y);
+                        const uint32_t g2 = ~(x.z ^ z.z ^ y.z), g3 = ~(x.w ^ z.w ^ y.w);
+                        part += __popc(g0) + __popc(g1) + __popc(g2) + __popc(g3);
+                        if (WEIGHTED)
+                            wpart += (int64_t)word_weight(planes, 4 * q, g0) + word_weight(planes, 4 * q + 1, g1) +
+                                     (int64_t)word_weight(planes, 4 * q + 2, g2) + word_weight(planes, 4 * q + 3, g3);
                     }
                 }
                 for (int q = sub + 8 * VQ; q < nq; q += 8) {
                     const uint4 x = __ldg(cj + q), z = __ldg(ck + q), y = __ldg(yq + q);
-                    part += __popc(~(x.x ^ z.x ^ y.x)) + __popc(~(x.y ^ z.y ^ y.y)) +
-                            __popc(~(x.z ^ z.z ^ y.z)) + __popc(~(x.w ^ z.w ^ y.w));
+                    const uint32_t g0 = ~(x.x ^ z.x ^ y.x), g1 = ~(x.y ^ z.y ^ y.y);
+                    const uint32_t g2 = ~(x.z ^ z.z ^ y.z), g3 = ~(x.w ^ z.w ^ y.w);
+                    part += __popc(g0) + __popc(g1) + __popc(g2) + __popc(g3);
+                    if (WEIGHTED)
+                        wpart += (int64_t)word_weight(planes, 4 * q, g0) + word_weight(planes, 4 * q + 1, g1) +
+                                 (int64_t)word_weight(planes, 4 * q + 2, g2) + word_weight(planes, 4 * q + 3, g3);
                 }
             }
             part += __shfl_xor_sync(0xffffffffu, part, 4);
@@ -229,8 +256,17 @@ __global__ void __launch_bounds__(JV_THREADS)
             const int got = __shfl_sync(0xffffffffu, part, 8 * (lane & 3));
             if ((lane >> 2) == st)
                 agree = got;
+            if (WEIGHTED) {
+                wpart += __shfl_xor_sync(0xffffffffu, wpart, 4);
+                wpart += __shfl_xor_sync(0xffffffffu, wpart, 2);
+                wpart += __shfl_xor_sync(0xffffffffu, wpart, 1);
+                const int64_t wgot = __shfl_sync(0xffffffffu, wpart, 8 * (lane & 3));
+                if ((lane >> 2) == st)
+                    wsum = wgot;
+            }
         }
-        if (valid && agree >= amin) {
+        const bool pass = WEIGHTED ? (double)(2 * wsum - wQ) >= kq : agree >= amin;
+        if (valid && pass) {
             uint32_t idx = atomicAdd(nrec, 1u);
             if (idx < rec_cap) {
                 uint32_t lo_c = j < k ? j : k, hi_c = j < k ? k : j;
@@ -378,13 +414,17 @@ cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_
                           int64_t *launches, const uint32_t *ybs, const int *abort_flag)
 {
     if (ybs)
-        verify_kernel<true><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
+        verify_kernel<true, false><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
             pk.Xc, pk.Wp, ybs, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits, rec_keys,
-            rec_agree, nrec, rec_cap, abort_flag);
-    else
-        verify_kernel<false><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
+            rec_agree, nrec, rec_cap, abort_flag, nullptr, 0, 0.0);
+    else if (pk.cdf)
+        verify_kernel<false, true><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
             pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits,
-            rec_keys, rec_agree, nrec, rec_cap, abort_flag);
+            rec_keys, rec_agree, nrec, rec_cap, abort_flag, pk.planes, (int64_t)pk.wtotal, pk.wkq);
+    else
+        verify_kernel<false, false><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
+            pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits,
+            rec_keys, rec_agree, nrec, rec_cap, abort_flag, nullptr, 0, 0.0);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -20,6 +20,7 @@
 // 32 bytes of row s_m (and s_{m+32} when M > 32) with two 16-byte loads; a
 // warp ballot per bit position transposes the M x 32 bit tile so that lane b
 // ends up with the key of column 32w + b.  Stores are coalesced.
+#include "rows.cuh"
 #include "xyz_internal.cuh"
 
 namespace xyz {
@@ -27,20 +28,6 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int KB_WARPS = 8;
-
-__device__ __forceinline__ uint64_t mix64(uint64_t z)
-{
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-
-// Row index of draw t: floor(u * n / 2^64) with u = splitmix64 output t.
-__device__ __forceinline__ int64_t draw_row(uint64_t seed, uint64_t t, int64_t n)
-{
-    uint64_t u = mix64(seed + (t + 1ULL) * 0x9E3779B97F4A7C15ULL);
-    return (int64_t)__umul64hi(u, (uint64_t)n);
-}
 
 __device__ __forceinline__ uint32_t transpose_take(uint32_t word, int lane)
 {
@@ -59,7 +46,7 @@ __global__ void __launch_bounds__(KB_WARPS * 32)
                     const uint32_t *__restrict__ yb, int64_t n, int64_t p, int M, uint64_t seed,
                     int64_t l0, int rbits, K *__restrict__ keys, uint32_t *__restrict__ vals,
                     uint8_t *__restrict__ cnz, uint64_t *__restrict__ raw_kx,
-                    uint64_t *__restrict__ raw_c)
+                    uint64_t *__restrict__ raw_c, const uint64_t *__restrict__ cdf, uint64_t wtot)
 {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -72,11 +59,11 @@ __global__ void __launch_bounds__(KB_WARPS * 32)
     int64_t s_lo = 0, s_hi = 0;
     uint32_t yb_lo = 0, yb_hi = 0;
     if (lane < M) {
-        s_lo = draw_row(seed, (uint64_t)run * (uint64_t)M + (uint64_t)lane, n);
+        s_lo = draw_row(seed, (uint64_t)run * (uint64_t)M + (uint64_t)lane, n, cdf, wtot);
         yb_lo = (yb[s_lo >> 5] >> (s_lo & 31)) & 1u;
     }
     if (lane + 32 < M) {
-        s_hi = draw_row(seed, (uint64_t)run * (uint64_t)M + (uint64_t)(lane + 32), n);
+        s_hi = draw_row(seed, (uint64_t)run * (uint64_t)M + (uint64_t)(lane + 32), n, cdf, wtot);
         yb_hi = (yb[s_hi >> 5] >> (s_hi & 31)) & 1u;
     }
     const uint64_t c = ((uint64_t)__ballot_sync(FULL, yb_hi) << 32) | __ballot_sync(FULL, yb_lo);
@@ -149,7 +136,8 @@ cudaError_t launch_keybuild(const Packed &pk, int M, uint64_t seed, int64_t l0, 
     int64_t groups = (pk.P + 7) / 8;
     dim3 grid((unsigned)((groups + KB_WARPS - 1) / KB_WARPS), (unsigned)R);
     keybuild_kernel<K><<<grid, KB_WARPS * 32, 0, s>>>(pk.Xr, pk.Pp, pk.P, pk.yb, pk.n, pk.p, M, seed,
-                                                      l0, rbits, keys, vals, cnz, raw_kx, raw_c);
+                                                      l0, rbits, keys, vals, cnz, raw_kx, raw_c,
+                                                      pk.cdf, pk.wtotal);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -1,0 +1,163 @@
+// Real-valued response (Section 3.1, continuous Y with binary X).
+//
+// The search samples row i with probability |Y_i| / ||Y||_1, forms Z from
+// the signs of Y, and weighs each agreeing row by |Y_i|.  The weights are
+// used in fixed point: with max |Y_i| = f 2^e (f in [0.5, 1)),
+// q_i = floor(|Y_i| 2^(24 - e) + 1/2), an integer in [0, 2^24] (every step
+// below is exact, so the result does not depend on the order of any sum).
+// Prepared once per response:
+//   yb      sign bits (1 for Y_i < 0; padding rows 1, so they never agree),
+//   planes  per 32-row word, 25 bit planes of the q of its rows,
+//   cdf     inclusive prefix sums of q (the weighted row draw, rows.cuh),
+//   total   Q = sum q.
+#include <math.h>
+
+#include "xyz_internal.cuh"
+
+namespace xyz {
+namespace {
+
+constexpr int WT_THREADS = 256;
+
+// max |Y_i| as the bits of a non-negative double (ordered like the value);
+// bad != 0 when some entry is not finite
+__global__ void maxabs_kernel(const double *__restrict__ Y, int64_t n,
+                              unsigned long long *__restrict__ maxbits, int *__restrict__ bad)
+{
+    unsigned long long m = 0;
+    int b = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double y = Y[i];
+        if (!isfinite(y)) {
+            b = 1;
+            continue;
+        }
+        const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(y));
+        m = v > m ? v : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v > m ? v : m;
+        b |= __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (m)
+            atomicMax(maxbits, m);
+        if (b)
+            atomicOr(bad, 1);
+    }
+}
+
+// One warp per 32-row word: fixed-point weights, sign bits and bit planes.
+__global__ void quantize_kernel(const double *__restrict__ Y, int64_t n, int64_t Wp,
+                                const unsigned long long *__restrict__ maxbits,
+                                uint64_t *__restrict__ q, uint32_t *__restrict__ yb,
+                                uint32_t *__restrict__ planes)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= Wp)
+        return;                                   // whole warp leaves together
+    int e = 0;
+    frexp(__longlong_as_double((long long)*maxbits), &e);
+    const int64_t i = 32 * w + lane;
+    uint64_t qv = 0;
+    uint32_t neg = 1;                             // padding rows: never agree
+    if (i < n) {
+        const double y = Y[i];
+        qv = isfinite(y) ? (uint64_t)floor(ldexp(fabs(y), 24 - e) + 0.5) : 0u;   // rejected later
+        neg = y < 0.0 ? 1u : 0u;
+        q[i] = qv;
+    }
+    const uint32_t sb = __ballot_sync(0xffffffffu, neg);
+    uint32_t mine = 0;                            // lane b keeps plane b
+#pragma unroll
+    for (int b = 0; b < XYZ_WPLANES; ++b) {
+        const uint32_t pb = __ballot_sync(0xffffffffu, (uint32_t)(qv >> b) & 1u);
+        if (lane == b)
+            mine = pb;
+    }
+    if (lane == 0)
+        yb[w] = sb;
+    if (lane < XYZ_WPLANES)
+        planes[w * XYZ_WPLANES + lane] = mine;
+}
+
+// exclusive prefix sums -> inclusive
+__global__ void inclusive_kernel(uint64_t *__restrict__ cdf, const uint64_t *__restrict__ q, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        cdf[i] += q[i];
+}
+
+// Weighted strengths of the output pairs: one warp per pair recomputes the
+// weight sum S of its agreeing rows; strength = (2 S - Q) / Q.
+__global__ void weighted_strength_kernel(const uint32_t *__restrict__ Xc, int64_t Wp,
+                                         const uint32_t *__restrict__ yb,
+                                         const uint32_t *__restrict__ planes, uint64_t Q,
+                                         PairOut *__restrict__ out, const uint32_t *__restrict__ nout)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t N = *nout;
+    for (int64_t t = wid; t < N; t += nw) {
+        const int64_t j = out[t].j, k = out[t].k;
+        int64_t S = 0;
+        for (int64_t w = lane; w < Wp; w += 32) {
+            const uint32_t g = ~(Xc[j * Wp + w] ^ Xc[k * Wp + w] ^ yb[w]);
+            const uint32_t *pl = planes + w * XYZ_WPLANES;
+            for (int b = 0; b < XYZ_WPLANES; ++b)
+                S += (int64_t)__popc(g & pl[b]) << b;
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            S += __shfl_xor_sync(0xffffffffu, S, o);
+        if (lane == 0)
+            out[t].strength = (float)((double)(2 * S - (int64_t)Q) / (double)Q);
+    }
+}
+
+}  // namespace
+
+size_t weights_scan_bytes(int64_t n) { return scan_temp_bytes(n); }
+
+cudaError_t launch_prepare_weights(const double *dY, int64_t n, int64_t Wp, uint64_t *q, uint32_t *yb,
+                                   uint32_t *planes, uint64_t *cdf, uint64_t *total,
+                                   unsigned long long *maxbits, int *bad, void *scan_tmp, cudaStream_t s,
+                                   int64_t *launches)
+{
+    cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    if (e != cudaSuccess)
+        return e;
+    int64_t g = (n + WT_THREADS - 1) / WT_THREADS;
+    g = g < 1 ? 1 : (g > 4096 ? 4096 : g);
+    maxabs_kernel<<<(unsigned)g, WT_THREADS, 0, s>>>(dY, n, maxbits, bad);
+    const int64_t qb = (Wp * 32 + WT_THREADS - 1) / WT_THREADS;
+    quantize_kernel<<<(unsigned)qb, WT_THREADS, 0, s>>>(dY, n, Wp, maxbits, q, yb, planes);
+    *launches += 2;
+    e = scan_u64_dev(q, cdf, nullptr, n, total, nullptr, scan_tmp, s, launches);
+    if (e != cudaSuccess)
+        return e;
+    inclusive_kernel<<<(unsigned)g, WT_THREADS, 0, s>>>(cdf, q, n);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weighted_strengths(const Packed &pk, PairOut *out, const uint32_t *nout, int64_t cap,
+                                      cudaStream_t s, int64_t *launches)
+{
+    if (cap <= 0)
+        return cudaSuccess;
+    int64_t blocks = (cap * 32 + WT_THREADS - 1) / WT_THREADS;
+    blocks = blocks > 4096 ? 4096 : (blocks < 1 ? 1 : blocks);
+    weighted_strength_kernel<<<(unsigned)blocks, WT_THREADS, 0, s>>>(pk.Xc, pk.Wp, pk.yb, pk.planes,
+                                                                     pk.wtotal, out, nout);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace xyz

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/xyz.h"
@@ -92,6 +93,9 @@ struct xyz_ctx {
     int64_t spill_flush = 0;     // filter path: launch groups per spill flush (0: one per search)
     DevBuf resp, ybs;            // batched search: response of each output pair, response bits
     DevBuf y_alt, y_stage;       // response updates: packed copy checked before use, host staging
+    // real response (Section 3.1): live weights and a staging set swapped in
+    // once a new response has been checked
+    DevBuf wq, wcdf, wplanes, wq2, wcdf2, wplanes2, wmeta, wscan, yreal;
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
     int64_t rec_cap = 1 << 16;
     int64_t chunk_entries = (int64_t)1 << 25;
@@ -139,7 +143,9 @@ static int64_t ws_bytes(const xyz_ctx *c)
                            &c->ents, &c->seg, &c->members, &c->kc_scratch,
                            &c->seg_keys, &c->seg_vals, &c->seg_count,
                            &c->buckets2, &c->pair_counts2, &c->pair_off2, &c->scan_tmp2,
-                           &c->resp, &c->ybs, &c->y_alt, &c->y_stage};
+                           &c->resp, &c->ybs, &c->y_alt, &c->y_stage,
+                           &c->wq, &c->wcdf, &c->wplanes, &c->wq2, &c->wcdf2, &c->wplanes2,
+                           &c->wmeta, &c->wscan, &c->yreal};
     int64_t s = 0;
     for (const DevBuf *b : all)
         s += (int64_t)b->bytes;
@@ -632,6 +638,9 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                          (PairOut *)c->out.ptr, ctr_nout(c), c->stream, &launches,
                          B > 1 ? (uint32_t *)c->resp.ptr : nullptr));
         tm.end();
+        if (c->pk.cdf && nrec > 0)
+            CU(launch_weighted_strengths(c->pk, (PairOut *)c->out.ptr, ctr_nout(c), (int64_t)nrec, c->stream,
+                                         &launches));
         uint32_t nout = 0;
         CU(cudaMemcpyAsync(&nout, ctr_nout(c), 4, cudaMemcpyDeviceToHost, c->stream));
         CU(cudaStreamSynchronize(c->stream));
@@ -739,7 +748,9 @@ void destroy_ctx(xyz_ctx *c)
                      &c->rec_agree_alt, &c->flags, &c->pos,       &c->out,      &c->dedup_tmp,
                      &c->raw,     &c->ents,        &c->seg,       &c->members,  &c->kc_scratch,
                      &c->seg_keys, &c->seg_vals,   &c->seg_count, &c->buckets2, &c->pair_counts2,
-                     &c->pair_off2, &c->scan_tmp2, &c->resp,   &c->ybs, &c->y_alt, &c->y_stage};
+                     &c->pair_off2, &c->scan_tmp2, &c->resp,   &c->ybs, &c->y_alt, &c->y_stage,
+                     &c->wq, &c->wcdf, &c->wplanes, &c->wq2, &c->wcdf2, &c->wplanes2,
+                     &c->wmeta, &c->wscan, &c->yreal};
     for (DevBuf *b : all)
         release(*b);
     if (c->own_stream && c->stream)
@@ -848,7 +859,60 @@ int xyz_set_y_dev(xyz_ctx *ctx, const int8_t *dY)
         return fail(XYZ_EINVAL, "entries of Y must be -1 or +1");
     CU(cudaMemcpyAsync(ctx->pk.yb, ctx->y_alt.ptr, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    ctx->pk.cdf = nullptr;               // binary response: uniform rows, plain agreement
+    ctx->pk.planes = nullptr;
+    ctx->pk.wtotal = 0;
     return XYZ_OK;
+}
+
+int xyz_set_y_real_dev(xyz_ctx *ctx, const double *dY)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!dY)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    if (!ctx->owns_packed)
+        return fail(XYZ_EINVAL, "context does not own its response");
+    const int64_t n = ctx->pk.n, Wp = ctx->pk.Wp;
+    if ((rc = ensure(ctx->y_alt, (size_t)Wp * 4)) || (rc = ensure(ctx->wq2, (size_t)n * 8)) ||
+        (rc = ensure(ctx->wcdf2, (size_t)n * 8)) ||
+        (rc = ensure(ctx->wplanes2, (size_t)Wp * XYZ_WPLANES * 4)) || (rc = ensure(ctx->wmeta, 64)) ||
+        (rc = ensure(ctx->wscan, weights_scan_bytes(n))))
+        return rc;
+    char *meta = (char *)ctx->wmeta.ptr;      // [0] max bits, [8] bad flag, [16] total
+    int64_t launches = 0;
+    CU(launch_prepare_weights(dY, n, Wp, (uint64_t *)ctx->wq2.ptr, (uint32_t *)ctx->y_alt.ptr,
+                              (uint32_t *)ctx->wplanes2.ptr, (uint64_t *)ctx->wcdf2.ptr,
+                              (uint64_t *)(meta + 16), (unsigned long long *)meta, (int *)(meta + 8),
+                              ctx->wscan.ptr, ctx->stream, &launches));
+    uint64_t host[3] = {0, 0, 0};
+    CU(cudaMemcpyAsync(host, meta, 24, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if ((host[1] & 0xFFFFFFFFu) || host[0] == 0)
+        return fail(XYZ_EINVAL, "entries of a real Y must be finite and not all zero");
+    CU(cudaMemcpyAsync(ctx->pk.yb, ctx->y_alt.ptr, (size_t)Wp * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    std::swap(ctx->wq, ctx->wq2);
+    std::swap(ctx->wcdf, ctx->wcdf2);
+    std::swap(ctx->wplanes, ctx->wplanes2);
+    ctx->pk.cdf = (const uint64_t *)ctx->wcdf.ptr;
+    ctx->pk.planes = (const uint32_t *)ctx->wplanes.ptr;
+    ctx->pk.wtotal = host[2];
+    return XYZ_OK;
+}
+
+int xyz_set_y_real(xyz_ctx *ctx, const double *Y)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!Y)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    if ((rc = ensure(ctx->yreal, (size_t)ctx->pk.n * 8)))
+        return rc;
+    CU(cudaMemcpyAsync(ctx->yreal.ptr, Y, (size_t)ctx->pk.n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    return xyz_set_y_real_dev(ctx, (const double *)ctx->yreal.ptr);
 }
 
 int xyz_set_y(xyz_ctx *ctx, const int8_t *Y)
@@ -893,7 +957,8 @@ int xyz_search_range(xyz_ctx *ctx, int64_t l0, int64_t l1, int32_t M, double kap
         return rc;
     const int64_t amin = amin_rule(ctx->pk.n, kappa);
     int64_t nout = 0;
-    if (amin > ctx->pk.n) {
+    ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;     // real response: 2S - Q >= kappa Q
+    if (amin > ctx->pk.n && !ctx->pk.cdf) {
         std::memset(&ctx->stats, 0, sizeof(ctx->stats));
         *pairs = nullptr;
         *npairs = 0;
@@ -931,6 +996,8 @@ int xyz_brute_force(xyz_ctx *ctx, double kappa, xyz_pair **pairs, int64_t *npair
     if ((rc = check_kappa(kappa)))
         return rc;
     xyz_ctx *c = ctx;
+    if (c->pk.cdf)
+        return fail(XYZ_EINVAL, "the exhaustive screen takes a binary response");
     const int64_t amin = amin_rule(c->pk.n, kappa);
     std::memset(&c->stats, 0, sizeof(c->stats));
     *pairs = nullptr;
@@ -1098,6 +1165,8 @@ int search_batch_dev(xyz_ctx *ctx, const int8_t *dYs, int32_t B, int32_t L, int3
         return fail(XYZ_EINVAL, "need B >= 1 and L >= 1");
     if ((rc = check_M(M)) || (rc = check_kappa(kappa)))
         return rc;
+    if (ctx->pk.cdf)
+        return fail(XYZ_EINVAL, "batched search takes binary responses");
     if ((rc = pack_responses(ctx, dYs, B)))
         return rc;
     const int64_t amin = amin_rule(ctx->pk.n, kappa);
@@ -1234,6 +1303,7 @@ int xyz_run_candidates(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, int3
     if ((rc = check_M(M)))
         return rc;
     int64_t nout = 0;
+    ctx->pk.wkq = -INFINITY;                           // every candidate passes
     if ((rc = run_search(ctx, run, run + 1, M, 0, seed, &nout)))
         return rc;
     int32_t *host = nullptr;

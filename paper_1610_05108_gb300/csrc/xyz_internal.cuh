@@ -41,7 +41,15 @@ struct Packed {
     uint32_t *Xc = nullptr;
     uint32_t *Xr = nullptr;
     uint32_t *yb = nullptr;
+    // real response (Section 3.1): weighted rows and weighted verification;
+    // null cdf = binary response
+    const uint64_t *cdf = nullptr;     // [n] cumulative fixed-point weights
+    uint64_t wtotal = 0;               // sum of the weights, cdf[n - 1]
+    const uint32_t *planes = nullptr;  // [Wp][XYZ_WPLANES] bit planes of the weights per word
+    double wkq = 0.0;                  // kappa * wtotal of the current search
 };
+
+constexpr int XYZ_WPLANES = 25;        // weights are integers in [0, 2^24]
 
 // One group of equal keys that yields candidates.  Entries [start, start+nA)
 // of the sorted arrays are side A, [start+nA, start+nA+nB) side B; nB == 0
@@ -167,6 +175,18 @@ cudaError_t launch_compact(const uint64_t *seg_keys, const uint32_t *seg_vals,
 
 // Host-side helpers shared by the API files.
 int64_t amin_rule(int64_t n, double kappa);
+
+// Real response (weights.cu): fixed-point weights q, sign bits, bit planes,
+// inclusive cdf and total of a device array of n doubles; maxbits / bad let
+// the host reject a response that is all zero or not finite.
+size_t weights_scan_bytes(int64_t n);
+cudaError_t launch_prepare_weights(const double *dY, int64_t n, int64_t Wp, uint64_t *q, uint32_t *yb,
+                                   uint32_t *planes, uint64_t *cdf, uint64_t *total,
+                                   unsigned long long *maxbits, int *bad, void *scan_tmp, cudaStream_t s,
+                                   int64_t *launches);
+// weighted strengths (2 S - Q) / Q of the first *nout output pairs
+cudaError_t launch_weighted_strengths(const Packed &pk, PairOut *out, const uint32_t *nout, int64_t cap,
+                                      cudaStream_t s, int64_t *launches);
 
 // Exhaustive screen (brute.cu): records (j << kbits | k, a) of every pair
 // j < k with a >= amin; blocks = brute_tiles(p).

@@ -63,6 +63,8 @@ SIGNATURES = {
     "xyz_create_dev": (ctypes.c_int, [_p, _p, _i64, _i64, _p, _p]),
     "xyz_set_y": (ctypes.c_int, [_p, _p]),
     "xyz_set_y_dev": (ctypes.c_int, [_p, _p]),
+    "xyz_set_y_real": (ctypes.c_int, [_p, _p]),
+    "xyz_set_y_real_dev": (ctypes.c_int, [_p, _p]),
     "xyz_destroy": (None, [_p]),
     "xyz_last_error": (ctypes.c_char_p, []),
     "xyz_info": (ctypes.c_int, [_p, _p, _p, _p]),
@@ -227,6 +229,16 @@ class Context:
 
     def set_y_dev(self, dY_ptr: int):
         _check(load().xyz_set_y_dev(self.handle, ctypes.c_void_p(dY_ptr)))
+
+    def set_y_real(self, Y: np.ndarray):
+        """Real-valued response (Section 3.1): weighted rows and strengths."""
+        Y = np.ascontiguousarray(Y, dtype=np.float64)
+        if Y.shape != (self.n,):
+            raise ValueError("Y must have shape (n,)")
+        _check(load().xyz_set_y_real(self.handle, _ptr(Y)))
+
+    def set_y_real_dev(self, dY_ptr: int):
+        _check(load().xyz_set_y_real_dev(self.handle, ctypes.c_void_p(dY_ptr)))
 
     # search ----------------------------------------------------------
     def search(self, L: int, M: int, kappa: float, seed: int) -> np.ndarray:

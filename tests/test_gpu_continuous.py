@@ -1,0 +1,124 @@
+"""Real-valued response (Section 3.1): the GPU search with weighted rows and
+weighted verification equals the oracle's continuous-response search pair
+for pair (agreement counts exact, strengths to float precision), reduces to
+the binary search for Y = +-1, draws the oracle's weighted rows, and rejects
+unusable responses without changing the context.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xyz():
+    from paper_1610_05108_gb300 import build, xyz as mod
+    build.build()
+    mod.load()
+    return mod
+
+
+def _X(n, p, seed):
+    rng = np.random.default_rng(seed)
+    return np.asfortranarray((rng.integers(0, 2, size=(n, p), dtype=np.int8) * 2 - 1).astype(np.int8)), rng
+
+
+def _arr(res):
+    if len(res) == 0:
+        return np.zeros((0, 3), np.int32)
+    return np.stack([res["j"], res["k"], res["agree"]], axis=1).astype(np.int32)
+
+
+def _check(xyz, orc, X, Y, L, M, kappa, seed):
+    with xyz.create(X, np.ones(X.shape[0], np.int8)) as ctx:
+        ctx.set_y_real(Y)
+        got = ctx.search(L, M, kappa, seed)
+    want, S = orc.xyz_weighted(X, Y, L, M, kappa, seed)
+    assert np.array_equal(_arr(got), want), (X.shape, L, M, kappa)
+    if len(want):
+        q, _ = orc.quantize_y(Y)
+        Q = float(q.sum())
+        strength = (2.0 * S - Q) / Q
+        assert np.allclose(got["strength"], strength.astype(np.float32), rtol=0, atol=1e-6)
+    return got
+
+
+@pytest.mark.parametrize("n,p,L,M,kappa", [
+    (200, 2000, 40, 9, 0.25),
+    (97, 513, 25, 6, 0.15),
+    (1000, 3000, 30, 12, 0.3),
+    (130, 400, 12, 33, -0.2),          # M >= 32: general sort path
+])
+def test_real_response_matches_oracle(xyz, orc, n, p, L, M, kappa):
+    X, rng = _X(n, p, n + p + M)
+    Y = rng.standard_t(3, size=n) + 2.0 * X[:, 5] * X[:, p - 3]
+    got = _check(xyz, orc, X, Y, L, M, kappa, 17)
+    if M < 30:
+        assert (5, p - 3) in set(zip(got["j"].tolist(), got["k"].tolist()))
+
+
+def test_real_pm1_equals_binary(xyz):
+    X, rng = _X(150, 1200, 3)
+    Yb = (X[:, 7] * X[:, 900]).astype(np.int8)
+    Yb[:20] = -Yb[:20]
+    with xyz.create(X, Yb) as ctx:
+        binary = ctx.search(30, 8, 0.2, 5)
+        ctx.set_y_real(Yb.astype(np.float64) * 3.5)
+        real = ctx.search(30, 8, 0.2, 5)
+        ctx.set_y(Yb)                                   # back to the binary mode
+        again = ctx.search(30, 8, 0.2, 5)
+    assert np.array_equal(_arr(binary), _arr(real))
+    assert np.allclose(binary["strength"], real["strength"], atol=1e-6)
+    assert np.array_equal(binary, again)
+
+
+def test_weighted_rows_and_candidates(xyz, orc):
+    X, rng = _X(300, 700, 8)
+    Y = rng.exponential(size=300) * np.where(rng.random(300) < 0.3, -1.0, 1.0)
+    Y[10:20] = 0.0
+    q, sgn = orc.quantize_y(Y)
+    with xyz.create(X, np.ones(300, np.int8)) as ctx:
+        ctx.set_y_real(Y)
+        for run in (0, 5, 77):
+            kx, c = ctx.run_keys(10, 123, run)
+            rows = orc.draw_rows_weighted(q, 123, run, 10)
+            assert not set(rows.tolist()) & set(range(10, 20))       # weight 0: never drawn
+            ox, oz = orc.keys(X, sgn, rows)
+            assert np.array_equal(kx, ox)
+            assert c == int(ox[0] ^ oz[0])
+            got = ctx.run_candidates(10, 123, run)
+            want, _ = orc.xyz_weighted_range(X, Y, run, run + 1, 10, -1.0, 123)
+            assert np.array_equal(got, want[:, :2])
+
+
+def test_section31_model_pair_found(xyz, orc):
+    # Y_i = X_i1 X_i2 + eps_i, sigma^2 = 0.5: the weighted strength of (1, 2)
+    # is about 0.94 while the rest stay near 0.5
+    X, rng = _X(2000, 5000, 21)
+    Y = X[:, 1].astype(np.float64) * X[:, 2] + rng.normal(0, np.sqrt(0.5), size=2000)
+    with xyz.create(X, np.ones(2000, np.int8)) as ctx:
+        ctx.set_y_real(Y)
+        got = ctx.search(20, 14, 0.6, 4)
+    assert list(zip(got["j"].tolist(), got["k"].tolist())) == [(1, 2)]
+    a, S = orc.weighted_agree(X, Y, 1, 2)
+    q, _ = orc.quantize_y(Y)
+    assert got["agree"][0] == a
+    assert abs(got["strength"][0] - (2 * S - q.sum()) / q.sum()) < 1e-6
+
+
+def test_unusable_real_response(xyz):
+    X, rng = _X(64, 300, 2)
+    Y = rng.normal(size=64)
+    with xyz.create(X, np.ones(64, np.int8)) as ctx:
+        ctx.set_y_real(Y)
+        before = ctx.search(10, 6, 0.1, 1)
+        for bad in (np.zeros(64), np.where(np.arange(64) == 3, np.nan, 1.0),
+                    np.where(np.arange(64) == 9, np.inf, 1.0)):
+            with pytest.raises(xyz.XyzError) as e:
+                ctx.set_y_real(bad)
+            assert e.value.code == xyz.XYZ_EINVAL
+        assert np.array_equal(ctx.search(10, 6, 0.1, 1), before)
+        with pytest.raises(xyz.XyzError):
+            ctx.brute_force(0.1)
+        with pytest.raises(xyz.XyzError):
+            ctx.search_batch(np.ones((2, 64), np.int8), 5, 6, 0.1, 1)
