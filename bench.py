@@ -25,7 +25,8 @@ responses, each with 3 planted pairs, kappa = 0.4, M by eq. bestM and L for
 call, shared row stream and keys) and once as 256 plain searches; both must
 give identical results.  --pattern scaling: Section 5.2's experiment (time to discover one planted
 pair of gamma in {0.7, 0.8, 0.9} against p, M from gamma0 = 0.55) with the
-exhaustive GPU screen beside it.  --pattern serve: a Poisson stream (200 requests/s) of
+exhaustive GPU screen beside it.  --pattern continuous: Section 3.1's
+real-valued response model with weighted rows.  --pattern serve: a Poisson stream (200 requests/s) of
 searches with L in [20, 200] and kappa in [0.2, 0.6] over resident SNP-shaped
 datasets of log-uniform n in [500, 8000] and p in [1e4, 5e5], each request
 with its own response (one planted pair of gamma in {0.7, 0.8, 0.9}) and M
@@ -712,6 +713,63 @@ def scaling_arm(args):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------- continuous pattern
+
+def continuous_arm(args):
+    """Section 3.1's model Y_i = X_ia X_ib + eps_i, eps ~ N(0, sigma^2), on
+    i.i.d. +-1 X (n = 2000, p = 100000): weighted rows and strengths, M from
+    gamma0 = 0.55, L for 95% recall of the planted pair from its weighted
+    strength in closed form; the same shape with the binary response
+    sgn(Y) timed beside it."""
+    import torch
+    from scipy.stats import norm
+    from paper_1610_05108_gb300 import build as _build
+    from paper_1610_05108_gb300 import xyz
+    _build.build()
+    xyz.load()
+    n, p = 2000, 100000
+    rng = np.random.default_rng(31)
+    X = np.asfortranarray((rng.integers(0, 2, size=(n, p), dtype=np.int8) * 2 - 1).astype(np.int8))
+    a, b = 123, 45678
+    M = xyz.M_for_gamma0(p, 0.55)
+    rows = []
+    ctx = xyz.create(X, np.ones(n, np.int8))
+    for s2 in (0.5, 1.0, 2.0):
+        sd = float(np.sqrt(s2))
+        Y = X[:, a].astype(np.float64) * X[:, b] + rng.normal(0, sd, size=n)
+        g = (norm.cdf(1 / sd) + sd * norm.pdf(1 / sd)) / (2 * norm.cdf(1 / sd) - 1 + 2 * sd * norm.pdf(1 / sd))
+        L = xyz.runs_for_recall(g ** M, 0.95)
+        kappa = 2 * (g - 0.1) - 1                  # well below the pair, far above the bulk
+        res_t = {}
+        for mode in ("real", "sign"):
+            if mode == "real":
+                ctx.set_y_real(Y)
+            else:
+                ctx.set_y(np.where(Y < 0, -1, 1).astype(np.int8))
+            ctx.search(L, M, kappa, 1)             # warm-up
+            ms, found = [], 0
+            for st in range(args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = ctx.search(L, M, kappa, 100 + st)
+                ms.append((time.perf_counter() - t0) * 1e3)
+                found += int((a, b) in set(zip(res["j"].tolist(), res["k"].tolist())))
+            res_t[mode] = {"ms_per_search": round(float(np.mean(ms)), 3),
+                           "value": p * (p - 1) / 2 / (float(np.mean(ms)) / 1e3),
+                           "recall": round(found / args.steps, 3)}
+        rows.append({"sigma2": s2, "gamma_weighted": round(float(g), 4), "M": M, "L": L,
+                     "kappa": round(kappa, 4), "real": res_t["real"], "sign_only": res_t["sign"]})
+        log(f"[bench] continuous sigma2={s2} L={L} real {res_t['real']} sign {res_t['sign']}")
+    ctx.close()
+    out = {"metric": METRIC, "pattern": "continuous", "unit": UNIT, "n_gpus": 1, "data": "synthetic",
+           "dtype": "u32 keys, int64 fixed-point weights",
+           "config": {"workload": f"iid +-1 X n={n} p={p}, Y = X_a X_b + N(0, sigma^2), weighted rows "
+                                  "(Section 3.1); 'sign_only' is the binary search on sgn(Y) with the same L",
+                      "steps": args.steps, "timing": "host wall clock per search, results on the host"},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -725,7 +783,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the L=100 and exhaustive-screen legs")
-    ap.add_argument("--pattern", choices=["search", "batch", "serve", "scaling"], default="search")
+    ap.add_argument("--pattern", choices=["search", "batch", "serve", "scaling", "continuous"],
+                    default="search")
     ap.add_argument("--batch-responses", type=int, default=256)
     ap.add_argument("--serve-datasets", type=int, default=6)
     ap.add_argument("--serve-requests", type=int, default=400)
@@ -747,6 +806,8 @@ def main(argv=None):
         serve_arm(args)
     elif args.pattern == "scaling":
         scaling_arm(args)
+    elif args.pattern == "continuous":
+        continuous_arm(args)
     else:
         gpu_arm(args)
 

@@ -71,6 +71,9 @@ def _load():
         "orc_xyz_weighted_range": (_i64, [_p, _p, _i64, _i64, _i64, _i64, _i32, _dbl, _u64, _p, _p,
                                           _i64]),
         "orc_brute_force_weighted": (_i64, [_p, _p, _i64, _i64, _dbl, _p, _p, _i64]),
+        "orc_kkt_threshold": (_i64, [_p, _i64, _dbl]),
+        "orc_kkt_brute": (_i64, [_p, _p, _i64, _i64, _dbl, _p, _p, _i64]),
+        "orc_kkt_xyz": (_i64, [_p, _p, _i64, _i64, _i64, _i32, _dbl, _u64, _p, _p, _i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -283,3 +286,36 @@ def xyz_weighted(X, Y, L: int, M: int, kappa: float, seed: int) -> tuple:
 def brute_force_weighted(X, Y, kappa: float) -> tuple:
     """Every pair passing R11 by the naive loop over all pairs."""
     return _weighted_call(_load().orc_brute_force_weighted, X, Y, float(kappa))
+
+
+# ------------------------------------------------- absolute value, KKT check
+# Section 4 with reading R12 of xyz_oracle.c.
+
+
+def xyz_abs(X, Y, L: int, M: int, kappa: float, seed: int) -> np.ndarray:
+    """Pairs with |Y^T(X_j o X_k)| / n >= kappa: the binary search with Y and
+    with -Y, united (Section 4 runs xyz on +-Y); (j, k, a) with a for +Y."""
+    X, Y, n, p = _check_xy(X, Y)
+    plus = xyz(X, Y, L, M, kappa, seed)
+    minus = xyz(X, (-Y).astype(np.int8), L, M, kappa, seed)
+    minus = minus.copy()
+    minus[:, 2] = n - minus[:, 2]
+    allp = {(int(j), int(k)): int(a) for j, k, a in minus}
+    allp.update({(int(j), int(k)): int(a) for j, k, a in plus})
+    return np.array([(j, k, allp[(j, k)]) for j, k in sorted(allp)], dtype=np.int32).reshape(-1, 3)
+
+
+def kkt_threshold(r, lam: float) -> int:
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    return int(_load().orc_kkt_threshold(_ptr(r), len(r), float(lam)))
+
+
+def kkt_brute(X, r, lam: float) -> tuple:
+    """KKT violators |r^T(X_j o X_k)| / n > lambda by the loop over all pairs
+    (R12): (j, k, a) triples and the signed integers 2S - Q."""
+    return _weighted_call(_load().orc_kkt_brute, X, r, float(lam))
+
+
+def kkt_xyz(X, r, L: int, M: int, lam: float, seed: int) -> tuple:
+    """The same check by the continuous-response search with +r and -r."""
+    return _weighted_call(_load().orc_kkt_xyz, X, r, int(L), int(M), float(lam), seed & (2**64 - 1))

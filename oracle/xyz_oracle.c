@@ -620,3 +620,122 @@ int64_t orc_brute_force_weighted(const int8_t *X, const double *Y, int64_t n, in
     free(q);
     return cnt;
 }
+
+/* -------------------------------------------- absolute value, Lasso screen */
+
+/* Section 4 runs the search with Y set to each of +r and -r to find the
+ * pairs with |r^T (X_j o X_k)| above a threshold.  The KKT check of
+ * Algorithm 3 (line 4) keeps the pairs with |r^T (X_j o X_k)| / n > lambda.
+ *
+ * Reading R12: with the fixed-point weights of R9 (q_i = floor(|r_i|
+ * 2^(24-e) + 1/2)), r^T (X_j o X_k) is taken as (2 S_jk - Q) 2^(e-24), so the
+ * strict test becomes the integer rule |2 S_jk - Q| >= t with
+ * t = floor(ldexp(lambda * (double)n, 24 - e)) + 1. */
+int64_t orc_kkt_threshold(const double *r, int64_t n, double lambda)
+{
+    double m = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double a = fabs(r[i]);
+        if (a > m)
+            m = a;
+    }
+    int e = 0;
+    frexp(m, &e);
+    return (int64_t)floor(ldexp(lambda * (double)n, 24 - e)) + 1;
+}
+
+/* The KKT violators V by the naive loop over all pairs, with R12: writes
+ * triples (j, k, a) and the signed integer 2 S - Q to `d`. */
+int64_t orc_kkt_brute(const int8_t *X, const double *r, int64_t n, int64_t p,
+                      double lambda, int32_t *out, int64_t *d, int64_t cap)
+{
+    int64_t *q = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int8_t *sgn = (int8_t *)malloc((size_t)n);
+    if (orc_quantize_y(r, n, q, sgn) != 0) {
+        free(q);
+        free(sgn);
+        return -1;
+    }
+    int64_t Q = 0;
+    for (int64_t i = 0; i < n; i++)
+        Q += q[i];
+    const int64_t t = orc_kkt_threshold(r, n, lambda);
+    int64_t cnt = 0;
+    for (int64_t j = 0; j < p; j++) {
+        for (int64_t k = j + 1; k < p; k++) {
+            int64_t S = 0;
+            int64_t a = orc_weighted_agree(X, sgn, q, n, j, k, &S);
+            int64_t v = 2 * S - Q;
+            if (v >= t || -v >= t) {
+                if (cnt < cap) {
+                    out[3 * cnt + 0] = (int32_t)j;
+                    out[3 * cnt + 1] = (int32_t)k;
+                    out[3 * cnt + 2] = (int32_t)a;
+                    d[cnt] = v;
+                }
+                cnt++;
+            }
+        }
+    }
+    free(sgn);
+    free(q);
+    return cnt;
+}
+
+/* The xyz form of the same check (Section 4): the continuous-response
+ * search with Y = +r and with Y = -r, each keeping sign * (2 S - Q) >= t,
+ * united; output as orc_kkt_brute, sorted by (j, k), each pair once. */
+int64_t orc_kkt_xyz(const int8_t *X, const double *r, int64_t n, int64_t p, int64_t L,
+                    int32_t M, double lambda, uint64_t seed, int32_t *out, int64_t *d, int64_t cap)
+{
+    int64_t *q = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int8_t *sgn = (int8_t *)malloc((size_t)n);
+    int8_t *neg = (int8_t *)malloc((size_t)n);
+    if (orc_quantize_y(r, n, q, sgn) != 0) {
+        free(q);
+        free(sgn);
+        free(neg);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; i++)
+        neg[i] = (int8_t)-sgn[i];
+    int64_t Q = 0;
+    for (int64_t i = 0; i < n; i++)
+        Q += q[i];
+    const int64_t t = orc_kkt_threshold(r, n, lambda);
+    int64_t *rows = (int64_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int64_t));
+    orc_vec found = {0, 0, 0};
+    orc_vec cand = {0, 0, 0};
+    for (int side = 0; side < 2; side++) {
+        const int8_t *s8 = side ? neg : sgn;
+        for (int64_t l = 0; l < L; l++) {
+            cand.n = 0;
+            orc_draw_rows_weighted(q, n, seed, l, M, rows);
+            int64_t ne = orc_rows_candidates(X, s8, n, p, rows, M, &cand);
+            for (int64_t e = 0; e < ne; e++) {
+                int32_t j = cand.v[e].j, k = cand.v[e].k;
+                int64_t S = 0;
+                int64_t a = orc_weighted_agree(X, sgn, q, n, j, k, &S);
+                int64_t v = 2 * S - Q;
+                if ((side ? -v : v) >= t)
+                    orc_vec_push(&found, j, k, (int32_t)a);
+            }
+        }
+    }
+    int64_t u = orc_sort_unique(found.v, found.n);
+    for (int64_t i = 0; i < u && i < cap; i++) {
+        out[3 * i + 0] = found.v[i].j;
+        out[3 * i + 1] = found.v[i].k;
+        out[3 * i + 2] = found.v[i].a;
+        int64_t S = 0;
+        orc_weighted_agree(X, sgn, q, n, found.v[i].j, found.v[i].k, &S);
+        d[i] = 2 * S - Q;
+    }
+    free(found.v);
+    free(cand.v);
+    free(rows);
+    free(neg);
+    free(sgn);
+    free(q);
+    return u;
+}

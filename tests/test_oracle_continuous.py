@@ -117,3 +117,44 @@ def test_weighted_search_is_subset_with_weighted_rows(orc):
           if j != k and np.array_equal(Xs[:, j], Zs[:, k])}
     one, _ = orc.xyz_weighted_range(X, Y, 3, 4, 7, -1.0, 5)
     assert {(int(j), int(k)) for j, k, _ in one} == eq
+
+
+def test_abs_search_is_union_of_signs(orc):
+    X, rng = _X(160, 500, 21)
+    Y = (X[:, 3] * X[:, 300]).astype(np.int8)
+    Y[:20] = -Y[:20]
+    Yn = (-(X[:, 40] * X[:, 41])).astype(np.int8)       # a negative interaction
+    Y[80:] = Yn[80:]
+    got = orc.xyz_abs(X, Y, 20, 5, 0.2, 3)
+    bf = orc.brute_force(X, Y, -1.0)                      # every pair with its a
+    n = 160
+    strong = {(int(j), int(k)): int(a) for j, k, a in bf if abs(2 * a - n) >= 0.2 * n}
+    for j, k, a in got:
+        assert strong[(int(j), int(k))] == int(a)
+    pairs = {(int(j), int(k)) for j, k, _ in got}
+    assert (40, 41) in pairs and (3, 300) in pairs
+    s = {(int(j), int(k)): (2 * int(a) - n) / n for j, k, a in got}
+    assert s[(40, 41)] < 0 < s[(3, 300)]
+
+
+def test_kkt_rule_matches_float_definition(orc):
+    X, rng = _X(120, 70, 22)
+    r = rng.normal(size=120) + 1.5 * X[:, 2] * X[:, 60] - 1.2 * X[:, 10] * X[:, 11]
+    r = r - r.mean()                                       # a centred residual
+    dots = (X.T.astype(np.float64) @ (X.astype(np.float64) * r[:, None])) / 120
+    for lam in (0.2, 0.4, 0.7):
+        got, d = orc.kkt_brute(X, r, lam)
+        want = [(j, k) for j in range(70) for k in range(j + 1, 70) if abs(dots[j, k]) > lam]
+        # the fixed-point rule agrees with the float definition except within
+        # 2^-24 max|r| n of the boundary (none here)
+        near = [abs(abs(dots[j, k]) - lam) for j in range(70) for k in range(j + 1, 70)]
+        assert min(near) > 1e-5
+        assert [tuple(v[:2]) for v in got] == want
+        _, e = np.frexp(np.abs(r).max())
+        assert np.allclose(d * 2.0 ** (int(e) - 24) / 120, [dots[j, k] for j, k, _ in got], atol=1e-5)
+    xs, dx = orc.kkt_xyz(X, r, 40, 4, 0.4, 9)
+    bf, db = orc.kkt_brute(X, r, 0.4)
+    bset = {(int(j), int(k)): int(v) for (j, k, _), v in zip(bf, db)}
+    for (j, k, _), v in zip(xs, dx):
+        assert bset[(int(j), int(k))] == int(v)
+    assert {(2, 60), (10, 11)} <= {(int(j), int(k)) for j, k, _ in xs}
