@@ -183,6 +183,27 @@ int xyz_search_batch(xyz_ctx *ctx, const int8_t *Ys, int32_t B, int32_t L, int32
 int xyz_search_batch_dev(xyz_ctx *ctx, const int8_t *dYs, int32_t B, int32_t L, int32_t M,
                          double kappa, uint64_t seed, xyz_pair **pairs, int64_t *offsets);
 
+/* Absolute-value search: the pairs with |Y^T(X_j o X_k)| / n >= kappa
+ * (|.| / ||Y||_1 for a real response), found as Section 4 does, by running
+ * the search with Y and with -Y (same rows, same seed) and uniting the two
+ * results.  Pairs are reported for +Y: agree counts the rows agreeing with
+ * Y and strength is signed (negative for the pairs found through -Y).  Each
+ * pair once, sorted by (j, k).  Arguments and errors as xyz_search. */
+int xyz_search_abs(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t seed, xyz_pair **pairs,
+                   int64_t *npairs);
+
+/* The interaction half of the KKT check of the Lasso active-set strategy
+ * (Section 4, Algorithm 3 line 4): with a real residual r (n doubles, e.g.
+ * Y - X_A beta_A - W_B theta_B, centred), the pairs with
+ * |r^T (X_j o X_k)| / n > lambda, searched with Y set to +r and to -r.  The
+ * context switches to the real response r (as xyz_set_y_real).  In the
+ * fixed-point form of xyz_set_y_real the test is |2 S - Q| >= t with
+ * t = floor(lambda * n * 2^(24 - e)) + 1.  Results: agree as for +r, and
+ * strength = r^T (X_j o X_k) / n from the fixed-point weights (signed).
+ * lambda >= 0 and finite, else XYZ_EINVAL. */
+int xyz_kkt_screen(xyz_ctx *ctx, const double *r, double lambda, int32_t L, int32_t M, uint64_t seed,
+                   xyz_pair **pairs, int64_t *npairs);
+
 /* Exhaustive screen: every pair j < k with (2a - n) >= kappa*n, i.e. I* of
  * eq. 1 under the >= reading -- the comparator the search is measured
  * against and the M = 0 case of Algorithm 2 (one empty key, every pair a

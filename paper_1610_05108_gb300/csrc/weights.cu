@@ -93,10 +93,11 @@ __global__ void inclusive_kernel(uint64_t *__restrict__ cdf, const uint64_t *__r
 }
 
 // Weighted strengths of the output pairs: one warp per pair recomputes the
-// weight sum S of its agreeing rows; strength = (2 S - Q) / Q.
+// weight sum S of its agreeing rows; strength = (2 S - Q) / Q, or
+// (2 S - Q) * scale when scale is set (the Lasso check reports r^T w / n).
 __global__ void weighted_strength_kernel(const uint32_t *__restrict__ Xc, int64_t Wp,
                                          const uint32_t *__restrict__ yb,
-                                         const uint32_t *__restrict__ planes, uint64_t Q,
+                                         const uint32_t *__restrict__ planes, uint64_t Q, double scale,
                                          PairOut *__restrict__ out, const uint32_t *__restrict__ nout)
 {
     const int lane = threadIdx.x & 31;
@@ -114,12 +115,34 @@ __global__ void weighted_strength_kernel(const uint32_t *__restrict__ Xc, int64_
         }
         for (int o = 16; o > 0; o >>= 1)
             S += __shfl_xor_sync(0xffffffffu, S, o);
-        if (lane == 0)
-            out[t].strength = (float)((double)(2 * S - (int64_t)Q) / (double)Q);
+        if (lane == 0) {
+            const double v = (double)(2 * S - (int64_t)Q);
+            out[t].strength = (float)(scale != 0.0 ? v * scale : v / (double)Q);
+        }
+    }
+}
+
+// Flip the response sign bits of the n valid rows (Y -> -Y); padding bits stay 1.
+__global__ void flip_kernel(uint32_t *__restrict__ yb, int64_t n, int64_t Wp)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < Wp; w += stride) {
+        const int64_t rows = n - 32 * w;
+        const uint32_t valid = rows >= 32 ? 0xFFFFFFFFu : (rows > 0 ? ((1u << rows) - 1u) : 0u);
+        yb[w] ^= valid;
     }
 }
 
 }  // namespace
+
+cudaError_t launch_flip_signs(const Packed &pk, cudaStream_t s, int64_t *launches)
+{
+    int64_t g = (pk.Wp + WT_THREADS - 1) / WT_THREADS;
+    g = g < 1 ? 1 : (g > 1024 ? 1024 : g);
+    flip_kernel<<<(unsigned)g, WT_THREADS, 0, s>>>(pk.yb, pk.n, pk.Wp);
+    *launches += 1;
+    return cudaGetLastError();
+}
 
 size_t weights_scan_bytes(int64_t n) { return scan_temp_bytes(n); }
 
@@ -155,7 +178,7 @@ cudaError_t launch_weighted_strengths(const Packed &pk, PairOut *out, const uint
     int64_t blocks = (cap * 32 + WT_THREADS - 1) / WT_THREADS;
     blocks = blocks > 4096 ? 4096 : (blocks < 1 ? 1 : blocks);
     weighted_strength_kernel<<<(unsigned)blocks, WT_THREADS, 0, s>>>(pk.Xc, pk.Wp, pk.yb, pk.planes,
-                                                                     pk.wtotal, out, nout);
+                                                                     pk.wtotal, pk.wscale, out, nout);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -96,6 +96,7 @@ struct xyz_ctx {
     // real response (Section 3.1): live weights and a staging set swapped in
     // once a new response has been checked
     DevBuf wq, wcdf, wplanes, wq2, wcdf2, wplanes2, wmeta, wscan, yreal;
+    int w_exp = 0;               // max|Y| = f 2^w_exp, f in [0.5, 1)
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
     int64_t rec_cap = 1 << 16;
     int64_t chunk_entries = (int64_t)1 << 25;
@@ -899,6 +900,9 @@ int xyz_set_y_real_dev(xyz_ctx *ctx, const double *dY)
     ctx->pk.cdf = (const uint64_t *)ctx->wcdf.ptr;
     ctx->pk.planes = (const uint32_t *)ctx->wplanes.ptr;
     ctx->pk.wtotal = host[2];
+    double maxabs = 0.0;
+    std::memcpy(&maxabs, &host[0], 8);
+    std::frexp(maxabs, &ctx->w_exp);
     return XYZ_OK;
 }
 
@@ -958,6 +962,7 @@ int xyz_search_range(xyz_ctx *ctx, int64_t l0, int64_t l1, int32_t M, double kap
     const int64_t amin = amin_rule(ctx->pk.n, kappa);
     int64_t nout = 0;
     ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;     // real response: 2S - Q >= kappa Q
+    ctx->pk.wscale = 0.0;
     if (amin > ctx->pk.n && !ctx->pk.cdf) {
         std::memset(&ctx->stats, 0, sizeof(ctx->stats));
         *pairs = nullptr;
@@ -1064,6 +1069,130 @@ int xyz_brute_force(xyz_ctx *ctx, double kappa, xyz_pair **pairs, int64_t *npair
         return XYZ_OK;
     }
     return fail(XYZ_ENOMEM, "result buffers kept overflowing");
+}
+
+namespace {
+
+// One search over runs [0, L) whose pass threshold is already on the context
+// (amin, or pk.wkq for a real response); results appended to `out`.
+int search_collect(xyz_ctx *c, int32_t L, int32_t M, int64_t amin, uint64_t seed, std::vector<xyz_pair> &out)
+{
+    int64_t nout = 0;
+    int rc = run_search(c, 0, L, M, amin, seed, &nout);
+    if (rc)
+        return rc;
+    const size_t at = out.size();
+    out.resize(at + (size_t)nout);
+    if (nout > 0) {
+        CU(cudaMemcpyAsync(out.data() + at, c->out.ptr, (size_t)nout * sizeof(xyz_pair), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return XYZ_OK;
+}
+
+// Both signs of the response (Section 4 runs xyz with Y set to +r and -r):
+// the second search runs on flipped sign bits; its pairs are reported for
+// +Y (agree -> n - agree, strength -> -strength) and united with the first
+// search's, each pair once, sorted by (j, k).
+int search_both_signs(xyz_ctx *c, int32_t L, int32_t M, int64_t amin_plus, int64_t amin_minus, uint64_t seed,
+                      xyz_pair **pairs, int64_t *npairs)
+{
+    std::vector<xyz_pair> plus, minus;
+    int rc = search_collect(c, L, M, amin_plus, seed, plus);
+    if (rc)
+        return rc;
+    int64_t launches = 0;
+    CU(launch_flip_signs(c->pk, c->stream, &launches));
+    rc = search_collect(c, L, M, amin_minus, seed, minus);
+    cudaError_t e = launch_flip_signs(c->pk, c->stream, &launches);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (rc)
+        return rc;
+    if (e != cudaSuccess)
+        return fail(XYZ_ECUDA, std::string("restoring the response signs: ") + cudaGetErrorString(e));
+    for (xyz_pair &q : minus) {
+        q.agree = (int32_t)c->pk.n - q.agree;
+        q.strength = -q.strength;
+    }
+    std::vector<xyz_pair> all;
+    all.reserve(plus.size() + minus.size());
+    size_t a = 0, b = 0;
+    auto less = [](const xyz_pair &x, const xyz_pair &y) { return x.j != y.j ? x.j < y.j : x.k < y.k; };
+    while (a < plus.size() || b < minus.size()) {
+        if (b == minus.size() || (a < plus.size() && less(plus[a], minus[b])))
+            all.push_back(plus[a++]);
+        else if (a == plus.size() || less(minus[b], plus[a]))
+            all.push_back(minus[b++]);
+        else {
+            all.push_back(plus[a++]);      // in both (kappa <= 0): the +Y result
+            ++b;
+        }
+    }
+    xyz_pair *host = nullptr;
+    if (!all.empty()) {
+        host = (xyz_pair *)std::malloc(all.size() * sizeof(xyz_pair));
+        if (!host)
+            return fail(XYZ_ENOMEM, "host allocation of results failed");
+        std::memcpy(host, all.data(), all.size() * sizeof(xyz_pair));
+    }
+    *pairs = host;
+    *npairs = (int64_t)all.size();
+    return XYZ_OK;
+}
+
+}  // namespace
+
+int xyz_search_abs(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t seed, xyz_pair **pairs,
+                   int64_t *npairs)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!pairs || !npairs)
+        return fail(XYZ_EINVAL, "null output pointer");
+    if (L < 1)
+        return fail(XYZ_EINVAL, "L must be >= 1");
+    if ((rc = check_M(M)) || (rc = check_kappa(kappa)))
+        return rc;
+    if (!ctx->owns_packed)
+        return fail(XYZ_EINVAL, "context does not own its response");
+    const int64_t amin = amin_rule(ctx->pk.n, kappa);
+    ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;
+    ctx->pk.wscale = 0.0;
+    *pairs = nullptr;
+    *npairs = 0;
+    if (amin > ctx->pk.n && !ctx->pk.cdf)
+        return XYZ_OK;
+    return search_both_signs(ctx, L, M, amin, amin, seed, pairs, npairs);
+}
+
+int xyz_kkt_screen(xyz_ctx *ctx, const double *r, double lambda, int32_t L, int32_t M, uint64_t seed,
+                   xyz_pair **pairs, int64_t *npairs)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!pairs || !npairs || !r)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    if (L < 1)
+        return fail(XYZ_EINVAL, "L must be >= 1");
+    if (!(lambda >= 0.0) || !std::isfinite(lambda))
+        return fail(XYZ_EINVAL, "lambda must be finite and >= 0");
+    if ((rc = check_M(M)))
+        return rc;
+    if ((rc = xyz_set_y_real(ctx, r)))
+        return rc;
+    // |r^T (X_j o X_k)| / n > lambda as the integer rule |2S - Q| >= t
+    const double t = std::floor(std::ldexp(lambda * (double)ctx->pk.n, 24 - ctx->w_exp)) + 1.0;
+    ctx->pk.wkq = t;
+    ctx->pk.wscale = std::ldexp(1.0, ctx->w_exp - 24) / (double)ctx->pk.n;
+    *pairs = nullptr;
+    *npairs = 0;
+    rc = search_both_signs(ctx, L, M, 0, 0, seed, pairs, npairs);
+    ctx->pk.wscale = 0.0;
+    return rc;
 }
 
 int xyz_search(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t seed, xyz_pair **pairs,

@@ -47,6 +47,7 @@ struct Packed {
     uint64_t wtotal = 0;               // sum of the weights, cdf[n - 1]
     const uint32_t *planes = nullptr;  // [Wp][XYZ_WPLANES] bit planes of the weights per word
     double wkq = 0.0;                  // kappa * wtotal of the current search
+    double wscale = 0.0;               // strength = (2S - Q) * wscale (0: divide by Q)
 };
 
 constexpr int XYZ_WPLANES = 25;        // weights are integers in [0, 2^24]
@@ -184,6 +185,8 @@ cudaError_t launch_prepare_weights(const double *dY, int64_t n, int64_t Wp, uint
                                    uint32_t *planes, uint64_t *cdf, uint64_t *total,
                                    unsigned long long *maxbits, int *bad, void *scan_tmp, cudaStream_t s,
                                    int64_t *launches);
+// Y -> -Y on the response sign bits of the valid rows
+cudaError_t launch_flip_signs(const Packed &pk, cudaStream_t s, int64_t *launches);
 // weighted strengths (2 S - Q) / Q of the first *nout output pairs
 cudaError_t launch_weighted_strengths(const Packed &pk, PairOut *out, const uint32_t *nout, int64_t cap,
                                       cudaStream_t s, int64_t *launches);

@@ -73,6 +73,8 @@ SIGNATURES = {
     "xyz_search_batch": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, _dbl, _u64, _p, _p]),
     "xyz_search_batch_dev": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, _dbl, _u64, _p, _p]),
     "xyz_brute_force": (ctypes.c_int, [_p, _dbl, _p, _p]),
+    "xyz_search_abs": (ctypes.c_int, [_p, _i32, _i32, _dbl, _u64, _p, _p]),
+    "xyz_kkt_screen": (ctypes.c_int, [_p, _p, _dbl, _i32, _i32, _u64, _p, _p]),
     "xyz_free_pairs": (None, [_p]),
     "xyz_free": (None, [_p]),
     "xyz_get_stats": (ctypes.c_int, [_p, _p]),
@@ -253,6 +255,25 @@ class Context:
         cnt = ctypes.c_int64(0)
         _check(load().xyz_search_range(self.handle, int(l0), int(l1), int(M), float(kappa),
                                        seed & (2**64 - 1), ctypes.byref(out), ctypes.byref(cnt)))
+        return _pairs_to_numpy(out, cnt.value)
+
+    def search_abs(self, L: int, M: int, kappa: float, seed: int) -> np.ndarray:
+        """Pairs with |Y^T(X_j o X_k)| / n >= kappa (searches with +Y and -Y)."""
+        out = ctypes.c_void_p()
+        cnt = ctypes.c_int64(0)
+        _check(load().xyz_search_abs(self.handle, int(L), int(M), float(kappa), seed & (2**64 - 1),
+                                     ctypes.byref(out), ctypes.byref(cnt)))
+        return _pairs_to_numpy(out, cnt.value)
+
+    def kkt_screen(self, r: np.ndarray, lam: float, L: int, M: int, seed: int) -> np.ndarray:
+        """Lasso KKT check: pairs with |r^T(X_j o X_k)| / n > lam."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        if r.shape != (self.n,):
+            raise ValueError("r must have shape (n,)")
+        out = ctypes.c_void_p()
+        cnt = ctypes.c_int64(0)
+        _check(load().xyz_kkt_screen(self.handle, _ptr(r), float(lam), int(L), int(M), seed & (2**64 - 1),
+                                     ctypes.byref(out), ctypes.byref(cnt)))
         return _pairs_to_numpy(out, cnt.value)
 
     def brute_force(self, kappa: float) -> np.ndarray:

@@ -122,3 +122,35 @@ def test_unusable_real_response(xyz):
             ctx.brute_force(0.1)
         with pytest.raises(xyz.XyzError):
             ctx.search_batch(np.ones((2, 64), np.int8), 5, 6, 0.1, 1)
+
+
+def test_abs_search_matches_oracle(xyz, orc):
+    X, rng = _X(160, 500, 21)
+    Y = (X[:, 3] * X[:, 300]).astype(np.int8)
+    Y[:20] = -Y[:20]
+    Y[80:] = (-(X[80:, 40] * X[80:, 41])).astype(np.int8)
+    with xyz.create(X, Y) as ctx:
+        got = ctx.search_abs(20, 5, 0.2, 3)
+        plain = ctx.search(20, 5, 0.2, 3)              # signs restored afterwards
+    want = orc.xyz_abs(X, Y, 20, 5, 0.2, 3)
+    assert np.array_equal(_arr(got), want)
+    assert np.allclose(got["strength"], (2.0 * want[:, 2] - 160) / 160)
+    assert np.array_equal(_arr(plain), orc.xyz(X, Y, 20, 5, 0.2, 3))
+    s = dict(zip(zip(got["j"].tolist(), got["k"].tolist()), got["strength"].tolist()))
+    assert s[(40, 41)] < 0 < s[(3, 300)]
+
+
+def test_kkt_screen_matches_oracle(xyz, orc):
+    X, rng = _X(300, 900, 22)
+    r = rng.normal(size=300) + 1.5 * X[:, 2] * X[:, 600] - 1.2 * X[:, 10] * X[:, 11]
+    r = r - r.mean()
+    with xyz.create(X, np.ones(300, np.int8)) as ctx:
+        for lam in (0.5, 0.8):
+            got = ctx.kkt_screen(r, lam, 40, 6, 9)
+            want, d = orc.kkt_xyz(X, r, 40, 6, lam, 9)
+            assert np.array_equal(_arr(got), want), lam
+            _, e = np.frexp(np.abs(r).max())
+            assert np.allclose(got["strength"], d * 2.0 ** (int(e) - 24) / 300, atol=1e-6)
+            assert {(2, 600), (10, 11)} <= set(zip(got["j"].tolist(), got["k"].tolist()))
+        with pytest.raises(xyz.XyzError):
+            ctx.kkt_screen(r, -1.0, 10, 6, 1)
