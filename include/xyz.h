@@ -204,6 +204,32 @@ int xyz_search_abs(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t se
 int xyz_kkt_screen(xyz_ctx *ctx, const double *r, double lambda, int32_t L, int32_t M, uint64_t seed,
                    xyz_pair **pairs, int64_t *npairs);
 
+/* Operating-point autotuner: eq. bestM chooses M from the paper's cost model
+ * (Section 2.3); this measures this implementation's cost instead.  For
+ * each M in [M_lo, M_hi] it takes L = xyz_runs_for_recall(gamma^M, recall)
+ * (eq. L_choice), times two short searches on the device (trial_runs and a
+ * quarter of it; CUDA events on the context's stream), fits time = a + b*runs
+ * and predicts the full search; *M_best / *L_best / *ms_best get the fastest.
+ * table (optional, 3*(M_hi - M_lo + 1) doubles) gets (M, L, predicted ms)
+ * rows, ms < 0 where L is out of range.  Searches on the context's data;
+ * results of later searches never depend on it.  0 < gamma < 1,
+ * 0 < recall < 1, 1 <= M_lo <= M_hi <= 64, trial_runs >= 8, else XYZ_EINVAL. */
+int xyz_autotune_M(xyz_ctx *ctx, double kappa, double gamma, double recall, int32_t M_lo, int32_t M_hi,
+                   uint64_t seed, int64_t trial_runs, int32_t *M_best, int64_t *L_best, double *ms_best,
+                   double *table);
+
+/* Many independent searches at once, each on its own context (instances of
+ * different n and p): search i is xyz_search(ctxs[i], L[i], M[i],
+ * kappa[i], seed[i]) and its result is identical to that call.  The launch
+ * groups of all searches are captured into one CUDA graph, forked over the
+ * contexts' streams so that they run concurrently, and launched once; each
+ * search then finishes (spilled runs, union) on its own stream.  Results go
+ * to one array: search i owns (*pairs)[offsets[i] .. offsets[i+1]); offsets
+ * has count + 1 entries.  Contexts must be distinct, on one device, with
+ * their own streams (XYZ_EINVAL otherwise). */
+int xyz_search_many(xyz_ctx **ctxs, int32_t count, const int32_t *L, const int32_t *M, const double *kappa,
+                    const uint64_t *seed, xyz_pair **pairs, int64_t *offsets);
+
 /* Exhaustive screen: every pair j < k with (2a - n) >= kappa*n, i.e. I* of
  * eq. 1 under the >= reading -- the comparator the search is measured
  * against and the M = 0 case of Algorithm 2 (one empty key, every pair a

@@ -394,8 +394,17 @@ uint64_t *ctr_total2(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c
 // (response, j, k), each once) go to the device `out` buffer, and their
 // responses to `resp` when B > 1; the count goes to *nout_host.  An
 // attempt that overflowed a buffer is redone once the buffer has grown.
+// Phases, so that the launch groups of several searches can be captured
+// into one CUDA graph: SP_PREPARE sizes the workspace only; SP_ENQUEUE
+// enqueues the launch groups (no host synchronisation, no allocation, spills
+// left for the end); SP_FINISH does the rest (spills, union) after they ran,
+// and returns SP_RERUN when a buffer overflowed so the caller redoes the
+// search with SP_ALL.
+enum SearchPhase { SP_ALL = 0, SP_ENQUEUE = 1, SP_FINISH = 2, SP_PREPARE = 3 };
+constexpr int SP_RERUN = 100;
+
 int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t l1, int M,
-                     int64_t amin, uint64_t seed, int64_t *nout_host)
+                     int64_t amin, uint64_t seed, int64_t *nout_host, int phase = SP_ALL)
 {
     const int64_t runs = l1 - l0;
     const int64_t p = c->pk.p;
@@ -408,14 +417,19 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
         return fail(XYZ_EINVAL, "too many runs x responses for one search");
     int rc;
     for (int attempt = 0; attempt < 8; ++attempt) {
-        if ((rc = ensure_search_ws(c, pl, B, runs)) || (rc = ensure_records(c, B)))
-            return rc;
+        if (phase != SP_FINISH) {
+            if ((rc = ensure_search_ws(c, pl, B, runs)) || (rc = ensure_records(c, B)))
+                return rc;
+            if (phase == SP_PREPARE)
+                return XYZ_OK;
+        }
         int64_t launches = 0;
-        Timer tm(c->timing, c->stream, &launches);
+        Timer tm(c->timing && phase == SP_ALL, c->stream, &launches);
         xyz_stats st;
         std::memset(&st, 0, sizeof(st));
-        CU(cudaMemsetAsync(c->counters.ptr, 0, 64, c->stream));
-        int64_t chunks = 0;
+        if (phase != SP_FINISH)
+            CU(cudaMemsetAsync(c->counters.ptr, 0, 64, c->stream));
+        int64_t chunks = phase == SP_FINISH ? (runs + pl.R - 1) / pl.R : 0;
         int64_t surv_total = 0;
         int key_bits_max = 0;
         bool redo = false;
@@ -485,9 +499,10 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                 CU(launch_seg_reset((uint32_t *)c->seg_count.ptr, c->stream, &launches));
                 return XYZ_OK;
             };
-            CU(launch_seg_reset((uint32_t *)c->seg_count.ptr, c->stream, &launches));
+            if (phase != SP_FINISH)
+                CU(launch_seg_reset((uint32_t *)c->seg_count.ptr, c->stream, &launches));
             int64_t since_flush = 0;
-            for (int64_t g0 = l0; g0 < l1 && !redo; g0 += pl.R) {
+            for (int64_t g0 = l0; g0 < l1 && !redo && phase != SP_FINISH; g0 += pl.R) {
                 const int64_t Rc = (l1 - g0) < pl.R ? (l1 - g0) : pl.R;
                 ++chunks;
                 CU(cudaMemsetAsync(ctr_u32(c), 0, 8, c->stream));   // buckets, members
@@ -514,20 +529,25 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches,
                                  B > 1 ? ybs : nullptr, ctr_sovf(c)));
                 tm.end();
-                if (c->spill_flush && ++since_flush == c->spill_flush && g0 + pl.R < l1) {
+                if (phase == SP_ALL && c->spill_flush && ++since_flush == c->spill_flush && g0 + pl.R < l1) {
                     since_flush = 0;
                     if ((rc = flush_spills()))
                         return rc;
                 }
             }
+            if (phase == SP_ENQUEUE)
+                return XYZ_OK;
             if (redo)
                 continue;
             if ((rc = flush_spills()))
                 return rc;
-            if (redo)
+            if (redo) {
+                if (phase == SP_FINISH)
+                    return SP_RERUN;
                 continue;
+            }
         } else {
-            for (int64_t g0 = l0; g0 < l1; g0 += pl.R) {
+            for (int64_t g0 = l0; g0 < l1 && phase != SP_FINISH; g0 += pl.R) {
                 const int64_t Rc = (l1 - g0) < pl.R ? (l1 - g0) : pl.R;
                 const int64_t Nc = Rc * p;
                 const int rb = ceil_log2(Rc);
@@ -606,6 +626,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                 tm.end();
             }
         }
+        if (phase == SP_ENQUEUE)
+            return XYZ_OK;
         // record count -> host
         uint32_t nrec = 0;
         uint64_t cand = 0;
@@ -623,6 +645,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
             if (want > (int64_t)0xF0000000LL)
                 return fail(XYZ_ENOMEM, "too many passing pairs for one search");
             c->rec_cap = want;
+            if (phase == SP_FINISH)
+                return SP_RERUN;
             continue;
         }
         tm.begin(ST_DEDUP);
@@ -1193,6 +1217,204 @@ int xyz_kkt_screen(xyz_ctx *ctx, const double *r, double lambda, int32_t L, int3
     rc = search_both_signs(ctx, L, M, 0, 0, seed, pairs, npairs);
     ctx->pk.wscale = 0.0;
     return rc;
+}
+
+int xyz_autotune_M(xyz_ctx *ctx, double kappa, double gamma, double recall, int32_t M_lo, int32_t M_hi,
+                   uint64_t seed, int64_t trial_runs, int32_t *M_best, int64_t *L_best, double *ms_best,
+                   double *table)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!M_best || !L_best || !ms_best)
+        return fail(XYZ_EINVAL, "null output pointer");
+    if ((rc = check_kappa(kappa)))
+        return rc;
+    if (!(gamma > 0.0 && gamma < 1.0) || !(recall > 0.0 && recall < 1.0))
+        return fail(XYZ_EINVAL, "need 0 < gamma < 1 and 0 < recall < 1");
+    if (M_lo < 1 || M_hi < M_lo || M_hi > XYZ_MAX_M || trial_runs < 8)
+        return fail(XYZ_EINVAL, "need 1 <= M_lo <= M_hi <= 64 and trial_runs >= 8");
+    const int64_t amin = amin_rule(ctx->pk.n, kappa);
+    ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;
+    ctx->pk.wscale = 0.0;
+    const bool timing = ctx->timing;
+    ctx->timing = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = -1.0;
+    int32_t bestM = 0;
+    int64_t bestL = 0;
+    for (int32_t M = M_lo; M <= M_hi; ++M) {
+        const int64_t L = xyz_runs_for_recall(std::pow(gamma, (double)M), recall);
+        double pred = -1.0;
+        if (L > 0 && L < ((int64_t)1 << 40)) {
+            // time on the device: a + b * runs from two trial lengths
+            const int64_t r2 = L < trial_runs ? L : trial_runs;
+            const int64_t r1 = r2 / 4 > 0 ? r2 / 4 : 1;
+            int64_t nout = 0;
+            double t[2] = {0.0, 0.0};
+            const int64_t rr[2] = {r1, r2};
+            if ((rc = run_search(ctx, 0, r1, M, amin, seed, &nout)))      // warm-up: workspace growth
+                break;
+            for (int i = 0; i < 2 && !rc; ++i) {
+                cudaEventRecord(e0, ctx->stream);
+                rc = run_search(ctx, 0, rr[i], M, amin, seed + 1 + (uint64_t)i, &nout);
+                cudaEventRecord(e1, ctx->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t[i] = ms;
+            }
+            if (rc)
+                break;
+            if (L <= trial_runs) {
+                pred = t[1];
+            } else {
+                const double b = r2 > r1 ? (t[1] - t[0]) / (double)(r2 - r1) : t[1] / (double)r2;
+                const double a = t[1] - b * (double)r2;
+                pred = (a > 0.0 ? a : 0.0) + (b > 0.0 ? b : t[1] / (double)r2) * (double)L;
+            }
+            if (best < 0.0 || pred < best) {
+                best = pred;
+                bestM = M;
+                bestL = L;
+            }
+        }
+        if (table) {
+            table[3 * (M - M_lo) + 0] = (double)M;
+            table[3 * (M - M_lo) + 1] = (double)L;
+            table[3 * (M - M_lo) + 2] = pred;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->timing = timing;
+    if (rc)
+        return rc;
+    if (best < 0.0)
+        return fail(XYZ_EINVAL, "no M in the range reaches the recall with fewer than 2^40 runs");
+    *M_best = bestM;
+    *L_best = bestL;
+    *ms_best = best;
+    return XYZ_OK;
+}
+
+int xyz_search_many(xyz_ctx **ctxs, int32_t count, const int32_t *L, const int32_t *M, const double *kappa,
+                    const uint64_t *seed, xyz_pair **pairs, int64_t *offsets)
+{
+    if (!ctxs || !L || !M || !kappa || !seed || !pairs || !offsets || count < 1)
+        return fail(XYZ_EINVAL, "null pointer argument or count < 1");
+    int rc;
+    std::vector<int64_t> amin((size_t)count);
+    std::vector<char> live((size_t)count, 0);
+    for (int32_t i = 0; i < count; ++i) {
+        if ((rc = check_ctx(ctxs[i])))
+            return rc;
+        if (L[i] < 1 || (rc = check_M(M[i])) || (rc = check_kappa(kappa[i])))
+            return rc ? rc : fail(XYZ_EINVAL, "L must be >= 1");
+        for (int32_t j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i])
+                return fail(XYZ_EINVAL, "each search needs its own context");
+        if (ctxs[i]->device != ctxs[0]->device || !ctxs[i]->stream)
+            return fail(XYZ_EINVAL, "contexts must share a device and own non-default streams");
+        amin[(size_t)i] = amin_rule(ctxs[i]->pk.n, kappa[i]);
+        ctxs[i]->pk.wkq = kappa[i] * (double)ctxs[i]->pk.wtotal;
+        ctxs[i]->pk.wscale = 0.0;
+        live[(size_t)i] = amin[(size_t)i] <= ctxs[i]->pk.n || ctxs[i]->pk.cdf;
+    }
+    // 1. workspace of every search, before any capture
+    int64_t nout = 0;
+    for (int32_t i = 0; i < count; ++i)
+        if (live[(size_t)i] &&
+            (rc = run_search_multi(ctxs[i], ctxs[i]->pk.yb, 1, 0, L[i], M[i], amin[(size_t)i], seed[i], &nout,
+                                   SP_PREPARE)))
+            return rc;
+    // 2. the launch groups of all searches, one stream each, captured into
+    //    one graph that forks from and joins to a capture stream
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev((size_t)count + 1, nullptr);
+    auto cleanup = [&]() {
+        if (exec)
+            cudaGraphExecDestroy(exec);
+        if (graph)
+            cudaGraphDestroy(graph);
+        for (cudaEvent_t e : ev)
+            if (e)
+                cudaEventDestroy(e);
+        if (cs)
+            cudaStreamDestroy(cs);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(ev[0], cs);
+    rc = XYZ_OK;
+    for (int32_t i = 0; i < count && e == cudaSuccess && !rc; ++i) {
+        if (!live[(size_t)i])
+            continue;
+        e = cudaStreamWaitEvent(ctxs[i]->stream, ev[0], 0);
+        if (e == cudaSuccess)
+            rc = run_search_multi(ctxs[i], ctxs[i]->pk.yb, 1, 0, L[i], M[i], amin[(size_t)i], seed[i], &nout,
+                                  SP_ENQUEUE);
+        if (e == cudaSuccess && !rc)
+            e = cudaEventRecord(ev[(size_t)i + 1], ctxs[i]->stream);
+        if (e == cudaSuccess && !rc)
+            e = cudaStreamWaitEvent(cs, ev[(size_t)i + 1], 0);
+    }
+    cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess)
+        e = ec;
+    if (e == cudaSuccess && !rc)
+        e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess && !rc)
+        e = cudaGraphLaunch(exec, cs);
+    if (e == cudaSuccess && !rc)
+        e = cudaStreamSynchronize(cs);
+    cleanup();
+    if (rc)
+        return rc;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(XYZ_ECUDA, std::string("graph of launch groups: ") + cudaGetErrorString(e));
+    }
+    // 3. per search: spills and union (a search whose buffers overflowed is
+    //    redone on its own), results in order
+    std::vector<xyz_pair> acc;
+    offsets[0] = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        xyz_ctx *c = ctxs[i];
+        int64_t no = 0;
+        if (live[(size_t)i]) {
+            rc = run_search_multi(c, c->pk.yb, 1, 0, L[i], M[i], amin[(size_t)i], seed[i], &no, SP_FINISH);
+            if (rc == SP_RERUN)
+                rc = run_search_multi(c, c->pk.yb, 1, 0, L[i], M[i], amin[(size_t)i], seed[i], &no, SP_ALL);
+            if (rc)
+                return rc;
+        }
+        const size_t at = acc.size();
+        acc.resize(at + (size_t)no);
+        if (no > 0) {
+            CU(cudaMemcpyAsync(acc.data() + at, c->out.ptr, (size_t)no * sizeof(xyz_pair), cudaMemcpyDeviceToHost,
+                               c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+        }
+        offsets[i + 1] = offsets[i] + no;
+    }
+    xyz_pair *host = nullptr;
+    if (!acc.empty()) {
+        host = (xyz_pair *)std::malloc(acc.size() * sizeof(xyz_pair));
+        if (!host)
+            return fail(XYZ_ENOMEM, "host allocation of results failed");
+        std::memcpy(host, acc.data(), acc.size() * sizeof(xyz_pair));
+    }
+    *pairs = host;
+    return XYZ_OK;
 }
 
 int xyz_search(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t seed, xyz_pair **pairs,

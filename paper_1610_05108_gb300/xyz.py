@@ -74,6 +74,8 @@ SIGNATURES = {
     "xyz_search_batch_dev": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, _dbl, _u64, _p, _p]),
     "xyz_brute_force": (ctypes.c_int, [_p, _dbl, _p, _p]),
     "xyz_search_abs": (ctypes.c_int, [_p, _i32, _i32, _dbl, _u64, _p, _p]),
+    "xyz_search_many": (ctypes.c_int, [_p, _i32, _p, _p, _p, _p, _p, _p]),
+    "xyz_autotune_M": (ctypes.c_int, [_p, _dbl, _dbl, _dbl, _i32, _i32, _u64, _i64, _p, _p, _p, _p]),
     "xyz_kkt_screen": (ctypes.c_int, [_p, _p, _dbl, _i32, _i32, _u64, _p, _p]),
     "xyz_free_pairs": (None, [_p]),
     "xyz_free": (None, [_p]),
@@ -257,6 +259,20 @@ class Context:
                                        seed & (2**64 - 1), ctypes.byref(out), ctypes.byref(cnt)))
         return _pairs_to_numpy(out, cnt.value)
 
+    def autotune_M(self, kappa: float, gamma: float, recall: float, M_lo: int, M_hi: int, seed: int = 1,
+                   trial_runs: int = 2048):
+        """(M, L, predicted ms, table) with the fastest measured search that
+        reaches `recall` for a pair of strength gamma (interaction strength
+        a/n, eq. def_gamma)."""
+        Mb = ctypes.c_int32(0)
+        Lb = ctypes.c_int64(0)
+        ms = ctypes.c_double(0)
+        table = np.zeros((M_hi - M_lo + 1, 3), dtype=np.float64)
+        _check(load().xyz_autotune_M(self.handle, float(kappa), float(gamma), float(recall), int(M_lo),
+                                     int(M_hi), seed & (2**64 - 1), int(trial_runs), ctypes.byref(Mb),
+                                     ctypes.byref(Lb), ctypes.byref(ms), _ptr(table)))
+        return Mb.value, Lb.value, ms.value, table
+
     def search_abs(self, L: int, M: int, kappa: float, seed: int) -> np.ndarray:
         """Pairs with |Y^T(X_j o X_k)| / n >= kappa (searches with +Y and -Y)."""
         out = ctypes.c_void_p()
@@ -359,6 +375,23 @@ class Context:
 
 def create(X: np.ndarray, Y: np.ndarray) -> Context:
     return Context.from_host(X, Y)
+
+
+def search_many(ctxs, L, M, kappa, seed) -> list:
+    """One search per context (sequences of equal length), launched as one
+    CUDA graph; list of per-search results."""
+    k = len(ctxs)
+    handles = (ctypes.c_void_p * k)(*[c.handle.value for c in ctxs])
+    La = np.ascontiguousarray(L, dtype=np.int32)
+    Ma = np.ascontiguousarray(M, dtype=np.int32)
+    ka = np.ascontiguousarray(kappa, dtype=np.float64)
+    sa = np.ascontiguousarray([int(v) & (2**64 - 1) for v in seed], dtype=np.uint64)
+    offs = np.zeros(k + 1, dtype=np.int64)
+    out = ctypes.c_void_p()
+    _check(load().xyz_search_many(ctypes.cast(handles, ctypes.c_void_p), k, _ptr(La), _ptr(Ma), _ptr(ka),
+                                  _ptr(sa), ctypes.byref(out), _ptr(offs)))
+    allp = _pairs_to_numpy(out, int(offs[-1]))
+    return [allp[offs[i]:offs[i + 1]].copy() for i in range(k)]
 
 
 class Server:

@@ -110,3 +110,22 @@ def test_batch_gwas_many_responses(xyz, orc):
     for b in (0, 23):
         res = got[b]
         assert np.array_equal(res["agree"], orc.agree_pairs(d.X, Ys[b], res["j"], res["k"]))
+
+
+def test_autotune_M_picks_a_measured_point(xyz):
+    X, rng = _rand(300, 4000, 41)
+    Y = (X[:, 10] * X[:, 20]).astype(np.int8)
+    Y[:30] = -Y[:30]
+    with xyz.create(X, Y) as ctx:
+        before = ctx.search(200, 12, 0.3, 9)
+        M, L, ms, table = ctx.autotune_M(0.3, 0.9, 0.95, 8, 14, seed=3, trial_runs=256)
+        after = ctx.search(200, 12, 0.3, 9)
+        assert np.array_equal(before, after)            # tuning leaves no trace in results
+        assert 8 <= M <= 14 and ms > 0
+        assert L == xyz.runs_for_recall(0.9 ** M, 0.95)
+        assert list(table[:, 0]) == list(range(8, 15))
+        assert table[M - 8, 2] == ms == min(t for t in table[:, 2] if t > 0)
+        found = ctx.search(3 * L, M, 0.3, 5)
+        assert (10, 20) in set(zip(found["j"].tolist(), found["k"].tolist()))
+        with pytest.raises(xyz.XyzError):
+            ctx.autotune_M(0.3, 1.5, 0.95, 8, 14)
