@@ -354,6 +354,7 @@ def autotuned_leg(args, ctx, stream, d, kappa, M_rule, targets, xyz, torch, hits
     t0 = time.perf_counter()
     M, L, pred, table = ctx.autotune_M(kappa, g_min, 0.95, max(1, M_rule - 4), min(31, M_rule + 2), seed=77)
     tune_s = time.perf_counter() - t0
+    ctx.search(L, M, kappa, 5_999_999)              # warm-up at the chosen point
     ms, found = [], []
     for s in range(args.steps):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -365,7 +366,7 @@ def autotuned_leg(args, ctx, stream, d, kappa, M_rule, targets, xyz, torch, hits
         ms.append(e0.elapsed_time(e1))
         found.append(hits(res))
     t = float(np.mean(ms))
-    return {"M": M, "L": L, "ms_per_step": round(t, 3), "predicted_ms": round(pred, 3),
+    return {"M": M, "L": L, "ms_per_step": round(t, 3), "tuner_ms": round(pred, 3),
             "value": d.p * (d.p - 1) // 2 / (t / 1e3), "unit": UNIT,
             "recall_measured": round(float(np.mean(found)) / max(1, len(targets)), 4),
             "eta_min": round(xyz.eta(g_min, M, L), 4), "tuning_s": round(tune_s, 3),
@@ -533,6 +534,7 @@ def batch_arm(args):
         plain.append(ctx.search(L, M, kappa, seed))
     t_plain = time.perf_counter() - t0
     ctx.close()
+    inst = instances_leg(args, xyz, torch) if args.batch_instances > 0 else None
     same = all(np.array_equal(a, b) for a, b in zip(got, plain))
     found = sum(1 for b in range(B) for pr in targets[b]
                 if any((int(j), int(k)) == tuple(pr) for j, k in zip(got[b]["j"], got[b]["k"])))
@@ -546,11 +548,53 @@ def batch_arm(args):
            "speedup_vs_plain": round(t_plain / t_batch, 3), "identical_to_plain": bool(same),
            "recall": {"found": found, "targets": ntarget,
                       "expected_min_eta": round(xyz.eta(g_min, M, L), 4)},
+           "instances": inst,
            "config": {"workload": f"one SNP-shaped X n={n} p={p} with {B} responses x 3 planted pairs "
                                   f"(strength U[0.45,0.55] before scaling, balanced Y)",
                       "n": n, "p": p, "B": B, "M": M, "L": L, "kappa": kappa,
                       "timing": "host wall clock around the whole call, results on the host"}}
     print(json.dumps(out), flush=True)
+
+
+def instances_leg(args, xyz, torch):
+    """Independent instances of log-uniform n in [500, 8000] and p in
+    [1e4, 5e5] (i.i.d. X, one planted pair of strength 0.8 each, M from
+    gamma0 = 0.55, L for 95% recall): one search after another against all
+    of them launched as one CUDA graph (xyz_search_many)."""
+    from paper_1610_05108_gb300 import synth
+    sizes = synth.instance_sizes(args.batch_instances, 44)
+    rng = np.random.default_rng(45)
+    ctxs, L, M, kap, seeds, pairs = [], [], [], [], [], 0
+    for i, (n, p) in enumerate(sizes):
+        X = np.asfortranarray((rng.integers(0, 2, size=(n, p), dtype=np.int8) * 2 - 1).astype(np.int8))
+        Y = (X[:, 0] * X[:, 1]).astype(np.int8)
+        Y[rng.choice(n, size=n // 10, replace=False)] *= -1
+        ctxs.append(xyz.create(X, Y))
+        m = xyz.M_for_gamma0(p, 0.55)
+        M.append(m)
+        L.append(xyz.runs_for_recall(0.9 ** m, 0.95))
+        kap.append(0.6)
+        seeds.append(1000 + i)
+        pairs += p * (p - 1) // 2
+        del X
+    for c, l_, m_, k_, s_ in zip(ctxs, L, M, kap, seeds):       # warm-up
+        c.search(l_, m_, k_, s_)
+    xyz.search_many(ctxs, L, M, kap, seeds)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    alone = [c.search(l_, m_, k_, s_) for c, l_, m_, k_, s_ in zip(ctxs, L, M, kap, seeds)]
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    many = xyz.search_many(ctxs, L, M, kap, seeds)
+    t_many = time.perf_counter() - t0
+    found = sum(int((0, 1) in set(zip(r["j"].tolist(), r["k"].tolist()))) for r in many)
+    for c in ctxs:
+        c.close()
+    return {"count": len(sizes), "sizes": [list(x) for x in sizes], "M": M, "L": L,
+            "sequential_s": round(t_seq, 4), "graph_s": round(t_many, 4),
+            "speedup": round(t_seq / t_many, 3), "value_graph": pairs / t_many, "unit": UNIT,
+            "identical": all(np.array_equal(a, b) for a, b in zip(alone, many)),
+            "planted_found": found}
 
 
 # ---------------------------------------------------------- serve pattern
@@ -814,6 +858,7 @@ def main(argv=None):
     ap.add_argument("--pattern", choices=["search", "batch", "serve", "scaling", "continuous"],
                     default="search")
     ap.add_argument("--batch-responses", type=int, default=256)
+    ap.add_argument("--batch-instances", type=int, default=16)
     ap.add_argument("--serve-datasets", type=int, default=6)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=200.0)

@@ -209,9 +209,11 @@ int xyz_kkt_screen(xyz_ctx *ctx, const double *r, double lambda, int32_t L, int3
  * each M in [M_lo, M_hi] it takes L = xyz_runs_for_recall(gamma^M, recall)
  * (eq. L_choice), times two short searches on the device (trial_runs and a
  * quarter of it; CUDA events on the context's stream), fits time = a + b*runs
- * and predicts the full search; *M_best / *L_best / *ms_best get the fastest.
- * table (optional, 3*(M_hi - M_lo + 1) doubles) gets (M, L, predicted ms)
- * rows, ms < 0 where L is out of range.  Searches on the context's data;
+ * and predicts the full search.  With a table, the two best predictions
+ * (when under 200 ms) are then timed as full searches and the faster one
+ * wins.  *M_best / *L_best / *ms_best get the chosen point.  table
+ * (optional, 3*(M_hi - M_lo + 1) doubles) gets (M, L, ms) rows: measured for
+ * the confirmed points, predicted for the rest, < 0 where L is out of range.  Searches on the context's data;
  * results of later searches never depend on it.  0 < gamma < 1,
  * 0 < recall < 1, 1 <= M_lo <= M_hi <= 64, trial_runs >= 8, else XYZ_EINVAL. */
 int xyz_autotune_M(xyz_ctx *ctx, double kappa, double gamma, double recall, int32_t M_lo, int32_t M_hi,

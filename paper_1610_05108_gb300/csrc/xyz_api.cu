@@ -1287,6 +1287,42 @@ int xyz_autotune_M(xyz_ctx *ctx, double kappa, double gamma, double recall, int3
             table[3 * (M - M_lo) + 2] = pred;
         }
     }
+    // confirm: the two best predictions, when they are short enough, are
+    // timed as full searches (after a warm-up that sizes their buffers)
+    if (!rc && best >= 0.0 && table) {
+        int32_t cand[2] = {bestM, -1};
+        double second = -1.0;
+        for (int32_t M = M_lo; M <= M_hi; ++M) {
+            const double pr = table[3 * (M - M_lo) + 2];
+            if (M != bestM && pr >= 0.0 && (second < 0.0 || pr < second)) {
+                second = pr;
+                cand[1] = M;
+            }
+        }
+        double bestMeasured = -1.0;
+        for (int i = 0; i < 2 && !rc; ++i) {
+            const int32_t M = cand[i];
+            if (M < 0 || table[3 * (M - M_lo) + 2] > 200.0)
+                continue;
+            const int64_t L = (int64_t)table[3 * (M - M_lo) + 1];
+            int64_t nout = 0;
+            if ((rc = run_search(ctx, 0, L, M, amin, seed + 7, &nout)))
+                break;
+            cudaEventRecord(e0, ctx->stream);
+            rc = run_search(ctx, 0, L, M, amin, seed + 8, &nout);
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            table[3 * (M - M_lo) + 2] = ms;
+            if (bestMeasured < 0.0 || ms < bestMeasured) {
+                bestMeasured = ms;
+                best = ms;
+                bestM = M;
+                bestL = L;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->timing = timing;

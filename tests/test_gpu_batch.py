@@ -124,7 +124,7 @@ def test_autotune_M_picks_a_measured_point(xyz):
         assert 8 <= M <= 14 and ms > 0
         assert L == xyz.runs_for_recall(0.9 ** M, 0.95)
         assert list(table[:, 0]) == list(range(8, 15))
-        assert table[M - 8, 2] == ms == min(t for t in table[:, 2] if t > 0)
+        assert table[M - 8, 2] == ms
         found = ctx.search(3 * L, M, 0.3, 5)
         assert (10, 20) in set(zip(found["j"].tolist(), found["k"].tolist()))
         with pytest.raises(xyz.XyzError):
