@@ -116,6 +116,16 @@ int xyz_create(const int8_t *X, const int8_t *Y, int64_t n, int64_t p, xyz_ctx *
 int xyz_create_dev(const int8_t *dX, const int8_t *dY, int64_t n, int64_t p, void *stream,
                    xyz_ctx **out);
 
+/* Real-valued X by the sign transform of Section 3.2: X~_ij = sgn(X_ij),
+ * an entry that is exactly 0 getting a fair coin (the top bit of splitmix64
+ * output j*n + i from state coin_seed, so the transform is reproducible).
+ * X: n x p column-major float (copied before the call returns); NaN gives
+ * XYZ_EINVAL.  The context holds the binary X~ and the response +1 until
+ * xyz_set_y / xyz_set_y_real; with a real Y the search computes the
+ * sign-transform strength of Section 3.2,
+ * 1/2 + sum_i Y_i sgn(X_ij) sgn(X_ik) / (2 ||Y||_1). */
+int xyz_create_sign(const float *X, int64_t n, int64_t p, uint64_t coin_seed, xyz_ctx **out);
+
 /* Replace the response Y (host pointer, n int8) of an existing context,
  * keeping packed X resident (Section 4 calls xyz repeatedly on one X with
  * changing responses). */

@@ -74,6 +74,7 @@ def _load():
         "orc_kkt_threshold": (_i64, [_p, _i64, _dbl]),
         "orc_kkt_brute": (_i64, [_p, _p, _i64, _i64, _dbl, _p, _p, _i64]),
         "orc_kkt_xyz": (_i64, [_p, _p, _i64, _i64, _i64, _i32, _dbl, _u64, _p, _p, _i64]),
+        "orc_sign_transform": (ctypes.c_int, [_p, _i64, _i64, _u64, _p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -319,3 +320,13 @@ def kkt_brute(X, r, lam: float) -> tuple:
 def kkt_xyz(X, r, L: int, M: int, lam: float, seed: int) -> tuple:
     """The same check by the continuous-response search with +r and -r."""
     return _weighted_call(_load().orc_kkt_xyz, X, r, int(L), int(M), float(lam), seed & (2**64 - 1))
+
+
+def sign_transform(X, coin_seed: int = 0) -> np.ndarray:
+    """Section 3.2's sign transform of a real X (R14): column-major int8 +-1."""
+    X = np.asfortranarray(X, dtype=np.float32)
+    n, p = X.shape
+    out = np.zeros((n, p), dtype=np.int8, order="F")
+    if _load().orc_sign_transform(_ptr(X), n, p, coin_seed & (2**64 - 1), _ptr(out)) != 0:
+        raise ValueError("entries of X must not be NaN")
+    return out

@@ -739,3 +739,25 @@ int64_t orc_kkt_xyz(const int8_t *X, const double *r, int64_t n, int64_t p, int6
     free(q);
     return u;
 }
+
+/* ------------------------------------------------------ continuous X */
+
+/* Section 3.2, the sign transform: X~_ij = sgn(X_ij), with a fair coin for
+ * an entry that is exactly 0.  Reading R14: the coin of entry (i, j) is the
+ * top bit of splitmix64 output t = j*n + i from state coin_seed (1 -> -1), so
+ * the transform is reproducible.  Returns 0, or -1 on a NaN. */
+int orc_sign_transform(const float *X, int64_t n, int64_t p, uint64_t coin_seed, int8_t *out)
+{
+    for (int64_t t = 0; t < n * p; t++) {
+        float x = X[t];
+        if (x != x)
+            return -1;
+        if (x < 0.0f)
+            out[t] = -1;
+        else if (x > 0.0f)
+            out[t] = 1;
+        else
+            out[t] = (orc_splitmix64_at(coin_seed, (uint64_t)t) >> 63) ? (int8_t)-1 : (int8_t)1;
+    }
+    return 0;
+}

@@ -12,6 +12,7 @@
 //   total   Q = sum q.
 #include <math.h>
 
+#include "rows.cuh"
 #include "xyz_internal.cuh"
 
 namespace xyz {
@@ -133,7 +134,44 @@ __global__ void flip_kernel(uint32_t *__restrict__ yb, int64_t n, int64_t Wp)
     }
 }
 
+// Sign transform of a real X (Section 3.2): -1 / +1 by sign; an entry that is
+// exactly 0 gets a fair coin, the top bit of splitmix64 output t = its
+// column-major index from the state coin_seed.  bad != 0 on a NaN.
+__global__ void sign_kernel(const float *__restrict__ X, int64_t count, uint64_t coin_seed,
+                            int8_t *__restrict__ out, int *__restrict__ bad)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride) {
+        const float x = X[t];
+        int8_t v;
+        if (x < 0.0f)
+            v = -1;
+        else if (x > 0.0f)
+            v = 1;
+        else if (x == 0.0f)
+            v = (mix64(coin_seed + ((uint64_t)t + 1ULL) * 0x9E3779B97F4A7C15ULL) >> 63) ? (int8_t)-1 : (int8_t)1;
+        else {
+            v = 1;
+            atomicOr(bad, 1);
+        }
+        out[t] = v;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_sign_transform(const float *dX, int64_t count, uint64_t coin_seed, int8_t *out, int *bad,
+                                  cudaStream_t s, int64_t *launches)
+{
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    if (e != cudaSuccess)
+        return e;
+    int64_t g = (count + WT_THREADS - 1) / WT_THREADS;
+    g = g < 1 ? 1 : (g > 65535 ? 65535 : g);
+    sign_kernel<<<(unsigned)g, WT_THREADS, 0, s>>>(dX, count, coin_seed, out, bad);
+    *launches += 1;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_flip_signs(const Packed &pk, cudaStream_t s, int64_t *launches)
 {

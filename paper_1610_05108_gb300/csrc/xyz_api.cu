@@ -835,6 +835,64 @@ int xyz_create_dev(const int8_t *dX, const int8_t *dY, int64_t n, int64_t p, voi
     return XYZ_OK;
 }
 
+int xyz_create_sign(const float *X, int64_t n, int64_t p, uint64_t coin_seed, xyz_ctx **out)
+{
+    if (!X || !out)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    int rc = check_dims(n, p);
+    if (rc)
+        return rc;
+    const size_t count = (size_t)n * (size_t)p;
+    float *dXf = nullptr;
+    int8_t *dX8 = nullptr, *dY = nullptr;
+    int *dbad = nullptr;
+    cudaStream_t s = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(dXf);
+        cudaFree(dX8);
+        cudaFree(dY);
+        cudaFree(dbad);
+        if (s)
+            cudaStreamDestroy(s);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&dXf, count * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&dX8, count);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&dY, (size_t)n);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&dbad, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(XYZ_ENOMEM, std::string("staging of a real X: ") + cudaGetErrorString(e));
+    }
+    int64_t launches = 0;
+    int bad = 0;
+    e = cudaMemcpyAsync(dXf, X, count * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(dY, 1, (size_t)n, s);          // default response: all +1
+    if (e == cudaSuccess)
+        e = launch_sign_transform(dXf, (int64_t)count, coin_seed, dX8, dbad, s, &launches);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(XYZ_ECUDA, std::string("sign transform: ") + cudaGetErrorString(e));
+    }
+    if (bad) {
+        cleanup();
+        return fail(XYZ_EINVAL, "entries of X must not be NaN");
+    }
+    rc = xyz_create_dev(dX8, dY, n, p, nullptr, out);
+    cleanup();
+    return rc;
+}
+
 int xyz_create(const int8_t *X, const int8_t *Y, int64_t n, int64_t p, xyz_ctx **out)
 {
     if (!X || !Y || !out)

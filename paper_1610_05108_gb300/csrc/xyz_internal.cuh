@@ -185,6 +185,9 @@ cudaError_t launch_prepare_weights(const double *dY, int64_t n, int64_t Wp, uint
                                    uint32_t *planes, uint64_t *cdf, uint64_t *total,
                                    unsigned long long *maxbits, int *bad, void *scan_tmp, cudaStream_t s,
                                    int64_t *launches);
+// sign transform of a real X (count entries) to -1 / +1, zeros by a fair coin
+cudaError_t launch_sign_transform(const float *dX, int64_t count, uint64_t coin_seed, int8_t *out, int *bad,
+                                  cudaStream_t s, int64_t *launches);
 // Y -> -Y on the response sign bits of the valid rows
 cudaError_t launch_flip_signs(const Packed &pk, cudaStream_t s, int64_t *launches);
 // weighted strengths (2 S - Q) / Q of the first *nout output pairs

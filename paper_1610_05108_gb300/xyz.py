@@ -61,6 +61,7 @@ class ServerStats(ctypes.Structure):
 SIGNATURES = {
     "xyz_create": (ctypes.c_int, [_p, _p, _i64, _i64, _p]),
     "xyz_create_dev": (ctypes.c_int, [_p, _p, _i64, _i64, _p, _p]),
+    "xyz_create_sign": (ctypes.c_int, [_p, _i64, _i64, _u64, _p]),
     "xyz_set_y": (ctypes.c_int, [_p, _p]),
     "xyz_set_y_dev": (ctypes.c_int, [_p, _p]),
     "xyz_set_y_real": (ctypes.c_int, [_p, _p]),
@@ -190,6 +191,15 @@ class Context:
             raise ValueError("Y must have shape (n,)")
         h = ctypes.c_void_p()
         _check(load().xyz_create(_ptr(X), _ptr(Y), n, p, ctypes.byref(h)))
+        return cls(h, n, p)
+
+    @classmethod
+    def from_real_sign(cls, X: np.ndarray, coin_seed: int = 0) -> "Context":
+        """Real X (n x p) through the sign transform of Section 3.2."""
+        X = np.asfortranarray(X, dtype=np.float32)
+        n, p = X.shape
+        h = ctypes.c_void_p()
+        _check(load().xyz_create_sign(_ptr(X), n, p, coin_seed & (2**64 - 1), ctypes.byref(h)))
         return cls(h, n, p)
 
     @classmethod

@@ -154,3 +154,23 @@ def test_kkt_screen_matches_oracle(xyz, orc):
             assert {(2, 600), (10, 11)} <= set(zip(got["j"].tolist(), got["k"].tolist()))
         with pytest.raises(xyz.XyzError):
             ctx.kkt_screen(r, -1.0, 10, 6, 1)
+
+
+def test_sign_transform_search_matches_oracle(xyz, orc):
+    rng = np.random.default_rng(40)
+    n, p = 500, 1500
+    X = rng.standard_t(5, size=(n, p)).astype(np.float32)
+    X[rng.random((n, p)) < 0.02] = 0.0                 # exact zeros take the coin
+    Y = X[:, 4].astype(np.float64) * X[:, 1000] + rng.normal(0, 0.7, size=n)
+    T = orc.sign_transform(X, coin_seed=5)
+    with xyz.Context.from_real_sign(X, coin_seed=5) as ctx:
+        kx, _ = ctx.run_keys(20, 1, 0)
+        ox, _ = orc.keys(T, np.ones(n, np.int8), orc.draw_rows(1, 0, 20, n))
+        assert np.array_equal(kx, ox)                  # the packed X is the transform
+        ctx.set_y_real(Y)
+        got = ctx.search(30, 10, 0.3, 2)
+    want, S = orc.xyz_weighted(T, Y, 30, 10, 0.3, 2)
+    assert np.array_equal(_arr(got), want)
+    assert (4, 1000) in set(zip(got["j"].tolist(), got["k"].tolist()))
+    with pytest.raises(xyz.XyzError):
+        xyz.Context.from_real_sign(np.full((4, 3), np.nan, np.float32))

@@ -158,3 +158,33 @@ def test_kkt_rule_matches_float_definition(orc):
     for (j, k, _), v in zip(xs, dx):
         assert bset[(int(j), int(k))] == int(v)
     assert {(2, 60), (10, 11)} <= {(int(j), int(k)) for j, k, _ in xs}
+
+
+def test_sign_transform_definition(orc):
+    rng = np.random.default_rng(30)
+    X = rng.normal(size=(50, 40)).astype(np.float32)
+    X[rng.random((50, 40)) < 0.3] = 0.0
+    T = orc.sign_transform(X, coin_seed=77)
+    nz = X != 0
+    assert np.array_equal(T[nz], np.sign(X[nz]).astype(np.int8))
+    # zeros: the top bit of splitmix64 output t = j*n + i
+    ii, jj = np.nonzero(~nz)
+    want = [(-1 if orc.splitmix64_at(77, int(j) * 50 + int(i)) >> 63 else 1) for i, j in zip(ii, jj)]
+    assert list(T[ii, jj]) == want
+    assert 0.35 < np.mean(np.array(want) == -1) < 0.65
+    with pytest.raises(ValueError):
+        orc.sign_transform(np.full((3, 3), np.nan, np.float32))
+
+
+def test_sign_transform_strength(orc):
+    """Section 3.2: with the sign transform the weighted strength of (j, k) is
+    1/2 + sum_i Y_i sgn(X_ij) sgn(X_ik) / (2 ||Y||_1)."""
+    rng = np.random.default_rng(31)
+    X = rng.standard_t(4, size=(400, 30)).astype(np.float32)
+    Y = X[:, 3].astype(np.float64) * X[:, 7] + rng.normal(0, 0.5, size=400)
+    T = orc.sign_transform(X)
+    for j, k in ((3, 7), (0, 1), (5, 20)):
+        _, S = orc.weighted_agree(T, Y, j, k)
+        q, _ = orc.quantize_y(Y)
+        g = 0.5 + np.sum(Y * np.sign(X[:, j]) * np.sign(X[:, k])) / (2 * np.abs(Y).sum())
+        assert abs(S / q.sum() - g) < 1e-6
