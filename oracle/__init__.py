@@ -75,6 +75,11 @@ def _load():
         "orc_kkt_brute": (_i64, [_p, _p, _i64, _i64, _dbl, _p, _p, _i64]),
         "orc_kkt_xyz": (_i64, [_p, _p, _i64, _i64, _i64, _i32, _dbl, _u64, _p, _p, _i64]),
         "orc_sign_transform": (ctypes.c_int, [_p, _i64, _i64, _u64, _p]),
+        "orc_unbiased_scale": (None, [_p, _p, _i64, _i64, _p, _p]),
+        "orc_unbiased_draw": (ctypes.c_int, [_p, _i64, _i64, _u64, _i64, _i32, _i32, _i64, _i64]),
+        "orc_real_dot": (_dbl, [_p, _p, _i64, _i64, _i64]),
+        "orc_xyz_unbiased_range": (_i64, [_p, _p, _i64, _i64, _i64, _i64, _i32, _dbl, _u64, _p, _p,
+                                          _i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -330,3 +335,39 @@ def sign_transform(X, coin_seed: int = 0) -> np.ndarray:
     if _load().orc_sign_transform(_ptr(X), n, p, coin_seed & (2**64 - 1), _ptr(out)) != 0:
         raise ValueError("entries of X must not be NaN")
     return out
+
+
+def unbiased_scale(X, Y) -> tuple:
+    """Row scaling of R15: X' = X / nu_i (float), Y' = Y nu_i^2."""
+    X = np.asfortranarray(X, dtype=np.float32)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    n, p = X.shape
+    Xs = np.zeros((n, p), dtype=np.float32, order="F")
+    Ys = np.zeros(n, dtype=np.float64)
+    _load().orc_unbiased_scale(_ptr(X), _ptr(Y), n, p, _ptr(Xs), _ptr(Ys))
+    return Xs, Ys
+
+
+def unbiased_draw(Xs, seed: int, run: int, M: int, m: int, i: int, j: int) -> int:
+    Xs = np.asfortranarray(Xs, dtype=np.float32)
+    n, p = Xs.shape
+    return int(_load().orc_unbiased_draw(_ptr(Xs), n, p, seed & (2**64 - 1), run, M, m, i, j))
+
+
+def xyz_unbiased_range(X, Y, l0: int, l1: int, M: int, kappa: float, seed: int) -> tuple:
+    """The unbiased-transform search (R15) over runs [l0, l1): sorted pairs
+    (count, 2) and their dot products sum_i Y'_i X'_ij X'_ik."""
+    X = np.asfortranarray(X, dtype=np.float32)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    n, p = X.shape
+    cap = 4096
+    while True:
+        out = np.zeros((cap, 2), dtype=np.int32)
+        dots = np.zeros(cap, dtype=np.float64)
+        cnt = _load().orc_xyz_unbiased_range(_ptr(X), _ptr(Y), n, p, l0, l1, M, float(kappa),
+                                             seed & (2**64 - 1), _ptr(out), _ptr(dots), cap)
+        if cnt < 0:
+            raise ValueError("the scaled response must be finite and not all zero")
+        if cnt <= cap:
+            return out[:cnt], dots[:cnt]
+        cap = cnt

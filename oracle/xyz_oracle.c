@@ -761,3 +761,121 @@ int orc_sign_transform(const float *X, int64_t n, int64_t p, uint64_t coin_seed,
     }
     return 0;
 }
+
+/* Section 3.2, the unbiased transform.
+ *
+ * Reading R15: rows are scaled first, nu_i = max_j |X_ij| (float),
+ * X'_ij = X_ij / nu_i (float division; a row of zeros stays 0) and
+ * Y'_i = Y_i nu_i^2 (double), so X' lies in [-1, 1] and Proposition
+ * "unbiased" applies to (Y', X').  The search is the continuous-response
+ * search of R9-R11 on Y' with the random binary X~ of each draw: for draw
+ * m of run l (row i = s_{l,m}) and column j, X~ = +1 with probability
+ * g(X'_ij) = (X'_ij + 1) / 2, decided by u24 < g 2^24 with u24 the top 24
+ * bits of splitmix64 output t = (l M + m) p + j from state
+ * seed + 0x632BE59BD9B4E019 (a stream separate from the rows'); every draw
+ * transforms independently.  Keys: bit m of column j is 1 iff X~ = -1.
+ * A candidate passes when sum_i Y'_i X'_ij X'_ik >= kappa ||Y'||_1 (double
+ * sums over i in order), i.e. gamma^g_jk >= (1 + kappa) / 2.
+ */
+
+/* Row scaling of R15: X' (n x p column-major float) and Y' (double). */
+void orc_unbiased_scale(const float *X, const double *Y, int64_t n, int64_t p, float *Xs, double *Ys)
+{
+    for (int64_t i = 0; i < n; i++) {
+        float nu = 0.0f;
+        for (int64_t j = 0; j < p; j++) {
+            float a = fabsf(X[j * n + i]);
+            if (a > nu)
+                nu = a;
+        }
+        for (int64_t j = 0; j < p; j++)
+            Xs[j * n + i] = nu > 0.0f ? X[j * n + i] / nu : 0.0f;
+        Ys[i] = Y[i] * ((double)nu * (double)nu);
+    }
+}
+
+/* R15: the transformed value (+1 / -1) of entry (i, j) in draw m of run l. */
+int orc_unbiased_draw(const float *Xs, int64_t n, int64_t p, uint64_t seed, int64_t run,
+                      int32_t M, int32_t m, int64_t i, int64_t j)
+{
+    uint64_t t = ((uint64_t)run * (uint64_t)M + (uint64_t)m) * (uint64_t)p + (uint64_t)j;
+    uint64_t u24 = orc_splitmix64_at(seed + 0x632BE59BD9B4E019ULL, t) >> 40;
+    float g = (Xs[j * n + i] + 1.0f) / 2.0f;
+    return ((double)u24 < (double)g * 16777216.0) ? 1 : -1;
+}
+
+/* sum_i Y'_i X'_ij X'_ik in double, i in order. */
+double orc_real_dot(const float *Xs, const double *Ys, int64_t n, int64_t j, int64_t k)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++)
+        s += Ys[i] * ((double)Xs[j * n + i] * (double)Xs[k * n + i]);
+    return s;
+}
+
+/* The search of R15 over runs [l0, l1): writes up to `cap` pairs (j, k) and
+ * their dot products, sorted, each pair once; returns the count, -1 when Y'
+ * is unusable (R9). */
+int64_t orc_xyz_unbiased_range(const float *X, const double *Y, int64_t n, int64_t p, int64_t l0,
+                               int64_t l1, int32_t M, double kappa, uint64_t seed, int32_t *out,
+                               double *dots, int64_t cap)
+{
+    float *Xs = (float *)malloc((size_t)(n * p) * sizeof(float));
+    double *Ys = (double *)malloc((size_t)n * sizeof(double));
+    int64_t *q = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int8_t *sgn = (int8_t *)malloc((size_t)n);
+    orc_unbiased_scale(X, Y, n, p, Xs, Ys);
+    if (orc_quantize_y(Ys, n, q, sgn) != 0) {
+        free(Xs);
+        free(Ys);
+        free(q);
+        free(sgn);
+        return -1;
+    }
+    double norm1 = 0.0;
+    for (int64_t i = 0; i < n; i++)
+        norm1 += fabs(Ys[i]);
+    int64_t *rows = (int64_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int64_t));
+    int8_t *Xt = (int8_t *)malloc((size_t)(n * p));
+    orc_vec found = {0, 0, 0};
+    orc_vec cand = {0, 0, 0};
+    for (int64_t l = l0; l < l1; l++) {
+        orc_draw_rows_weighted(q, n, seed, l, M, rows);
+        /* the transformed matrix restricted to this run's draws: draw m is
+         * stored in "row" m of an M x p matrix */
+        int8_t *Xm = (int8_t *)malloc((size_t)((M > 0 ? M : 1) * p));
+        int8_t *Sm = (int8_t *)malloc((size_t)(M > 0 ? M : 1));
+        int64_t *idx = (int64_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int64_t));
+        for (int32_t m = 0; m < M; m++) {
+            for (int64_t j = 0; j < p; j++)
+                Xm[j * M + m] = (int8_t)orc_unbiased_draw(Xs, n, p, seed, l, M, m, rows[m], j);
+            Sm[m] = sgn[rows[m]];
+            idx[m] = m;
+        }
+        cand.n = 0;
+        int64_t ne = orc_rows_candidates(Xm, Sm, M, p, idx, M, &cand);
+        for (int64_t e = 0; e < ne; e++) {
+            int32_t j = cand.v[e].j, k = cand.v[e].k;
+            if (orc_real_dot(Xs, Ys, n, j, k) >= kappa * norm1)
+                orc_vec_push(&found, j, k, 0);
+        }
+        free(idx);
+        free(Sm);
+        free(Xm);
+    }
+    int64_t u = orc_sort_unique(found.v, found.n);
+    for (int64_t i = 0; i < u && i < cap; i++) {
+        out[2 * i + 0] = found.v[i].j;
+        out[2 * i + 1] = found.v[i].k;
+        dots[i] = orc_real_dot(Xs, Ys, n, found.v[i].j, found.v[i].k);
+    }
+    free(found.v);
+    free(cand.v);
+    free(Xt);
+    free(rows);
+    free(sgn);
+    free(q);
+    free(Ys);
+    free(Xs);
+    return u;
+}

@@ -188,3 +188,47 @@ def test_sign_transform_strength(orc):
         q, _ = orc.quantize_y(Y)
         g = 0.5 + np.sum(Y * np.sign(X[:, j]) * np.sign(X[:, k])) / (2 * np.abs(Y).sum())
         assert abs(S / q.sum() - g) < 1e-6
+
+
+def test_unbiased_transform_is_unbiased_and_matches_proposition(orc):
+    """Section 3.2: the transform has E X~ = X' (Proposition 'unbiased') and a
+    match probability 1/2 + sum_i Y'_i X'_ij X'_ik / (2 ||Y'||_1) under
+    |Y'|-weighted row draws (the proposition on transformed strengths)."""
+    rng = np.random.default_rng(50)
+    n, p = 6, 3
+    X = rng.uniform(-2, 2, size=(n, p)).astype(np.float32)
+    Y = rng.normal(size=n)
+    Xs, Ys = orc.unbiased_scale(X, Y)
+    assert np.all(np.abs(Xs) <= 1) and np.allclose(np.abs(Xs).max(axis=1), 1)
+    nu = np.abs(X).max(axis=1).astype(np.float64)
+    assert np.allclose(Ys, Y * nu * nu)
+    # unbiasedness of the per-draw transform, entry by entry
+    R = 6000
+    for i, j in ((0, 0), (3, 1), (5, 2)):
+        v = [orc.unbiased_draw(Xs, 9, r, 1, 0, i, j) for r in range(R)]
+        assert abs(np.mean(v) - Xs[i, j]) < 5 / np.sqrt(R)
+    # match probability of (0, 1) with |Y'| weighted rows
+    q, sgn = orc.quantize_y(Ys)
+    hits = 0
+    T = 20000
+    rows = orc.draw_rows_weighted(q, 11, 0, T)
+    for t, i in enumerate(rows):
+        a = orc.unbiased_draw(Xs, 11, 0, T, t, int(i), 0)
+        b = orc.unbiased_draw(Xs, 11, 0, T, t, int(i), 1)
+        hits += int(a * b == sgn[i])
+    gamma = 0.5 + np.sum(Ys * Xs[:, 0].astype(np.float64) * Xs[:, 1]) / (2 * np.abs(Ys).sum())
+    assert abs(hits / T - gamma) < 5 * np.sqrt(gamma * (1 - gamma) / T)
+
+
+def test_unbiased_search_subset_of_exact_screen(orc):
+    rng = np.random.default_rng(51)
+    n, p = 200, 120
+    X = rng.uniform(-1, 1, size=(n, p)).astype(np.float32)
+    Y = X[:, 3].astype(np.float64) * X[:, 90] + rng.normal(0, 0.05, size=n)
+    pairs, dots = orc.xyz_unbiased_range(X, Y, 0, 60, 6, 0.3, 4)
+    Xs, Ys = orc.unbiased_scale(X, Y)
+    G = Xs.T.astype(np.float64) @ (Xs.astype(np.float64) * Ys[:, None])
+    thr = 0.3 * np.abs(Ys).sum()
+    for (j, k), d in zip(pairs, dots):
+        assert abs(G[j, k] - d) < 1e-9 * np.abs(Ys).sum() and d >= thr
+    assert (3, 90) in {(int(j), int(k)) for j, k in pairs}
