@@ -126,6 +126,23 @@ int xyz_create_dev(const int8_t *dX, const int8_t *dY, int64_t n, int64_t p, voi
  * 1/2 + sum_i Y_i sgn(X_ij) sgn(X_ik) / (2 ||Y||_1). */
 int xyz_create_sign(const float *X, int64_t n, int64_t p, uint64_t coin_seed, xyz_ctx **out);
 
+/* Real-valued X by the unbiased transform of Section 3.2.  Rows are scaled,
+ * nu_i = max_j |X_ij|, X'_ij = X_ij / nu_i (float; a row of zeros stays 0),
+ * Y'_i = Y_i nu_i^2, and the search draws rows with probability
+ * |Y'_i| / ||Y'||_1 (fixed point as xyz_set_y_real), binarises every drawn
+ * entry afresh with P(X~ = +1) = (X'_ij + 1)/2 (u24 < (X' + 1)/2 * 2^24, u24
+ * the top 24 bits of splitmix64 output (l M + m) p + j from state
+ * seed + 0x632BE59BD9B4E019), and keeps a candidate when the real inner
+ * product sum_i Y'_i X'_ij X'_ik (float, eight partial sums per candidate)
+ * is >= kappa ||Y'||_1 -- by the proposition on the unbiased transform its
+ * strength gamma^g_jk >= (1 + kappa)/2.  Results: agree = -1, strength =
+ * sum_i Y'_i X'_ij X'_ik / ||Y'||_1.  X: n x p column-major float, Y: n
+ * doubles (copied; NaN in X or an unusable Y' gives XYZ_EINVAL).  Searches
+ * need M <= 31 and p <= 262144; a new response goes through xyz_set_y_real
+ * (which scales it); binary responses, batched search, the exhaustive screen,
+ * xyz_search_abs and xyz_kkt_screen are XYZ_EINVAL on such a context. */
+int xyz_create_unbiased(const float *X, const double *Y, int64_t n, int64_t p, xyz_ctx **out);
+
 /* Replace the response Y (host pointer, n int8) of an existing context,
  * keeping packed X resident (Section 4 calls xyz repeatedly on one X with
  * changing responses). */

@@ -102,6 +102,10 @@ __device__ __forceinline__ uint32_t canon(uint32_t kx, uint32_t c, int tb, uint3
 // holds, per CTA, the keys of its current run in bit-major order: kx of
 // column 32w + cc at cc * P + w.
 //
+// MB = 0: real X through the unbiased transform (Section 3.2); the keys are
+// drawn from the scaled real rows Xrs (row pitch Pf floats) instead of the
+// packed bits.
+//
 // BATCH: B responses share X and the row stream.  The keys of a run and its
 // filter F are built once; pass 2, refinement and grouping then run once per
 // response b (its response key c_b), and buckets carry b in their `pad`
@@ -117,7 +121,8 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                   uint8_t *__restrict__ cnz, uint32_t *__restrict__ members,
                   uint32_t *__restrict__ members_count, Bucket *__restrict__ buckets,
                   uint64_t *__restrict__ pair_counts, uint32_t *__restrict__ nbuckets,
-                  const uint64_t *__restrict__ cdf, uint64_t wtot)
+                  const uint64_t *__restrict__ cdf, uint64_t wtot, const float *__restrict__ Xrs,
+                  int64_t Pf)
 {
     using SegKey = uint64_t;
     extern __shared__ __align__(16) uint32_t fl_smem[];
@@ -188,10 +193,33 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             const bool need = BATCH || c_sh != 0;    // c == 0 keeps every column
             for (uint32_t w = t; w < P32; w += T) {
                 uint32_t A[32];
+                if (MB == 0) {
+                    // real X, unbiased transform (Section 3.2): bit m of column
+                    // 32w + cc is 1 when draw m's random binarisation of
+                    // X'[s_m, j] is -1, i.e. u24 >= (X' + 1) / 2 * 2^24 with
+                    // u24 the top bits of splitmix64 output (l M + m) p + j
+                    // of the transform stream
 #pragma unroll
-                for (int m = 0; m < 32; ++m)
-                    A[m] = (m < MB && m < M) ? __ldg(Xr + rowoff[m] + w) : 0u;
-                transpose32(A);
+                    for (int cc = 0; cc < 32; ++cc)
+                        A[cc] = 0u;
+                    const uint64_t col0 = 32ULL * w;
+                    const uint64_t seed2 = seed + 0x632BE59BD9B4E019ULL;
+                    for (int m = 0; m < M; ++m) {
+                        const float *xr = Xrs + rowidx[m] * Pf + col0;
+                        const uint64_t tb = ((uint64_t)(l0 + r) * (uint64_t)M + (uint64_t)m) * (uint64_t)p + col0;
+#pragma unroll
+                        for (int cc = 0; cc < 32; ++cc) {
+                            const float g = (__ldg(xr + cc) + 1.0f) * 0.5f;
+                            const uint64_t u = mix64(seed2 + (tb + (uint64_t)cc + 1ULL) * 0x9E3779B97F4A7C15ULL);
+                            A[cc] |= ((float)(uint32_t)(u >> 40) < g * 16777216.0f ? 0u : 1u) << m;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 32; ++m)
+                        A[m] = (m < MB && m < M) ? __ldg(Xr + rowoff[m] + w) : 0u;
+                    transpose32(A);
+                }
 #pragma unroll
                 for (int cc = 0; cc < 32; ++cc)
                     kcs[cc * P32 + w] = A[cc];         // bit-major: coalesced across the warp
@@ -593,11 +621,13 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
                            int64_t, int, uint64_t, int64_t, int, int, int, int, int64_t, uint32_t, uint32_t,
                            uint32_t *, void *, uint32_t *, uint32_t *, uint32_t, int *, uint8_t *,
                            uint32_t *, uint32_t *, Bucket *, uint64_t *, uint32_t *, const uint64_t *,
-                           uint64_t);
+                           uint64_t, const float *, int64_t);
     KernT kern;
     if (batch)
         kern = M <= 8 ? filter_kernel<8, true> : M <= 16 ? filter_kernel<16, true>
                : M <= 24 ? filter_kernel<24, true> : filter_kernel<32, true>;
+    else if (pk.Xrs)
+        kern = filter_kernel<0, false>;        // real X, unbiased transform
     else
         kern = M <= 8 ? filter_kernel<8, false> : M <= 16 ? filter_kernel<16, false>
                : M <= 24 ? filter_kernel<24, false> : filter_kernel<32, false>;
@@ -607,7 +637,7 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
     kern<<<grid, filter_threads(pk.P), smem, s>>>(pk.Xr, pk.Pp, pk.P, ybs, pk.Wp, B, pk.n, pk.p, M, seed, l0, R,
                                         NB, BB, rbits, rbase, mcap, bcap, kc_scratch, seg_keys, seg_vals,
                                         seg_count, seg_cap, overflow, cnz, members, members_count,
-                                        buckets, pair_counts, nbuckets, pk.cdf, pk.wtotal);
+                                        buckets, pair_counts, nbuckets, pk.cdf, pk.wtotal, pk.Xrs, pk.Pf);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -413,6 +413,9 @@ cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_
                           uint32_t *rec_agree, uint32_t *nrec, uint32_t rec_cap, cudaStream_t s,
                           int64_t *launches, const uint32_t *ybs, const int *abort_flag)
 {
+    if (pk.Xcs && !ybs)       // real X (unbiased transform): real inner products
+        return launch_verify_real(pk, buckets, pair_off, nbuckets, total_pairs, vals, kbits, rec_keys,
+                                  rec_agree, nrec, rec_cap, s, launches, abort_flag);
     if (ybs)
         verify_kernel<true, false><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
             pk.Xc, pk.Wp, ybs, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits, rec_keys,

@@ -97,6 +97,8 @@ struct xyz_ctx {
     // once a new response has been checked
     DevBuf wq, wcdf, wplanes, wq2, wcdf2, wplanes2, wmeta, wscan, yreal;
     int w_exp = 0;               // max|Y| = f 2^w_exp, f in [0.5, 1)
+    // real X through the unbiased transform (Section 3.2)
+    DevBuf xrs, xcs, xnu, ypr, ysf, rbad;
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
     int64_t rec_cap = 1 << 16;
     int64_t chunk_entries = (int64_t)1 << 25;
@@ -146,7 +148,8 @@ static int64_t ws_bytes(const xyz_ctx *c)
                            &c->buckets2, &c->pair_counts2, &c->pair_off2, &c->scan_tmp2,
                            &c->resp, &c->ybs, &c->y_alt, &c->y_stage,
                            &c->wq, &c->wcdf, &c->wplanes, &c->wq2, &c->wcdf2, &c->wplanes2,
-                           &c->wmeta, &c->wscan, &c->yreal};
+                           &c->wmeta, &c->wscan, &c->yreal,
+                           &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->rbad};
     int64_t s = 0;
     for (const DevBuf *b : all)
         s += (int64_t)b->bytes;
@@ -411,6 +414,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
     Plan pl = make_plan(c, runs, M, B);
     if (B > 1 && !pl.filter)
         return fail(XYZ_EINVAL, "batched search needs M <= 31 and p <= 262144");
+    if (c->pk.Xrs && (!pl.filter || B > 1))
+        return fail(XYZ_EINVAL, "a real X needs M <= 31, p <= 262144 and one response");
     const int bbits = ceil_log2(B);
     const int rbits = ceil_log2(runs);
     if (pl.filter && bbits + rbits + M > 64)
@@ -663,7 +668,10 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                          (PairOut *)c->out.ptr, ctr_nout(c), c->stream, &launches,
                          B > 1 ? (uint32_t *)c->resp.ptr : nullptr));
         tm.end();
-        if (c->pk.cdf && nrec > 0)
+        if (c->pk.Xcs && nrec > 0)
+            CU(launch_real_strengths(c->pk, (PairOut *)c->out.ptr, ctr_nout(c), (int64_t)nrec, c->stream,
+                                     &launches));
+        else if (c->pk.cdf && nrec > 0)
             CU(launch_weighted_strengths(c->pk, (PairOut *)c->out.ptr, ctr_nout(c), (int64_t)nrec, c->stream,
                                          &launches));
         uint32_t nout = 0;
@@ -775,7 +783,8 @@ void destroy_ctx(xyz_ctx *c)
                      &c->seg_keys, &c->seg_vals,   &c->seg_count, &c->buckets2, &c->pair_counts2,
                      &c->pair_off2, &c->scan_tmp2, &c->resp,   &c->ybs, &c->y_alt, &c->y_stage,
                      &c->wq, &c->wcdf, &c->wplanes, &c->wq2, &c->wcdf2, &c->wplanes2,
-                     &c->wmeta, &c->wscan, &c->yreal};
+                     &c->wmeta, &c->wscan, &c->yreal,
+                     &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->rbad};
     for (DevBuf *b : all)
         release(*b);
     if (c->own_stream && c->stream)
@@ -893,6 +902,65 @@ int xyz_create_sign(const float *X, int64_t n, int64_t p, uint64_t coin_seed, xy
     return rc;
 }
 
+int xyz_create_unbiased(const float *X, const double *Y, int64_t n, int64_t p, xyz_ctx **out)
+{
+    if (!X || !Y || !out)
+        return fail(XYZ_EINVAL, "null pointer argument");
+    int rc = check_dims(n, p);
+    if (rc)
+        return rc;
+    xyz_ctx *c = nullptr;
+    if ((rc = xyz_create_sign(X, n, p, 0, &c)))      // packed sign bits: the binary view of X
+        return rc;
+    const int64_t Pf = (p + 31) / 32 * 32, Wf = (n + 31) / 32 * 32;
+    const size_t count = (size_t)n * (size_t)p;
+    DevBuf dX, dY;
+    auto bail = [&](int code) {
+        release(dX);
+        release(dY);
+        std::string msg = g_err;
+        destroy_ctx(c);
+        g_err = msg;
+        return code;
+    };
+    if ((rc = ensure(dX, count * sizeof(float))) || (rc = ensure(dY, (size_t)n * 8)) ||
+        (rc = ensure(c->xrs, (size_t)n * Pf * sizeof(float))) ||
+        (rc = ensure(c->xcs, (size_t)p * Wf * sizeof(float))) || (rc = ensure(c->xnu, (size_t)n * 4)) ||
+        (rc = ensure(c->ysf, (size_t)Wf * 4)) || (rc = ensure(c->rbad, 16)))
+        return bail(rc);
+    int64_t launches = 0;
+    unsigned bad = 0;
+    cudaError_t e = cudaMemcpyAsync(dX.ptr, X, count * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dY.ptr, Y, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_unbiased_scale((const float *)dX.ptr, n, p, Pf, Wf, (float *)c->xrs.ptr, (float *)c->xcs.ptr,
+                                  (float *)c->xnu.ptr, (unsigned *)c->rbad.ptr, c->stream, &launches);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&bad, c->rbad.ptr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        fail(XYZ_ECUDA, std::string("scaling a real X: ") + cudaGetErrorString(e));
+        return bail(XYZ_ECUDA);
+    }
+    if (bad) {
+        fail(XYZ_EINVAL, "entries of X must not be NaN");
+        return bail(XYZ_EINVAL);
+    }
+    c->pk.Xrs = (const float *)c->xrs.ptr;
+    c->pk.Pf = Pf;
+    c->pk.Xcs = (const float *)c->xcs.ptr;
+    c->pk.Wf = Wf;
+    c->pk.ysf = (const float *)c->ysf.ptr;
+    if ((rc = xyz_set_y_real_dev(c, (const double *)dY.ptr)))
+        return bail(rc);
+    release(dX);
+    release(dY);
+    *out = c;
+    return XYZ_OK;
+}
+
 int xyz_create(const int8_t *X, const int8_t *Y, int64_t n, int64_t p, xyz_ctx **out)
 {
     if (!X || !Y || !out)
@@ -924,6 +992,8 @@ int xyz_set_y_dev(xyz_ctx *ctx, const int8_t *dY)
     int rc = check_ctx(ctx);
     if (rc)
         return rc;
+    if (ctx->pk.Xrs)
+        return fail(XYZ_EINVAL, "a real X takes a real response (xyz_set_y_real)");
     if (!dY)
         return fail(XYZ_EINVAL, "null pointer argument");
     // pack into a second buffer first so a bad Y leaves the context unchanged
@@ -958,6 +1028,15 @@ int xyz_set_y_real_dev(xyz_ctx *ctx, const double *dY)
     if (!ctx->owns_packed)
         return fail(XYZ_EINVAL, "context does not own its response");
     const int64_t n = ctx->pk.n, Wp = ctx->pk.Wp;
+    if (ctx->pk.Xrs) {
+        // real X: the response of the scaled rows, Y'_i = Y_i nu_i^2
+        int64_t launches = 0;
+        if ((rc = ensure(ctx->ypr, (size_t)n * 8)))
+            return rc;
+        CU(launch_unbiased_y(dY, (const float *)ctx->xnu.ptr, n, ctx->pk.Wf, (double *)ctx->ypr.ptr,
+                             (float *)ctx->ysf.ptr, ctx->stream, &launches));
+        dY = (const double *)ctx->ypr.ptr;
+    }
     if ((rc = ensure(ctx->y_alt, (size_t)Wp * 4)) || (rc = ensure(ctx->wq2, (size_t)n * 8)) ||
         (rc = ensure(ctx->wcdf2, (size_t)n * 8)) ||
         (rc = ensure(ctx->wplanes2, (size_t)Wp * XYZ_WPLANES * 4)) || (rc = ensure(ctx->wmeta, 64)) ||
@@ -985,6 +1064,16 @@ int xyz_set_y_real_dev(xyz_ctx *ctx, const double *dY)
     double maxabs = 0.0;
     std::memcpy(&maxabs, &host[0], 8);
     std::frexp(maxabs, &ctx->w_exp);
+    if (ctx->pk.Xrs) {
+        // ||Y'||_1 in double, rows in order
+        std::vector<double> yp((size_t)n);
+        CU(cudaMemcpyAsync(yp.data(), dY, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        double s1 = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            s1 += std::fabs(yp[(size_t)i]);
+        ctx->pk.rnorm = s1;
+    }
     return XYZ_OK;
 }
 
@@ -1045,6 +1134,7 @@ int xyz_search_range(xyz_ctx *ctx, int64_t l0, int64_t l1, int32_t M, double kap
     int64_t nout = 0;
     ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;     // real response: 2S - Q >= kappa Q
     ctx->pk.wscale = 0.0;
+    ctx->pk.rkq = (float)(kappa * ctx->pk.rnorm);      // real X: dot >= kappa ||Y'||_1
     if (amin > ctx->pk.n && !ctx->pk.cdf) {
         std::memset(&ctx->stats, 0, sizeof(ctx->stats));
         *pairs = nullptr;
@@ -1238,8 +1328,8 @@ int xyz_search_abs(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t se
         return fail(XYZ_EINVAL, "L must be >= 1");
     if ((rc = check_M(M)) || (rc = check_kappa(kappa)))
         return rc;
-    if (!ctx->owns_packed)
-        return fail(XYZ_EINVAL, "context does not own its response");
+    if (!ctx->owns_packed || ctx->pk.Xrs)
+        return fail(XYZ_EINVAL, "needs a binary X on a context that owns its response");
     const int64_t amin = amin_rule(ctx->pk.n, kappa);
     ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;
     ctx->pk.wscale = 0.0;
@@ -1264,6 +1354,8 @@ int xyz_kkt_screen(xyz_ctx *ctx, const double *r, double lambda, int32_t L, int3
         return fail(XYZ_EINVAL, "lambda must be finite and >= 0");
     if ((rc = check_M(M)))
         return rc;
+    if (ctx->pk.Xrs)
+        return fail(XYZ_EINVAL, "the KKT check takes a binary X");
     if ((rc = xyz_set_y_real(ctx, r)))
         return rc;
     // |r^T (X_j o X_k)| / n > lambda as the integer rule |2S - Q| >= t
@@ -1749,6 +1841,7 @@ int xyz_run_candidates(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, int3
         return rc;
     int64_t nout = 0;
     ctx->pk.wkq = -INFINITY;                           // every candidate passes
+    ctx->pk.rkq = -INFINITY;
     if ((rc = run_search(ctx, run, run + 1, M, 0, seed, &nout)))
         return rc;
     int32_t *host = nullptr;

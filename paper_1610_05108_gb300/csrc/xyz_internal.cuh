@@ -48,6 +48,14 @@ struct Packed {
     const uint32_t *planes = nullptr;  // [Wp][XYZ_WPLANES] bit planes of the weights per word
     double wkq = 0.0;                  // kappa * wtotal of the current search
     double wscale = 0.0;               // strength = (2S - Q) * wscale (0: divide by Q)
+    // real X through the unbiased transform (Section 3.2); null = binary X
+    const float *Xrs = nullptr;        // [n][Pf] rows of X' = X / nu_i (padding 0)
+    int64_t Pf = 0;                    // row pitch in floats, a multiple of 32
+    const float *Xcs = nullptr;        // [p][Wf] columns of X' (padding 0)
+    int64_t Wf = 0;                    // column pitch in floats, a multiple of 32
+    const float *ysf = nullptr;        // [Wf] Y' = Y nu_i^2 as float (padding 0)
+    float rkq = 0.0f;                  // pass: sum_i Y'_i X'_ij X'_ik >= rkq
+    double rnorm = 0.0;                // ||Y'||_1 (reported strength = dot / rnorm)
 };
 
 constexpr int XYZ_WPLANES = 25;        // weights are integers in [0, 2^24]
@@ -187,6 +195,17 @@ cudaError_t launch_prepare_weights(const double *dY, int64_t n, int64_t Wp, uint
                                    int64_t *launches);
 // sign transform of a real X (count entries) to -1 / +1, zeros by a fair coin
 cudaError_t launch_sign_transform(const float *dX, int64_t count, uint64_t coin_seed, int8_t *out, int *bad,
+                                  cudaStream_t s, int64_t *launches);
+// Real X, unbiased transform (realx.cu).
+cudaError_t launch_unbiased_scale(const float *dX, int64_t n, int64_t p, int64_t Pf, int64_t Wf, float *Xrs,
+                                  float *Xcs, float *nu, unsigned *bad, cudaStream_t s, int64_t *launches);
+cudaError_t launch_unbiased_y(const double *dY, const float *nu, int64_t n, int64_t Wf, double *yprime,
+                              float *ysf, cudaStream_t s, int64_t *launches);
+cudaError_t launch_verify_real(const Packed &pk, const Bucket *buckets, const uint64_t *pair_off,
+                               const uint32_t *nbuckets, const uint64_t *total_pairs, const uint32_t *vals,
+                               int kbits, uint64_t *rec_keys, uint32_t *rec_agree, uint32_t *nrec,
+                               uint32_t rec_cap, cudaStream_t s, int64_t *launches, const int *abort_flag);
+cudaError_t launch_real_strengths(const Packed &pk, PairOut *out, const uint32_t *nout, int64_t cap,
                                   cudaStream_t s, int64_t *launches);
 // Y -> -Y on the response sign bits of the valid rows
 cudaError_t launch_flip_signs(const Packed &pk, cudaStream_t s, int64_t *launches);

@@ -62,6 +62,7 @@ SIGNATURES = {
     "xyz_create": (ctypes.c_int, [_p, _p, _i64, _i64, _p]),
     "xyz_create_dev": (ctypes.c_int, [_p, _p, _i64, _i64, _p, _p]),
     "xyz_create_sign": (ctypes.c_int, [_p, _i64, _i64, _u64, _p]),
+    "xyz_create_unbiased": (ctypes.c_int, [_p, _p, _i64, _i64, _p]),
     "xyz_set_y": (ctypes.c_int, [_p, _p]),
     "xyz_set_y_dev": (ctypes.c_int, [_p, _p]),
     "xyz_set_y_real": (ctypes.c_int, [_p, _p]),
@@ -200,6 +201,18 @@ class Context:
         n, p = X.shape
         h = ctypes.c_void_p()
         _check(load().xyz_create_sign(_ptr(X), n, p, coin_seed & (2**64 - 1), ctypes.byref(h)))
+        return cls(h, n, p)
+
+    @classmethod
+    def from_real_unbiased(cls, X: np.ndarray, Y: np.ndarray) -> "Context":
+        """Real X (n x p) and real Y through the unbiased transform (Section 3.2)."""
+        X = np.asfortranarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float64)
+        n, p = X.shape
+        if Y.shape != (n,):
+            raise ValueError("Y must have shape (n,)")
+        h = ctypes.c_void_p()
+        _check(load().xyz_create_unbiased(_ptr(X), _ptr(Y), n, p, ctypes.byref(h)))
         return cls(h, n, p)
 
     @classmethod

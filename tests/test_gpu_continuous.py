@@ -174,3 +174,58 @@ def test_sign_transform_search_matches_oracle(xyz, orc):
     assert (4, 1000) in set(zip(got["j"].tolist(), got["k"].tolist()))
     with pytest.raises(xyz.XyzError):
         xyz.Context.from_real_sign(np.full((4, 3), np.nan, np.float32))
+
+
+def _unbiased_data(n, p, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-1.5, 1.5, size=(n, p)).astype(np.float32)
+    X[rng.random((n, p)) < 0.01] = 0.0
+    Y = X[:, 2].astype(np.float64) * X[:, p - 5] + rng.normal(0, 0.1, size=n)
+    return X, Y
+
+
+def test_unbiased_candidates_exact(xyz, orc):
+    X, Y = _unbiased_data(160, 900, 60)
+    with xyz.Context.from_real_unbiased(X, Y) as ctx:
+        for run in (0, 3, 11):
+            got = ctx.run_candidates(8, 21, run)
+            want, _ = orc.xyz_unbiased_range(X, Y, run, run + 1, 8, -1.0, 21)
+            assert np.array_equal(got, want), run
+
+
+@pytest.mark.parametrize("n,p,L,M,kappa", [(160, 900, 40, 8, 0.2), (301, 2500, 30, 10, 0.25)])
+def test_unbiased_search_matches_oracle(xyz, orc, n, p, L, M, kappa):
+    X, Y = _unbiased_data(n, p, n + p)
+    with xyz.Context.from_real_unbiased(X, Y) as ctx:
+        got = ctx.search(L, M, kappa, 8)
+    pairs, dots = orc.xyz_unbiased_range(X, Y, 0, L, M, -1.0, 8)     # every candidate with its dot
+    Xs, Ys = orc.unbiased_scale(X, Y)
+    norm1 = np.abs(Ys).sum()
+    thr, tol = kappa * norm1, 1e-4 * norm1
+    cand = {(int(j), int(k)): d for (j, k), d in zip(pairs, dots)}
+    gotset = set(zip(got["j"].tolist(), got["k"].tolist()))
+    for pk_, d in cand.items():
+        if d >= thr + tol:
+            assert pk_ in gotset
+    for pk_, s_ in zip(zip(got["j"].tolist(), got["k"].tolist()), got["strength"].tolist()):
+        assert pk_ in cand and cand[pk_] >= thr - tol
+        assert abs(s_ - cand[pk_] / norm1) < 1e-5
+    assert (got["agree"] == -1).all()
+    assert (2, p - 5) in gotset
+
+
+def test_unbiased_context_limits(xyz):
+    X, Y = _unbiased_data(64, 200, 3)
+    with xyz.Context.from_real_unbiased(X, Y) as ctx:
+        with pytest.raises(xyz.XyzError):
+            ctx.set_y(np.ones(64, np.int8))
+        with pytest.raises(xyz.XyzError):
+            ctx.search_abs(5, 6, 0.3, 1)
+        with pytest.raises(xyz.XyzError):
+            ctx.search(5, 40, 0.3, 1)                   # M >= 32: no real-X path
+        ctx.set_y_real(-Y)                              # a new response is scaled too
+        assert len(ctx.search(20, 6, 0.2, 1)) >= 0
+    Xn = X.copy()
+    Xn[5, 7] = np.nan
+    with pytest.raises(xyz.XyzError):
+        xyz.Context.from_real_unbiased(Xn, Y)
