@@ -74,7 +74,17 @@ __device__ __forceinline__ void bloom_pos(uint32_t h, int shift, uint32_t &word,
 {
     word = (h * 0x9E3779B1u) >> shift;          // shift = 32 - log2(filter words)
     const uint32_t y = h * 0x7FEB352Du + 0x165667B1u;
-    mask = (1u << (y >> 27)) | (1u << ((y >> 22) & 31u));
+    // bits y >> 27 and (y >> 22) mod 32; the funnel shift takes its amount mod 32
+    mask = (1u << (y >> 27)) | __funnelshift_l(1u, 1u, y >> 22);
+}
+
+// 1 when both bits of h are set in its word of F (the same positions as
+// bloom_pos), else 0: two shifts of the loaded word instead of a mask.
+__device__ __forceinline__ uint32_t bloom_has(const uint32_t *F, uint32_t h, int shift)
+{
+    const uint32_t f = F[(h * 0x9E3779B1u) >> shift];
+    const uint32_t y = h * 0x7FEB352Du + 0x165667B1u;
+    return (f >> (y >> 27)) & __funnelshift_r(f, f, y >> 22) & 1u;
 }
 
 // Canonical key of a surviving column (keys.cu): group h = min(kx, kx ^ c)
@@ -272,11 +282,8 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                         keep = valid;
                     } else {
 #pragma unroll
-                        for (int cc = 0; cc < 32; ++cc) {
-                            uint32_t word, mask;
-                            bloom_pos(kcs[cc * P32 + w] ^ c, fshift, word, mask);
-                            keep |= ((F[word] & mask) == mask ? 1u : 0u) << cc;
-                        }
+                        for (int cc = 0; cc < 32; ++cc)
+                            keep += bloom_has(F, kcs[cc * P32 + w] ^ c, fshift) << cc;
                         keep &= valid;
                     }
                     kmask[w] = keep;
