@@ -235,12 +235,21 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                     kcs[cc * P32 + w] = A[cc];         // bit-major: coalesced across the warp
                 if (need) {
                     const uint32_t ncol = (32 * w + 32 <= p32) ? 32u : p32 - 32 * w;
+                    if (ncol == 32) {                  // every word but the last
 #pragma unroll
-                    for (int cc = 0; cc < 32; ++cc) {
-                        if ((uint32_t)cc < ncol) {
+                        for (int cc = 0; cc < 32; ++cc) {
                             uint32_t word, mask;
                             bloom_pos(A[cc], fshift, word, mask);
                             atomicOr(F + word, mask);
+                        }
+                    } else {
+#pragma unroll
+                        for (int cc = 0; cc < 32; ++cc) {
+                            if ((uint32_t)cc < ncol) {
+                                uint32_t word, mask;
+                                bloom_pos(A[cc], fshift, word, mask);
+                                atomicOr(F + word, mask);
+                            }
                         }
                     }
                 }
