@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(JV_THREADS)
                   const uint32_t *__restrict__ vals, int64_t amin, int kbits,
                   uint64_t *__restrict__ rec_keys, uint32_t *__restrict__ rec_agree,
                   uint32_t *__restrict__ nrec, uint32_t rec_cap, const int *__restrict__ abort_flag,
-                  const uint32_t *__restrict__ planes, int64_t wQ, double kq)
+                  const uint32_t *__restrict__ planes, int64_t wQ, double kq,
+                  const uint32_t *__restrict__ bstart, int64_t bstart_cap)
 {
     // WEIGHTED (real response, Section 3.1): yb holds the signs of Y; a
     // candidate passes when (double)(2 S - Q) >= kappa * Q, S the weight sum
@@ -168,18 +169,22 @@ __global__ void __launch_bounds__(JV_THREADS)
     // buckets (each holds >= 1), so every lane then searches only that window.
     for (uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < T; t0 += stride) {
         uint32_t base = 0;
-        if (lane == 0) {
-            uint32_t lo = 0, hi = nb;      // pair_off[lo] <= t0 < pair_off[hi], pair_off[nb] = T
-            while (hi - lo > 1) {
-                uint32_t mid = lo + (hi - lo) / 2;
-                if (pair_off[mid] <= t0)
-                    lo = mid;
-                else
-                    hi = mid;
+        if (bstart && (int64_t)(t0 >> 5) < bstart_cap) {
+            base = bstart[t0 >> 5];        // bucket of candidate t0, precomputed
+        } else {
+            if (lane == 0) {
+                uint32_t lo = 0, hi = nb;      // pair_off[lo] <= t0 < pair_off[hi] (reading T for [nb])
+                while (hi - lo > 1) {
+                    uint32_t mid = lo + (hi - lo) / 2;
+                    if (pair_off[mid] <= t0)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                base = lo;
             }
-            base = lo;
+            base = __shfl_sync(0xffffffffu, base, 0);
         }
-        base = __shfl_sync(0xffffffffu, base, 0);
         const uint64_t t = t0 + lane;
         const bool valid = t < T;
         uint32_t j = 0, k = 0, resp = 0;
@@ -274,6 +279,27 @@ __global__ void __launch_bounds__(JV_THREADS)
                 rec_agree[idx] = (uint32_t)agree;
             }
         }
+    }
+}
+
+// For every block of 32 consecutive candidates, the bucket holding its first
+// candidate: bucket b writes the blocks that start in [pair_off[b],
+// pair_off[b+1]), so every block below bstart_cap gets exactly one writer.
+__global__ void block_start_kernel(const uint64_t *__restrict__ pair_off, const uint32_t *__restrict__ nbuckets,
+                                   const uint64_t *__restrict__ total_pairs, uint32_t *__restrict__ bstart,
+                                   int64_t bstart_cap)
+{
+    const uint32_t nb = *nbuckets;
+    const uint64_t T = *total_pairs;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += stride) {
+        // the scan leaves pair_off[nb] unwritten: the last bucket ends at T
+        const uint64_t lo = pair_off[b], hi = b + 1 < nb ? pair_off[b + 1] : T;
+        uint64_t k1 = (hi + 31) >> 5;
+        if (k1 > (uint64_t)bstart_cap)
+            k1 = (uint64_t)bstart_cap;
+        for (uint64_t k = (lo + 31) >> 5; k < k1; ++k)
+            bstart[k] = (uint32_t)b;
     }
 }
 
@@ -411,23 +437,32 @@ cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_
                           const uint32_t *nbuckets, const uint64_t *total_pairs,
                           const uint32_t *vals, int64_t amin, int kbits, uint64_t *rec_keys,
                           uint32_t *rec_agree, uint32_t *nrec, uint32_t rec_cap, cudaStream_t s,
-                          int64_t *launches, const uint32_t *ybs, const int *abort_flag)
+                          int64_t *launches, const uint32_t *ybs, const int *abort_flag, uint32_t *bstart,
+                          int64_t bstart_cap)
 {
     if (pk.Xcs && !ybs)       // real X (unbiased transform): real inner products
         return launch_verify_real(pk, buckets, pair_off, nbuckets, total_pairs, vals, kbits, rec_keys,
                                   rec_agree, nrec, rec_cap, s, launches, abort_flag);
+    if (bstart && bstart_cap > 0) {
+        block_start_kernel<<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(pair_off, nbuckets, total_pairs,
+                                                                               bstart, bstart_cap);
+        *launches += 1;
+    } else {
+        bstart = nullptr;
+    }
     if (ybs)
         verify_kernel<true, false><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
             pk.Xc, pk.Wp, ybs, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits, rec_keys,
-            rec_agree, nrec, rec_cap, abort_flag, nullptr, 0, 0.0);
+            rec_agree, nrec, rec_cap, abort_flag, nullptr, 0, 0.0, bstart, bstart_cap);
     else if (pk.cdf)
         verify_kernel<false, true><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
             pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits,
-            rec_keys, rec_agree, nrec, rec_cap, abort_flag, pk.planes, (int64_t)pk.wtotal, pk.wkq);
+            rec_keys, rec_agree, nrec, rec_cap, abort_flag, pk.planes, (int64_t)pk.wtotal, pk.wkq, bstart,
+            bstart_cap);
     else
         verify_kernel<false, false><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
             pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits,
-            rec_keys, rec_agree, nrec, rec_cap, abort_flag, nullptr, 0, 0.0);
+            rec_keys, rec_agree, nrec, rec_cap, abort_flag, nullptr, 0, 0.0, bstart, bstart_cap);
     *launches += 1;
     return cudaGetLastError();
 }

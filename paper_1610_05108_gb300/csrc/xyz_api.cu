@@ -99,6 +99,7 @@ struct xyz_ctx {
     int w_exp = 0;               // max|Y| = f 2^w_exp, f in [0.5, 1)
     // real X through the unbiased transform (Section 3.2)
     DevBuf xrs, xcs, xnu, ypr, ysf, rbad;
+    DevBuf vstart;               // verification: bucket of each block of 32 candidates
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
     int64_t rec_cap = 1 << 16;
     int64_t chunk_entries = (int64_t)1 << 25;
@@ -149,7 +150,7 @@ static int64_t ws_bytes(const xyz_ctx *c)
                            &c->resp, &c->ybs, &c->y_alt, &c->y_stage,
                            &c->wq, &c->wcdf, &c->wplanes, &c->wq2, &c->wcdf2, &c->wplanes2,
                            &c->wmeta, &c->wscan, &c->yreal,
-                           &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->rbad};
+                           &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->rbad, &c->vstart};
     int64_t s = 0;
     for (const DevBuf *b : all)
         s += (int64_t)b->bytes;
@@ -353,10 +354,14 @@ int ensure_search_ws(xyz_ctx *c, const Plan &pl, int B, int64_t runs)
     return XYZ_OK;
 }
 
+constexpr int64_t VSTART_CAP = (int64_t)1 << 22;   // blocks of 32 candidates with a precomputed bucket
+
 int ensure_records(xyz_ctx *c, int B)
 {
     const int64_t cap = c->rec_cap;
     int rc;
+    if ((rc = ensure(c->vstart, (size_t)VSTART_CAP * 4)))
+        return rc;
     if ((rc = ensure(c->rec_keys, cap * 8)) || (rc = ensure(c->rec_keys_alt, cap * 8)) ||
         (rc = ensure(c->rec_agree, cap * 4)) || (rc = ensure(c->rec_agree_alt, cap * 4)) ||
         (rc = ensure(c->flags, cap * 4)) || (rc = ensure(c->pos, cap * 4)) ||
@@ -499,7 +504,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  (const uint64_t *)c->pair_off2.ptr, ctr_nbuckets2(c), ctr_total2(c), vs,
                                  amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
                                  (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
-                                 c->stream, &launches, B > 1 ? ybs : nullptr));
+                                 c->stream, &launches, B > 1 ? ybs : nullptr, nullptr,
+                                 (uint32_t *)c->vstart.ptr, VSTART_CAP));
                 tm.end();
                 CU(launch_seg_reset((uint32_t *)c->seg_count.ptr, c->stream, &launches));
                 return XYZ_OK;
@@ -532,7 +538,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  (const uint32_t *)c->members.ptr, amin, pl.kbits,
                                  (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
                                  ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches,
-                                 B > 1 ? ybs : nullptr, ctr_sovf(c)));
+                                 B > 1 ? ybs : nullptr, ctr_sovf(c), (uint32_t *)c->vstart.ptr, VSTART_CAP));
                 tm.end();
                 if (phase == SP_ALL && c->spill_flush && ++since_flush == c->spill_flush && g0 + pl.R < l1) {
                     since_flush = 0;
@@ -582,7 +588,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                      (const uint64_t *)c->pair_off.ptr, ctr_nbuckets(c), ctr_total(c),
                                      (const uint32_t *)c->members.ptr, amin, pl.kbits,
                                      (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
-                                     ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches));
+                                     ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches, nullptr,
+                                     nullptr, (uint32_t *)c->vstart.ptr, VSTART_CAP));
                     tm.end();
                     continue;
                 }
@@ -627,7 +634,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  (const uint64_t *)c->pair_off.ptr, ctr_nbuckets(c), ctr_total(c), vs,
                                  amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
                                  (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
-                                 c->stream, &launches));
+                                 c->stream, &launches, nullptr, nullptr, (uint32_t *)c->vstart.ptr,
+                                 VSTART_CAP));
                 tm.end();
             }
         }
@@ -784,7 +792,7 @@ void destroy_ctx(xyz_ctx *c)
                      &c->pair_off2, &c->scan_tmp2, &c->resp,   &c->ybs, &c->y_alt, &c->y_stage,
                      &c->wq, &c->wcdf, &c->wplanes, &c->wq2, &c->wcdf2, &c->wplanes2,
                      &c->wmeta, &c->wscan, &c->yreal,
-                     &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->rbad};
+                     &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->rbad, &c->vstart};
     for (DevBuf *b : all)
         release(*b);
     if (c->own_stream && c->stream)

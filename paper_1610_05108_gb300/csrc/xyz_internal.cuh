@@ -126,7 +126,8 @@ cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_
                           const uint32_t *vals, int64_t amin, int kbits, uint64_t *rec_keys,
                           uint32_t *rec_agree, uint32_t *nrec, uint32_t rec_cap, cudaStream_t s,
                           int64_t *launches, const uint32_t *ybs = nullptr,
-                          const int *abort_flag = nullptr);
+                          const int *abort_flag = nullptr, uint32_t *bstart = nullptr,
+                          int64_t bstart_cap = 0);
 
 // Sorted records -> unique xyz pairs (device array), count in *nout.
 struct PairOut {
