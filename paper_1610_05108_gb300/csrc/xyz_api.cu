@@ -12,6 +12,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -100,6 +102,7 @@ struct xyz_ctx {
     // real X through the unbiased transform (Section 3.2)
     DevBuf xrs, xcs, xnu, ypr, ysf, rbad;
     DevBuf vstart;               // verification: bucket of each block of 32 candidates
+    DevBuf pXc, pXr, pyb, pbad;  // packed X, response bits, input-check flag (owned contexts)
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
     int64_t rec_cap = 1 << 16;
     int64_t chunk_entries = (int64_t)1 << 25;
@@ -109,15 +112,60 @@ struct xyz_ctx {
     xyz_stats stats;
 };
 
+// Workspace blocks released by a context (grown or destroyed) are kept per
+// device and handed to the next request of a similar size, so that creating
+// contexts, growing workspaces and serving searches do not pay cudaMalloc /
+// cudaFree (which synchronise the device) in steady state.  A block is
+// released only when its context's stream has no work in flight (after a
+// finished search, or the synchronisation in destroy_ctx).
+std::mutex g_pool_mu;
+std::multimap<std::pair<int, size_t>, void *> g_pool;   // (device, bytes) -> block
+size_t g_pool_bytes = 0;
+constexpr size_t POOL_CAP = (size_t)64 << 30;
+
+void pool_put(void *p, size_t bytes)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (g_pool_bytes + bytes > POOL_CAP) {
+        cudaFree(p);
+        return;
+    }
+    g_pool.emplace(std::make_pair(dev, bytes), p);
+    g_pool_bytes += bytes;
+}
+
+// a cached block of want..2*want bytes on the current device, or null
+void *pool_get(size_t want, size_t *got)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pool.lower_bound(std::make_pair(dev, want));
+    if (it == g_pool.end() || it->first.first != dev || it->first.second > 2 * want)
+        return nullptr;
+    void *p = it->second;
+    *got = it->first.second;
+    g_pool_bytes -= *got;
+    g_pool.erase(it);
+    return p;
+}
+
 static int ensure(DevBuf &b, size_t bytes)
 {
     if (b.bytes >= bytes && b.ptr)
         return XYZ_OK;
     if (b.ptr)
-        cudaFree(b.ptr);
+        pool_put(b.ptr, b.bytes);
     b.ptr = nullptr;
     b.bytes = 0;
     size_t want = bytes < 256 ? 256 : bytes;
+    size_t got = 0;
+    if ((b.ptr = pool_get(want, &got))) {
+        b.bytes = got;
+        return XYZ_OK;
+    }
     cudaError_t e = cudaMalloc(&b.ptr, want);
     if (e != cudaSuccess) {
         b.ptr = nullptr;
@@ -132,7 +180,7 @@ static int ensure(DevBuf &b, size_t bytes)
 static void release(DevBuf &b)
 {
     if (b.ptr)
-        cudaFree(b.ptr);
+        pool_put(b.ptr, b.bytes);
     b.ptr = nullptr;
     b.bytes = 0;
 }
@@ -752,12 +800,14 @@ int create_common(const int8_t *dX, const int8_t *dY, int64_t n, int64_t p, cuda
     pk.P = (p + 31) / 32;
     pk.Pp = (pk.P + 7) / 8 * 8;
     size_t bXc = (size_t)p * pk.Wp * 4, bXr = (size_t)n * pk.Pp * 4, byb = (size_t)pk.Wp * 4;
-    cudaError_t e;
-    if ((e = cudaMalloc(&pk.Xc, bXc)) != cudaSuccess || (e = cudaMalloc(&pk.Xr, bXr)) != cudaSuccess ||
-        (e = cudaMalloc(&pk.yb, byb)) != cudaSuccess || (e = cudaMalloc(&c->d_bad, 16)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(XYZ_ENOMEM, std::string("cudaMalloc of packed X failed: ") + cudaGetErrorString(e));
-    }
+    int rc;
+    if ((rc = ensure(c->pXc, bXc)) || (rc = ensure(c->pXr, bXr)) || (rc = ensure(c->pyb, byb)) ||
+        (rc = ensure(c->pbad, 16)))
+        return rc;
+    pk.Xc = (uint32_t *)c->pXc.ptr;
+    pk.Xr = (uint32_t *)c->pXr.ptr;
+    pk.yb = (uint32_t *)c->pyb.ptr;
+    c->d_bad = (int *)c->pbad.ptr;
     c->packed_bytes = (int64_t)(bXc + bXr + byb);
     CU(cudaMemsetAsync(c->d_bad, 0, 16, stream));
     int64_t launches = 0;
@@ -777,12 +827,14 @@ void destroy_ctx(xyz_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream)
         cudaStreamSynchronize(c->stream);
-    if (c->owns_packed) {
-        cudaFree(c->pk.Xc);
-        cudaFree(c->pk.Xr);
-        cudaFree(c->pk.yb);
+    if (c->owns_packed) {                 // packed X, response bits and flag: cached blocks
+        release(c->pXc);
+        release(c->pXr);
+        release(c->pyb);
+        release(c->pbad);
+    } else {
+        cudaFree(c->d_bad);
     }
-    cudaFree(c->d_bad);
     DevBuf *all[] = {&c->keysA,   &c->keysB,       &c->valsA,     &c->valsB,    &c->radix_tmp,
                      &c->cnz,     &c->buckets,     &c->pair_counts, &c->pair_off, &c->scan_tmp,
                      &c->counters, &c->rec_keys,   &c->rec_keys_alt, &c->rec_agree,
@@ -976,22 +1028,23 @@ int xyz_create(const int8_t *X, const int8_t *Y, int64_t n, int64_t p, xyz_ctx *
     int rc = check_dims(n, p);
     if (rc)
         return rc;
-    int8_t *dX = nullptr, *dY = nullptr;
-    cudaError_t e;
-    if ((e = cudaMalloc(&dX, (size_t)n * p)) != cudaSuccess || (e = cudaMalloc(&dY, (size_t)n)) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(dX);
-        return fail(XYZ_ENOMEM, std::string("cudaMalloc of input staging failed: ") + cudaGetErrorString(e));
+    DevBuf sX, sY;                              // staging, from the block cache
+    if ((rc = ensure(sX, (size_t)n * p)) || (rc = ensure(sY, (size_t)n))) {
+        release(sX);
+        return rc;
     }
-    if ((e = cudaMemcpy(dX, X, (size_t)n * p, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(dY, Y, (size_t)n, cudaMemcpyHostToDevice)) != cudaSuccess) {
-        cudaFree(dX);
-        cudaFree(dY);
+    cudaError_t e;
+    if ((e = cudaMemcpy(sX.ptr, X, (size_t)n * p, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(sY.ptr, Y, (size_t)n, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        release(sX);
+        release(sY);
         return fail(XYZ_ECUDA, std::string("cudaMemcpy of X/Y: ") + cudaGetErrorString(e));
     }
-    rc = xyz_create_dev(dX, dY, n, p, nullptr, out);
-    cudaFree(dX);
-    cudaFree(dY);
+    rc = xyz_create_dev((const int8_t *)sX.ptr, (const int8_t *)sY.ptr, n, p, nullptr, out);
+    if (!rc)
+        cudaStreamSynchronize((*out)->stream);  // packing read the staging buffers
+    release(sX);
+    release(sY);
     return rc;
 }
 
