@@ -43,27 +43,28 @@ constexpr int FL_FWORDS = 1 << (FL_LOGF - 5);     // 32768 words (128 KB)
 constexpr int FL_LOGR = 13;
 constexpr int FL_RWORDS = 1 << FL_LOGR;           // refinement filter, in the survivor array
 constexpr int FL_KWORDS = 262144 / 32;            // keep-mask words: p <= 262144
-constexpr int FL_LOGT = 13;
-constexpr int FL_T = 1 << FL_LOGT;                // grouping table slots (key + packed counts)
+constexpr int FL_LOGT_B = 13;                     // grouping table slots, batched kernel: 2^13
 constexpr int FL_ROUNDS = 3;                      // refinement rounds at most
 constexpr uint32_t FL_EMPTY = 0xFFFFFFFFu;
 
 // Shared-memory layout, in 32-bit words.  One response per run: the filter
 // F is dead once the survivors are known, so the grouping table takes its
-// place and the survivor array can hold 6144 entries.  Several responses per
+// place and the survivor array can hold 8192 entries.  Several responses per
 // run: F must outlive every response's grouping, so the table has its own
 // region (where the keep mask also lives) and the survivor array holds 4096.
 template <bool BATCH>
 struct FlLayout {
-    static constexpr int SMAX = BATCH ? 4096 : 6144;           // survivors grouped on chip
+    static constexpr int SMAX = BATCH ? 4096 : 8192;           // survivors grouped on chip
+    static constexpr int LOGT = BATCH ? FL_LOGT_B : 14;        // grouping table slots: 2^LOGT
+    static constexpr int T = 1 << LOGT;
     static constexpr int OFF_SV = FL_FWORDS;                   // [SMAX] u64 | refinement filter
     static constexpr int OFF_KM = OFF_SV + 2 * SMAX;           // [FL_KWORDS] keep mask
-    static constexpr int OFF_TAB = BATCH ? OFF_KM : 0;         // [FL_T] keys, [FL_T] counts
-    static constexpr int WORDS = BATCH ? OFF_TAB + 2 * FL_T : OFF_KM + FL_KWORDS;
+    static constexpr int OFF_TAB = BATCH ? OFF_KM : 0;         // [T] keys, [T] counts
+    static constexpr int WORDS = BATCH ? OFF_TAB + 2 * T : OFF_KM + FL_KWORDS;
     static_assert(2 * SMAX >= FL_RWORDS, "the refinement filter fits the survivor array");
-    static_assert(!BATCH || 2 * FL_T >= FL_KWORDS, "the keep mask lies inside the table");
-    static_assert(BATCH || 2 * FL_T <= FL_FWORDS, "the table fits the filter's memory");
-    static_assert(SMAX < FL_T, "the table has a free slot for every survivor");
+    static_assert(!BATCH || 2 * T >= FL_KWORDS, "the keep mask lies inside the table");
+    static_assert(BATCH || 2 * T <= FL_FWORDS, "the table fits the filter's memory");
+    static_assert(SMAX < T, "the table has a free slot for every survivor");
 };
 
 // Blocked Bloom filter of 2^k words: a key selects one 32-bit word and
@@ -101,7 +102,7 @@ __device__ __forceinline__ uint32_t canon(uint32_t kx, uint32_t c, int tb, uint3
 
 // One CTA per run at a time (passes 1-2 as described at the top of the
 // file).  When the run keeps at most FL_SMAX columns they are grouped on
-// chip: a hash table of FL_T group keys with packed side counts, each group
+// chip: a hash table of group keys with packed side counts, each group
 // with candidates becomes a bucket (bucket and member space reserved with
 // one global atomic pair per run) and its members are written side A first.
 // A run that keeps more, after refinement (for example every column of a run
@@ -142,8 +143,8 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     uint64_t *sv = reinterpret_cast<uint64_t *>(fl_smem + Lay::OFF_SV);      // [FL_SMAX]
     uint32_t *rf = fl_smem + Lay::OFF_SV;                                    // [FL_RWORDS]
     uint32_t *kmask = fl_smem + Lay::OFF_KM;                                 // [FL_KWORDS]
-    uint32_t *tkey = fl_smem + Lay::OFF_TAB;                                 // [FL_T]
-    uint32_t *tcnt = fl_smem + Lay::OFF_TAB + FL_T;                          // [FL_T]
+    uint32_t *tkey = fl_smem + Lay::OFF_TAB;                                 // [Lay::T]
+    uint32_t *tcnt = fl_smem + Lay::OFF_TAB + Lay::T;                        // [Lay::T]
     const int t = threadIdx.x;
     const int lane = t & 31, wp = t >> 5;
     __shared__ int64_t rowoff[32];      // row s_m times the row pitch
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             // response, the filter are dead)
             // table of 2^tlog slots, at least twice the survivors
             int tlog = 8;
-            while (tlog < FL_LOGT && (1u << tlog) < 2 * s)
+            while (tlog < Lay::LOGT && (1u << tlog) < 2 * s)
                 ++tlog;
             const int tsize = 1 << tlog;
             for (int i = t; i < tsize; i += T) {

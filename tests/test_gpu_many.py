@@ -40,7 +40,7 @@ def test_many_equals_alone(xyz, orc):
         (1000, 300, 40, 10, 0.2, 3),
         (150, 700, 10, 33, 0.1, 4),          # general sort path
         (64, 300000, 2, 10, 0.6, 5),         # partitioned grouping
-        (120, 6500, 6, 4, 0.95, 6),          # c = 0 runs spill to the sort path
+        (120, 9000, 6, 4, 0.95, 6),          # c = 0 runs spill to the sort path
         (90, 400, 5, 8, 1.0, 7),             # nothing passes
     ]
     data = [_inst(n, p, 10 + i, pair=(1, p - 1)) for i, (n, p, *_rest) in enumerate(specs)]

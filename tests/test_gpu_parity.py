@@ -81,8 +81,8 @@ def _cand_cases():
     yield "lsd_path_M33", X, Y, 33, range(2)
     yield "lsd_path_M40", X, Y, 40, range(1)
     yield "part_path_M31", X, Y, 31, range(2)
-    X, Y = _rand(90, 7000, 18)
-    Y[:] = 1                                   # c = 0: all 7000 columns survive -> spill path
+    X, Y = _rand(90, 9000, 18)
+    Y[:] = 1                                   # c = 0: all 9000 columns survive -> spill path
     yield "spill_c_zero", X, Y, 13, range(2)
 
 
@@ -180,9 +180,9 @@ def test_search_independent_of_filter(xyz, orc, M):
 
 def test_search_mixing_spilled_and_on_chip_runs(xyz, orc):
     # Y mostly +1: with M = 4 most runs draw only +1 rows (c = 0, every
-    # column survives, p > 6144 -> general sort path), the others are grouped
+    # column survives, p > 8192 -> general sort path), the others are grouped
     # on chip; both feed one result.
-    X, Y = _rand(120, 6500, 19)
+    X, Y = _rand(120, 9000, 19)
     Y[:] = 1
     Y[:6] = -1
     Y = Y * (X[:, 2] * X[:, 3]) * (X[:, 2] * X[:, 3])     # keep +-1, no change
@@ -196,12 +196,12 @@ def test_search_mixing_spilled_and_on_chip_runs(xyz, orc):
 def test_spill_flush_windows_do_not_change_results(xyz, orc):
     # spilled runs grouped through the sort once per search, after every
     # launch group, and after every third one: one result
-    X, Y = _rand(120, 6500, 19)
+    X, Y = _rand(120, 9000, 19)
     Y[:] = 1
     Y[:6] = -1
     want = orc.xyz(X, Y, 12, 4, 0.9, 5)
     with xyz.create(X, Y) as ctx:
-        ctx.set_chunk_entries(6500 // 8)          # one run per launch group
+        ctx.set_chunk_entries(9000 // 8)          # one run per launch group
         for flush in (0, 1, 3):
             ctx.set_spill_flush(flush)
             got = _pairs_array(ctx.search(12, 4, 0.9, 5))
