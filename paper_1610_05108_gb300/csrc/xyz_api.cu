@@ -100,7 +100,7 @@ struct xyz_ctx {
     DevBuf wq, wcdf, wplanes, wq2, wcdf2, wplanes2, wmeta, wscan, yreal;
     int w_exp = 0;               // max|Y| = f 2^w_exp, f in [0.5, 1)
     // real X through the unbiased transform (Section 3.2)
-    DevBuf xrs, xcs, xnu, ypr, ysf, rbad;
+    DevBuf xrs, xcs, xnu, ypr, ysf, ysf2, rbad;
     DevBuf vstart;               // verification: bucket of each block of 32 candidates
     DevBuf pXc, pXr, pyb, pbad;  // packed X, response bits, input-check flag (owned contexts)
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
@@ -198,7 +198,7 @@ static int64_t ws_bytes(const xyz_ctx *c)
                            &c->resp, &c->ybs, &c->y_alt, &c->y_stage,
                            &c->wq, &c->wcdf, &c->wplanes, &c->wq2, &c->wcdf2, &c->wplanes2,
                            &c->wmeta, &c->wscan, &c->yreal,
-                           &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->rbad, &c->vstart};
+                           &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->ysf2, &c->rbad, &c->vstart};
     int64_t s = 0;
     for (const DevBuf *b : all)
         s += (int64_t)b->bytes;
@@ -844,7 +844,7 @@ void destroy_ctx(xyz_ctx *c)
                      &c->pair_off2, &c->scan_tmp2, &c->resp,   &c->ybs, &c->y_alt, &c->y_stage,
                      &c->wq, &c->wcdf, &c->wplanes, &c->wq2, &c->wcdf2, &c->wplanes2,
                      &c->wmeta, &c->wscan, &c->yreal,
-                     &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->rbad, &c->vstart};
+                     &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->ysf2, &c->rbad, &c->vstart};
     for (DevBuf *b : all)
         release(*b);
     if (c->own_stream && c->stream)
@@ -1090,12 +1090,13 @@ int xyz_set_y_real_dev(xyz_ctx *ctx, const double *dY)
         return fail(XYZ_EINVAL, "context does not own its response");
     const int64_t n = ctx->pk.n, Wp = ctx->pk.Wp;
     if (ctx->pk.Xrs) {
-        // real X: the response of the scaled rows, Y'_i = Y_i nu_i^2
+        // real X: the response of the scaled rows, Y'_i = Y_i nu_i^2 (its
+        // float copy goes to a second buffer, swapped in once Y' is accepted)
         int64_t launches = 0;
-        if ((rc = ensure(ctx->ypr, (size_t)n * 8)))
+        if ((rc = ensure(ctx->ypr, (size_t)n * 8)) || (rc = ensure(ctx->ysf2, (size_t)ctx->pk.Wf * 4)))
             return rc;
         CU(launch_unbiased_y(dY, (const float *)ctx->xnu.ptr, n, ctx->pk.Wf, (double *)ctx->ypr.ptr,
-                             (float *)ctx->ysf.ptr, ctx->stream, &launches));
+                             (float *)ctx->ysf2.ptr, ctx->stream, &launches));
         dY = (const double *)ctx->ypr.ptr;
     }
     if ((rc = ensure(ctx->y_alt, (size_t)Wp * 4)) || (rc = ensure(ctx->wq2, (size_t)n * 8)) ||
@@ -1119,6 +1120,10 @@ int xyz_set_y_real_dev(xyz_ctx *ctx, const double *dY)
     std::swap(ctx->wq, ctx->wq2);
     std::swap(ctx->wcdf, ctx->wcdf2);
     std::swap(ctx->wplanes, ctx->wplanes2);
+    if (ctx->pk.Xrs) {
+        std::swap(ctx->ysf, ctx->ysf2);
+        ctx->pk.ysf = (const float *)ctx->ysf.ptr;
+    }
     ctx->pk.cdf = (const uint64_t *)ctx->wcdf.ptr;
     ctx->pk.planes = (const uint32_t *)ctx->wplanes.ptr;
     ctx->pk.wtotal = host[2];
