@@ -341,6 +341,90 @@ __global__ void unique_scatter_kernel(const uint64_t *__restrict__ keys,
     }
 }
 
+// The union of a small record set (at most UQ_SMALL records) in one CTA:
+// bitonic sort of (key, agree) in shared memory, then the first record of
+// every key is written to its place; same result as the sort + unique pair.
+constexpr int UQ_SMALL = 2048;
+constexpr int UQ_THREADS = 1024;
+
+__global__ void __launch_bounds__(UQ_THREADS)
+    unique_small_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ agree, int N, int kbits,
+                        int64_t n, PairOut *__restrict__ out, uint32_t *__restrict__ nout,
+                        uint32_t *__restrict__ resp)
+{
+    __shared__ uint64_t sk[UQ_SMALL];
+    __shared__ uint32_t sa[UQ_SMALL];
+    __shared__ uint32_t wsum[UQ_THREADS / 32];
+    const int t = threadIdx.x;
+    int size = 1;
+    while (size < N)
+        size <<= 1;
+    for (int i = t; i < size; i += UQ_THREADS) {
+        sk[i] = i < N ? keys[i] : ~0ULL;
+        sa[i] = i < N ? agree[i] : 0u;
+    }
+    __syncthreads();
+    for (int k = 2; k <= size; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = t; i < size; i += UQ_THREADS) {
+                const int l = i ^ jj;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const uint64_t a = sk[i], b = sk[l];
+                    if ((a > b) == up) {
+                        sk[i] = b;
+                        sk[l] = a;
+                        const uint32_t x = sa[i];
+                        sa[i] = sa[l];
+                        sa[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // first record of each key: flag, block-wide exclusive scan (two per thread)
+    const int i0 = 2 * t, i1 = 2 * t + 1;
+    const uint32_t f0 = (i0 < N && (i0 == 0 || sk[i0] != sk[i0 - 1])) ? 1u : 0u;
+    const uint32_t f1 = (i1 < N && sk[i1] != sk[i1 - 1]) ? 1u : 0u;
+    const uint32_t mine = f0 + f1;
+    const int lane = t & 31, wp = t >> 5;
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    if (lane == 31)
+        wsum[wp] = incl;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int w = 0; w < UQ_THREADS / 32; ++w) {
+        before += w < wp ? wsum[w] : 0u;
+        total += wsum[w];
+    }
+    uint32_t pos = before + incl - mine;
+    const uint64_t kmask = (kbits >= 64) ? ~0ULL : ((1ULL << kbits) - 1ULL);
+    for (int q = 0; q < 2; ++q) {
+        const int i = q ? i1 : i0;
+        if (q ? f1 : f0) {
+            const uint64_t key = sk[i];
+            PairOut o;
+            o.j = (int32_t)((key >> kbits) & kmask);
+            o.k = (int32_t)(key & kmask);
+            o.agree = (int32_t)sa[i];
+            o.strength = (float)((double)(2 * (int64_t)sa[i] - n) / (double)n);
+            out[pos] = o;
+            if (resp)
+                resp[pos] = (uint32_t)(key >> (2 * kbits));
+            ++pos;
+        }
+    }
+    if (t == 0)
+        *nout = total;
+}
+
 __global__ void agree_pairs_kernel(const uint32_t *__restrict__ Xc, int64_t Wp,
                                    const uint32_t *__restrict__ yb, const int32_t *__restrict__ j,
                                    const int32_t *__restrict__ k, int64_t count,
@@ -482,6 +566,19 @@ cudaError_t launch_unique(const uint64_t *rec_keys, const uint32_t *rec_agree, c
         return e;
     unique_scatter_kernel<<<g, JV_THREADS, 0, s>>>(rec_keys, rec_agree, nrec, cap, flags, pos, kbits,
                                                    n, out, resp);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+int64_t unique_small_cap() { return UQ_SMALL; }
+
+cudaError_t launch_unique_small(const uint64_t *rec_keys, const uint32_t *rec_agree, int64_t N, int kbits,
+                                int64_t n, PairOut *out, uint32_t *nout, cudaStream_t s, int64_t *launches,
+                                uint32_t *resp)
+{
+    if (N < 1 || N > UQ_SMALL)
+        return cudaErrorInvalidValue;
+    unique_small_kernel<<<1, UQ_THREADS, 0, s>>>(rec_keys, rec_agree, (int)N, kbits, n, out, nout, resp);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -711,18 +711,24 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
             continue;
         }
         tm.begin(ST_DEDUP);
-        bool alt = false;
-        char *dt = (char *)c->dedup_tmp.ptr;
-        size_t rt = radix_temp_bytes(c->rec_cap);
-        CU(radix_sort64((uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
-                        (uint64_t *)c->rec_keys_alt.ptr, (uint32_t *)c->rec_agree_alt.ptr,
-                        (int64_t)nrec, bbits + 2 * pl.kbits, dt, &alt, c->stream, &launches));
-        const uint64_t *rk = (const uint64_t *)(alt ? c->rec_keys_alt.ptr : c->rec_keys.ptr);
-        const uint32_t *ra = (const uint32_t *)(alt ? c->rec_agree_alt.ptr : c->rec_agree.ptr);
-        CU(launch_unique(rk, ra, ctr_nrec(c), c->rec_cap, pl.kbits, c->pk.n,
-                         (uint32_t *)c->flags.ptr, (uint32_t *)c->pos.ptr, dt + rt,
-                         (PairOut *)c->out.ptr, ctr_nout(c), c->stream, &launches,
-                         B > 1 ? (uint32_t *)c->resp.ptr : nullptr));
+        if (nrec > 0 && (int64_t)nrec <= unique_small_cap()) {
+            CU(launch_unique_small((const uint64_t *)c->rec_keys.ptr, (const uint32_t *)c->rec_agree.ptr,
+                                   (int64_t)nrec, pl.kbits, c->pk.n, (PairOut *)c->out.ptr, ctr_nout(c),
+                                   c->stream, &launches, B > 1 ? (uint32_t *)c->resp.ptr : nullptr));
+        } else if (nrec > 0) {
+            bool alt = false;
+            char *dt = (char *)c->dedup_tmp.ptr;
+            size_t rt = radix_temp_bytes(c->rec_cap);
+            CU(radix_sort64((uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
+                            (uint64_t *)c->rec_keys_alt.ptr, (uint32_t *)c->rec_agree_alt.ptr,
+                            (int64_t)nrec, bbits + 2 * pl.kbits, dt, &alt, c->stream, &launches));
+            const uint64_t *rk = (const uint64_t *)(alt ? c->rec_keys_alt.ptr : c->rec_keys.ptr);
+            const uint32_t *ra = (const uint32_t *)(alt ? c->rec_agree_alt.ptr : c->rec_agree.ptr);
+            CU(launch_unique(rk, ra, ctr_nrec(c), c->rec_cap, pl.kbits, c->pk.n,
+                             (uint32_t *)c->flags.ptr, (uint32_t *)c->pos.ptr, dt + rt,
+                             (PairOut *)c->out.ptr, ctr_nout(c), c->stream, &launches,
+                             B > 1 ? (uint32_t *)c->resp.ptr : nullptr));
+        }
         tm.end();
         if (c->pk.Xcs && nrec > 0)
             CU(launch_real_strengths(c->pk, (PairOut *)c->out.ptr, ctr_nout(c), (int64_t)nrec, c->stream,
@@ -1268,7 +1274,13 @@ int xyz_brute_force(xyz_ctx *ctx, double kappa, xyz_pair **pairs, int64_t *npair
             continue;
         }
         uint32_t nout = 0;
-        if (nrec > 0) {
+        if (nrec > 0 && (int64_t)nrec <= unique_small_cap()) {
+            CU(launch_unique_small((const uint64_t *)c->rec_keys.ptr, (const uint32_t *)c->rec_agree.ptr,
+                                   (int64_t)nrec, kbits, c->pk.n, (PairOut *)c->out.ptr, ctr_nout(c), c->stream,
+                                   &launches));
+            CU(cudaMemcpyAsync(&nout, ctr_nout(c), 4, cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+        } else if (nrec > 0) {
             // order the passing pairs by (j, k)
             bool alt = false;
             char *dt = (char *)c->dedup_tmp.ptr;

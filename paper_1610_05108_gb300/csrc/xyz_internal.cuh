@@ -134,6 +134,12 @@ struct PairOut {
     int32_t j, k, agree;
     float strength;
 };
+// the union of at most unique_small_cap() records (N known on the host) in
+// one CTA; the same output as radix_sort64 + launch_unique
+int64_t unique_small_cap();
+cudaError_t launch_unique_small(const uint64_t *rec_keys, const uint32_t *rec_agree, int64_t N, int kbits,
+                                int64_t n, PairOut *out, uint32_t *nout, cudaStream_t s, int64_t *launches,
+                                uint32_t *resp = nullptr);
 cudaError_t launch_unique(const uint64_t *rec_keys, const uint32_t *rec_agree, const uint32_t *nrec,
                           int64_t cap, int kbits, int64_t n, uint32_t *flags, uint32_t *pos,
                           void *scan_temp, PairOut *out, uint32_t *nout, cudaStream_t s,
