@@ -419,9 +419,9 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
 
             // grouping on chip in the table (the keep mask and, for one
             // response, the filter are dead)
-            // table of 2^tlog slots, at least twice the survivors
+            // table of 2^tlog slots, at least 4/3 of the survivors (load <= 3/4)
             int tlog = 8;
-            while (tlog < Lay::LOGT && (1u << tlog) < 2 * s)
+            while (tlog < Lay::LOGT && 3u * (1u << tlog) < 4 * s)
                 ++tlog;
             const int tsize = 1 << tlog;
             for (int i = t; i < tsize; i += T) {
