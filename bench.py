@@ -168,7 +168,7 @@ def load_traffic():
     return out
 
 
-# Work per unit of each stage (one run = p columns), stated in the design doc:
+# Work per unit of each stage (one run = p columns):
 #   keys (survivor filter, ALU-bound): 28 integer operations per column and
 #       run -- 12.5 for the 32 x 32 bit transpose that forms the M-bit keys
 #       (400 ops per 32 columns), 6 to insert kx into the blocked Bloom

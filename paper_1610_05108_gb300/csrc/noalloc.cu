@@ -126,7 +126,7 @@ extern "C" int xyz_run_candidates_noalloc(xyz_ctx *ctx, int32_t M, uint64_t seed
     const int64_t p = pk.p;
     if ((int64_t)radix_temp_bytes(p) > RADIX_BYTES || (int64_t)scan_temp_bytes(NA_BCAP) > SCAN_BYTES ||
         (int64_t)(radix_temp_bytes(NA_REC) + scan_temp_bytes(NA_REC)) > DEDUP_BYTES)
-        return fail(XYZ_EINVAL, "scratch layout too small for this build");
+        return fail(XYZ_EINVAL, "scratch layout too small for this library");
     const int dev = ctx_device(ctx);
     NA_CU(cudaSetDevice(dev));
     unsigned char *base = nullptr;
