@@ -315,11 +315,19 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 wbase = __shfl_sync(FULL, wbase, 31);
                 uint32_t o = wbase + incl - cnt;
                 while (keep && o < (uint32_t)FL_SMAX) {
-                    const int cc = __ffs(keep) - 1;
+                    // two survivors per step, so that their key re-reads overlap
+                    const int c0 = __ffs(keep) - 1;
                     keep &= keep - 1;
-                    const uint32_t kx = kcs[cc * P32 + w];   // survivors only: re-read, cache-hot
-                    sv[o] = ((uint64_t)canon(kx, c, tb, lowmask) << 32) | (32 * w + cc);
-                    ++o;
+                    const bool two = keep != 0 && o + 1 < (uint32_t)FL_SMAX;
+                    const int c1 = two ? __ffs(keep) - 1 : c0;
+                    if (two)
+                        keep &= keep - 1;
+                    const uint32_t k0 = kcs[c0 * P32 + w];   // survivors only: re-read, cache-hot
+                    const uint32_t k1 = kcs[c1 * P32 + w];
+                    sv[o] = ((uint64_t)canon(k0, c, tb, lowmask) << 32) | (32 * w + c0);
+                    if (two)
+                        sv[o + 1] = ((uint64_t)canon(k1, c, tb, lowmask) << 32) | (32 * w + c1);
+                    o += two ? 2u : 1u;
                 }
             }
             __syncthreads();
@@ -338,12 +346,21 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                     const uint32_t salt = 0x9E3779B9u * (uint32_t)round;
                     for (uint32_t w = t; w < P32; w += T) {
                         uint32_t keep = kmask[w];
-                        while (keep) {
-                            const int cc = __ffs(keep) - 1;
+                        while (keep) {                 // two keys per step
+                            const int c0 = __ffs(keep) - 1;
                             keep &= keep - 1;
+                            const bool two = keep != 0;
+                            const int c1 = two ? __ffs(keep) - 1 : c0;
+                            if (two)
+                                keep &= keep - 1;
+                            const uint32_t k0 = kcs[c0 * P32 + w], k1 = kcs[c1 * P32 + w];
                             uint32_t word, mask;
-                            bloom_pos(mix32(kcs[cc * P32 + w] ^ salt), 32 - FL_LOGR, word, mask);
+                            bloom_pos(mix32(k0 ^ salt), 32 - FL_LOGR, word, mask);
                             atomicOr(rf + word, mask);
+                            if (two) {
+                                bloom_pos(mix32(k1 ^ salt), 32 - FL_LOGR, word, mask);
+                                atomicOr(rf + word, mask);
+                            }
                         }
                     }
                     __syncthreads();
@@ -351,13 +368,21 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                         const uint32_t w = st * T + t;
                         uint32_t keep = w < P32 ? kmask[w] : 0u;
                         uint32_t left = keep;
-                        while (left) {
-                            const int cc = __ffs(left) - 1;
+                        while (left) {                 // two keys per step
+                            const int c0 = __ffs(left) - 1;
                             left &= left - 1;
+                            const bool two = left != 0;
+                            const int c1 = two ? __ffs(left) - 1 : c0;
+                            if (two)
+                                left &= left - 1;
+                            const uint32_t k0 = kcs[c0 * P32 + w], k1 = kcs[c1 * P32 + w];
                             uint32_t word, mask;
-                            bloom_pos(mix32((kcs[cc * P32 + w] ^ c) ^ salt), 32 - FL_LOGR, word, mask);
+                            bloom_pos(mix32((k0 ^ c) ^ salt), 32 - FL_LOGR, word, mask);
                             if ((rf[word] & mask) != mask)
-                                keep &= ~(1u << cc);
+                                keep &= ~(1u << c0);
+                            bloom_pos(mix32((k1 ^ c) ^ salt), 32 - FL_LOGR, word, mask);
+                            if ((rf[word] & mask) != mask)
+                                keep &= ~(1u << c1);
                         }
                         if (w < P32)
                             kmask[w] = keep;
@@ -397,19 +422,28 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                         wbase = atomicAdd(to_global ? &cursor : &scur, wtot);
                     wbase = __shfl_sync(FULL, wbase, 31);
                     uint32_t o = wbase + incl - cnt;
-                    while (keep) {
-                        const int cc = __ffs(keep) - 1;
-                        keep &= keep - 1;
-                        const uint32_t key = canon(kcs[cc * P32 + w], c, tb, lowmask);
+                    auto emit = [&](uint32_t at, uint32_t key, int cc) {
                         if (to_global) {
-                            if (o < seg_cap) {
-                                okeys[o] = runbits | (SegKey)key;
-                                ovals[o] = 32 * w + cc;
+                            if (at < seg_cap) {
+                                okeys[at] = runbits | (SegKey)key;
+                                ovals[at] = 32 * w + cc;
                             }
-                        } else if (o < (uint32_t)FL_SMAX) {
-                            sv[o] = ((uint64_t)key << 32) | (32 * w + cc);
+                        } else if (at < (uint32_t)FL_SMAX) {
+                            sv[at] = ((uint64_t)key << 32) | (32 * w + cc);
                         }
-                        ++o;
+                    };
+                    while (keep) {                     // two survivors per step
+                        const int c0 = __ffs(keep) - 1;
+                        keep &= keep - 1;
+                        const bool two = keep != 0;
+                        const int c1 = two ? __ffs(keep) - 1 : c0;
+                        if (two)
+                            keep &= keep - 1;
+                        const uint32_t k0 = kcs[c0 * P32 + w], k1 = kcs[c1 * P32 + w];
+                        emit(o, canon(k0, c, tb, lowmask), c0);
+                        if (two)
+                            emit(o + 1, canon(k1, c, tb, lowmask), c1);
+                        o += two ? 2u : 1u;
                     }
                 }
                 __syncthreads();
