@@ -114,7 +114,7 @@ __device__ __forceinline__ int agree_cols(const uint32_t *__restrict__ Xc, int64
 // pieces of the two columns (fully used 128-byte segments) and summing their
 // popcounts with shuffles.  Each lane keeps its pieces of the response bits
 // in registers across the steps.
-constexpr int VQ = 4;   // response pieces per lane held in registers (columns up to 4096 rows)
+// VQ: response pieces per lane held in registers (columns up to VQ * 1024 rows)
 
 // Weighted agreement of one 32-row word (Section 3.1): sum over the agreeing
 // rows of their fixed-point weights, from the weights' bit planes of that
@@ -129,8 +129,8 @@ __device__ __forceinline__ int32_t word_weight(const uint32_t *__restrict__ plan
     return s;                     // <= 32 (2^25 - 1) < 2^31
 }
 
-template <bool BATCH, bool WEIGHTED>
-__global__ void __launch_bounds__(JV_THREADS)
+template <bool BATCH, bool WEIGHTED, int VQ>
+__global__ void __launch_bounds__(JV_THREADS, (VQ == 2 && !WEIGHTED) ? 5 : 1)   // 5: 48 registers
     verify_kernel(const uint32_t *__restrict__ Xc, int64_t Wp, const uint32_t *__restrict__ yb,
                   const Bucket *__restrict__ buckets, const uint64_t *__restrict__ pair_off,
                   const uint32_t *__restrict__ nbuckets, const uint64_t *__restrict__ total_pairs,
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(JV_THREADS)
                   uint64_t *__restrict__ rec_keys, uint32_t *__restrict__ rec_agree,
                   uint32_t *__restrict__ nrec, uint32_t rec_cap, const int *__restrict__ abort_flag,
                   const uint32_t *__restrict__ planes, int64_t wQ, double kq,
-                  const uint32_t *__restrict__ bstart, int64_t bstart_cap)
+                  const uint32_t *__restrict__ bstart, int64_t bstart_cap, int *__restrict__ verr)
 {
     // WEIGHTED (real response, Section 3.1): yb holds the signs of Y; a
     // candidate passes when (double)(2 S - Q) >= kappa * Q, S the weight sum
@@ -164,9 +164,8 @@ __global__ void __launch_bounds__(JV_THREADS)
         yr[i] = q < nq ? __ldg(y4 + q) : make_uint4(0, 0, 0, 0);
     }
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    // Each warp takes 32 consecutive candidates.  Lane 0 finds the bucket of
-    // the first by binary search; 32 consecutive candidates span at most 32
-    // buckets (each holds >= 1), so every lane then searches only that window.
+    // Each warp takes 32 consecutive candidates; the bucket of the first comes
+    // from the block starts (else lane 0's binary search).
     for (uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < T; t0 += stride) {
         uint32_t base = 0;
         if (bstart && (int64_t)(t0 >> 5) < bstart_cap) {
@@ -186,21 +185,33 @@ __global__ void __launch_bounds__(JV_THREADS)
             base = __shfl_sync(0xffffffffu, base, 0);
         }
         const uint64_t t = t0 + lane;
-        const bool valid = t < T;
+        bool valid = t < T;
+        // Bucket of each lane's candidate.  32 consecutive candidates span
+        // buckets base .. base + 31 (each holds >= 1), so lane i reads the
+        // start of bucket base + 1 + i (one coalesced load); a start at
+        // offset d in 1..31 of the block sets bit d, and a lane's bucket is
+        // base plus the bits at or below its offset.
+        const uint32_t bi = base + 1u + (uint32_t)lane;
+        const uint64_t po = bi < nb ? pair_off[bi] : ~0ULL;
+        const uint64_t d = po - t0;
+        const uint32_t mark = __reduce_or_sync(0xffffffffu, d < 32 ? (1u << d) : 0u);
         uint32_t j = 0, k = 0, resp = 0;
         if (valid) {
-            uint32_t lo = base, hi = (nb - base > 33u) ? base + 33u : nb;
-            while (hi - lo > 1) {
-                uint32_t mid = lo + (hi - lo) / 2;
-                if (pair_off[mid] <= t)
-                    lo = mid;
-                else
-                    hi = mid;
-            }
+            const uint32_t lo = base + __popc(mark & (0xFFFFFFFFu >> (31 - lane)));
             const Bucket B = buckets[lo];
             const uint64_t u = t - pair_off[lo];
+            // self-check: the offset must lie inside the bucket before any of
+            // its members is read; a miss is reported, never dereferenced
+            const uint64_t np = B.nB ? (uint64_t)B.nA * B.nB : (uint64_t)B.nA * (B.nA - 1) / 2;
+            if (u >= np) {
+                valid = false;
+                if (verr)
+                    atomicOr(verr, 2);
+            }
             resp = B.pad;
-            if (B.nB) {
+            if (!valid) {
+                // nothing to read
+            } else if (B.nB) {
                 uint64_t ia = u / B.nB, ib = u - ia * B.nB;
                 j = vals[B.start + ia];
                 k = vals[B.start + B.nA + ib];
@@ -486,6 +497,17 @@ int64_t max_resident_blocks()
     return (int64_t)g_sm_count * 8;
 }
 
+// One block per resident slot of the kernel on every SM: the grid-stride
+// loops then finish in a single wave, with no half-filled second one.
+template <typename Kern>
+unsigned resident_grid(Kern kernel)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, JV_THREADS, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 4;
+    return (unsigned)(max_resident_blocks() / 8 * per_sm);
+}
+
 template <typename K>
 cudaError_t join_impl(const K *keys, int64_t N, int M, int rbits, int runbits, const uint8_t *cnz,
                       Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
@@ -522,7 +544,7 @@ cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_
                           const uint32_t *vals, int64_t amin, int kbits, uint64_t *rec_keys,
                           uint32_t *rec_agree, uint32_t *nrec, uint32_t rec_cap, cudaStream_t s,
                           int64_t *launches, const uint32_t *ybs, const int *abort_flag, uint32_t *bstart,
-                          int64_t bstart_cap)
+                          int64_t bstart_cap, int *verr)
 {
     if (pk.Xcs && !ybs)       // real X (unbiased transform): real inner products
         return launch_verify_real(pk, buckets, pair_off, nbuckets, total_pairs, vals, kbits, rec_keys,
@@ -534,19 +556,27 @@ cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_
     } else {
         bstart = nullptr;
     }
-    if (ybs)
-        verify_kernel<true, false><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
-            pk.Xc, pk.Wp, ybs, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits, rec_keys,
-            rec_agree, nrec, rec_cap, abort_flag, nullptr, 0, 0.0, bstart, bstart_cap);
-    else if (pk.cdf)
-        verify_kernel<false, true><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
-            pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits,
-            rec_keys, rec_agree, nrec, rec_cap, abort_flag, pk.planes, (int64_t)pk.wtotal, pk.wkq, bstart,
-            bstart_cap);
-    else
-        verify_kernel<false, false><<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(
-            pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs, vals, amin, kbits,
-            rec_keys, rec_agree, nrec, rec_cap, abort_flag, nullptr, 0, 0.0, bstart, bstart_cap);
+    // response pieces held in registers: 2 per lane covers columns of up to
+    // 2048 rows (16 pieces of 16 bytes), 4 up to 4096; longer columns read
+    // the rest from memory
+    const bool short_cols = pk.Wp <= 64;
+    if (ybs) {
+        auto k = short_cols ? verify_kernel<true, false, 2> : verify_kernel<true, false, 4>;
+        k<<<resident_grid(k), JV_THREADS, 0, s>>>(pk.Xc, pk.Wp, ybs, buckets, pair_off, nbuckets, total_pairs,
+                                                  vals, amin, kbits, rec_keys, rec_agree, nrec, rec_cap,
+                                                  abort_flag, nullptr, 0, 0.0, bstart, bstart_cap, verr);
+    } else if (pk.cdf) {
+        auto k = short_cols ? verify_kernel<false, true, 2> : verify_kernel<false, true, 4>;
+        k<<<resident_grid(k), JV_THREADS, 0, s>>>(pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs,
+                                                  vals, amin, kbits, rec_keys, rec_agree, nrec, rec_cap,
+                                                  abort_flag, pk.planes, (int64_t)pk.wtotal, pk.wkq, bstart,
+                                                  bstart_cap, verr);
+    } else {
+        auto k = short_cols ? verify_kernel<false, false, 2> : verify_kernel<false, false, 4>;
+        k<<<resident_grid(k), JV_THREADS, 0, s>>>(pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs,
+                                                  vals, amin, kbits, rec_keys, rec_agree, nrec, rec_cap,
+                                                  abort_flag, nullptr, 0, 0.0, bstart, bstart_cap, verr);
+    }
     *launches += 1;
     return cudaGetLastError();
 }

@@ -140,7 +140,7 @@ extern "C" int xyz_run_candidates_noalloc(xyz_ctx *ctx, int32_t M, uint64_t seed
     uint8_t *cnz = (uint8_t *)(base + OFF_CNZ);
     Bucket *buckets = (Bucket *)(base + OFF_BUCKETS);
     uint64_t *pcount = (uint64_t *)(base + OFF_PCOUNT), *poff = (uint64_t *)(base + OFF_POFF);
-    uint32_t *ctr = (uint32_t *)(base + OFF_CTR);           // [0] buckets [1] records [2] unique
+    uint32_t *ctr = (uint32_t *)(base + OFF_CTR);           // [0] buckets [1] records [2] unique [3] error
     uint64_t *total = (uint64_t *)(base + OFF_CTR + 16);
     uint64_t *cand = (uint64_t *)(base + OFF_CTR + 24);
     uint64_t *rkeys = (uint64_t *)(base + OFF_RKEYS), *rkeys_alt = (uint64_t *)(base + OFF_RKEYS_ALT);
@@ -161,11 +161,16 @@ extern "C" int xyz_run_candidates_noalloc(xyz_ctx *ctx, int32_t M, uint64_t seed
     const uint32_t *vs = alt ? valsB : valsA;
     NA_CU(launch_join64(ks, p, M, 0, cnz, buckets, pcount, ctr, s, &launches));
     NA_CU(scan_u64_dev(pcount, poff, ctr, bcap, total, cand, base + OFF_SCAN, s, &launches));
+    int *verr = (int *)(ctr + 3);
     NA_CU(launch_verify(pk, buckets, poff, ctr, total, vs, 0, kbits, rkeys, ragree, ctr + 1,
-                        (uint32_t)NA_REC, s, &launches));
+                        (uint32_t)NA_REC, s, &launches, nullptr, nullptr, nullptr, 0, verr));
     uint32_t nrec = 0;
+    int err = 0;
     NA_CU(cudaMemcpyAsync(&nrec, ctr + 1, 4, cudaMemcpyDeviceToHost, s));
+    NA_CU(cudaMemcpyAsync(&err, verr, 4, cudaMemcpyDeviceToHost, s));
     NA_CU(cudaStreamSynchronize(s));
+    if (err)
+        return fail(XYZ_ECUDA, "internal error: a candidate's offset lies outside its bucket");
     if ((int64_t)nrec > NA_REC)
         return fail(XYZ_ENOMEM, "run has " + std::to_string(nrec) +
                                     " candidates, above the allocation-free limit XYZ_NOALLOC_MAX_PAIRS = " +

@@ -553,7 +553,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
                                  (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
                                  c->stream, &launches, B > 1 ? ybs : nullptr, nullptr,
-                                 (uint32_t *)c->vstart.ptr, VSTART_CAP));
+                                 (uint32_t *)c->vstart.ptr, VSTART_CAP, ctr_err(c)));
                 tm.end();
                 CU(launch_seg_reset((uint32_t *)c->seg_count.ptr, c->stream, &launches));
                 return XYZ_OK;
@@ -586,7 +586,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  (const uint32_t *)c->members.ptr, amin, pl.kbits,
                                  (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
                                  ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches,
-                                 B > 1 ? ybs : nullptr, ctr_sovf(c), (uint32_t *)c->vstart.ptr, VSTART_CAP));
+                                 B > 1 ? ybs : nullptr, ctr_sovf(c), (uint32_t *)c->vstart.ptr, VSTART_CAP,
+                                 ctr_err(c)));
                 tm.end();
                 if (phase == SP_ALL && c->spill_flush && ++since_flush == c->spill_flush && g0 + pl.R < l1) {
                     since_flush = 0;
@@ -637,7 +638,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                      (const uint32_t *)c->members.ptr, amin, pl.kbits,
                                      (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
                                      ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches, nullptr,
-                                     nullptr, (uint32_t *)c->vstart.ptr, VSTART_CAP));
+                                     nullptr, (uint32_t *)c->vstart.ptr, VSTART_CAP, ctr_err(c)));
                     tm.end();
                     continue;
                 }
@@ -683,7 +684,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
                                  (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
                                  c->stream, &launches, nullptr, nullptr, (uint32_t *)c->vstart.ptr,
-                                 VSTART_CAP));
+                                 VSTART_CAP, ctr_err(c)));
                 tm.end();
             }
         }
@@ -697,6 +698,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
         CU(cudaMemcpyAsync(&cand, ctr_cand(c), 8, cudaMemcpyDeviceToHost, c->stream));
         CU(cudaMemcpyAsync(&err, ctr_err(c), 4, cudaMemcpyDeviceToHost, c->stream));
         CU(cudaStreamSynchronize(c->stream));
+        if (err & 2)
+            return fail(XYZ_ECUDA, "internal error: a candidate's offset lies outside its bucket");
         if (err)
             return fail(XYZ_ECUDA, "grouping table could not separate a partition's keys");
         if ((int64_t)nrec > c->rec_cap) {

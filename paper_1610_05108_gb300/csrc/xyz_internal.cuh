@@ -120,14 +120,16 @@ cudaError_t launch_join64(const uint64_t *keys, int64_t N, int M, int rbits, con
                           cudaStream_t s, int64_t *launches, int runbits = -1);
 
 // Verify every candidate of the buckets; append passing (key, agree)
-// records, key = j * 2^kbits + k with j < k.
+// records, key = j * 2^kbits + k with j < k.  verr (may be null) gets bit 2
+// when a candidate's offset is not inside the bucket its lookup found (an
+// internal error; the candidate is skipped, none of its members is read).
 cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_t *pair_off,
                           const uint32_t *nbuckets, const uint64_t *total_pairs,
                           const uint32_t *vals, int64_t amin, int kbits, uint64_t *rec_keys,
                           uint32_t *rec_agree, uint32_t *nrec, uint32_t rec_cap, cudaStream_t s,
                           int64_t *launches, const uint32_t *ybs = nullptr,
                           const int *abort_flag = nullptr, uint32_t *bstart = nullptr,
-                          int64_t bstart_cap = 0);
+                          int64_t bstart_cap = 0, int *verr = nullptr);
 
 // Sorted records -> unique xyz pairs (device array), count in *nout.
 struct PairOut {
