@@ -106,7 +106,11 @@ typedef struct xyz_stats {
  * response bits; Z is never materialised (its bits are X's bits xor Y's).
  * X: host pointer, n*p int8, column-major.  Y: host pointer, n int8.
  * n >= 1, 2 <= p < 2^31, n < 2^31.  Any entry other than -1/+1 gives
- * XYZ_EINVAL.  On success *out owns all device state. */
+ * XYZ_EINVAL.  On success *out owns all device state.  When both buffers
+ * are page-locked host memory mapped into the device's address space (for
+ * example cudaHostAlloc or torch's pin_memory), the pack kernel reads them
+ * in place -- one pass over X, no staging copy; pageable buffers are copied
+ * to the device first.  Either way X and Y are not referenced after return. */
 int xyz_create(const int8_t *X, const int8_t *Y, int64_t n, int64_t p, xyz_ctx **out);
 
 /* Same as xyz_create with X and Y already in device memory (e.g. torch

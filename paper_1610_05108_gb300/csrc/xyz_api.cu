@@ -861,6 +861,19 @@ void destroy_ctx(xyz_ctx *c)
     delete c;
 }
 
+// Device address of a host pointer that lies in page-locked memory mapped
+// into the device's address space, else null (pageable memory, or any
+// error, which is cleared).
+const void *mapped_device_ptr(const void *h)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 int check_dims(int64_t n, int64_t p)
 {
     if (n < 1 || n >= ((int64_t)1 << 31))
@@ -1037,6 +1050,12 @@ int xyz_create(const int8_t *X, const int8_t *Y, int64_t n, int64_t p, xyz_ctx *
     int rc = check_dims(n, p);
     if (rc)
         return rc;
+    // Pinned host buffers that the device can address (mapped page-locked
+    // memory): the pack kernel reads them directly, so the transfer and the
+    // packing are one pass over X and no staging copy is made.
+    const int8_t *mX = (const int8_t *)mapped_device_ptr(X), *mY = (const int8_t *)mapped_device_ptr(Y);
+    if (mX && mY)
+        return xyz_create_dev(mX, mY, n, p, nullptr, out);   // returns after the pack has run
     DevBuf sX, sY;                              // staging, from the block cache
     if ((rc = ensure(sX, (size_t)n * p)) || (rc = ensure(sY, (size_t)n))) {
         release(sX);
