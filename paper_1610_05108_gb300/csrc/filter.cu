@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                   uint32_t *__restrict__ members_count, Bucket *__restrict__ buckets,
                   uint64_t *__restrict__ pair_counts, uint32_t *__restrict__ nbuckets,
                   const uint64_t *__restrict__ cdf, uint64_t wtot, const float *__restrict__ Xrs,
-                  int64_t Pf)
+                  int64_t Pf, int part_max, uint32_t *__restrict__ work)
 {
     using SegKey = uint64_t;
     extern __shared__ __align__(16) uint32_t fl_smem[];
@@ -157,6 +157,9 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     const int T = (int)blockDim.x;      // a multiple of 32, at most FL_THREADS
     const int nwarps = T >> 5;
     __shared__ uint32_t mbase_sh, bbase_sh;
+    __shared__ uint32_t hist[32];       // survivors per bin of the group-key hash (partitioned runs)
+    __shared__ uint32_t pstart[33];     // partition q covers bins [pstart[q], pstart[q + 1])
+    __shared__ uint32_t seg0_sh, nparts_sh;
     uint32_t *kcs = kc_scratch + (int64_t)blockIdx.x * 32 * P;
     SegKey *okeys = reinterpret_cast<SegKey *>(seg_keys_v) + (int64_t)blockIdx.x * seg_cap;
     uint32_t *ovals = seg_vals + (int64_t)blockIdx.x * seg_cap;
@@ -173,8 +176,16 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         cursor = seg_count[blockIdx.x];     // segments fill across launch groups
 
     // work item = (run r, block of responses [b0, b1)); the keys of the run
-    // and its filter are built once per item
-    for (int item = blockIdx.x; item < R * NB; item += gridDim.x) {
+    // and its filter are built once per item.  Items are taken from a
+    // launch-wide counter, so a CTA that drew an expensive run takes fewer.
+    __shared__ int item_sh;
+    for (;;) {
+        if (t == 0)
+            item_sh = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int item = item_sh;           // every thread reads it before the next barrier
+        if (item >= R * NB)
+            break;
         const int r = item / NB;
         const int b0 = (item - r * NB) * BB;
         const int b1 = (b0 + BB < B) ? b0 + BB : B;
@@ -332,6 +343,10 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             }
             __syncthreads();
             uint32_t s = ns;
+            uint32_t nparts = 1;                // groupings on chip of this (run, response)
+            bool from_seg = false;              // their entries come from the segment
+            uint32_t s_all = 0;                 // entries of the run in the segment
+            const uint32_t kcmask = (1u << M) - 1u;   // M <= 31 on this path
 
             if (s > (uint32_t)FL_SMAX) {
                 // refinement: a fresh filter of the survivors' keys (in the
@@ -400,8 +415,10 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 // emit what is left: to the survivor array when it fits, else
                 // to the CTA's global segment with the composite key
                 const bool to_global = s > (uint32_t)FL_SMAX;
-                if (t == 0)
+                if (t == 0) {
                     scur = 0;
+                    seg0_sh = cursor;               // this run's entries start here
+                }
                 __syncthreads();
                 for (uint32_t st = 0; st < steps; ++st) {
                     const uint32_t w = st * T + t;
@@ -447,116 +464,174 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                     }
                 }
                 __syncthreads();
-                if (to_global)
-                    continue;               // the general path groups this run
+                if (to_global) {
+                    // Partitions on chip: the run's entries, now in the
+                    // segment, fall into 32 bins by a hash of their group key;
+                    // contiguous bin ranges of at most FL_SMAX entries are
+                    // grouped one after the other (a group lies in one bin).
+                    // A bin above FL_SMAX, more than part_max ranges or a full
+                    // segment leave the run to the general path.
+                    if (part_max <= 0 || (uint64_t)seg0_sh + s > seg_cap)
+                        continue;
+                    if (t < 32)
+                        hist[t] = 0;
+                    __syncthreads();
+                    for (uint32_t i = t; i < s; i += T) {
+                        const uint32_t Kc = (uint32_t)(okeys[seg0_sh + i] & kcmask);
+                        atomicAdd(&hist[mix32(nz ? (Kc >> 1) : Kc) >> 27], 1u);
+                    }
+                    __syncthreads();
+                    if (t == 0) {
+                        uint32_t np = 0, acc = 0;
+                        bool ok = true;
+                        pstart[0] = 0;
+                        for (int bn = 0; bn < 32; ++bn) {
+                            const uint32_t h = hist[bn];
+                            ok = ok && h <= (uint32_t)FL_SMAX;
+                            if (acc + h > (uint32_t)FL_SMAX) {
+                                pstart[++np] = (uint32_t)bn;
+                                acc = 0;
+                            }
+                            acc += h;
+                        }
+                        pstart[++np] = 32;
+                        nparts_sh = (ok && np <= (uint32_t)part_max) ? np : 0u;
+                    }
+                    __syncthreads();
+                    nparts = nparts_sh;
+                    if (nparts == 0)
+                        continue;           // the general path groups this run
+                    from_seg = true;
+                    s_all = s;
+                }
             }
 
-            // grouping on chip in the table (the keep mask and, for one
-            // response, the filter are dead)
-            // table of 2^tlog slots, at least 4/3 of the survivors (load <= 3/4)
-            int tlog = 8;
-            while (tlog < Lay::LOGT && 3u * (1u << tlog) < 4 * s)
-                ++tlog;
-            const int tsize = 1 << tlog;
-            for (int i = t; i < tsize; i += T) {
-                tkey[i] = FL_EMPTY;
-                tcnt[i] = 0;
-            }
-            __syncthreads();
-            // phase I: insert group keys, count sides (A high half, B low
-            // half); keep (side, slot, j)
-            for (uint32_t i = t; i < s; i += T) {
-                const uint64_t e = sv[i];
-                const uint32_t Kc = (uint32_t)(e >> 32);
-                const uint32_t g = nz ? (Kc >> 1) : Kc;
-                const uint32_t side = nz ? (Kc & 1u) : 0u;
-                uint32_t slot = (g * 0x9E3779B1u) >> (32 - tlog);
-                for (int probe = 0; probe < tsize; ++probe) {    // s < tsize: always ends
-                    const uint32_t old = atomicCAS(&tkey[slot], FL_EMPTY, g);
-                    if (old == FL_EMPTY || old == g)
-                        break;
-                    slot = (slot + 1) & (tsize - 1);
-                }
-                atomicAdd(&tcnt[slot], side ? 1u : 0x10000u);
-                sv[i] = ((uint64_t)((side << 31) | slot) << 32) | (uint32_t)e;
-            }
-            __syncthreads();
-            // phase II: groups with candidates -> buckets; one global atomic
-            // pair per (run, response) reserves their space.  Afterwards
-            // tkey / tcnt of a bucket's slot are the end cursors of its sides
-            // A / B, and tcnt is FL_EMPTY for a slot without a bucket.
-            {
-                // each thread owns a contiguous range of slots; the value of
-                // a slot is members << 16 | 1 when its group yields a bucket
-                const int per = (tsize + T - 1) / T;
-                const int s0 = t * per < tsize ? t * per : tsize;
-                const int s1 = s0 + per < tsize ? s0 + per : tsize;
-                auto slot_value = [&](int slot) -> uint32_t {
-                    if (tkey[slot] == FL_EMPTY)
-                        return 0u;
-                    const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
-                    const bool ok = nz ? (nA > 0 && nB > 0) : (nA > 1);
-                    return ok ? ((nA + nB) << 16) | 1u : 0u;
-                };
-                uint32_t mysum = 0;
-                for (int slot = s0; slot < s1; ++slot)
-                    mysum += slot_value(slot);
-                uint32_t incl = mysum;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o)
-                        incl += y;
-                }
-                if (lane == 31)
-                    wsum[wp] = incl;
-                __syncthreads();
-                uint32_t before = 0, total = 0;
-                for (int i = 0; i < nwarps; ++i) {
-                    before += (i < wp) ? wsum[i] : 0u;
-                    total += wsum[i];
-                }
-                if (t == 0) {
-                    const uint32_t mt = total >> 16, bt = total & 0xFFFFu;
-                    mbase_sh = bt ? atomicAdd(members_count, mt) : 0u;
-                    bbase_sh = bt ? atomicAdd(nbuckets, bt) : 0u;
-                    if (bt && ((uint64_t)mbase_sh + mt > mcap || (uint64_t)bbase_sh + bt > bcap)) {
-                        atomicOr(overflow, 2);      // host grows the space and redoes the search
-                        mbase_sh = 0xFFFFFFFFu;
+            for (uint32_t part = 0; part < nparts; ++part) {
+                if (from_seg) {
+                    // this partition's entries from the segment to the survivor array
+                    if (t == 0)
+                        scur = 0;
+                    __syncthreads();
+                    const uint32_t blo = pstart[part], bhi = pstart[part + 1];
+                    for (uint32_t i = t; i < s_all; i += T) {
+                        const uint64_t key = okeys[seg0_sh + i];
+                        const uint32_t Kc = (uint32_t)(key & kcmask);
+                        const uint32_t bn = mix32(nz ? (Kc >> 1) : Kc) >> 27;
+                        if (bn >= blo && bn < bhi)
+                            sv[atomicAdd(&scur, 1u)] = ((uint64_t)Kc << 32) | ovals[seg0_sh + i];
                     }
+                    __syncthreads();
+                    s = scur;
+                }
+                // grouping on chip in the table (the keep mask and, for one
+                // response, the filter are dead)
+                // table of 2^tlog slots, at least 4/3 of the survivors (load <= 3/4)
+                int tlog = 8;
+                while (tlog < Lay::LOGT && 3u * (1u << tlog) < 4 * s)
+                    ++tlog;
+                const int tsize = 1 << tlog;
+                for (int i = t; i < tsize; i += T) {
+                    tkey[i] = FL_EMPTY;
+                    tcnt[i] = 0;
                 }
                 __syncthreads();
-                if (mbase_sh == 0xFFFFFFFFu)
-                    continue;
-                uint32_t run_off = before + incl - mysum;
-                for (int slot = s0; slot < s1; ++slot) {
-                    const uint32_t v = slot_value(slot);
-                    if (v) {
+                // phase I: insert group keys, count sides (A high half, B low
+                // half); keep (side, slot, j)
+                for (uint32_t i = t; i < s; i += T) {
+                    const uint64_t e = sv[i];
+                    const uint32_t Kc = (uint32_t)(e >> 32);
+                    const uint32_t g = nz ? (Kc >> 1) : Kc;
+                    const uint32_t side = nz ? (Kc & 1u) : 0u;
+                    uint32_t slot = (g * 0x9E3779B1u) >> (32 - tlog);
+                    for (int probe = 0; probe < tsize; ++probe) {    // s < tsize: always ends
+                        const uint32_t old = atomicCAS(&tkey[slot], FL_EMPTY, g);
+                        if (old == FL_EMPTY || old == g)
+                            break;
+                        slot = (slot + 1) & (tsize - 1);
+                    }
+                    atomicAdd(&tcnt[slot], side ? 1u : 0x10000u);
+                    sv[i] = ((uint64_t)((side << 31) | slot) << 32) | (uint32_t)e;
+                }
+                __syncthreads();
+                // phase II: groups with candidates -> buckets; one global atomic
+                // pair per (run, response) reserves their space.  Afterwards
+                // tkey / tcnt of a bucket's slot are the end cursors of its sides
+                // A / B, and tcnt is FL_EMPTY for a slot without a bucket.
+                {
+                    // each thread owns a contiguous range of slots; the value of
+                    // a slot is members << 16 | 1 when its group yields a bucket
+                    const int per = (tsize + T - 1) / T;
+                    const int s0 = t * per < tsize ? t * per : tsize;
+                    const int s1 = s0 + per < tsize ? s0 + per : tsize;
+                    auto slot_value = [&](int slot) -> uint32_t {
+                        if (tkey[slot] == FL_EMPTY)
+                            return 0u;
                         const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
-                        const uint32_t base = mbase_sh + (run_off >> 16);
-                        const uint32_t bi = bbase_sh + (run_off & 0xFFFFu);
-                        buckets[bi] = Bucket{base, nA, nz ? nB : 0u, (uint32_t)b};
-                        pair_counts[bi] = nz ? (uint64_t)nA * nB : (uint64_t)nA * (nA - 1) / 2;
-                        tkey[slot] = base + nA;          // end of side A: cursor counts down
-                        tcnt[slot] = base + nA + nB;     // end of side B
-                    } else {
-                        tcnt[slot] = FL_EMPTY;
+                        const bool ok = nz ? (nA > 0 && nB > 0) : (nA > 1);
+                        return ok ? ((nA + nB) << 16) | 1u : 0u;
+                    };
+                    uint32_t mysum = 0;
+                    for (int slot = s0; slot < s1; ++slot)
+                        mysum += slot_value(slot);
+                    uint32_t incl = mysum;
+    #pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= o)
+                            incl += y;
                     }
-                    run_off += v;
+                    if (lane == 31)
+                        wsum[wp] = incl;
+                    __syncthreads();
+                    uint32_t before = 0, total = 0;
+                    for (int i = 0; i < nwarps; ++i) {
+                        before += (i < wp) ? wsum[i] : 0u;
+                        total += wsum[i];
+                    }
+                    if (t == 0) {
+                        const uint32_t mt = total >> 16, bt = total & 0xFFFFu;
+                        mbase_sh = bt ? atomicAdd(members_count, mt) : 0u;
+                        bbase_sh = bt ? atomicAdd(nbuckets, bt) : 0u;
+                        if (bt && ((uint64_t)mbase_sh + mt > mcap || (uint64_t)bbase_sh + bt > bcap)) {
+                            atomicOr(overflow, 2);      // host grows the space and redoes the search
+                            mbase_sh = 0xFFFFFFFFu;
+                        }
+                    }
+                    __syncthreads();
+                    if (mbase_sh == 0xFFFFFFFFu)
+                        continue;
+                    uint32_t run_off = before + incl - mysum;
+                    for (int slot = s0; slot < s1; ++slot) {
+                        const uint32_t v = slot_value(slot);
+                        if (v) {
+                            const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
+                            const uint32_t base = mbase_sh + (run_off >> 16);
+                            const uint32_t bi = bbase_sh + (run_off & 0xFFFFu);
+                            buckets[bi] = Bucket{base, nA, nz ? nB : 0u, (uint32_t)b};
+                            pair_counts[bi] = nz ? (uint64_t)nA * nB : (uint64_t)nA * (nA - 1) / 2;
+                            tkey[slot] = base + nA;          // end of side A: cursor counts down
+                            tcnt[slot] = base + nA + nB;     // end of side B
+                        } else {
+                            tcnt[slot] = FL_EMPTY;
+                        }
+                        run_off += v;
+                    }
                 }
+                __syncthreads();
+                // phase III: members, side A first
+                for (uint32_t i = t; i < s; i += T) {
+                    const uint64_t e = sv[i];
+                    const uint32_t hi = (uint32_t)(e >> 32);
+                    const uint32_t slot = hi & 0x7FFFFFFFu;
+                    if (tcnt[slot] == FL_EMPTY)
+                        continue;
+                    const uint32_t pos = atomicSub((hi >> 31) ? &tcnt[slot] : &tkey[slot], 1u) - 1u;
+                    members[pos] = (uint32_t)e;
+                }
+                __syncthreads();
             }
-            __syncthreads();
-            // phase III: members, side A first
-            for (uint32_t i = t; i < s; i += T) {
-                const uint64_t e = sv[i];
-                const uint32_t hi = (uint32_t)(e >> 32);
-                const uint32_t slot = hi & 0x7FFFFFFFu;
-                if (tcnt[slot] == FL_EMPTY)
-                    continue;
-                const uint32_t pos = atomicSub((hi >> 31) ? &tcnt[slot] : &tkey[slot], 1u) - 1u;
-                members[pos] = (uint32_t)e;
-            }
-            __syncthreads();
+            if (from_seg && t == 0)
+                cursor = seg0_sh;               // grouped on chip: the entries leave the segment
         }
     }
     if (t == 0) {
@@ -664,7 +739,7 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
                           uint32_t *seg_vals, uint32_t *seg_count, uint32_t seg_cap, int *overflow,
                           uint8_t *cnz, uint32_t *members, uint32_t *members_count, Bucket *buckets,
                           uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
-                          int64_t *launches)
+                          int64_t *launches, int part_max, uint32_t *work)
 {
     const bool batch = B > 1;
     const size_t smem = filter_smem_bytes(batch);
@@ -672,7 +747,7 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
                            int64_t, int, uint64_t, int64_t, int, int, int, int, int64_t, uint32_t, uint32_t,
                            uint32_t *, void *, uint32_t *, uint32_t *, uint32_t, int *, uint8_t *,
                            uint32_t *, uint32_t *, Bucket *, uint64_t *, uint32_t *, const uint64_t *,
-                           uint64_t, const float *, int64_t);
+                           uint64_t, const float *, int64_t, int, uint32_t *);
     KernT kern;
     if (batch)
         kern = M <= 8 ? filter_kernel<8, true> : M <= 16 ? filter_kernel<16, true>
@@ -688,7 +763,8 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
     kern<<<grid, filter_threads(pk.P), smem, s>>>(pk.Xr, pk.Pp, pk.P, ybs, pk.Wp, B, pk.n, pk.p, M, seed, l0, R,
                                         NB, BB, rbits, rbase, mcap, bcap, kc_scratch, seg_keys, seg_vals,
                                         seg_count, seg_cap, overflow, cnz, members, members_count,
-                                        buckets, pair_counts, nbuckets, pk.cdf, pk.wtotal, pk.Xrs, pk.Pf);
+                                        buckets, pair_counts, nbuckets, pk.cdf, pk.wtotal, pk.Xrs, pk.Pf,
+                                        part_max, work);
     *launches += 1;
     return cudaGetLastError();
 }

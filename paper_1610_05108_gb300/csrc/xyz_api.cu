@@ -93,6 +93,7 @@ struct xyz_ctx {
     int64_t seg_cap = 0;         // filter path: survivors one CTA may write per group
     int64_t mem_cap = 0;         // filter path: members of on-chip groups per launch group
     int64_t spill_flush = 0;     // filter path: launch groups per spill flush (0: one per search)
+    int onchip_parts = 0;        // filter path: hash partitions on chip for runs past its capacity
     DevBuf resp, ybs;            // batched search: response of each output pair, response bits
     DevBuf y_alt, y_stage;       // response updates: packed copy checked before use, host staging
     // real response (Section 3.1): live weights and a staging set swapped in
@@ -423,7 +424,8 @@ int ensure_records(xyz_ctx *c, int B)
 // Device counters: per launch group (cleared before each group) the bucket
 // and member counts; per search the spill count and overflow flags, the
 // spill-path bucket count, the record and output counts, the error flag,
-// the group's candidate total, the candidate sum and the spill total.
+// the group's candidate total, the candidate sum, the spill total and the
+// filter's work-item counter.
 uint32_t *ctr_u32(xyz_ctx *c) { return reinterpret_cast<uint32_t *>(c->counters.ptr); }
 uint32_t *ctr_nbuckets(xyz_ctx *c) { return ctr_u32(c) + 0; }
 uint32_t *ctr_members(xyz_ctx *c) { return ctr_u32(c) + 1; }
@@ -436,6 +438,7 @@ int *ctr_err(xyz_ctx *c) { return reinterpret_cast<int *>(ctr_u32(c) + 7); }
 uint64_t *ctr_total(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 32); }
 uint64_t *ctr_cand(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 40); }
 uint64_t *ctr_total2(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 48); }
+uint32_t *ctr_work(xyz_ctx *c) { return reinterpret_cast<uint32_t *>((char *)c->counters.ptr + 56); }
 
 #define CU(expr)                                                                         \
     do {                                                                                 \
@@ -565,6 +568,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                 const int64_t Rc = (l1 - g0) < pl.R ? (l1 - g0) : pl.R;
                 ++chunks;
                 CU(cudaMemsetAsync(ctr_u32(c), 0, 8, c->stream));   // buckets, members
+                CU(cudaMemsetAsync(ctr_work(c), 0, 4, c->stream));  // the filter's work items
                 tm.begin(ST_KEYS);
                 CU(launch_filter(c->pk, ybs, B, M, seed, g0, (int)Rc, pl.NB, pl.BB, rbits, g0 - l0,
                                  grid, (uint32_t)(c->mem_cap < 0xFFFFFFFELL ? c->mem_cap : 0xFFFFFFFELL),
@@ -573,7 +577,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  (uint32_t *)c->seg_count.ptr, (uint32_t)c->seg_cap, ctr_sovf(c),
                                  (uint8_t *)c->cnz.ptr, (uint32_t *)c->members.ptr, ctr_members(c),
                                  (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
-                                 ctr_nbuckets(c), c->stream, &launches));
+                                 ctr_nbuckets(c), c->stream, &launches, c->onchip_parts, ctr_work(c)));
                 tm.end();
                 tm.begin(ST_JOIN);
                 CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
@@ -1892,6 +1896,14 @@ int xyz_set_spill_flush(xyz_ctx *ctx, int64_t groups)
     if (!ctx || groups < 0)
         return fail(XYZ_EINVAL, "need a context and groups >= 0");
     ctx->spill_flush = groups;
+    return XYZ_OK;
+}
+
+int xyz_set_onchip_partitions(xyz_ctx *ctx, int32_t max_parts)
+{
+    if (!ctx || max_parts < 0 || max_parts > 32)
+        return fail(XYZ_EINVAL, "need a context and max_parts in [0, 32]");
+    ctx->onchip_parts = max_parts;
     return XYZ_OK;
 }
 

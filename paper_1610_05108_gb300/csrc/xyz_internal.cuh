@@ -178,14 +178,17 @@ int64_t filter_run_cap();
 // go to the per-CTA segments as ((b << rbits | run) << M | Kc, j) and the
 // segments fill across launch groups (reset with launch_seg_reset, joined
 // with launch_compact).  overflow bit 1: a segment overflowed; bit 2: the
-// member/bucket space (mcap/bcap) did.
+// member/bucket space (mcap/bcap) did.  A run whose survivors pass the
+// on-chip capacity is grouped on chip in at most part_max hash partitions
+// of its group keys when they fit (0: never; it then always spills).  work:
+// a zeroed counter from which the CTAs take their work items.
 cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, uint64_t seed,
                           int64_t l0, int R, int NB, int BB, int rbits, int64_t rbase, int grid,
                           uint32_t mcap, uint32_t bcap, uint32_t *kc_scratch, uint64_t *seg_keys,
                           uint32_t *seg_vals, uint32_t *seg_count, uint32_t seg_cap, int *overflow,
                           uint8_t *cnz, uint32_t *members, uint32_t *members_count, Bucket *buckets,
                           uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
-                          int64_t *launches);
+                          int64_t *launches, int part_max, uint32_t *work);
 cudaError_t launch_seg_reset(uint32_t *seg_count, cudaStream_t s, int64_t *launches);
 cudaError_t launch_compact(const uint64_t *seg_keys, const uint32_t *seg_vals,
                            const uint32_t *seg_count, uint32_t seg_cap, int nseg, uint64_t *out_keys,

@@ -86,6 +86,7 @@ SIGNATURES = {
     "xyz_set_chunk_entries": (ctypes.c_int, [_p, _i64]),
     "xyz_set_filter": (ctypes.c_int, [_p, ctypes.c_int]),
     "xyz_set_spill_flush": (ctypes.c_int, [_p, _i64]),
+    "xyz_set_onchip_partitions": (ctypes.c_int, [_p, ctypes.c_int32]),
     "xyz_run_keys": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _p]),
     "xyz_run_candidates": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _p]),
     "xyz_agree": (ctypes.c_int, [_p, _p, _p, _i64, _p]),
@@ -351,6 +352,9 @@ class Context:
 
     def set_spill_flush(self, groups: int):
         _check(load().xyz_set_spill_flush(self.handle, int(groups)))
+
+    def set_onchip_partitions(self, max_parts: int):
+        _check(load().xyz_set_onchip_partitions(self.handle, int(max_parts)))
 
     def info(self) -> dict:
         n, p, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -59,16 +59,19 @@ def test_batch_equals_single_searches_and_oracle(xyz, orc):
 
 
 def test_batch_with_spilled_responses(xyz, orc):
-    # response 1 is all +1: c = 0 in every run, all 6500 columns survive and
-    # its runs go through the sort path; the others stay on chip
+    # response 1 is all +1: c = 0 in every run, all 6500 columns survive:
+    # its runs go through the sort path, or through hash partitions on chip;
+    # the others stay on chip
     X, rng = _rand(100, 6500, 32)
     Ys = _responses(X, rng, 3)
     Ys[1] = 1
     L, M, kappa, seed = 6, 12, 0.9, 7
-    with xyz.create(X, Ys[0]) as ctx:
-        got = ctx.search_batch(Ys, L, M, kappa, seed)
-    for b in range(3):
-        assert np.array_equal(_arr(got[b]), orc.xyz(X, Ys[b], L, M, kappa, seed)), b
+    for parts in (0, 32):                     # sort path, then partitions on chip
+        with xyz.create(X, Ys[0]) as ctx:
+            ctx.set_onchip_partitions(parts)
+            got = ctx.search_batch(Ys, L, M, kappa, seed)
+        for b in range(3):
+            assert np.array_equal(_arr(got[b]), orc.xyz(X, Ys[b], L, M, kappa, seed)), (parts, b)
 
 
 def test_batch_of_one_and_lsd_fallback(xyz, orc):

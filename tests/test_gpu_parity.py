@@ -186,11 +186,52 @@ def test_search_mixing_spilled_and_on_chip_runs(xyz, orc):
     Y[:] = 1
     Y[:6] = -1
     Y = Y * (X[:, 2] * X[:, 3]) * (X[:, 2] * X[:, 3])     # keep +-1, no change
+    want = orc.xyz(X, Y, 12, 4, 0.9, 5)
     with xyz.create(X, Y) as ctx:
+        ctx.set_onchip_partitions(0)               # every overflowing run spills
         got = _pairs_array(ctx.search(12, 4, 0.9, 5))
         st = ctx.stats()
-    assert st["survivors"] > 0
-    assert np.array_equal(got, orc.xyz(X, Y, 12, 4, 0.9, 5))
+        assert st["survivors"] > 0
+        assert np.array_equal(got, want)
+        ctx.set_onchip_partitions(32)              # hash partitions on chip
+        got = _pairs_array(ctx.search(12, 4, 0.9, 5))
+        st = ctx.stats()
+        assert st["survivors"] == 0
+        assert np.array_equal(got, want)
+
+
+def test_onchip_partitions_match_oracle(xyz, orc):
+    # Y mostly +1 and M = 10: most runs have c = 0, and in the others nearly
+    # every key has a partner, so about 20000 columns survive per run -- three
+    # or more partitions of at most 8192 on chip.  A lower limit sends the run
+    # to the sort; every limit gives the oracle's result and the same E_l.
+    X, Y = _rand(64, 20000, 23)
+    Y[:] = 1
+    Y[:3] = -1
+    L, M, kappa, seed = 6, 10, 0.4, 12
+    want = orc.xyz(X, Y, L, M, kappa, seed)
+    assert len(want) > 100
+    cands = {}
+    with xyz.create(X, Y) as ctx:
+        for parts in (0, 1, 2, 3, 32):
+            ctx.set_onchip_partitions(parts)
+            got = _pairs_array(ctx.search(L, M, kappa, seed))
+            st = ctx.stats()
+            assert np.array_equal(got, want), parts
+            cands[parts] = st["candidates"]
+            if parts == 32:
+                assert st["survivors"] == 0
+            if parts <= 2:
+                assert st["survivors"] > 0
+    assert len(set(cands.values())) == 1, cands
+
+
+def test_onchip_partitions_argument_check(xyz):
+    X, Y = _rand(40, 100, 24)
+    with xyz.create(X, Y) as ctx:
+        for bad in (-1, 33):
+            with pytest.raises(xyz.XyzError):
+                ctx.set_onchip_partitions(bad)
 
 
 def test_spill_flush_windows_do_not_change_results(xyz, orc):
@@ -202,6 +243,7 @@ def test_spill_flush_windows_do_not_change_results(xyz, orc):
     want = orc.xyz(X, Y, 12, 4, 0.9, 5)
     with xyz.create(X, Y) as ctx:
         ctx.set_chunk_entries(9000 // 8)          # one run per launch group
+        ctx.set_onchip_partitions(0)              # overflowing runs spill (the default)
         for flush in (0, 1, 3):
             ctx.set_spill_flush(flush)
             got = _pairs_array(ctx.search(12, 4, 0.9, 5))
