@@ -280,7 +280,9 @@ int xyz_get_stats(const xyz_ctx *ctx, xyz_stats *out);
 int xyz_set_timing(xyz_ctx *ctx, int enable);
 
 /* Tuning: at most `entries` sorted keys (runs x p) per launch group; one run
- * per group when entries < p.  Results never depend on it.  Default 2^25. */
+ * per group when entries < p.  The filter path, which sorts only a few
+ * percent of the columns, puts up to 64 x entries / p runs (at most 16384)
+ * in a group.  Results never depend on it.  Default 2^25. */
 int xyz_set_chunk_entries(xyz_ctx *ctx, int64_t entries);
 
 /* Tuning: 1 (default) lets searches with M <= 31 and p <= 262144 drop, per

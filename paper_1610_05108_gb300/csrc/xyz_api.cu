@@ -306,14 +306,16 @@ Plan make_plan(const xyz_ctx *c, int64_t runs, int M, int B)
     if (pl.kbits < 1)
         pl.kbits = 1;
     if (pl.filter) {
-        // a launch group holds about 2048 (run, response) items; only a few
-        // percent of a run's columns survive, so it may span eight times the
-        // entry budget
-        int64_t rf = B > 1 ? (4096 / B > 0 ? 4096 / B : 1) : 8 * entries / p;
+        // only a few percent of a run's columns survive, so a launch group may
+        // span 64 times the entry budget (up to 16384 runs: the whole of most
+        // searches); every launch group ends with a tail of CTAs finishing
+        // their last runs, so fewer groups are faster.  Batches keep about
+        // 4096 (run, response) items.
+        int64_t rf = B > 1 ? (4096 / B > 0 ? 4096 / B : 1) : 64 * entries / p;
         if (rf < 1)
             rf = 1;
-        if (rf > 4096)
-            rf = 4096;
+        if (rf > 16384)
+            rf = 16384;
         pl.R = runs < rf ? runs : rf;
         // enough (run, response block) items for every SM
         const int64_t want = 2 * (int64_t)filter_grid();

@@ -155,7 +155,7 @@ def test_search_independent_of_launch_grouping(xyz):
     Y[:20] = -Y[:20]
     with xyz.create(X, Y) as ctx:
         ref = ctx.search(37, 5, 0.1, 5)
-        for entries in (900, 900 * 3, 900 * 8 + 5, 10**9):
+        for entries in (10, 100, 900, 900 * 3, 900 * 8 + 5, 10**9):
             ctx.set_chunk_entries(entries)
             got = ctx.search(37, 5, 0.1, 5)
             assert np.array_equal(got, ref), entries
@@ -242,7 +242,7 @@ def test_spill_flush_windows_do_not_change_results(xyz, orc):
     Y[:6] = -1
     want = orc.xyz(X, Y, 12, 4, 0.9, 5)
     with xyz.create(X, Y) as ctx:
-        ctx.set_chunk_entries(9000 // 8)          # one run per launch group
+        ctx.set_chunk_entries(9000 // 64)         # one run per launch group
         ctx.set_onchip_partitions(0)              # overflowing runs spill (the default)
         for flush in (0, 1, 3):
             ctx.set_spill_flush(flush)
