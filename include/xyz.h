@@ -300,11 +300,8 @@ int xyz_set_spill_flush(xyz_ctx *ctx, int64_t groups);
  * holds is grouped on chip in up to max_parts passes, each over the
  * survivors whose group key hashes into one range of 32 bins (a group never
  * straddles two); a run that needs more passes, or has a single bin above
- * the capacity, goes through the sort as above.  0 (the default) sends
- * every such run to the sort: the CTA that groups a large run on chip
- * finishes its launch group late, which on the SNP-shaped benchmark costs
- * about what the sort saves.  0 <= max_parts <= 32.  Results never depend
- * on it. */
+ * the capacity, goes through the sort as above.  0 sends every such run to
+ * the sort.  0 <= max_parts <= 32, default 32.  Results never depend on it. */
 int xyz_set_onchip_partitions(xyz_ctx *ctx, int32_t max_parts);
 
 /* --------------------------------------------------- parity / observability */

@@ -93,7 +93,7 @@ struct xyz_ctx {
     int64_t seg_cap = 0;         // filter path: survivors one CTA may write per group
     int64_t mem_cap = 0;         // filter path: members of on-chip groups per launch group
     int64_t spill_flush = 0;     // filter path: launch groups per spill flush (0: one per search)
-    int onchip_parts = 0;        // filter path: hash partitions on chip for runs past its capacity
+    int onchip_parts = 32;       // filter path: hash partitions on chip for runs past its capacity
     DevBuf resp, ybs;            // batched search: response of each output pair, response bits
     DevBuf y_alt, y_stage;       // response updates: packed copy checked before use, host staging
     // real response (Section 3.1): live weights and a staging set swapped in

@@ -243,7 +243,7 @@ def test_spill_flush_windows_do_not_change_results(xyz, orc):
     want = orc.xyz(X, Y, 12, 4, 0.9, 5)
     with xyz.create(X, Y) as ctx:
         ctx.set_chunk_entries(9000 // 64)         # one run per launch group
-        ctx.set_onchip_partitions(0)              # overflowing runs spill (the default)
+        ctx.set_onchip_partitions(0)              # overflowing runs spill
         for flush in (0, 1, 3):
             ctx.set_spill_flush(flush)
             got = _pairs_array(ctx.search(12, 4, 0.9, 5))
