@@ -296,10 +296,14 @@ __global__ void __launch_bounds__(JV_THREADS, (VQ == 2 && !WEIGHTED) ? 5 : 1)   
 // For every block of 32 consecutive candidates, the bucket holding its first
 // candidate: bucket b writes the blocks that start in [pair_off[b],
 // pair_off[b+1]), so every block below bstart_cap gets exactly one writer.
+// abort_flag as in verify_kernel: when the producer ran out of bucket space
+// its bucket count passes the arrays, and nothing is read.
 __global__ void block_start_kernel(const uint64_t *__restrict__ pair_off, const uint32_t *__restrict__ nbuckets,
                                    const uint64_t *__restrict__ total_pairs, uint32_t *__restrict__ bstart,
-                                   int64_t bstart_cap)
+                                   int64_t bstart_cap, const int *__restrict__ abort_flag)
 {
+    if (abort_flag && (*(volatile const int *)abort_flag & 2))
+        return;
     const uint32_t nb = *nbuckets;
     const uint64_t T = *total_pairs;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -551,7 +555,7 @@ cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_
                                   rec_agree, nrec, rec_cap, s, launches, abort_flag);
     if (bstart && bstart_cap > 0) {
         block_start_kernel<<<(unsigned)max_resident_blocks(), JV_THREADS, 0, s>>>(pair_off, nbuckets, total_pairs,
-                                                                               bstart, bstart_cap);
+                                                                               bstart, bstart_cap, abort_flag);
         *launches += 1;
     } else {
         bstart = nullptr;

@@ -511,10 +511,11 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                   (uint64_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr, ctr_nsurv(c),
                                   c->stream, &launches));
                 tm.end();
-                uint32_t ns = 0;
+                uint32_t ns = 0, mem_tried = 0;
                 int sovf = 0;
                 CU(cudaMemcpyAsync(&ns, ctr_nsurv(c), 4, cudaMemcpyDeviceToHost, c->stream));
                 CU(cudaMemcpyAsync(&sovf, ctr_sovf(c), 4, cudaMemcpyDeviceToHost, c->stream));
+                CU(cudaMemcpyAsync(&mem_tried, ctr_members(c), 4, cudaMemcpyDeviceToHost, c->stream));
                 CU(cudaStreamSynchronize(c->stream));
                 if (sovf & 1) {
                     // a spill segment overflowed: larger segments up to a
@@ -528,7 +529,10 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                     redo = true;
                 }
                 if (sovf & 2) {
-                    c->mem_cap *= 2;               // the on-chip groups' members did
+                    // the on-chip groups' members did: at least double, and at
+                    // least what the last launch group tried to reserve
+                    const int64_t want = (int64_t)mem_tried + (int64_t)mem_tried / 4;
+                    c->mem_cap = want > 2 * c->mem_cap ? want : 2 * c->mem_cap;
                     redo = true;
                 }
                 if (redo || ns == 0)

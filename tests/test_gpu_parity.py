@@ -226,6 +226,23 @@ def test_onchip_partitions_match_oracle(xyz, orc):
     assert len(set(cands.values())) == 1, cands
 
 
+def test_member_space_overflow_regrows(xyz, orc):
+    # M = 13 over 30000 random columns: nearly every key has a partner, so
+    # almost every column survives and the on-chip groups of the first
+    # attempt need about seven times the member space first reserved.  The
+    # launch group is abandoned (nothing reads the bucket arrays past their
+    # end), the space grows to what was asked for and the search is redone.
+    X, Y = _rand(64, 30000, 29)
+    L, M, kappa, seed = 12, 13, 0.5, 3
+    want = orc.xyz(X, Y, L, M, kappa, seed)
+    assert len(want) > 0
+    with xyz.create(X, Y) as ctx:
+        got = _pairs_array(ctx.search(L, M, kappa, seed))
+        again = _pairs_array(ctx.search(L, M, kappa, seed))
+    assert np.array_equal(got, want)
+    assert np.array_equal(again, want)
+
+
 def test_onchip_partitions_argument_check(xyz):
     X, Y = _rand(40, 100, 24)
     with xyz.create(X, Y) as ctx:
