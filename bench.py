@@ -521,7 +521,7 @@ def batch_arm(args):
     _, _, agree = ctx.sample_agree(10**6, 0x5EED)             # plug-in M of eq. bestM
     M, _ = xyz.best_M(n, p, (1 + kappa) / 2, agree)
     L = xyz.runs_for_recall(g_min ** M, 0.95)
-    ctx.search_batch(Ys[:8], L, M, kappa, seed)                 # warm-up (workspace growth)
+    ctx.search_batch(Ys, L, M, kappa, seed + 1)                 # warm-up: sizes the workspace for B
     ctx.search(L, M, kappa, seed)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
