@@ -285,9 +285,13 @@ int xyz_set_timing(xyz_ctx *ctx, int enable);
  * in a group.  Results never depend on it.  Default 2^25. */
 int xyz_set_chunk_entries(xyz_ctx *ctx, int64_t entries);
 
-/* Tuning: 1 (default) lets searches with M <= 31 and p <= 262144 drop, per
- * run, the columns that cannot be in any candidate pair before grouping;
- * 0 groups every column.  Results never depend on it. */
+/* Tuning: 1 (default) lets searches drop, per run, the columns that cannot
+ * be in any candidate pair before grouping: with one shared-memory filter
+ * of the run's keys when M <= 31 and p <= 262144, and otherwise -- one
+ * binary response, M <= 28, p <= 2^27 -- with the keys split into 16
+ * linear classes, one filter per class in turn.  2 uses the class-split
+ * form wherever it applies (also at small p); 0 groups every column.
+ * XYZ_EINVAL for other values.  Results never depend on it. */
 int xyz_set_filter(xyz_ctx *ctx, int enable);
 
 /* Tuning (filter path): runs whose survivors do not fit on chip are grouped

@@ -100,6 +100,208 @@ __device__ __forceinline__ uint32_t canon(uint32_t kx, uint32_t c, int tb, uint3
     return ((above | (h & lowmask)) << 1) | ((kx != h) ? 1u : 0u);
 }
 
+// Where the on-chip grouping writes its buckets and members, and the
+// space it may use (reserved with one global atomic pair per grouping).
+struct GroupOut {
+    uint32_t *members;
+    uint32_t *members_count;
+    Bucket *buckets;
+    uint64_t *pair_counts;
+    uint32_t *nbuckets;
+    uint32_t mcap, bcap;
+    int *overflow;
+};
+
+// Groups the s <= SMAX survivors (Kc << 32 | j) in sv on chip: a hash table
+// of group keys with packed side counts (tkey / tcnt); each group with
+// candidates becomes a bucket (response b in its pad) and its members are
+// written side A first.  Called by every thread of the CTA.
+template <class Lay>
+__device__ __forceinline__ void group_on_chip(uint64_t *sv, uint32_t s, uint32_t *tkey, uint32_t *tcnt, bool nz,
+                                              int b, const GroupOut &g)
+{
+    __shared__ uint32_t mbase_sh, bbase_sh;
+    __shared__ uint32_t wsum[FL_THREADS / 32];
+    const int t = threadIdx.x, T = (int)blockDim.x;
+    const int lane = t & 31, wp = t >> 5, nwarps = T >> 5;
+    uint32_t *members = g.members;
+    Bucket *buckets = g.buckets;
+    uint64_t *pair_counts = g.pair_counts;
+    // grouping on chip in the table (the keep mask and, for one
+    // response, the filter are dead)
+    // table of 2^tlog slots, at least 4/3 of the survivors (load <= 3/4)
+    int tlog = 8;
+    while (tlog < Lay::LOGT && 3u * (1u << tlog) < 4 * s)
+        ++tlog;
+    const int tsize = 1 << tlog;
+    for (int i = t; i < tsize; i += T) {
+        tkey[i] = FL_EMPTY;
+        tcnt[i] = 0;
+    }
+    __syncthreads();
+    // phase I: insert group keys, count sides (A high half, B low
+    // half); keep (side, slot, j)
+    for (uint32_t i = t; i < s; i += T) {
+        const uint64_t e = sv[i];
+        const uint32_t Kc = (uint32_t)(e >> 32);
+        const uint32_t g = nz ? (Kc >> 1) : Kc;
+        const uint32_t side = nz ? (Kc & 1u) : 0u;
+        uint32_t slot = (g * 0x9E3779B1u) >> (32 - tlog);
+        for (int probe = 0; probe < tsize; ++probe) {    // s < tsize: always ends
+            const uint32_t old = atomicCAS(&tkey[slot], FL_EMPTY, g);
+            if (old == FL_EMPTY || old == g)
+                break;
+            slot = (slot + 1) & (tsize - 1);
+        }
+        atomicAdd(&tcnt[slot], side ? 1u : 0x10000u);
+        sv[i] = ((uint64_t)((side << 31) | slot) << 32) | (uint32_t)e;
+    }
+    __syncthreads();
+    // phase II: groups with candidates -> buckets; one global atomic
+    // pair per (run, response) reserves their space.  Afterwards
+    // tkey / tcnt of a bucket's slot are the end cursors of its sides
+    // A / B, and tcnt is FL_EMPTY for a slot without a bucket.
+    {
+        // each thread owns a contiguous range of slots; the value of
+        // a slot is members << 16 | 1 when its group yields a bucket
+        const int per = (tsize + T - 1) / T;
+        const int s0 = t * per < tsize ? t * per : tsize;
+        const int s1 = s0 + per < tsize ? s0 + per : tsize;
+        auto slot_value = [&](int slot) -> uint32_t {
+            if (tkey[slot] == FL_EMPTY)
+                return 0u;
+            const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
+            const bool ok = nz ? (nA > 0 && nB > 0) : (nA > 1);
+            return ok ? ((nA + nB) << 16) | 1u : 0u;
+        };
+        uint32_t mysum = 0;
+        for (int slot = s0; slot < s1; ++slot)
+            mysum += slot_value(slot);
+        uint32_t incl = mysum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        if (lane == 31)
+            wsum[wp] = incl;
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int i = 0; i < nwarps; ++i) {
+            before += (i < wp) ? wsum[i] : 0u;
+            total += wsum[i];
+        }
+        if (t == 0) {
+            const uint32_t mt = total >> 16, bt = total & 0xFFFFu;
+            mbase_sh = bt ? atomicAdd(g.members_count, mt) : 0u;
+            bbase_sh = bt ? atomicAdd(g.nbuckets, bt) : 0u;
+            if (bt && ((uint64_t)mbase_sh + mt > g.mcap || (uint64_t)bbase_sh + bt > g.bcap)) {
+                atomicOr(g.overflow, 2);      // host grows the space and redoes the search
+                mbase_sh = 0xFFFFFFFFu;
+            }
+        }
+        __syncthreads();
+        if (mbase_sh == 0xFFFFFFFFu)
+            return;          // the host grows the space and redoes the search
+        uint32_t run_off = before + incl - mysum;
+        for (int slot = s0; slot < s1; ++slot) {
+            const uint32_t v = slot_value(slot);
+            if (v) {
+                const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
+                const uint32_t base = mbase_sh + (run_off >> 16);
+                const uint32_t bi = bbase_sh + (run_off & 0xFFFFu);
+                buckets[bi] = Bucket{base, nA, nz ? nB : 0u, (uint32_t)b};
+                pair_counts[bi] = nz ? (uint64_t)nA * nB : (uint64_t)nA * (nA - 1) / 2;
+                tkey[slot] = base + nA;          // end of side A: cursor counts down
+                tcnt[slot] = base + nA + nB;     // end of side B
+            } else {
+                tcnt[slot] = FL_EMPTY;
+            }
+            run_off += v;
+        }
+    }
+    __syncthreads();
+    // phase III: members, side A first
+    for (uint32_t i = t; i < s; i += T) {
+        const uint64_t e = sv[i];
+        const uint32_t hi = (uint32_t)(e >> 32);
+        const uint32_t slot = hi & 0x7FFFFFFFu;
+        if (tcnt[slot] == FL_EMPTY)
+            continue;
+        const uint32_t pos = atomicSub((hi >> 31) ? &tcnt[slot] : &tkey[slot], 1u) - 1u;
+        members[pos] = (uint32_t)e;
+    }
+    __syncthreads();
+}
+
+// The s entries of one (run, response) at seg[seg0 ..) -- key runbits | Kc
+// and column -- grouped on chip: they fall into 32 bins by a hash of their
+// group key, and contiguous bin ranges of at most SMAX entries are gathered
+// into sv and grouped one after the other (a group lies in one bin).
+// Returns false, with nothing grouped, when a bin is above SMAX, more than
+// part_max ranges are needed or the entries did not all fit the segment;
+// the run then stays in the segment for the general path.  Called by every
+// thread of the CTA.
+template <class Lay>
+__device__ __forceinline__ bool group_from_segment(const uint64_t *okeys, const uint32_t *ovals, uint32_t seg0,
+                                                   uint32_t s, uint32_t seg_cap, int part_max, uint32_t kcmask,
+                                                   uint64_t *sv, uint32_t *tkey, uint32_t *tcnt, bool nz, int b,
+                                                   const GroupOut &g)
+{
+    __shared__ uint32_t hist[32];       // entries per bin of the group-key hash
+    __shared__ uint32_t pstart[33];     // partition q covers bins [pstart[q], pstart[q + 1])
+    __shared__ uint32_t nparts_sh, scur;
+    constexpr int SMAX = Lay::SMAX;
+    const int t = threadIdx.x, T = (int)blockDim.x;
+    if (part_max <= 0 || (uint64_t)seg0 + s > seg_cap)
+        return false;
+    if (t < 32)
+        hist[t] = 0;
+    __syncthreads();
+    for (uint32_t i = t; i < s; i += T) {
+        const uint32_t Kc = (uint32_t)(okeys[seg0 + i] & kcmask);
+        atomicAdd(&hist[mix32(nz ? (Kc >> 1) : Kc) >> 27], 1u);
+    }
+    __syncthreads();
+    if (t == 0) {
+        uint32_t np = 0, acc = 0;
+        bool ok = true;
+        pstart[0] = 0;
+        for (int bn = 0; bn < 32; ++bn) {
+            const uint32_t h = hist[bn];
+            ok = ok && h <= (uint32_t)SMAX;
+            if (acc + h > (uint32_t)SMAX) {
+                pstart[++np] = (uint32_t)bn;
+                acc = 0;
+            }
+            acc += h;
+        }
+        pstart[++np] = 32;
+        nparts_sh = (ok && np <= (uint32_t)part_max) ? np : 0u;
+    }
+    __syncthreads();
+    const uint32_t nparts = nparts_sh;
+    if (nparts == 0)
+        return false;
+    for (uint32_t part = 0; part < nparts; ++part) {
+        // this partition's entries from the segment to the survivor array
+        if (t == 0)
+            scur = 0;
+        __syncthreads();
+        const uint32_t blo = pstart[part], bhi = pstart[part + 1];
+        for (uint32_t i = t; i < s; i += T) {
+            const uint32_t Kc = (uint32_t)(okeys[seg0 + i] & kcmask);
+            const uint32_t bn = mix32(nz ? (Kc >> 1) : Kc) >> 27;
+            if (bn >= blo && bn < bhi)
+                sv[atomicAdd(&scur, 1u)] = ((uint64_t)Kc << 32) | ovals[seg0 + i];
+        }
+        __syncthreads();
+        group_on_chip<Lay>(sv, scur, tkey, tcnt, nz, b, g);
+    }
+    return true;
+}
+
 // One CTA per run at a time (passes 1-2 as described at the top of the
 // file).  When the run keeps at most FL_SMAX columns they are grouped on
 // chip: a hash table of group keys with packed side counts, each group
@@ -153,13 +355,9 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     __shared__ uint32_t cursor;         // global segment fill
     __shared__ uint32_t ns;             // survivors of the current (run, response)
     __shared__ uint32_t scur;           // survivor array fill after refinement
-    __shared__ uint32_t wsum[FL_THREADS / 32];
     const int T = (int)blockDim.x;      // a multiple of 32, at most FL_THREADS
-    const int nwarps = T >> 5;
-    __shared__ uint32_t mbase_sh, bbase_sh;
-    __shared__ uint32_t hist[32];       // survivors per bin of the group-key hash (partitioned runs)
-    __shared__ uint32_t pstart[33];     // partition q covers bins [pstart[q], pstart[q + 1])
-    __shared__ uint32_t seg0_sh, nparts_sh;
+    __shared__ uint32_t seg0_sh;        // first segment entry of the current (run, response)
+    const GroupOut gout{members, members_count, buckets, pair_counts, nbuckets, mcap, bcap, overflow};
     uint32_t *kcs = kc_scratch + (int64_t)blockIdx.x * 32 * P;
     SegKey *okeys = reinterpret_cast<SegKey *>(seg_keys_v) + (int64_t)blockIdx.x * seg_cap;
     uint32_t *ovals = seg_vals + (int64_t)blockIdx.x * seg_cap;
@@ -343,9 +541,6 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             }
             __syncthreads();
             uint32_t s = ns;
-            uint32_t nparts = 1;                // groupings on chip of this (run, response)
-            bool from_seg = false;              // their entries come from the segment
-            uint32_t s_all = 0;                 // entries of the run in the segment
             const uint32_t kcmask = (1u << M) - 1u;   // M <= 31 on this path
 
             if (s > (uint32_t)FL_SMAX) {
@@ -465,174 +660,223 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 }
                 __syncthreads();
                 if (to_global) {
-                    // Partitions on chip: the run's entries, now in the
-                    // segment, fall into 32 bins by a hash of their group key;
-                    // contiguous bin ranges of at most FL_SMAX entries are
-                    // grouped one after the other (a group lies in one bin).
-                    // A bin above FL_SMAX, more than part_max ranges or a full
-                    // segment leave the run to the general path.
-                    if (part_max <= 0 || (uint64_t)seg0_sh + s > seg_cap)
-                        continue;
-                    if (t < 32)
-                        hist[t] = 0;
-                    __syncthreads();
-                    for (uint32_t i = t; i < s; i += T) {
-                        const uint32_t Kc = (uint32_t)(okeys[seg0_sh + i] & kcmask);
-                        atomicAdd(&hist[mix32(nz ? (Kc >> 1) : Kc) >> 27], 1u);
-                    }
-                    __syncthreads();
-                    if (t == 0) {
-                        uint32_t np = 0, acc = 0;
-                        bool ok = true;
-                        pstart[0] = 0;
-                        for (int bn = 0; bn < 32; ++bn) {
-                            const uint32_t h = hist[bn];
-                            ok = ok && h <= (uint32_t)FL_SMAX;
-                            if (acc + h > (uint32_t)FL_SMAX) {
-                                pstart[++np] = (uint32_t)bn;
-                                acc = 0;
-                            }
-                            acc += h;
-                        }
-                        pstart[++np] = 32;
-                        nparts_sh = (ok && np <= (uint32_t)part_max) ? np : 0u;
-                    }
-                    __syncthreads();
-                    nparts = nparts_sh;
-                    if (nparts == 0)
-                        continue;           // the general path groups this run
-                    from_seg = true;
-                    s_all = s;
+                    // the run's entries are in the segment: grouped on chip in
+                    // partitions when they fit, else left to the general path
+                    if (group_from_segment<Lay>(okeys, ovals, seg0_sh, s, seg_cap, part_max, kcmask, sv, tkey,
+                                                tcnt, nz, b, gout) &&
+                        t == 0)
+                        cursor = seg0_sh;           // grouped on chip: the entries leave the segment
+                    continue;
                 }
             }
-
-            for (uint32_t part = 0; part < nparts; ++part) {
-                if (from_seg) {
-                    // this partition's entries from the segment to the survivor array
-                    if (t == 0)
-                        scur = 0;
-                    __syncthreads();
-                    const uint32_t blo = pstart[part], bhi = pstart[part + 1];
-                    for (uint32_t i = t; i < s_all; i += T) {
-                        const uint64_t key = okeys[seg0_sh + i];
-                        const uint32_t Kc = (uint32_t)(key & kcmask);
-                        const uint32_t bn = mix32(nz ? (Kc >> 1) : Kc) >> 27;
-                        if (bn >= blo && bn < bhi)
-                            sv[atomicAdd(&scur, 1u)] = ((uint64_t)Kc << 32) | ovals[seg0_sh + i];
-                    }
-                    __syncthreads();
-                    s = scur;
-                }
-                // grouping on chip in the table (the keep mask and, for one
-                // response, the filter are dead)
-                // table of 2^tlog slots, at least 4/3 of the survivors (load <= 3/4)
-                int tlog = 8;
-                while (tlog < Lay::LOGT && 3u * (1u << tlog) < 4 * s)
-                    ++tlog;
-                const int tsize = 1 << tlog;
-                for (int i = t; i < tsize; i += T) {
-                    tkey[i] = FL_EMPTY;
-                    tcnt[i] = 0;
-                }
-                __syncthreads();
-                // phase I: insert group keys, count sides (A high half, B low
-                // half); keep (side, slot, j)
-                for (uint32_t i = t; i < s; i += T) {
-                    const uint64_t e = sv[i];
-                    const uint32_t Kc = (uint32_t)(e >> 32);
-                    const uint32_t g = nz ? (Kc >> 1) : Kc;
-                    const uint32_t side = nz ? (Kc & 1u) : 0u;
-                    uint32_t slot = (g * 0x9E3779B1u) >> (32 - tlog);
-                    for (int probe = 0; probe < tsize; ++probe) {    // s < tsize: always ends
-                        const uint32_t old = atomicCAS(&tkey[slot], FL_EMPTY, g);
-                        if (old == FL_EMPTY || old == g)
-                            break;
-                        slot = (slot + 1) & (tsize - 1);
-                    }
-                    atomicAdd(&tcnt[slot], side ? 1u : 0x10000u);
-                    sv[i] = ((uint64_t)((side << 31) | slot) << 32) | (uint32_t)e;
-                }
-                __syncthreads();
-                // phase II: groups with candidates -> buckets; one global atomic
-                // pair per (run, response) reserves their space.  Afterwards
-                // tkey / tcnt of a bucket's slot are the end cursors of its sides
-                // A / B, and tcnt is FL_EMPTY for a slot without a bucket.
-                {
-                    // each thread owns a contiguous range of slots; the value of
-                    // a slot is members << 16 | 1 when its group yields a bucket
-                    const int per = (tsize + T - 1) / T;
-                    const int s0 = t * per < tsize ? t * per : tsize;
-                    const int s1 = s0 + per < tsize ? s0 + per : tsize;
-                    auto slot_value = [&](int slot) -> uint32_t {
-                        if (tkey[slot] == FL_EMPTY)
-                            return 0u;
-                        const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
-                        const bool ok = nz ? (nA > 0 && nB > 0) : (nA > 1);
-                        return ok ? ((nA + nB) << 16) | 1u : 0u;
-                    };
-                    uint32_t mysum = 0;
-                    for (int slot = s0; slot < s1; ++slot)
-                        mysum += slot_value(slot);
-                    uint32_t incl = mysum;
-    #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t y = __shfl_up_sync(FULL, incl, o);
-                        if (lane >= o)
-                            incl += y;
-                    }
-                    if (lane == 31)
-                        wsum[wp] = incl;
-                    __syncthreads();
-                    uint32_t before = 0, total = 0;
-                    for (int i = 0; i < nwarps; ++i) {
-                        before += (i < wp) ? wsum[i] : 0u;
-                        total += wsum[i];
-                    }
-                    if (t == 0) {
-                        const uint32_t mt = total >> 16, bt = total & 0xFFFFu;
-                        mbase_sh = bt ? atomicAdd(members_count, mt) : 0u;
-                        bbase_sh = bt ? atomicAdd(nbuckets, bt) : 0u;
-                        if (bt && ((uint64_t)mbase_sh + mt > mcap || (uint64_t)bbase_sh + bt > bcap)) {
-                            atomicOr(overflow, 2);      // host grows the space and redoes the search
-                            mbase_sh = 0xFFFFFFFFu;
-                        }
-                    }
-                    __syncthreads();
-                    if (mbase_sh == 0xFFFFFFFFu)
-                        continue;
-                    uint32_t run_off = before + incl - mysum;
-                    for (int slot = s0; slot < s1; ++slot) {
-                        const uint32_t v = slot_value(slot);
-                        if (v) {
-                            const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
-                            const uint32_t base = mbase_sh + (run_off >> 16);
-                            const uint32_t bi = bbase_sh + (run_off & 0xFFFFu);
-                            buckets[bi] = Bucket{base, nA, nz ? nB : 0u, (uint32_t)b};
-                            pair_counts[bi] = nz ? (uint64_t)nA * nB : (uint64_t)nA * (nA - 1) / 2;
-                            tkey[slot] = base + nA;          // end of side A: cursor counts down
-                            tcnt[slot] = base + nA + nB;     // end of side B
-                        } else {
-                            tcnt[slot] = FL_EMPTY;
-                        }
-                        run_off += v;
-                    }
-                }
-                __syncthreads();
-                // phase III: members, side A first
-                for (uint32_t i = t; i < s; i += T) {
-                    const uint64_t e = sv[i];
-                    const uint32_t hi = (uint32_t)(e >> 32);
-                    const uint32_t slot = hi & 0x7FFFFFFFu;
-                    if (tcnt[slot] == FL_EMPTY)
-                        continue;
-                    const uint32_t pos = atomicSub((hi >> 31) ? &tcnt[slot] : &tkey[slot], 1u) - 1u;
-                    members[pos] = (uint32_t)e;
-                }
-                __syncthreads();
-            }
-            if (from_seg && t == 0)
-                cursor = seg0_sh;               // grouped on chip: the entries leave the segment
+            group_on_chip<Lay>(sv, s, tkey, tcnt, nz, b, gout);
         }
+    }
+    if (t == 0) {
+        seg_count[blockIdx.x] = cursor < seg_cap ? cursor : seg_cap;
+        if (cursor > seg_cap)
+            atomicOr(overflow, 1);
+    }
+}
+
+// Class of a key: bit b is the parity of the key bits m with m % 4 == b.
+// The map is linear over GF(2), so class(k ^ c) = class(k) ^ class(c).
+__device__ __forceinline__ uint32_t key_class(uint32_t k)
+{
+    uint32_t q = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        q |= (uint32_t)(__popc(k & (0x11111111u << b)) & 1) << b;
+    return q;
+}
+
+// The survivor filter for p too large for one shared-memory filter of all
+// its keys (the same decisions as filter_kernel, for one response and
+// M <= 28).  The keys of a run are split into 16 classes by key_class:
+//
+//   pass 1  build the keys (the transpose also carries the four class
+//           parities, formed from the sampled row words in rows 28-31) and
+//           append each to its class in the thread's own sub-bucket, a
+//           strip of the CTA's global lists (counts in shared memory);
+//   rounds  for each class q: a fresh filter F of the class-q keys, tested
+//           by the keys k of class q ^ class(c) -- exactly those with
+//           k ^ c in class q, so every key k ^ c is looked up in the filter
+//           that holds its class; survivors go to the CTA's segment as
+//           (runbits | Kc, j).
+//
+// Each round's filter holds about p/16 keys, which keeps its load, and with
+// it the false-positive rate, near that of filter_kernel at p/16 columns.
+// The survivors of the run are then grouped on chip from the segment (hash
+// partitions), or left there for the general sort when a partition bin is
+// above the chip's capacity.  A sub-bucket that overflows sets overflow bit
+// 4 (the host enlarges the lists and redoes the search).
+template <int MB>
+__global__ void __launch_bounds__(FL_THREADS, 1)
+    filter_big_kernel(const uint32_t *__restrict__ Xr, int64_t Pp, int64_t P, const uint32_t *__restrict__ yb,
+                      int64_t n, int64_t p, int M, uint64_t seed, int64_t l0, int R, int rbits, int64_t rbase,
+                      uint32_t mcap, uint32_t bcap, uint32_t *__restrict__ lst_keys,
+                      uint32_t *__restrict__ lst_cols, uint32_t lcap, void *__restrict__ seg_keys_v,
+                      uint32_t *__restrict__ seg_vals, uint32_t *__restrict__ seg_count, uint32_t seg_cap,
+                      int *__restrict__ overflow, uint8_t *__restrict__ cnz, uint32_t *__restrict__ members,
+                      uint32_t *__restrict__ members_count, Bucket *__restrict__ buckets,
+                      uint64_t *__restrict__ pair_counts, uint32_t *__restrict__ nbuckets,
+                      const uint64_t *__restrict__ cdf, uint64_t wtot, int part_max, uint32_t *__restrict__ work)
+{
+    using Lay = FlLayout<false>;
+    extern __shared__ __align__(16) uint32_t fl_smem[];
+    uint32_t *F = fl_smem;                                                   // [FL_FWORDS]
+    uint64_t *sv = reinterpret_cast<uint64_t *>(fl_smem + Lay::OFF_SV);      // [SMAX]
+    uint16_t *cnt = reinterpret_cast<uint16_t *>(fl_smem + Lay::OFF_KM);     // [16][T] sub-bucket fills
+    uint32_t *tkey = fl_smem + Lay::OFF_TAB;                                 // [Lay::T], after the rounds
+    uint32_t *tcnt = fl_smem + Lay::OFF_TAB + Lay::T;
+    const int t = threadIdx.x;
+    const int lane = t & 31, wp = t >> 5;
+    const int T = (int)blockDim.x;
+    __shared__ int64_t rowoff[32];
+    __shared__ uint32_t c_sh, cursor, seg0_sh;
+    __shared__ int item_sh, lovf_sh;
+    const GroupOut gout{members, members_count, buckets, pair_counts, nbuckets, mcap, bcap, overflow};
+    const uint32_t P32 = (uint32_t)P, p32 = (uint32_t)p;
+    const uint32_t steps = (P32 + T - 1) / T;
+    const int fshift = 32 - (FL_LOGF - 5);
+    const uint32_t kcmask = (1u << M) - 1u;                                  // M <= 28
+    // slot i of this thread's class-q sub-bucket: (q * lcap + i) * T + t
+    uint32_t *lk = lst_keys + (int64_t)blockIdx.x * 16 * lcap * T;
+    uint32_t *lc = lst_cols + (int64_t)blockIdx.x * 16 * lcap * T;
+    uint64_t *okeys = reinterpret_cast<uint64_t *>(seg_keys_v) + (int64_t)blockIdx.x * seg_cap;
+    uint32_t *ovals = seg_vals + (int64_t)blockIdx.x * seg_cap;
+    if (t == 0)
+        cursor = seg_count[blockIdx.x];     // segments fill across launch groups
+
+    for (;;) {
+        if (t == 0)
+            item_sh = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int r = item_sh;
+        if (r >= R)
+            break;
+        const uint64_t rl = (uint64_t)(rbase + r);
+        if (wp == 0) {
+            int64_t srow = 0;
+            if (lane < M)
+                srow = draw_row(seed, (uint64_t)(l0 + r) * (uint64_t)M + (uint64_t)lane, n, cdf, wtot);
+            rowoff[lane] = srow * Pp;
+            const uint32_t ybit = lane < M ? (yb[srow >> 5] >> (srow & 31)) & 1u : 0u;
+            const uint32_t c = __ballot_sync(FULL, ybit);
+            if (lane == 0) {
+                c_sh = c;
+                cnz[rl] = (c != 0);
+                lovf_sh = 0;
+                seg0_sh = cursor;
+            }
+        }
+        for (int i = t; i < 16 * T; i += T)
+            cnt[i] = 0;
+        __syncthreads();
+        const uint32_t c = c_sh;
+        const bool nz = c != 0;
+
+        // pass 1: keys with their classes, into the thread's sub-buckets
+        for (uint32_t st = 0; st < steps; ++st) {
+            const uint32_t w = st * T + t;
+            if (w >= P32)
+                continue;
+            uint32_t A[32];
+#pragma unroll
+            for (int m = 0; m < 32; ++m)
+                A[m] = (m < MB && m < M) ? __ldg(Xr + rowoff[m] + w) : 0u;
+            uint32_t Q[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int m = 0; m < MB && m < 28; ++m)
+                Q[m & 3] ^= A[m];                // rows past M are zero
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                A[28 + b] = Q[b];
+            transpose32(A);
+            const uint32_t ncol = (32 * w + 32 <= p32) ? 32u : p32 - 32 * w;
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc) {
+                if ((uint32_t)cc < ncol) {
+                    const uint32_t q = A[cc] >> 28;
+                    const uint32_t i = cnt[q * T + t];
+                    if (i < lcap) {
+                        const int64_t at = ((int64_t)q * lcap + i) * T + t;
+                        lk[at] = A[cc] & kcmask;
+                        lc[at] = 32 * w + cc;
+                        cnt[q * T + t] = (uint16_t)(i + 1);
+                    } else {
+                        lovf_sh = 1;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (lovf_sh) {
+            if (t == 0)
+                atomicOr(overflow, 4);       // the host enlarges the sub-buckets and redoes the search
+            continue;
+        }
+        const int tb = nz ? 31 - __clz(c) : 0;
+        const uint32_t lowmask = nz ? ((1u << tb) - 1u) : 0u;
+        const uint64_t runbits = rl << M;
+
+        // entries of class q2 that pass (all of them when c == 0) to the
+        // segment, warp-aggregated
+        auto emit_class = [&](uint32_t q2, bool test) {
+            const uint32_t n2 = cnt[q2 * T + t];
+            const uint32_t nmax = __reduce_max_sync(FULL, n2);
+            for (uint32_t i = 0; i < nmax; ++i) {
+                bool pass = false;
+                uint32_t k = 0;
+                const int64_t at = ((int64_t)q2 * lcap + i) * T + t;
+                if (i < n2) {
+                    k = lk[at];
+                    pass = !test || bloom_has(F, k ^ c, fshift);
+                }
+                const uint32_t bal = __ballot_sync(FULL, pass);
+                if (bal == 0)
+                    continue;
+                uint32_t base = 0;
+                if (lane == 0)
+                    base = atomicAdd(&cursor, (uint32_t)__popc(bal));
+                base = __shfl_sync(FULL, base, 0);
+                if (pass) {
+                    const uint32_t o = base + __popc(bal & ((1u << lane) - 1u));
+                    if (o < seg_cap) {
+                        okeys[o] = runbits | canon(k, c, tb, lowmask);
+                        ovals[o] = lc[at];
+                    }
+                }
+            }
+        };
+        if (!nz) {
+            // c == 0: every column survives
+            for (uint32_t q = 0; q < 16; ++q)
+                emit_class(q, false);
+        } else {
+            const uint32_t cq = key_class(c);
+            for (uint32_t q = 0; q < 16; ++q) {
+                for (int i = t; i < FL_FWORDS; i += T)
+                    F[i] = 0;
+                __syncthreads();
+                const uint32_t nq = cnt[q * T + t];
+                for (uint32_t i = 0; i < nq; ++i) {
+                    uint32_t word, mask;
+                    bloom_pos(lk[((int64_t)q * lcap + i) * T + t], fshift, word, mask);
+                    atomicOr(F + word, mask);
+                }
+                __syncthreads();
+                emit_class(q ^ cq, true);
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        const uint32_t seg0 = seg0_sh, s = cursor - seg0;
+        __syncthreads();                     // every thread has read the cursor
+        if (group_from_segment<Lay>(okeys, ovals, seg0, s, seg_cap, part_max, kcmask, sv, tkey, tcnt, nz, 0,
+                                    gout) &&
+            t == 0)
+            cursor = seg0;                   // grouped on chip: the entries leave the segment
     }
     if (t == 0) {
         seg_count[blockIdx.x] = cursor < seg_cap ? cursor : seg_cap;
@@ -716,6 +960,21 @@ int filter_grid()
 
 size_t filter_scratch_words(int64_t p) { return (size_t)filter_grid() * 32 * (size_t)((p + 31) / 32); }
 
+bool filter_big_supported(int64_t p, int M) { return M >= 1 && M <= 28 && p >= 2 && p <= ((int64_t)1 << 27); }
+
+uint32_t filter_big_lcap(int64_t p)
+{
+    const int64_t P = (p + 31) / 32;
+    const int T = filter_threads(P);
+    const int64_t steps = (P + T - 1) / T;
+    return (uint32_t)(3 * steps + 16);   // a thread meets 32 steps keys, 2 steps per class on average
+}
+
+size_t filter_big_list_words(int64_t p, uint32_t lcap)
+{
+    return (size_t)filter_grid() * 16 * (size_t)lcap * (size_t)filter_threads((p + 31) / 32);
+}
+
 cudaError_t launch_seg_reset(uint32_t *seg_count, cudaStream_t s, int64_t *launches)
 {
     seg_reset_kernel<<<1, 256, 0, s>>>(seg_count, filter_grid());
@@ -765,6 +1024,31 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
                                         seg_count, seg_cap, overflow, cnz, members, members_count,
                                         buckets, pair_counts, nbuckets, pk.cdf, pk.wtotal, pk.Xrs, pk.Pf,
                                         part_max, work);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter_big(const Packed &pk, int M, uint64_t seed, int64_t l0, int R, int rbits, int64_t rbase,
+                              int grid, uint32_t mcap, uint32_t bcap, uint32_t *lst_keys, uint32_t *lst_cols,
+                              uint32_t lcap, uint64_t *seg_keys, uint32_t *seg_vals, uint32_t *seg_count,
+                              uint32_t seg_cap, int *overflow, uint8_t *cnz, uint32_t *members,
+                              uint32_t *members_count, Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
+                              cudaStream_t s, int64_t *launches, int part_max, uint32_t *work)
+{
+    const size_t smem = filter_smem_bytes(false);
+    using KernT = void (*)(const uint32_t *, int64_t, int64_t, const uint32_t *, int64_t, int64_t, int, uint64_t,
+                           int64_t, int, int, int64_t, uint32_t, uint32_t, uint32_t *, uint32_t *, uint32_t, void *,
+                           uint32_t *, uint32_t *, uint32_t, int *, uint8_t *, uint32_t *, uint32_t *, Bucket *,
+                           uint64_t *, uint32_t *, const uint64_t *, uint64_t, int, uint32_t *);
+    const KernT kern = M <= 8 ? filter_big_kernel<8> : M <= 16 ? filter_big_kernel<16>
+                       : M <= 24 ? filter_big_kernel<24> : filter_big_kernel<32>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    kern<<<grid, filter_threads(pk.P), smem, s>>>(pk.Xr, pk.Pp, pk.P, pk.yb, pk.n, pk.p, M, seed, l0, R, rbits, rbase,
+                                                  mcap, bcap, lst_keys, lst_cols, lcap, seg_keys, seg_vals, seg_count,
+                                                  seg_cap, overflow, cnz, members, members_count, buckets,
+                                                  pair_counts, nbuckets, pk.cdf, pk.wtotal, part_max, work);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -87,6 +87,7 @@ struct xyz_ctx {
     DevBuf counters;   // see the ctr_* accessors
     DevBuf ents, seg, members;   // partitioned grouping
     DevBuf kc_scratch;           // filter path: one key row per CTA
+    DevBuf lst_keys, lst_cols;   // class-split filter: per-thread class sub-buckets of keys and columns
     DevBuf seg_keys, seg_vals, seg_count;   // filter path: per-CTA survivor segments
     DevBuf buckets2, pair_counts2, pair_off2, scan_tmp2;   // filter path: spilled runs
     int64_t surv_cap = 0;        // filter path: survivor capacity (CTAs x segment)
@@ -108,6 +109,9 @@ struct xyz_ctx {
     int64_t rec_cap = 1 << 16;
     int64_t chunk_entries = (int64_t)1 << 25;
     bool use_filter = true;
+    bool force_big = false;      // class-split filter wherever it applies (xyz_set_filter 2)
+    uint32_t big_lcap = 0;       // class-split filter: slots per thread and class (grown on overflow)
+    bool big_off = false;        // class-split filter given up (its classes were too uneven)
 
     bool timing = false;
     xyz_stats stats;
@@ -193,7 +197,7 @@ static int64_t ws_bytes(const xyz_ctx *c)
                            &c->pair_off, &c->scan_tmp,   &c->counters,  &c->rec_keys,
                            &c->rec_keys_alt, &c->rec_agree, &c->rec_agree_alt, &c->flags,
                            &c->pos,     &c->out,         &c->dedup_tmp, &c->raw,
-                           &c->ents, &c->seg, &c->members, &c->kc_scratch,
+                           &c->ents, &c->seg, &c->members, &c->kc_scratch, &c->lst_keys, &c->lst_cols,
                            &c->seg_keys, &c->seg_vals, &c->seg_count,
                            &c->buckets2, &c->pair_counts2, &c->pair_off2, &c->scan_tmp2,
                            &c->resp, &c->ybs, &c->y_alt, &c->y_stage,
@@ -282,6 +286,7 @@ struct Plan {
     int64_t R;        // runs per launch group
     int NB, BB;       // filter path: response blocks per run, responses per block
     bool filter;      // per-run survivor filter with on-chip grouping (M <= 31, p <= 262144)
+    bool big;         // ... in its class-split form (one response, M <= 28, larger p)
     bool part;        // partitioned grouping (M <= 31, large p)
     bool k64;         // 64-bit composite keys (LSD path)
     int kbits;        // bits of a column index (record keys use 2*kbits)
@@ -299,6 +304,12 @@ Plan make_plan(const xyz_ctx *c, int64_t runs, int M, int B)
         rmax = 65535;
     int64_t R = runs < rmax ? runs : rmax;
     pl.filter = (c->use_filter || B > 1) && filter_supported(p, M);
+    // one binary response past the shared-memory filter's p (or forced):
+    // the class-split filter, on the same buffers and host loop
+    pl.big = c->use_filter && !c->big_off && B == 1 && !c->pk.Xrs && filter_big_supported(p, M) &&
+             (!pl.filter || c->force_big);
+    if (pl.big)
+        pl.filter = true;
     pl.part = !pl.filter && part_supported(p, M);
     pl.k64 = false;
     pl.NB = pl.BB = 1;
@@ -371,7 +382,15 @@ int ensure_search_ws(xyz_ctx *c, const Plan &pl, int B, int64_t runs)
         const int64_t mcap = c->mem_cap;
         const int64_t mb = mcap / 2 + 1;
         const int64_t cnz_bytes = (int64_t)B << ceil_log2(runs);
-        if ((rc = ensure(c->kc_scratch, filter_scratch_words(c->pk.p) * 4)) ||
+        if (pl.big) {
+            const uint32_t want = filter_big_lcap(c->pk.p);
+            if (c->big_lcap < want)
+                c->big_lcap = want;
+            const size_t words = filter_big_list_words(c->pk.p, c->big_lcap);
+            if ((rc = ensure(c->lst_keys, words * 4)) || (rc = ensure(c->lst_cols, words * 4)))
+                return rc;
+        }
+        if ((rc = ensure(c->kc_scratch, pl.big ? 4 : filter_scratch_words(c->pk.p) * 4)) ||
             (rc = ensure(c->seg_keys, (size_t)cap * 8)) || (rc = ensure(c->seg_vals, (size_t)cap * 4)) ||
             (rc = ensure(c->seg_count, (size_t)grid * 4)) ||
             (rc = ensure(c->keysA, cap * 8)) || (rc = ensure(c->keysB, cap * 8)) ||
@@ -469,7 +488,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
 {
     const int64_t runs = l1 - l0;
     const int64_t p = c->pk.p;
-    Plan pl = make_plan(c, runs, M, B);
+    Plan pl = make_plan(c, runs, M, B);            // replanned when the class-split filter is given up
     if (B > 1 && !pl.filter)
         return fail(XYZ_EINVAL, "batched search needs M <= 31 and p <= 262144");
     if (c->pk.Xrs && (!pl.filter || B > 1))
@@ -528,6 +547,19 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                                         : ((l1 - l0 + pl.R - 1) / pl.R + 1) / 2;
                     redo = true;
                 }
+                if (sovf & 4) {
+                    // a class sub-bucket of the class-split filter did: twice
+                    // the room once, then (classes that uneven) the path
+                    // without it
+                    const uint32_t lmax = 2 * filter_big_lcap(p);
+                    if (c->big_lcap >= lmax) {
+                        c->big_off = true;
+                        pl = make_plan(c, runs, M, B);
+                    } else {
+                        c->big_lcap = lmax;
+                    }
+                    redo = true;
+                }
                 if (sovf & 2) {
                     // the on-chip groups' members did: at least double, and at
                     // least what the last launch group tried to reserve
@@ -576,14 +608,24 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                 CU(cudaMemsetAsync(ctr_u32(c), 0, 8, c->stream));   // buckets, members
                 CU(cudaMemsetAsync(ctr_work(c), 0, 4, c->stream));  // the filter's work items
                 tm.begin(ST_KEYS);
-                CU(launch_filter(c->pk, ybs, B, M, seed, g0, (int)Rc, pl.NB, pl.BB, rbits, g0 - l0,
-                                 grid, (uint32_t)(c->mem_cap < 0xFFFFFFFELL ? c->mem_cap : 0xFFFFFFFELL),
-                                 (uint32_t)mb, (uint32_t *)c->kc_scratch.ptr,
-                                 (uint64_t *)c->seg_keys.ptr, (uint32_t *)c->seg_vals.ptr,
-                                 (uint32_t *)c->seg_count.ptr, (uint32_t)c->seg_cap, ctr_sovf(c),
-                                 (uint8_t *)c->cnz.ptr, (uint32_t *)c->members.ptr, ctr_members(c),
-                                 (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
-                                 ctr_nbuckets(c), c->stream, &launches, c->onchip_parts, ctr_work(c)));
+                if (pl.big)
+                    CU(launch_filter_big(c->pk, M, seed, g0, (int)Rc, rbits, g0 - l0, grid,
+                                         (uint32_t)(c->mem_cap < 0xFFFFFFFELL ? c->mem_cap : 0xFFFFFFFELL),
+                                         (uint32_t)mb, (uint32_t *)c->lst_keys.ptr, (uint32_t *)c->lst_cols.ptr,
+                                         c->big_lcap, (uint64_t *)c->seg_keys.ptr, (uint32_t *)c->seg_vals.ptr,
+                                         (uint32_t *)c->seg_count.ptr, (uint32_t)c->seg_cap, ctr_sovf(c),
+                                         (uint8_t *)c->cnz.ptr, (uint32_t *)c->members.ptr, ctr_members(c),
+                                         (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
+                                         ctr_nbuckets(c), c->stream, &launches, c->onchip_parts, ctr_work(c)));
+                else
+                    CU(launch_filter(c->pk, ybs, B, M, seed, g0, (int)Rc, pl.NB, pl.BB, rbits, g0 - l0,
+                                     grid, (uint32_t)(c->mem_cap < 0xFFFFFFFELL ? c->mem_cap : 0xFFFFFFFELL),
+                                     (uint32_t)mb, (uint32_t *)c->kc_scratch.ptr,
+                                     (uint64_t *)c->seg_keys.ptr, (uint32_t *)c->seg_vals.ptr,
+                                     (uint32_t *)c->seg_count.ptr, (uint32_t)c->seg_cap, ctr_sovf(c),
+                                     (uint8_t *)c->cnz.ptr, (uint32_t *)c->members.ptr, ctr_members(c),
+                                     (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
+                                     ctr_nbuckets(c), c->stream, &launches, c->onchip_parts, ctr_work(c)));
                 tm.end();
                 tm.begin(ST_JOIN);
                 CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
@@ -858,7 +900,7 @@ void destroy_ctx(xyz_ctx *c)
                      &c->cnz,     &c->buckets,     &c->pair_counts, &c->pair_off, &c->scan_tmp,
                      &c->counters, &c->rec_keys,   &c->rec_keys_alt, &c->rec_agree,
                      &c->rec_agree_alt, &c->flags, &c->pos,       &c->out,      &c->dedup_tmp,
-                     &c->raw,     &c->ents,        &c->seg,       &c->members,  &c->kc_scratch,
+                     &c->raw,     &c->ents,        &c->seg,       &c->members,  &c->kc_scratch, &c->lst_keys, &c->lst_cols,
                      &c->seg_keys, &c->seg_vals,   &c->seg_count, &c->buckets2, &c->pair_counts2,
                      &c->pair_off2, &c->scan_tmp2, &c->resp,   &c->ybs, &c->y_alt, &c->y_stage,
                      &c->wq, &c->wcdf, &c->wplanes, &c->wq2, &c->wcdf2, &c->wplanes2,
@@ -1893,7 +1935,10 @@ int xyz_set_filter(xyz_ctx *ctx, int enable)
 {
     if (!ctx)
         return fail(XYZ_EINVAL, "null context");
+    if (enable < 0 || enable > 2)
+        return fail(XYZ_EINVAL, "enable must be 0, 1 or 2");
     ctx->use_filter = enable != 0;
+    ctx->force_big = enable == 2;
     return XYZ_OK;
 }
 

@@ -169,6 +169,17 @@ cudaError_t launch_group(const Packed &pk, int R, const uint64_t *ents, const ui
 
 // Per-run survivor filter (filter.cu), used for M <= 31 and moderate p.
 bool filter_supported(int64_t p, int M);
+// The class-split filter (filter_big_kernel) for one response and M <= 28
+// at any p up to 2^27: per-thread class sub-buckets of lcap slots each.
+bool filter_big_supported(int64_t p, int M);
+uint32_t filter_big_lcap(int64_t p);
+size_t filter_big_list_words(int64_t p, uint32_t lcap);
+cudaError_t launch_filter_big(const Packed &pk, int M, uint64_t seed, int64_t l0, int R, int rbits, int64_t rbase,
+                              int grid, uint32_t mcap, uint32_t bcap, uint32_t *lst_keys, uint32_t *lst_cols,
+                              uint32_t lcap, uint64_t *seg_keys, uint32_t *seg_vals, uint32_t *seg_count,
+                              uint32_t seg_cap, int *overflow, uint8_t *cnz, uint32_t *members,
+                              uint32_t *members_count, Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
+                              cudaStream_t s, int64_t *launches, int part_max, uint32_t *work);
 int filter_grid();
 size_t filter_scratch_words(int64_t p);
 int64_t filter_run_cap();

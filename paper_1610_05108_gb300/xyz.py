@@ -347,8 +347,11 @@ class Context:
     def set_chunk_entries(self, entries: int):
         _check(load().xyz_set_chunk_entries(self.handle, int(entries)))
 
-    def set_filter(self, on: bool):
-        _check(load().xyz_set_filter(self.handle, 1 if on else 0))
+    def set_filter(self, on):
+        """True / 1: the survivor filter where it applies (default); False /
+        0: group every column; 2: the class-split filter wherever it applies."""
+        mode = int(on) if not isinstance(on, bool) else (1 if on else 0)
+        _check(load().xyz_set_filter(self.handle, mode))
 
     def set_spill_flush(self, groups: int):
         _check(load().xyz_set_spill_flush(self.handle, int(groups)))
