@@ -696,8 +696,10 @@ __device__ __forceinline__ uint32_t key_class(uint32_t k)
 //
 //   pass 1  build the keys (the transpose also carries the four class
 //           parities, formed from the sampled row words in rows 28-31) and
-//           append each to its class in the thread's own sub-bucket, a
-//           strip of the CTA's global lists (counts in shared memory);
+//           append each to its class: each warp stages its keys per class
+//           in shared memory (the filter and survivor array are free until
+//           the rounds) and moves them to the CTA's class lists 16 at a
+//           time, so the lists are written in whole sectors;
 //   rounds  for each class q: a fresh filter F of the class-q keys, tested
 //           by the keys k of class q ^ class(c) -- exactly those with
 //           k ^ c in class q, so every key k ^ c is looked up in the filter
@@ -708,8 +710,8 @@ __device__ __forceinline__ uint32_t key_class(uint32_t k)
 // it the false-positive rate, near that of filter_kernel at p/16 columns.
 // The survivors of the run are then grouped on chip from the segment (hash
 // partitions), or left there for the general sort when a partition bin is
-// above the chip's capacity.  A sub-bucket that overflows sets overflow bit
-// 4 (the host enlarges the lists and redoes the search).
+// above the chip's capacity.  A class list that overflows sets overflow
+// bit 4 (the host enlarges the lists and redoes the search).
 template <int MB>
 __global__ void __launch_bounds__(FL_THREADS, 1)
     filter_big_kernel(const uint32_t *__restrict__ Xr, int64_t Pp, int64_t P, const uint32_t *__restrict__ yb,
@@ -723,30 +725,69 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                       const uint64_t *__restrict__ cdf, uint64_t wtot, int part_max, uint32_t *__restrict__ work)
 {
     using Lay = FlLayout<false>;
+    constexpr int FB_WARPS = FL_THREADS / 32;
+    constexpr uint32_t FB_BUF = 48;                // staged entries per warp and class
+    constexpr uint32_t FB_NONE = 0xFFFFFFFFu;      // padding key (real keys have M <= 28 bits)
+    static_assert(2 * FB_WARPS * 16 * (int)FB_BUF <= Lay::OFF_KM, "staging fits the filter and survivor array");
+    static_assert(FB_WARPS * 16 <= FL_KWORDS, "staged counts fit the keep-mask region");
     extern __shared__ __align__(16) uint32_t fl_smem[];
-    uint32_t *F = fl_smem;                                                   // [FL_FWORDS]
-    uint64_t *sv = reinterpret_cast<uint64_t *>(fl_smem + Lay::OFF_SV);      // [SMAX]
-    uint16_t *cnt = reinterpret_cast<uint16_t *>(fl_smem + Lay::OFF_KM);     // [16][T] sub-bucket fills
+    uint32_t *F = fl_smem;                                                   // [FL_FWORDS], in the rounds
+    uint64_t *sv = reinterpret_cast<uint64_t *>(fl_smem + Lay::OFF_SV);      // [SMAX], after the rounds
     uint32_t *tkey = fl_smem + Lay::OFF_TAB;                                 // [Lay::T], after the rounds
     uint32_t *tcnt = fl_smem + Lay::OFF_TAB + Lay::T;
     const int t = threadIdx.x;
     const int lane = t & 31, wp = t >> 5;
     const int T = (int)blockDim.x;
+    // pass 1 staging: per warp and class FB_BUF keys and columns, and counts
+    uint32_t *mk = fl_smem + wp * 16 * FB_BUF;
+    uint32_t *mc = fl_smem + FB_WARPS * 16 * FB_BUF + wp * 16 * FB_BUF;
+    uint32_t *mw = fl_smem + Lay::OFF_KM + wp * 16;
     __shared__ int64_t rowoff[32];
     __shared__ uint32_t c_sh, cursor, seg0_sh;
+    __shared__ uint32_t cls_n[16];                 // fill of each class list
     __shared__ int item_sh, lovf_sh;
     const GroupOut gout{members, members_count, buckets, pair_counts, nbuckets, mcap, bcap, overflow};
     const uint32_t P32 = (uint32_t)P, p32 = (uint32_t)p;
     const uint32_t steps = (P32 + T - 1) / T;
     const int fshift = 32 - (FL_LOGF - 5);
     const uint32_t kcmask = (1u << M) - 1u;                                  // M <= 28
-    // slot i of this thread's class-q sub-bucket: (q * lcap + i) * T + t
-    uint32_t *lk = lst_keys + (int64_t)blockIdx.x * 16 * lcap * T;
-    uint32_t *lc = lst_cols + (int64_t)blockIdx.x * 16 * lcap * T;
+    uint32_t *lk = lst_keys + (int64_t)blockIdx.x * 16 * lcap;               // [16][lcap]
+    uint32_t *lc = lst_cols + (int64_t)blockIdx.x * 16 * lcap;
     uint64_t *okeys = reinterpret_cast<uint64_t *>(seg_keys_v) + (int64_t)blockIdx.x * seg_cap;
     uint32_t *ovals = seg_vals + (int64_t)blockIdx.x * seg_cap;
     if (t == 0)
         cursor = seg_count[blockIdx.x];     // segments fill across launch groups
+
+    // the first 16 staged entries of class q (cntq staged) to the class list;
+    // the rest move down.  Executed by the whole warp.
+    auto flush16 = [&](uint32_t q, uint32_t cntq) {
+        uint32_t pos = 0;
+        if (lane == 0)
+            pos = atomicAdd(&cls_n[q], 16u);
+        pos = __shfl_sync(FULL, pos, 0);
+        if (pos + 16 <= lcap) {
+            if (lane < 16) {
+                lk[(int64_t)q * lcap + pos + lane] = mk[q * FB_BUF + lane];
+                lc[(int64_t)q * lcap + pos + lane] = mc[q * FB_BUF + lane];
+            }
+        } else if (lane == 0) {
+            lovf_sh = 1;
+        }
+        const uint32_t rest = cntq - 16;         // <= 32
+        uint32_t ek = 0, ec = 0;
+        if ((uint32_t)lane < rest) {
+            ek = mk[q * FB_BUF + 16 + lane];
+            ec = mc[q * FB_BUF + 16 + lane];
+        }
+        __syncwarp();
+        if ((uint32_t)lane < rest) {
+            mk[q * FB_BUF + lane] = ek;
+            mc[q * FB_BUF + lane] = ec;
+        }
+        if (lane == 0)
+            mw[q] = rest;
+        __syncwarp();
+    };
 
     for (;;) {
         if (t == 0)
@@ -770,21 +811,22 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 seg0_sh = cursor;
             }
         }
-        for (int i = t; i < 16 * T; i += T)
-            cnt[i] = 0;
+        if (lane < 16)
+            mw[lane] = 0;
+        if (t < 16)
+            cls_n[t] = 0;
         __syncthreads();
         const uint32_t c = c_sh;
         const bool nz = c != 0;
 
-        // pass 1: keys with their classes, into the thread's sub-buckets
+        // pass 1: keys with their classes, staged per warp and class
         for (uint32_t st = 0; st < steps; ++st) {
             const uint32_t w = st * T + t;
-            if (w >= P32)
-                continue;
+            const bool wv = w < P32;
             uint32_t A[32];
 #pragma unroll
             for (int m = 0; m < 32; ++m)
-                A[m] = (m < MB && m < M) ? __ldg(Xr + rowoff[m] + w) : 0u;
+                A[m] = (wv && m < MB && m < M) ? __ldg(Xr + rowoff[m] + w) : 0u;
             uint32_t Q[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int m = 0; m < MB && m < 28; ++m)
@@ -793,27 +835,49 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             for (int b = 0; b < 4; ++b)
                 A[28 + b] = Q[b];
             transpose32(A);
-            const uint32_t ncol = (32 * w + 32 <= p32) ? 32u : p32 - 32 * w;
+            const uint32_t ncol = !wv ? 0u : (32 * w + 32 <= p32) ? 32u : p32 - 32 * w;
 #pragma unroll
             for (int cc = 0; cc < 32; ++cc) {
-                if ((uint32_t)cc < ncol) {
-                    const uint32_t q = A[cc] >> 28;
-                    const uint32_t i = cnt[q * T + t];
-                    if (i < lcap) {
-                        const int64_t at = ((int64_t)q * lcap + i) * T + t;
-                        lk[at] = A[cc] & kcmask;
-                        lc[at] = 32 * w + cc;
-                        cnt[q * T + t] = (uint16_t)(i + 1);
-                    } else {
-                        lovf_sh = 1;
+                // room for this step's appends: no class above 16 staged
+                for (;;) {
+                    uint32_t full = __ballot_sync(FULL, lane < 16 && mw[lane] > 16);
+                    if (!full)
+                        break;
+                    while (full) {
+                        const uint32_t q = __ffs(full) - 1;
+                        full &= full - 1;
+                        flush16(q, mw[q]);
                     }
                 }
+                if ((uint32_t)cc < ncol) {
+                    const uint32_t q = A[cc] >> 28;
+                    const uint32_t slot = atomicAdd(&mw[q], 1u);     // < FB_BUF
+                    mk[q * FB_BUF + slot] = A[cc] & kcmask;
+                    mc[q * FB_BUF + slot] = 32 * w + cc;
+                }
+                __syncwarp();
+            }
+        }
+        // what is still staged, the last entries of a class padded to 16
+        for (uint32_t q = 0; q < 16; ++q) {
+            uint32_t left = mw[q];
+            while (left >= 16) {
+                flush16(q, left);
+                left = mw[q];
+            }
+            if (left > 0) {
+                if ((uint32_t)lane >= left && lane < 16) {
+                    mk[q * FB_BUF + lane] = FB_NONE;
+                    mc[q * FB_BUF + lane] = 0;
+                }
+                __syncwarp();
+                flush16(q, 16);
             }
         }
         __syncthreads();
         if (lovf_sh) {
             if (t == 0)
-                atomicOr(overflow, 4);       // the host enlarges the sub-buckets and redoes the search
+                atomicOr(overflow, 4);       // the host enlarges the class lists and redoes the search
             continue;
         }
         const int tb = nz ? 31 - __clz(c) : 0;
@@ -821,17 +885,16 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         const uint64_t runbits = rl << M;
 
         // entries of class q2 that pass (all of them when c == 0) to the
-        // segment, warp-aggregated
+        // segment, warp-aggregated; the whole CTA walks the class list
         auto emit_class = [&](uint32_t q2, bool test) {
-            const uint32_t n2 = cnt[q2 * T + t];
-            const uint32_t nmax = __reduce_max_sync(FULL, n2);
-            for (uint32_t i = 0; i < nmax; ++i) {
+            const uint32_t n2 = cls_n[q2] < lcap ? cls_n[q2] : lcap;
+            for (uint32_t i0 = 0; i0 < n2; i0 += T) {
+                const uint32_t i = i0 + t;
                 bool pass = false;
                 uint32_t k = 0;
-                const int64_t at = ((int64_t)q2 * lcap + i) * T + t;
                 if (i < n2) {
-                    k = lk[at];
-                    pass = !test || bloom_has(F, k ^ c, fshift);
+                    k = lk[(int64_t)q2 * lcap + i];
+                    pass = k != FB_NONE && (!test || bloom_has(F, k ^ c, fshift));
                 }
                 const uint32_t bal = __ballot_sync(FULL, pass);
                 if (bal == 0)
@@ -844,7 +907,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                     const uint32_t o = base + __popc(bal & ((1u << lane) - 1u));
                     if (o < seg_cap) {
                         okeys[o] = runbits | canon(k, c, tb, lowmask);
-                        ovals[o] = lc[at];
+                        ovals[o] = lc[(int64_t)q2 * lcap + i];
                     }
                 }
             }
@@ -859,11 +922,14 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 for (int i = t; i < FL_FWORDS; i += T)
                     F[i] = 0;
                 __syncthreads();
-                const uint32_t nq = cnt[q * T + t];
-                for (uint32_t i = 0; i < nq; ++i) {
-                    uint32_t word, mask;
-                    bloom_pos(lk[((int64_t)q * lcap + i) * T + t], fshift, word, mask);
-                    atomicOr(F + word, mask);
+                const uint32_t nq = cls_n[q] < lcap ? cls_n[q] : lcap;
+                for (uint32_t i = t; i < nq; i += T) {
+                    const uint32_t k = lk[(int64_t)q * lcap + i];
+                    if (k != FB_NONE) {
+                        uint32_t word, mask;
+                        bloom_pos(k, fshift, word, mask);
+                        atomicOr(F + word, mask);
+                    }
                 }
                 __syncthreads();
                 emit_class(q ^ cq, true);
@@ -964,15 +1030,16 @@ bool filter_big_supported(int64_t p, int M) { return M >= 1 && M <= 28 && p >= 2
 
 uint32_t filter_big_lcap(int64_t p)
 {
-    const int64_t P = (p + 31) / 32;
-    const int T = filter_threads(P);
-    const int64_t steps = (P + T - 1) / T;
-    return (uint32_t)(3 * steps + 16);   // a thread meets 32 steps keys, 2 steps per class on average
+    // a class list holds p / 16 keys on average: room for 1.5 times that,
+    // plus the padding of every warp's last flush (< 16 per warp)
+    const int64_t l = (3 * p + 31) / 32 + 16 * (FL_THREADS / 32);
+    return (uint32_t)((l + 15) / 16 * 16);
 }
 
 size_t filter_big_list_words(int64_t p, uint32_t lcap)
 {
-    return (size_t)filter_grid() * 16 * (size_t)lcap * (size_t)filter_threads((p + 31) / 32);
+    (void)p;
+    return (size_t)filter_grid() * 16 * (size_t)lcap;
 }
 
 cudaError_t launch_seg_reset(uint32_t *seg_count, cudaStream_t s, int64_t *launches)

@@ -87,7 +87,7 @@ struct xyz_ctx {
     DevBuf counters;   // see the ctr_* accessors
     DevBuf ents, seg, members;   // partitioned grouping
     DevBuf kc_scratch;           // filter path: one key row per CTA
-    DevBuf lst_keys, lst_cols;   // class-split filter: per-thread class sub-buckets of keys and columns
+    DevBuf lst_keys, lst_cols;   // class-split filter: per-CTA class lists of keys and columns
     DevBuf seg_keys, seg_vals, seg_count;   // filter path: per-CTA survivor segments
     DevBuf buckets2, pair_counts2, pair_off2, scan_tmp2;   // filter path: spilled runs
     int64_t surv_cap = 0;        // filter path: survivor capacity (CTAs x segment)
@@ -110,7 +110,7 @@ struct xyz_ctx {
     int64_t chunk_entries = (int64_t)1 << 25;
     bool use_filter = true;
     bool force_big = false;      // class-split filter wherever it applies (xyz_set_filter 2)
-    uint32_t big_lcap = 0;       // class-split filter: slots per thread and class (grown on overflow)
+    uint32_t big_lcap = 0;       // class-split filter: entries per class list and CTA (grown on overflow)
     bool big_off = false;        // class-split filter given up (its classes were too uneven)
 
     bool timing = false;
@@ -548,9 +548,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                     redo = true;
                 }
                 if (sovf & 4) {
-                    // a class sub-bucket of the class-split filter did: twice
-                    // the room once, then (classes that uneven) the path
-                    // without it
+                    // a class list of the class-split filter did: twice the
+                    // room once, then (classes that uneven) the path without it
                     const uint32_t lmax = 2 * filter_big_lcap(p);
                     if (c->big_lcap >= lmax) {
                         c->big_off = true;

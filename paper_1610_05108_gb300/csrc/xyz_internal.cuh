@@ -170,7 +170,7 @@ cudaError_t launch_group(const Packed &pk, int R, const uint64_t *ents, const ui
 // Per-run survivor filter (filter.cu), used for M <= 31 and moderate p.
 bool filter_supported(int64_t p, int M);
 // The class-split filter (filter_big_kernel) for one response and M <= 28
-// at any p up to 2^27: per-thread class sub-buckets of lcap slots each.
+// at any p up to 2^27: per-CTA lists of lcap entries for each of 16 classes.
 bool filter_big_supported(int64_t p, int M);
 uint32_t filter_big_lcap(int64_t p);
 size_t filter_big_list_words(int64_t p, uint32_t lcap);

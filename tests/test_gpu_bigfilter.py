@@ -3,7 +3,8 @@ shared-memory filter per class in turn): the search it serves must equal the
 oracle's and the other paths' exactly -- at small p with the filter forced,
 past the single filter's limit of p = 262144, for c = 0 runs, for runs that
 overflow the on-chip capacity (hash partitions and the sort), and when a
-class sub-bucket overflows and the search is redone with larger ones.
+class list overflows and the search is redone with larger ones or without
+the class-split form.
 """
 import numpy as np
 import pytest
@@ -101,9 +102,10 @@ def test_class_split_above_the_single_filter(xyz, orc):
 
 def test_class_split_sub_bucket_overflow_regrows(xyz, orc):
     # two column patterns only (v and v * Y): every run has two distinct keys,
-    # so each thread's keys fall into one or two classes and overflow the
-    # sub-buckets sized for 16 balanced classes; the search is redone with
-    # larger ones.  Every pair (j < 1000 <= k) is a candidate in every run.
+    # so all keys fall into one or two classes and overflow the class lists
+    # sized for 16 balanced classes; the search is redone with larger lists
+    # and then without the class-split form.  Every pair (j < 1000 <= k) is
+    # a candidate in every run.
     n, p = 64, 2000
     rng = np.random.default_rng(51)
     v = (rng.integers(0, 2, size=n, dtype=np.int8) * 2 - 1).astype(np.int8)
@@ -121,10 +123,9 @@ def test_class_split_sub_bucket_overflow_regrows(xyz, orc):
 
 
 def test_class_split_gives_way_when_classes_are_too_uneven(xyz, orc):
-    # 163840 identical columns: every key of a run is in one class, so each
-    # thread meets its 256 keys in one class -- more than twice the room of
-    # sub-buckets sized for 16 balanced classes.  The search falls back to
-    # the path without the class-split filter and
+    # 163840 identical columns: every key of a run is in one class -- more
+    # than twice the room of class lists sized for 16 balanced classes.  The
+    # search falls back to the path without the class-split filter and
     # gives the oracle's (empty) result; c != 0 in every run (half the rows
     # of Y are -1), so no pair is a candidate.
     n, p = 64, 163840
