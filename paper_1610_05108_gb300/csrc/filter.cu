@@ -1,12 +1,14 @@
 // Per-run survivor filter for the equal-pairs search (Algorithm 2 steps
-// 3-4), used for M <= 31 when p is small enough for a shared-memory filter.
+// 3-4): filter_kernel for M <= 31 when p is small enough for one
+// shared-memory filter of a run's keys, filter_big_kernel (further down)
+// for larger p with the keys split into 16 linear classes.
 //
 // In run l with response key c, columns j and k form a candidate exactly
 // when kx_j ^ kx_k = c (keys.cu: X_j and Z_k agree on the sampled rows).  A
 // column can therefore only be part of a candidate pair if the key kx_j ^ c
 // is present among the run's column keys.  Almost every column fails that
 // test, so the grouping of equal canonical keys only needs the few that
-// pass.  One CTA (1024 threads) handles one run at a time:
+// pass.  One CTA (640-1024 threads) handles one run at a time:
 //
 //   pass 1  build the keys of all p columns (each thread: the words of the M
 //           sampled rows, transposed in registers), store kx to the CTA's
@@ -23,10 +25,12 @@
 // bucket.  When a run keeps more columns than the chip can group, the
 // survivors are filtered again with a fresh filter built from the survivors
 // alone (refinement: a candidate pair's columns are both survivors, so
-// they still find each other), and only what remains after a few rounds is
-// spilled to the CTA's global segment for the general sort and join.  The
-// survivors of a run are grouped on chip into buckets and members, ready
-// for verification.  In a run with c == 0 every column survives.
+// they still find each other), and what remains after a few rounds goes to
+// the CTA's global segment: grouped from there on chip in hash partitions
+// of the group keys, or, when one partition is still too large, left for
+// the general sort and join.  The survivors of a run are grouped on chip
+// into buckets and members, ready for verification.  In a run with c == 0
+// every column survives.
 #include <type_traits>
 
 #include "bits.cuh"
