@@ -155,7 +155,6 @@ int xyz_set_y(xyz_ctx *ctx, const int8_t *Y);
 /* xyz_set_y with Y in device memory. */
 int xyz_set_y_dev(xyz_ctx *ctx, const int8_t *dY);
 
-/* Release a context and its device memory.  NULL is ignored. */
 /* Real-valued response (Section 3.1, continuous Y with binary X): the rows
  * of a run are drawn with probability |Y_i| / ||Y||_1, Z = sgn(Y) o X
  * (sgn(0) = +1), and a candidate passes when Y^T(X_j o X_k) >= kappa ||Y||_1,
@@ -173,6 +172,7 @@ int xyz_set_y_dev(xyz_ctx *ctx, const int8_t *dY);
 int xyz_set_y_real(xyz_ctx *ctx, const double *Y);
 int xyz_set_y_real_dev(xyz_ctx *ctx, const double *dY);
 
+/* Release a context and its device memory.  NULL is ignored. */
 void xyz_destroy(xyz_ctx *ctx);
 
 /* Message of the last failed call on this thread ("" if none). */
@@ -373,7 +373,13 @@ int32_t xyz_M_for_gamma0(int64_t p, double gamma0);
  * exits.  The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress, with the context's device current), so make the first
  * call before beginning any stream capture on that device.  Calls share the
- * array: calls that overlap on the GPU race and must be serialised.
+ * array: calls that overlap on the GPU race and must be serialised.  The
+ * cached address is that of the device's primary context: after a
+ * cudaDeviceReset of the device, do not call this entry point on it again in
+ * the same process.  The caller's current device is restored on return.
+ * Binary and real-valued (xyz_set_y_real) responses are taken, whatever
+ * search ran on the context before; contexts of real X built by
+ * xyz_create_unbiased are refused (XYZ_EINVAL).
  * ctx: a context with p <= XYZ_NOALLOC_MAX_P (else XYZ_EINVAL).  jk: host array
  * of 2*cap int32 that receives the pairs (j0,k0,j1,k1,...), j < k, sorted;
  * *count gets their number.  A run with more than XYZ_NOALLOC_MAX_PAIRS or

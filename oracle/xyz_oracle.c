@@ -836,7 +836,6 @@ int64_t orc_xyz_unbiased_range(const float *X, const double *Y, int64_t n, int64
     for (int64_t i = 0; i < n; i++)
         norm1 += fabs(Ys[i]);
     int64_t *rows = (int64_t *)malloc((size_t)(M > 0 ? M : 1) * sizeof(int64_t));
-    int8_t *Xt = (int8_t *)malloc((size_t)(n * p));
     orc_vec found = {0, 0, 0};
     orc_vec cand = {0, 0, 0};
     for (int64_t l = l0; l < l1; l++) {
@@ -871,7 +870,6 @@ int64_t orc_xyz_unbiased_range(const float *X, const double *Y, int64_t n, int64
     }
     free(found.v);
     free(cand.v);
-    free(Xt);
     free(rows);
     free(sgn);
     free(q);

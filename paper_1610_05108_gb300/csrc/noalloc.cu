@@ -23,6 +23,19 @@
 // call, and everything else is fully written before it is read.  Calls that
 // overlap on the GPU (from different threads or streams) race on the array
 // and must be serialised by the caller.
+//
+// The cached address belongs to the device's primary context: after a
+// cudaDeviceReset on that device the cache is stale, and this entry point
+// must not be called there again in the same process (every context of the
+// library created before the reset is invalid by then anyway).
+//
+// The pass threshold of the verification is taken from a private copy of
+// the context's packed description with every threshold at -infinity, so a
+// weighted context returns its whole candidate set whatever search ran on it
+// before, and the context itself is not written.  Contexts built by the
+// unbiased transform of real X (whose keys come from a random binarisation
+// inside the survivor filter) are refused.
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -95,6 +108,17 @@ int ceil_log2_na(int64_t x)
     return b;
 }
 
+// Restores the caller's current device when the entry point returns.
+struct DeviceRestore {
+    int prev = -1;
+    DeviceRestore() { cudaGetDevice(&prev); }
+    ~DeviceRestore()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
 #define NA_CU(expr)                                                                      \
     do {                                                                                 \
         cudaError_t _e = (expr);                                                         \
@@ -118,7 +142,13 @@ extern "C" int xyz_run_candidates_noalloc(xyz_ctx *ctx, int32_t M, uint64_t seed
         return fail(XYZ_EINVAL, "M must be in [0, 64]");
     if (run < 0)
         return fail(XYZ_EINVAL, "run must be >= 0");
-    const Packed &pk = *ctx_packed(ctx);
+    // every candidate passes: thresholds at -infinity in a private copy
+    Packed pk = *ctx_packed(ctx);
+    pk.wkq = -INFINITY;
+    pk.rkq = -INFINITY;
+    if (pk.Xrs)
+        return fail(XYZ_EINVAL, "the allocation-free entry point does not take contexts of real X "
+                                "(xyz_create_unbiased); use xyz_run_candidates");
     if (pk.p > NA_P)
         return fail(XYZ_EINVAL, "p = " + std::to_string(pk.p) +
                                     " exceeds the allocation-free limit XYZ_NOALLOC_MAX_P = " +
@@ -128,6 +158,7 @@ extern "C" int xyz_run_candidates_noalloc(xyz_ctx *ctx, int32_t M, uint64_t seed
         (int64_t)(radix_temp_bytes(NA_REC) + scan_temp_bytes(NA_REC)) > DEDUP_BYTES)
         return fail(XYZ_EINVAL, "scratch layout too small for this library");
     const int dev = ctx_device(ctx);
+    DeviceRestore restore;
     NA_CU(cudaSetDevice(dev));
     unsigned char *base = nullptr;
     int rc = scratch_for(dev, &base);
