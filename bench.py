@@ -332,6 +332,10 @@ def gpu_arm(args):
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                        "p99": round(float(np.percentile(lat, 99)), 3), "n": len(lat)},
         "roofline": roofline,
+        "search_stats": {"attempts": [int(x["attempts"]) for x in stats],
+                         "filter_kept_per_run": round(sum(x["filter_kept"] for x in stats) / max(1, runs), 1),
+                         "candidates_per_run": round(cand / max(1, runs), 1),
+                         "spilled_per_search": round(surv / max(1, len(stats)), 1)},
         "gpu_launches": gpu_launches,
         "clocks": clocks,
     }

@@ -97,6 +97,8 @@ typedef struct xyz_stats {
     int64_t launches_verify;
     int64_t launches_dedup;
     int64_t survivors;        /* entries that reached the sort (all of them without the filter) */
+    int64_t filter_kept;      /* columns kept by the survivor filter, summed over runs (0 without it) */
+    int64_t attempts;         /* 1, plus one for every redo after a buffer grew */
 } xyz_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -92,6 +92,23 @@ __device__ __forceinline__ uint32_t bloom_has(const uint32_t *F, uint32_t h, int
     return (f >> (y >> 27)) & __funnelshift_r(f, f, y >> 22) & 1u;
 }
 
+// The same with three bits per key in the word (bits y >> 27, (y >> 22) mod
+// 32 and (y >> 17) mod 32): fewer false positives for a filter whose words
+// hold few keys each (the class-split filter's).
+__device__ __forceinline__ void bloom_pos3(uint32_t h, int shift, uint32_t &word, uint32_t &mask)
+{
+    word = (h * 0x9E3779B1u) >> shift;
+    const uint32_t y = h * 0x7FEB352Du + 0x165667B1u;
+    mask = (1u << (y >> 27)) | __funnelshift_l(1u, 1u, y >> 22) | __funnelshift_l(1u, 1u, y >> 17);
+}
+
+__device__ __forceinline__ uint32_t bloom_has3(const uint32_t *F, uint32_t h, int shift)
+{
+    const uint32_t f = F[(h * 0x9E3779B1u) >> shift];
+    const uint32_t y = h * 0x7FEB352Du + 0x165667B1u;
+    return (f >> (y >> 27)) & __funnelshift_r(f, f, y >> 22) & __funnelshift_r(f, f, y >> 17) & 1u;
+}
+
 // Canonical key of a surviving column (keys.cu): group h = min(kx, kx ^ c)
 // with bit tb = msb(c) removed, shifted left, side bit kx != h at the bottom.
 __device__ __forceinline__ uint32_t canon(uint32_t kx, uint32_t c, int tb, uint32_t lowmask)
@@ -245,13 +262,15 @@ __device__ __forceinline__ void group_on_chip(uint64_t *sv, uint32_t s, uint32_t
 // into sv and grouped one after the other (a group lies in one bin).
 // Returns false, with nothing grouped, when a bin is above SMAX, more than
 // part_max ranges are needed or the entries did not all fit the segment;
-// the run then stays in the segment for the general path.  Called by every
-// thread of the CTA.
+// the run then stays in the segment for the general path.  With xlat, the
+// segment values are places in the class lists (class << 27 | index) and the
+// column is xlat[class * xcap + index].  Called by every thread of the CTA.
 template <class Lay>
 __device__ __forceinline__ bool group_from_segment(const uint64_t *okeys, const uint32_t *ovals, uint32_t seg0,
                                                    uint32_t s, uint32_t seg_cap, int part_max, uint32_t kcmask,
                                                    uint64_t *sv, uint32_t *tkey, uint32_t *tcnt, bool nz, int b,
-                                                   const GroupOut &g)
+                                                   const GroupOut &g, const uint32_t *xlat = nullptr,
+                                                   uint32_t xcap = 0)
 {
     __shared__ uint32_t hist[32];       // entries per bin of the group-key hash
     __shared__ uint32_t pstart[33];     // partition q covers bins [pstart[q], pstart[q + 1])
@@ -263,9 +282,18 @@ __device__ __forceinline__ bool group_from_segment(const uint64_t *okeys, const 
     if (t < 32)
         hist[t] = 0;
     __syncthreads();
-    for (uint32_t i = t; i < s; i += T) {
-        const uint32_t Kc = (uint32_t)(okeys[seg0 + i] & kcmask);
-        atomicAdd(&hist[mix32(nz ? (Kc >> 1) : Kc) >> 27], 1u);
+    constexpr int GB = 4;               // segment entries per thread and step (loads in flight)
+    for (uint32_t i0 = t; i0 - t < s; i0 += GB * (uint32_t)T) {
+        uint32_t Kc[GB];
+#pragma unroll
+        for (int u = 0; u < GB; ++u) {
+            const uint32_t i = i0 + u * (uint32_t)T;
+            Kc[u] = i < s ? (uint32_t)(okeys[seg0 + i] & kcmask) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < GB; ++u)
+            if (i0 + u * (uint32_t)T < s)
+                atomicAdd(&hist[mix32(nz ? (Kc[u] >> 1) : Kc[u]) >> 27], 1u);
     }
     __syncthreads();
     if (t == 0) {
@@ -294,11 +322,31 @@ __device__ __forceinline__ bool group_from_segment(const uint64_t *okeys, const 
             scur = 0;
         __syncthreads();
         const uint32_t blo = pstart[part], bhi = pstart[part + 1];
-        for (uint32_t i = t; i < s; i += T) {
-            const uint32_t Kc = (uint32_t)(okeys[seg0 + i] & kcmask);
-            const uint32_t bn = mix32(nz ? (Kc >> 1) : Kc) >> 27;
-            if (bn >= blo && bn < bhi)
-                sv[atomicAdd(&scur, 1u)] = ((uint64_t)Kc << 32) | ovals[seg0 + i];
+        for (uint32_t i0 = t; i0 - t < s; i0 += GB * (uint32_t)T) {
+            uint32_t Kc[GB];
+#pragma unroll
+            for (int u = 0; u < GB; ++u) {
+                const uint32_t i = i0 + u * (uint32_t)T;
+                Kc[u] = i < s ? (uint32_t)(okeys[seg0 + i] & kcmask) : 0u;
+            }
+            bool in[GB];
+            uint32_t col[GB];
+#pragma unroll
+            for (int u = 0; u < GB; ++u) {
+                const uint32_t bn = mix32(nz ? (Kc[u] >> 1) : Kc[u]) >> 27;
+                in[u] = i0 + u * (uint32_t)T < s && bn >= blo && bn < bhi;
+                col[u] = in[u] ? ovals[seg0 + i0 + u * (uint32_t)T] : 0u;
+            }
+            if (xlat) {
+#pragma unroll
+                for (int u = 0; u < GB; ++u)
+                    if (in[u])
+                        col[u] = xlat[(int64_t)(col[u] >> 27) * xcap + (col[u] & 0x7FFFFFFu)];
+            }
+#pragma unroll
+            for (int u = 0; u < GB; ++u)
+                if (in[u])
+                    sv[atomicAdd(&scur, 1u)] = ((uint64_t)Kc[u] << 32) | col[u];
         }
         __syncthreads();
         group_on_chip<Lay>(sv, scur, tkey, tcnt, nz, b, g);
@@ -339,7 +387,8 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                   uint32_t *__restrict__ members_count, Bucket *__restrict__ buckets,
                   uint64_t *__restrict__ pair_counts, uint32_t *__restrict__ nbuckets,
                   const uint64_t *__restrict__ cdf, uint64_t wtot, const float *__restrict__ Xrs,
-                  int64_t Pf, int part_max, uint32_t *__restrict__ work)
+                  int64_t Pf, int part_max, uint32_t *__restrict__ work,
+                  unsigned long long *__restrict__ kept)
 {
     using SegKey = uint64_t;
     extern __shared__ __align__(16) uint32_t fl_smem[];
@@ -546,6 +595,8 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             __syncthreads();
             uint32_t s = ns;
             const uint32_t kcmask = (1u << M) - 1u;   // M <= 31 on this path
+            if (t == 0)
+                atomicAdd(kept, (unsigned long long)s);
 
             if (s > (uint32_t)FL_SMAX) {
                 // refinement: a fresh filter of the survivors' keys (in the
@@ -700,10 +751,14 @@ __device__ __forceinline__ uint32_t key_class(uint32_t k)
 //
 //   pass 1  build the keys (the transpose also carries the four class
 //           parities, formed from the sampled row words in rows 28-31) and
-//           append each to its class: each warp stages its keys per class
-//           in shared memory (the filter and survivor array are free until
-//           the rounds) and moves them to the CTA's class lists 16 at a
-//           time, so the lists are written in whole sectors;
+//           write each to its class list, a tile of T words (32 T columns)
+//           at a time, in two halves of 16 columns per word: each thread
+//           counts its columns per class (a popcount of the class mask of
+//           its word), one scan over the CTA's 16 x T counts gives every
+//           thread its staging position per class, the keys and columns
+//           are scattered into shared memory in class order, and each
+//           class's part of the half-tile is copied to the end of its class
+//           list with consecutive threads on consecutive entries;
 //   rounds  for each class q: a fresh filter F of the class-q keys, tested
 //           by the keys k of class q ^ class(c) -- exactly those with
 //           k ^ c in class q, so every key k ^ c is looked up in the filter
@@ -726,33 +781,49 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                       int *__restrict__ overflow, uint8_t *__restrict__ cnz, uint32_t *__restrict__ members,
                       uint32_t *__restrict__ members_count, Bucket *__restrict__ buckets,
                       uint64_t *__restrict__ pair_counts, uint32_t *__restrict__ nbuckets,
-                      const uint64_t *__restrict__ cdf, uint64_t wtot, int part_max, uint32_t *__restrict__ work)
+                      const uint64_t *__restrict__ cdf, uint64_t wtot, int part_max, uint32_t *__restrict__ work,
+                      unsigned long long *__restrict__ kept)
 {
     using Lay = FlLayout<false>;
-    constexpr int FB_WARPS = FL_THREADS / 32;
-    constexpr uint32_t FB_BUF = 48;                // staged entries per warp and class
-    constexpr uint32_t FB_NONE = 0xFFFFFFFFu;      // padding key (real keys have M <= 28 bits)
-    static_assert(2 * FB_WARPS * 16 * (int)FB_BUF <= Lay::OFF_KM, "staging fits the filter and survivor array");
-    static_assert(FB_WARPS * 16 <= FL_KWORDS, "staged counts fit the keep-mask region");
+    // pass 1 staging, in the memory of the filter and survivor array (dead
+    // until the rounds): one half-tile's entries (column << 32 | key, 16 T
+    // of them) in class order, and the per-thread class cursors, which hold
+    // the cursors of both half-tiles (low and high 16 bits).  Cursor (q, t)
+    // sits at q Tp + t + 4 (t / 32), with the class stride Tp >= T + T/8 a
+    // multiple of 32: the scan's 16-entry chunks and the scatter's cursor
+    // accesses are then free of bank conflicts.
+    constexpr int FB_STAGE = 16 * FL_THREADS;      // entries of a half-tile, 8 bytes each
+    constexpr int FB_CUR = 2 * FB_STAGE;
+    constexpr int FB_RB = 8;                       // list entries per thread and step in the rounds
+    constexpr int FB_EB = 8;                       // of which emitted together
+    constexpr int FB_EMIT = FL_FWORDS;            // rounds: per-warp buffers of passing entries
+    constexpr int FB_QSHIFT = 27;                  // list place = class << 27 | index (lcap < 2^27)
+    static_assert(FB_EMIT + (FL_THREADS / 32) * FB_EB * 32 * 2 <= Lay::WORDS, "emission buffers fit");
+    static_assert(FB_CUR + 16 * (FL_THREADS + FL_THREADS / 8) <= Lay::WORDS,
+                  "staging and cursors fit the shared memory");
+    static_assert(FB_STAGE < 65536, "a half-tile's positions fit 16 bits");
     extern __shared__ __align__(16) uint32_t fl_smem[];
     uint32_t *F = fl_smem;                                                   // [FL_FWORDS], in the rounds
     uint64_t *sv = reinterpret_cast<uint64_t *>(fl_smem + Lay::OFF_SV);      // [SMAX], after the rounds
     uint32_t *tkey = fl_smem + Lay::OFF_TAB;                                 // [Lay::T], after the rounds
     uint32_t *tcnt = fl_smem + Lay::OFF_TAB + Lay::T;
+    uint64_t *stg = reinterpret_cast<uint64_t *>(fl_smem);                   // [16 T] staged entries
+    uint32_t *cur = fl_smem + FB_CUR;                                        // [16][T + T/8] cursors
     const int t = threadIdx.x;
     const int lane = t & 31, wp = t >> 5;
-    const int T = (int)blockDim.x;
-    // pass 1 staging: per warp and class FB_BUF keys and columns, and counts
-    uint32_t *mk = fl_smem + wp * 16 * FB_BUF;
-    uint32_t *mc = fl_smem + FB_WARPS * 16 * FB_BUF + wp * 16 * FB_BUF;
-    uint32_t *mw = fl_smem + Lay::OFF_KM + wp * 16;
+    const int T = (int)blockDim.x;                 // a multiple of 32, at most FL_THREADS
+    const int nwarps = T >> 5;
+    const int Tp = (T + T / 8 + 31) / 32 * 32;     // class stride of the cursors (a multiple of 32 words)
+    const int tt = t + 4 * wp;                     // padded place of thread t in a class
     __shared__ int64_t rowoff[32];
     __shared__ uint32_t c_sh, cursor, seg0_sh;
     __shared__ uint32_t cls_n[16];                 // fill of each class list
+    __shared__ uint32_t cbase[17];                 // staging start of each class, both halves; [16]: totals
+    __shared__ int64_t dstoff[16];                 // list index of staged entry i of class q: dstoff[q] + i
+    __shared__ uint32_t wsum[FL_THREADS / 32];
     __shared__ int item_sh, lovf_sh;
     const GroupOut gout{members, members_count, buckets, pair_counts, nbuckets, mcap, bcap, overflow};
     const uint32_t P32 = (uint32_t)P, p32 = (uint32_t)p;
-    const uint32_t steps = (P32 + T - 1) / T;
     const int fshift = 32 - (FL_LOGF - 5);
     const uint32_t kcmask = (1u << M) - 1u;                                  // M <= 28
     uint32_t *lk = lst_keys + (int64_t)blockIdx.x * 16 * lcap;               // [16][lcap]
@@ -761,37 +832,6 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     uint32_t *ovals = seg_vals + (int64_t)blockIdx.x * seg_cap;
     if (t == 0)
         cursor = seg_count[blockIdx.x];     // segments fill across launch groups
-
-    // the first 16 staged entries of class q (cntq staged) to the class list;
-    // the rest move down.  Executed by the whole warp.
-    auto flush16 = [&](uint32_t q, uint32_t cntq) {
-        uint32_t pos = 0;
-        if (lane == 0)
-            pos = atomicAdd(&cls_n[q], 16u);
-        pos = __shfl_sync(FULL, pos, 0);
-        if (pos + 16 <= lcap) {
-            if (lane < 16) {
-                lk[(int64_t)q * lcap + pos + lane] = mk[q * FB_BUF + lane];
-                lc[(int64_t)q * lcap + pos + lane] = mc[q * FB_BUF + lane];
-            }
-        } else if (lane == 0) {
-            lovf_sh = 1;
-        }
-        const uint32_t rest = cntq - 16;         // <= 32
-        uint32_t ek = 0, ec = 0;
-        if ((uint32_t)lane < rest) {
-            ek = mk[q * FB_BUF + 16 + lane];
-            ec = mc[q * FB_BUF + 16 + lane];
-        }
-        __syncwarp();
-        if ((uint32_t)lane < rest) {
-            mk[q * FB_BUF + lane] = ek;
-            mc[q * FB_BUF + lane] = ec;
-        }
-        if (lane == 0)
-            mw[q] = rest;
-        __syncwarp();
-    };
 
     for (;;) {
         if (t == 0)
@@ -815,22 +855,21 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 seg0_sh = cursor;
             }
         }
-        if (lane < 16)
-            mw[lane] = 0;
         if (t < 16)
             cls_n[t] = 0;
         __syncthreads();
         const uint32_t c = c_sh;
         const bool nz = c != 0;
 
-        // pass 1: keys with their classes, staged per warp and class
-        for (uint32_t st = 0; st < steps; ++st) {
-            const uint32_t w = st * T + t;
-            const bool wv = w < P32;
-            uint32_t A[32];
+        // pass 1: keys with their classes, sorted into the class lists one
+        // tile of T words at a time.  The sampled row words of the next
+        // tile are loaded while the current tile's last half is copied out.
+        uint32_t A[32];
 #pragma unroll
-            for (int m = 0; m < 32; ++m)
-                A[m] = (wv && m < MB && m < M) ? __ldg(Xr + rowoff[m] + w) : 0u;
+        for (int m = 0; m < 32; ++m)
+            A[m] = (t < (int)P32 && m < MB && m < M) ? __ldg(Xr + rowoff[m] + t) : 0u;
+        for (uint32_t tile0 = 0; tile0 < P32; tile0 += (uint32_t)T) {
+            const uint32_t w = tile0 + t;
             uint32_t Q[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int m = 0; m < MB && m < 28; ++m)
@@ -839,43 +878,128 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             for (int b = 0; b < 4; ++b)
                 A[28 + b] = Q[b];
             transpose32(A);
-            const uint32_t ncol = !wv ? 0u : (32 * w + 32 <= p32) ? 32u : p32 - 32 * w;
+            const uint32_t ncol = w >= P32 ? 0u : (32 * w + 32 <= p32) ? 32u : p32 - 32 * w;
+            const uint32_t vm = ncol == 32 ? FULL : ((1u << ncol) - 1u);
+            {
+                // class masks of the word: bit cc of lo[q & 3] & hi[q >> 2]
+                // is set when column cc is of class q (bits 0-1 of q from
+                // Q[0..1], bits 2-3 from Q[2..3]); counts of both halves,
+                // the second in the high 16 bits
+                const uint32_t lo[4] = {~Q[0] & ~Q[1] & vm, Q[0] & ~Q[1] & vm, ~Q[0] & Q[1] & vm, Q[0] & Q[1] & vm};
+                const uint32_t hi[4] = {~Q[2] & ~Q[3], Q[2] & ~Q[3], ~Q[2] & Q[3], Q[2] & Q[3]};
 #pragma unroll
-            for (int cc = 0; cc < 32; ++cc) {
-                // room for this step's appends: no class above 16 staged
-                for (;;) {
-                    uint32_t full = __ballot_sync(FULL, lane < 16 && mw[lane] > 16);
-                    if (!full)
-                        break;
-                    while (full) {
-                        const uint32_t q = __ffs(full) - 1;
-                        full &= full - 1;
-                        flush16(q, mw[q]);
+                for (int q = 0; q < 16; ++q) {
+                    const uint32_t mq = lo[q & 3] & hi[q >> 2];
+                    cur[q * Tp + tt] = __popc(mq & 0xFFFFu) | ((uint32_t)__popc(mq >> 16) << 16);
+                }
+            }
+            __syncthreads();
+            // exclusive scan of the counts in class-major order: thread t
+            // takes the chunk of the 16 consecutive counts 16t..16t+15 (one
+            // class, since 16 divides T); both halves at once, since no
+            // half's sum reaches 2^16
+            const int cq0 = (16 * t) / T, ct0 = 16 * t - cq0 * T;     // chunk: class cq0, threads ct0..ct0+15
+            uint4 *chunk = reinterpret_cast<uint4 *>(cur + cq0 * Tp + ct0 + 4 * (ct0 >> 5));
+            uint32_t csum = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint4 x = chunk[i];
+                csum += x.x + x.y + x.z + x.w;
+            }
+            uint32_t incl = csum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            if (lane == 31)
+                wsum[wp] = incl;
+            __syncthreads();
+            if (wp == 0) {
+                const uint32_t x = lane < nwarps ? wsum[lane] : 0u;
+                uint32_t wi = x;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(FULL, wi, o);
+                    if (lane >= o)
+                        wi += y;
+                }
+                if (lane < nwarps)
+                    wsum[lane] = wi - x;     // exclusive over warps
+                if (lane == 31)
+                    cbase[16] = wi;          // entries of each half
+            }
+            __syncthreads();
+            {
+                const uint32_t off = wsum[wp] + incl - csum;
+                if (ct0 == 0)
+                    cbase[cq0] = off;             // the chunk starts its class
+                uint32_t run = off;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    uint4 x = chunk[i];
+                    const uint32_t a = run, b = a + x.x, c2 = b + x.y, d = c2 + x.z;
+                    run = d + x.w;
+                    chunk[i] = make_uint4(a, b, c2, d);
+                }
+            }
+            __syncthreads();
+            const uint32_t col0 = 32 * w;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                // scatter this half in class order (cursor field h)
+                const uint32_t hm = vm & (h ? 0xFFFF0000u : 0x0000FFFFu);
+                const uint32_t inc = h ? 0x10000u : 1u;
+                const bool full = hm == (h ? 0xFFFF0000u : 0x0000FFFFu);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int cc = 16 * h + i;
+                    if (full || ((hm >> cc) & 1u)) {
+                        uint32_t *cq = cur + (A[cc] >> 28) * Tp + tt;
+                        const uint32_t cv = *cq;
+                        *cq = cv + inc;
+                        stg[h ? (cv >> 16) : (cv & 0xFFFFu)] = ((uint64_t)(col0 + cc) << 32) | (A[cc] & kcmask);
                     }
                 }
-                if ((uint32_t)cc < ncol) {
-                    const uint32_t q = A[cc] >> 28;
-                    const uint32_t slot = atomicAdd(&mw[q], 1u);     // < FB_BUF
-                    mk[q * FB_BUF + slot] = A[cc] & kcmask;
-                    mc[q * FB_BUF + slot] = 32 * w + cc;
+                if (t < 16) {
+                    // list space for each class part of this half
+                    const uint32_t b0 = h ? (cbase[t] >> 16) : (cbase[t] & 0xFFFFu);
+                    const uint32_t b1 = h ? (cbase[t + 1] >> 16) : (cbase[t + 1] & 0xFFFFu);
+                    const uint32_t g = cls_n[t];
+                    dstoff[t] = (int64_t)t * lcap + g - b0;
+                    if ((uint64_t)g + (b1 - b0) > lcap)
+                        lovf_sh = 1;
+                    else
+                        cls_n[t] = g + (b1 - b0);
                 }
-                __syncwarp();
-            }
-        }
-        // what is still staged, the last entries of a class padded to 16
-        for (uint32_t q = 0; q < 16; ++q) {
-            uint32_t left = mw[q];
-            while (left >= 16) {
-                flush16(q, left);
-                left = mw[q];
-            }
-            if (left > 0) {
-                if ((uint32_t)lane >= left && lane < 16) {
-                    mk[q * FB_BUF + lane] = FB_NONE;
-                    mc[q * FB_BUF + lane] = 0;
+                if (h == 1) {
+                    // the sampled row words of the next tile, in flight
+                    // during the copy-out
+                    const uint32_t wn = w + (uint32_t)T;
+#pragma unroll
+                    for (int m = 0; m < 32; ++m)
+                        A[m] = (wn < P32 && m < MB && m < M) ? __ldg(Xr + rowoff[m] + wn) : 0u;
                 }
-                __syncwarp();
-                flush16(q, 16);
+                __syncthreads();
+                if (!lovf_sh) {
+                    // to the class lists, consecutive threads on consecutive
+                    // entries; a thread's entries are in increasing class
+                    const uint32_t tot = h ? (cbase[16] >> 16) : (cbase[16] & 0xFFFFu);
+                    uint32_t q = 0;
+                    uint32_t nxt = h ? (cbase[1] >> 16) : (cbase[1] & 0xFFFFu);
+                    for (uint32_t i = t; i < tot; i += (uint32_t)T) {
+                        while (i >= nxt) {           // q <= 15: i < the total
+                            ++q;
+                            nxt = h ? (cbase[q + 1] >> 16) : (cbase[q + 1] & 0xFFFFu);
+                        }
+                        const uint64_t e = stg[i];
+                        const int64_t g = dstoff[q] + i;
+                        lk[g] = (uint32_t)e;
+                        lc[g] = (uint32_t)(e >> 32);
+                    }
+                }
+                __syncthreads();                 // the staging is reused by the next half
             }
         }
         __syncthreads();
@@ -889,30 +1013,65 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         const uint64_t runbits = rl << M;
 
         // entries of class q2 that pass (all of them when c == 0) to the
-        // segment, warp-aggregated; the whole CTA walks the class list
+        // segment; the whole CTA walks the class list, each thread FB_RB
+        // entries at a time (independent loads in flight).  A warp gathers
+        // its passing entries (key, list index) in its shared buffer and
+        // writes them to the segment with consecutive lanes, after one
+        // reservation.  The segment value is the entry's place in the class
+        // lists, q2 << FB_QSHIFT | index; the grouping looks the column up
+        // (and a run left in the segment has its columns looked up in place),
+        // so no warp waits on that load here.
+        uint64_t *wbuf = reinterpret_cast<uint64_t *>(fl_smem + FB_EMIT) + wp * (FB_EB * 32);
         auto emit_class = [&](uint32_t q2, bool test) {
             const uint32_t n2 = cls_n[q2] < lcap ? cls_n[q2] : lcap;
-            for (uint32_t i0 = 0; i0 < n2; i0 += T) {
-                const uint32_t i = i0 + t;
-                bool pass = false;
-                uint32_t k = 0;
-                if (i < n2) {
-                    k = lk[(int64_t)q2 * lcap + i];
-                    pass = k != FB_NONE && (!test || bloom_has(F, k ^ c, fshift));
+            const uint32_t *lkq = lk + (int64_t)q2 * lcap;
+            for (uint32_t i0 = t; i0 - t < n2; i0 += FB_RB * (uint32_t)T) {
+                uint32_t k[FB_RB];
+#pragma unroll
+                for (int u = 0; u < FB_RB; ++u) {
+                    const uint32_t i = i0 + u * (uint32_t)T;
+                    k[u] = i < n2 ? lkq[i] : 0u;
                 }
-                const uint32_t bal = __ballot_sync(FULL, pass);
-                if (bal == 0)
-                    continue;
-                uint32_t base = 0;
-                if (lane == 0)
-                    base = atomicAdd(&cursor, (uint32_t)__popc(bal));
-                base = __shfl_sync(FULL, base, 0);
-                if (pass) {
-                    const uint32_t o = base + __popc(bal & ((1u << lane) - 1u));
-                    if (o < seg_cap) {
-                        okeys[o] = runbits | canon(k, c, tb, lowmask);
-                        ovals[o] = lc[(int64_t)q2 * lcap + i];
+                uint32_t pm = 0;           // bit u: entry i0 + u T passes
+#pragma unroll
+                for (int u = 0; u < FB_RB; ++u) {
+                    const uint32_t i = i0 + u * (uint32_t)T;
+                    if (i < n2 && (!test || bloom_has3(F, k[u] ^ c, fshift)))
+                        pm |= 1u << u;
+                }
+#pragma unroll
+                for (int e0 = 0; e0 < FB_RB; e0 += FB_EB) {
+                    const uint32_t pe = (pm >> e0) & ((1u << FB_EB) - 1u);
+                    const uint32_t cnt = __popc(pe);
+                    uint32_t incl = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= o)
+                            incl += y;
                     }
+                    const uint32_t wt = __shfl_sync(FULL, incl, 31);
+                    if (wt == 0)
+                        continue;
+                    uint32_t o = incl - cnt;
+#pragma unroll
+                    for (int u = 0; u < FB_EB; ++u)
+                        if ((pe >> u) & 1u)
+                            wbuf[o++] = ((uint64_t)(i0 + (e0 + u) * (uint32_t)T) << 32) | k[e0 + u];
+                    uint32_t base = 0;
+                    if (lane == 0)
+                        base = atomicAdd(&cursor, wt);
+                    base = __shfl_sync(FULL, base, 0);
+                    __syncwarp();
+                    for (uint32_t e = lane; e < wt; e += 32) {
+                        const uint64_t v = wbuf[e];
+                        const uint32_t at = base + e;
+                        if (at < seg_cap) {
+                            okeys[at] = runbits | canon((uint32_t)v, c, tb, lowmask);
+                            ovals[at] = (q2 << FB_QSHIFT) | (uint32_t)(v >> 32);   // column looked up later
+                        }
+                    }
+                    __syncwarp();
                 }
             }
         };
@@ -923,16 +1082,25 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         } else {
             const uint32_t cq = key_class(c);
             for (uint32_t q = 0; q < 16; ++q) {
-                for (int i = t; i < FL_FWORDS; i += T)
-                    F[i] = 0;
+                for (int i = t; i < FL_FWORDS / 4; i += T)
+                    reinterpret_cast<uint4 *>(F)[i] = make_uint4(0u, 0u, 0u, 0u);
                 __syncthreads();
                 const uint32_t nq = cls_n[q] < lcap ? cls_n[q] : lcap;
-                for (uint32_t i = t; i < nq; i += T) {
-                    const uint32_t k = lk[(int64_t)q * lcap + i];
-                    if (k != FB_NONE) {
-                        uint32_t word, mask;
-                        bloom_pos(k, fshift, word, mask);
-                        atomicOr(F + word, mask);
+                const uint32_t *lkq = lk + (int64_t)q * lcap;
+                for (uint32_t i0 = t; i0 - t < nq; i0 += FB_RB * (uint32_t)T) {
+                    uint32_t k[FB_RB];
+#pragma unroll
+                    for (int u = 0; u < FB_RB; ++u) {
+                        const uint32_t i = i0 + u * (uint32_t)T;
+                        k[u] = i < nq ? lkq[i] : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < FB_RB; ++u) {
+                        if (i0 + u * (uint32_t)T < nq) {
+                            uint32_t word, mask;
+                            bloom_pos3(k[u], fshift, word, mask);
+                            atomicOr(F + word, mask);
+                        }
                     }
                 }
                 __syncthreads();
@@ -942,11 +1110,33 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         }
         __syncthreads();
         const uint32_t seg0 = seg0_sh, s = cursor - seg0;
+        if (t == 0)
+            atomicAdd(kept, (unsigned long long)s);
         __syncthreads();                     // every thread has read the cursor
         if (group_from_segment<Lay>(okeys, ovals, seg0, s, seg_cap, part_max, kcmask, sv, tkey, tcnt, nz, 0,
-                                    gout) &&
-            t == 0)
-            cursor = seg0;                   // grouped on chip: the entries leave the segment
+                                    gout, lc, lcap)) {
+            if (t == 0)
+                cursor = seg0;               // grouped on chip: the entries leave the segment
+        } else {
+            // left for the general path: the columns in place of the list places
+            const uint32_t sn = seg0 >= seg_cap ? 0u : (s < seg_cap - seg0 ? s : seg_cap - seg0);
+            for (uint32_t i0 = t; i0 - t < sn; i0 += 4 * (uint32_t)T) {
+                uint32_t v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t i = i0 + u * (uint32_t)T;
+                    v[u] = i < sn ? ovals[seg0 + i] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u * (uint32_t)T < sn)
+                        v[u] = lc[(int64_t)(v[u] >> FB_QSHIFT) * lcap + (v[u] & ((1u << FB_QSHIFT) - 1u))];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u * (uint32_t)T < sn)
+                        ovals[seg0 + i0 + u * (uint32_t)T] = v[u];
+            }
+        }
     }
     if (t == 0) {
         seg_count[blockIdx.x] = cursor < seg_cap ? cursor : seg_cap;
@@ -1035,7 +1225,7 @@ bool filter_big_supported(int64_t p, int M) { return M >= 1 && M <= 28 && p >= 2
 uint32_t filter_big_lcap(int64_t p)
 {
     // a class list holds p / 16 keys on average: room for 1.5 times that,
-    // plus the padding of every warp's last flush (< 16 per warp)
+    // plus some slack for small p; list places must stay below 2^27
     const int64_t l = (3 * p + 31) / 32 + 16 * (FL_THREADS / 32);
     return (uint32_t)((l + 15) / 16 * 16);
 }
@@ -1069,7 +1259,7 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
                           uint32_t *seg_vals, uint32_t *seg_count, uint32_t seg_cap, int *overflow,
                           uint8_t *cnz, uint32_t *members, uint32_t *members_count, Bucket *buckets,
                           uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
-                          int64_t *launches, int part_max, uint32_t *work)
+                          int64_t *launches, int part_max, uint32_t *work, unsigned long long *kept)
 {
     const bool batch = B > 1;
     const size_t smem = filter_smem_bytes(batch);
@@ -1077,7 +1267,7 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
                            int64_t, int, uint64_t, int64_t, int, int, int, int, int64_t, uint32_t, uint32_t,
                            uint32_t *, void *, uint32_t *, uint32_t *, uint32_t, int *, uint8_t *,
                            uint32_t *, uint32_t *, Bucket *, uint64_t *, uint32_t *, const uint64_t *,
-                           uint64_t, const float *, int64_t, int, uint32_t *);
+                           uint64_t, const float *, int64_t, int, uint32_t *, unsigned long long *);
     KernT kern;
     if (batch)
         kern = M <= 8 ? filter_kernel<8, true> : M <= 16 ? filter_kernel<16, true>
@@ -1094,7 +1284,7 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
                                         NB, BB, rbits, rbase, mcap, bcap, kc_scratch, seg_keys, seg_vals,
                                         seg_count, seg_cap, overflow, cnz, members, members_count,
                                         buckets, pair_counts, nbuckets, pk.cdf, pk.wtotal, pk.Xrs, pk.Pf,
-                                        part_max, work);
+                                        part_max, work, kept);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -1104,13 +1294,15 @@ cudaError_t launch_filter_big(const Packed &pk, int M, uint64_t seed, int64_t l0
                               uint32_t lcap, uint64_t *seg_keys, uint32_t *seg_vals, uint32_t *seg_count,
                               uint32_t seg_cap, int *overflow, uint8_t *cnz, uint32_t *members,
                               uint32_t *members_count, Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
-                              cudaStream_t s, int64_t *launches, int part_max, uint32_t *work)
+                              cudaStream_t s, int64_t *launches, int part_max, uint32_t *work,
+                              unsigned long long *kept)
 {
     const size_t smem = filter_smem_bytes(false);
     using KernT = void (*)(const uint32_t *, int64_t, int64_t, const uint32_t *, int64_t, int64_t, int, uint64_t,
                            int64_t, int, int, int64_t, uint32_t, uint32_t, uint32_t *, uint32_t *, uint32_t, void *,
                            uint32_t *, uint32_t *, uint32_t, int *, uint8_t *, uint32_t *, uint32_t *, Bucket *,
-                           uint64_t *, uint32_t *, const uint64_t *, uint64_t, int, uint32_t *);
+                           uint64_t *, uint32_t *, const uint64_t *, uint64_t, int, uint32_t *,
+                           unsigned long long *);
     const KernT kern = M <= 8 ? filter_big_kernel<8> : M <= 16 ? filter_big_kernel<16>
                        : M <= 24 ? filter_big_kernel<24> : filter_big_kernel<32>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1119,7 +1311,7 @@ cudaError_t launch_filter_big(const Packed &pk, int M, uint64_t seed, int64_t l0
     kern<<<grid, filter_threads(pk.P), smem, s>>>(pk.Xr, pk.Pp, pk.P, pk.yb, pk.n, pk.p, M, seed, l0, R, rbits, rbase,
                                                   mcap, bcap, lst_keys, lst_cols, lcap, seg_keys, seg_vals, seg_count,
                                                   seg_cap, overflow, cnz, members, members_count, buckets,
-                                                  pair_counts, nbuckets, pk.cdf, pk.wtotal, part_max, work);
+                                                  pair_counts, nbuckets, pk.cdf, pk.wtotal, part_max, work, kept);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -401,7 +401,7 @@ int ensure_search_ws(xyz_ctx *c, const Plan &pl, int B, int64_t runs)
             (rc = ensure(c->scan_tmp, scan_temp_bytes(mb))) ||
             (rc = ensure(c->buckets2, sb * sizeof(Bucket))) || (rc = ensure(c->pair_counts2, sb * 8)) ||
             (rc = ensure(c->pair_off2, sb * 8)) || (rc = ensure(c->scan_tmp2, scan_temp_bytes(sb))) ||
-            (rc = ensure(c->counters, 64)))
+            (rc = ensure(c->counters, 128)))
             return rc;
         return XYZ_OK;
     }
@@ -410,7 +410,7 @@ int ensure_search_ws(xyz_ctx *c, const Plan &pl, int B, int64_t runs)
             (rc = ensure(c->seg, part_seg_words(c->pk.p, (int)pl.R) * 4)) ||
             (rc = ensure(c->cnz, pl.R)) || (rc = ensure(c->buckets, bcap * sizeof(Bucket))) ||
             (rc = ensure(c->pair_counts, bcap * 8)) || (rc = ensure(c->pair_off, bcap * 8)) ||
-            (rc = ensure(c->scan_tmp, scan_temp_bytes(bcap))) || (rc = ensure(c->counters, 64)))
+            (rc = ensure(c->scan_tmp, scan_temp_bytes(bcap))) || (rc = ensure(c->counters, 128)))
             return rc;
         return XYZ_OK;
     }
@@ -419,7 +419,7 @@ int ensure_search_ws(xyz_ctx *c, const Plan &pl, int B, int64_t runs)
         (rc = ensure(c->radix_tmp, radix_temp_bytes(N))) || (rc = ensure(c->cnz, pl.R)) ||
         (rc = ensure(c->buckets, bcap * sizeof(Bucket))) ||
         (rc = ensure(c->pair_counts, bcap * 8)) || (rc = ensure(c->pair_off, bcap * 8)) ||
-        (rc = ensure(c->scan_tmp, scan_temp_bytes(bcap))) || (rc = ensure(c->counters, 64)))
+        (rc = ensure(c->scan_tmp, scan_temp_bytes(bcap))) || (rc = ensure(c->counters, 128)))
         return rc;
     return XYZ_OK;
 }
@@ -445,8 +445,8 @@ int ensure_records(xyz_ctx *c, int B)
 // Device counters: per launch group (cleared before each group) the bucket
 // and member counts; per search the spill count and overflow flags, the
 // spill-path bucket count, the record and output counts, the error flag,
-// the group's candidate total, the candidate sum, the spill total and the
-// filter's work-item counter.
+// the group's candidate total, the candidate sum, the spill total, the
+// filter's work-item counter and the columns the filter kept.
 uint32_t *ctr_u32(xyz_ctx *c) { return reinterpret_cast<uint32_t *>(c->counters.ptr); }
 uint32_t *ctr_nbuckets(xyz_ctx *c) { return ctr_u32(c) + 0; }
 uint32_t *ctr_members(xyz_ctx *c) { return ctr_u32(c) + 1; }
@@ -460,6 +460,10 @@ uint64_t *ctr_total(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c-
 uint64_t *ctr_cand(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 40); }
 uint64_t *ctr_total2(xyz_ctx *c) { return reinterpret_cast<uint64_t *>((char *)c->counters.ptr + 48); }
 uint32_t *ctr_work(xyz_ctx *c) { return reinterpret_cast<uint32_t *>((char *)c->counters.ptr + 56); }
+unsigned long long *ctr_kept(xyz_ctx *c)
+{
+    return reinterpret_cast<unsigned long long *>((char *)c->counters.ptr + 64);
+}
 
 #define CU(expr)                                                                         \
     do {                                                                                 \
@@ -510,7 +514,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
         xyz_stats st;
         std::memset(&st, 0, sizeof(st));
         if (phase != SP_FINISH)
-            CU(cudaMemsetAsync(c->counters.ptr, 0, 64, c->stream));
+            CU(cudaMemsetAsync(c->counters.ptr, 0, 128, c->stream));
         int64_t chunks = phase == SP_FINISH ? (runs + pl.R - 1) / pl.R : 0;
         int64_t surv_total = 0;
         int key_bits_max = 0;
@@ -615,7 +619,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                          (uint32_t *)c->seg_count.ptr, (uint32_t)c->seg_cap, ctr_sovf(c),
                                          (uint8_t *)c->cnz.ptr, (uint32_t *)c->members.ptr, ctr_members(c),
                                          (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
-                                         ctr_nbuckets(c), c->stream, &launches, c->onchip_parts, ctr_work(c)));
+                                         ctr_nbuckets(c), c->stream, &launches, c->onchip_parts, ctr_work(c),
+                                         ctr_kept(c)));
                 else
                     CU(launch_filter(c->pk, ybs, B, M, seed, g0, (int)Rc, pl.NB, pl.BB, rbits, g0 - l0,
                                      grid, (uint32_t)(c->mem_cap < 0xFFFFFFFELL ? c->mem_cap : 0xFFFFFFFELL),
@@ -624,7 +629,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                      (uint32_t *)c->seg_count.ptr, (uint32_t)c->seg_cap, ctr_sovf(c),
                                      (uint8_t *)c->cnz.ptr, (uint32_t *)c->members.ptr, ctr_members(c),
                                      (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
-                                     ctr_nbuckets(c), c->stream, &launches, c->onchip_parts, ctr_work(c)));
+                                     ctr_nbuckets(c), c->stream, &launches, c->onchip_parts, ctr_work(c),
+                                         ctr_kept(c)));
                 tm.end();
                 tm.begin(ST_JOIN);
                 CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
@@ -791,10 +797,14 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
             CU(launch_weighted_strengths(c->pk, (PairOut *)c->out.ptr, ctr_nout(c), (int64_t)nrec, c->stream,
                                          &launches));
         uint32_t nout = 0;
+        unsigned long long kept = 0;
         CU(cudaMemcpyAsync(&nout, ctr_nout(c), 4, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(&kept, ctr_kept(c), 8, cudaMemcpyDeviceToHost, c->stream));
         CU(cudaStreamSynchronize(c->stream));
         if (nrec == 0)
             nout = 0;
+        st.attempts = attempt + 1;
+        st.filter_kept = pl.filter ? (int64_t)kept : 0;
         st.runs = runs;
         st.chunks = chunks;
         st.runs_per_chunk = pl.R;
@@ -1328,10 +1338,10 @@ int xyz_brute_force(xyz_ctx *ctx, double kappa, xyz_pair **pairs, int64_t *npair
         return XYZ_OK;
     const int kbits = ceil_log2(c->pk.p) < 1 ? 1 : ceil_log2(c->pk.p);
     for (int attempt = 0; attempt < 8; ++attempt) {
-        if ((rc = ensure_records(c, 1)) || (rc = ensure(c->counters, 64)))
+        if ((rc = ensure_records(c, 1)) || (rc = ensure(c->counters, 128)))
             return rc;
         int64_t launches = 0;
-        CU(cudaMemsetAsync(c->counters.ptr, 0, 64, c->stream));
+        CU(cudaMemsetAsync(c->counters.ptr, 0, 128, c->stream));
         CU(launch_brute(c->pk, amin, kbits, (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
                         ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches));
         uint32_t nrec = 0;

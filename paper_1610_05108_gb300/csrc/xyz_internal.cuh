@@ -179,7 +179,8 @@ cudaError_t launch_filter_big(const Packed &pk, int M, uint64_t seed, int64_t l0
                               uint32_t lcap, uint64_t *seg_keys, uint32_t *seg_vals, uint32_t *seg_count,
                               uint32_t seg_cap, int *overflow, uint8_t *cnz, uint32_t *members,
                               uint32_t *members_count, Bucket *buckets, uint64_t *pair_counts, uint32_t *nbuckets,
-                              cudaStream_t s, int64_t *launches, int part_max, uint32_t *work);
+                              cudaStream_t s, int64_t *launches, int part_max, uint32_t *work,
+                              unsigned long long *kept);
 int filter_grid();
 size_t filter_scratch_words(int64_t p);
 int64_t filter_run_cap();
@@ -199,7 +200,7 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
                           uint32_t *seg_vals, uint32_t *seg_count, uint32_t seg_cap, int *overflow,
                           uint8_t *cnz, uint32_t *members, uint32_t *members_count, Bucket *buckets,
                           uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
-                          int64_t *launches, int part_max, uint32_t *work);
+                          int64_t *launches, int part_max, uint32_t *work, unsigned long long *kept);
 cudaError_t launch_seg_reset(uint32_t *seg_count, cudaStream_t s, int64_t *launches);
 cudaError_t launch_compact(const uint64_t *seg_keys, const uint32_t *seg_vals,
                            const uint32_t *seg_count, uint32_t seg_cap, int nseg, uint64_t *out_keys,

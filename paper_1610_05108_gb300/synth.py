@@ -96,27 +96,49 @@ def _ndtri(f: np.ndarray) -> np.ndarray:
 
 
 def gwas_X(n: int, p: int, rng: np.random.Generator, block: int = 20, rho: float = 0.6,
-           fmin: float = 0.05, fmax: float = 0.5, chunk_cols: int = 20000):
-    """SNP-shaped +-1 matrix (latent AR(1) in blocks, minor frequency f_j)."""
+           fmin: float = 0.05, fmax: float = 0.5, chunk_cols: int = 10000, workers: int = 0):
+    """SNP-shaped +-1 matrix (latent AR(1) in blocks, minor frequency f_j).
+
+    Columns are made in chunks of whole blocks; chunk i draws its normals
+    from its own generator, seeded by the i-th of a list of seeds drawn from
+    ``rng``, so the chunks are made by ``workers`` threads (0: one per core)
+    and the result depends only on ``rng``."""
+    import concurrent.futures as cf
+    import os
+
     f = rng.uniform(fmin, fmax, size=p)
     thr = _ndtri(f).astype(np.float32)
     X = np.empty((n, p), dtype=np.int8, order="F")
     s = np.float32(math.sqrt(1.0 - rho * rho))
     rho32 = np.float32(rho)
     chunk_cols = max(block, (chunk_cols // block) * block)
-    for c0 in range(0, p, chunk_cols):
+    starts = list(range(0, p, chunk_cols))
+    seeds = rng.integers(0, 2**63 - 1, size=len(starts), dtype=np.int64)
+
+    def one(i):
+        c0 = starts[i]
         c1 = min(p, c0 + chunk_cols)
-        e = rng.standard_normal(size=(c1 - c0, n), dtype=np.float32)  # column-major rows
+        g = np.random.Generator(np.random.PCG64(int(seeds[i])))
+        e = g.standard_normal(size=(c1 - c0, n), dtype=np.float32)  # column-major rows
         # the chain restarts at every block start (c0 is one); step all blocks
         # of the chunk together, one position within the block at a time
         nb = -(-(c1 - c0) // block)
         u = np.zeros((nb * block, n), dtype=np.float32)
         u[: c1 - c0] = e
+        del e
         u = u.reshape(nb, block, n)
         for t in range(1, block):
             u[:, t] = rho32 * u[:, t - 1] + s * u[:, t]
         u = u.reshape(nb * block, n)[: c1 - c0]
         X[:, c0:c1] = np.where(u < thr[c0:c1, None], np.int8(-1), np.int8(1)).T
+
+    nw = workers or min(16, os.cpu_count() or 1)
+    if nw <= 1 or len(starts) == 1:
+        for i in range(len(starts)):
+            one(i)
+    else:
+        with cf.ThreadPoolExecutor(max_workers=nw) as ex:
+            list(ex.map(one, range(len(starts))))
     return X, f
 
 
