@@ -1,42 +1,47 @@
 #!/usr/bin/env python3
 """Benchmark: interaction pairs screened per second at >= 95% planted recall.
 
-Workload (default): the SNP-shaped binary problem n = 2000, p = 100000 with
-5 planted pairs (realised strengths ~0.17..0.50) and 10 main effects; kappa =
-0.3, so the planted pairs with strength >= 0.3 are the targets.  M is the
-plug-in minimiser of eq. bestM (gamma = (1 + kappa)/2, sum of gamma_jk^M
-estimated from 10^6 pairs sampled on the GPU) and L is the least number of
+Workload (default, ``gwas_large``): the SNP-shaped binary problem n = 4000,
+p = 1,000,000 (about 5e11 pairs) with 10 planted pairs of target strength
+U[0.15, 0.5] (realised after the generator's feasibility scaling: 0.12 ..
+0.37) and 10 main effects.  kappa = 0.28, so the 4 planted pairs with
+strength >= 0.28 are the targets; M = 23 from the gamma0 = 0.55 rule of
+Section 5.2 (M = round(log p / log(1/0.55))), and L is the least number of
 runs that finds the weakest target with probability >= 0.95 (eq. L_choice).
-One step is one complete search (all L runs: keys, grouping, verification,
-union) with its own seed; "pairs screened" is p(p-1)/2 per search.
+One step is one complete search (all L runs: keys, survivor filter,
+grouping, verification, union) with its own seed; "pairs screened" is
+p(p-1)/2 per search.  The recall gate reports, per target, how often the
+timed searches found it against its own eta(M, L).
 
 Timing: inputs are resident in HBM before the timed region; each step is
 bracketed by CUDA events on the library's stream, and a 256 MiB buffer is
-written between steps to flush L2.  The e2e figure repeats the step through
-the public host-pointer API: pinned host X/Y -> xyz_create (copy + pack) ->
-xyz_search -> results to host -> xyz_destroy.
+written between steps to flush L2 (outside the timed window).  The e2e
+figure repeats the step through the public host-pointer API: pinned host
+X/Y -> xyz_create (copy + pack) -> xyz_search -> results to host ->
+xyz_destroy.  The roofline denominators are measured in the same run by the
+library's probe (xyz_probe_peaks): integer ALU-pipe and popcount rates at
+the clock of the moment.
 
---impl reference times the CPU oracle (plain C, one core) on a bounded
-sample of the same workload and scales it to one search.
+Extra keys of the default line: the operating point chosen by the
+library's autotuner (M by measured cost, same recall target), the point of
+eq. bestM (the paper's plug-in rule), the exhaustive GPU screen of all
+pairs, the oracle on all host cores (cpu_baseline), and the two patterns
+(``batch``: 256 responses on one X plus 64 uneven instances; ``serve``: a
+Poisson stream over 32 resident datasets), each against the plain
+one-search-per-call path.
 
---pattern batch: one SNP-shaped X (n = 2000, p = 200000) with 256 balanced
-responses, each with 3 planted pairs, kappa = 0.4, M by eq. bestM and L for
-95% recall of the weakest target, screened once by the batched search (one
-call, shared row stream and keys) and once as 256 plain searches; both must
-give identical results.  --pattern scaling: Section 5.2's experiment (time to discover one planted
-pair of gamma in {0.7, 0.8, 0.9} against p, M from gamma0 = 0.55) with the
-exhaustive GPU screen beside it.  --pattern continuous: Section 3.1's
-real-valued response model with weighted rows.  --pattern serve: a Poisson stream (200 requests/s) of
-searches with L in [20, 200] and kappa in [0.2, 0.6] over resident SNP-shaped
-datasets of log-uniform n in [500, 8000] and p in [1e4, 5e5], each request
-with its own response (one planted pair of gamma in {0.7, 0.8, 0.9}) and M
-from the gamma0 = 0.55 rule of Section 5.2; reports p50/p99 latency and
-throughput of the server against the same requests run one after another.
+--impl reference times the CPU oracle (plain C) on all host cores on a
+bounded sample of runs of the same workload and operating point.  With
+--gpus N > 1 (under torchrun) one search's runs are split over the ranks by
+run range (xyz_search_range) and merged on rank 0 (strong scaling);
+--scaling weak gives every rank its own searches instead.  --pattern
+batch|serve|scaling|continuous runs one pattern alone.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -49,7 +54,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-METRIC = "interaction pairs screened/s at \u226595% planted recall; p50/p99 search latency"
+METRIC = "interaction pairs screened/s at ≥95% planted recall; p50/p99 search latency"
 UNIT = "pairs/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
@@ -62,7 +67,12 @@ def log(*a):
 
 def make_workload(name: str):
     from paper_1610_05108_gb300 import synth
-    if name == "gwas":
+    if name == "gwas_large":
+        d = synth.config_gwas_large(1)
+        kappa = 0.28
+        label = ("gwas n=4000 p=1000000 (AR(0.6) blocks of 20, MAF U[0.05,0.5], 10 planted pairs "
+                 "U[0.15,0.5] + 10 main effects)")
+    elif name == "gwas":
         d = synth.config_gwas(1)
         kappa = 0.3
         label = "gwas n=2000 p=100000 (AR(0.6) blocks of 20, MAF U[0.05,0.5], 5 planted pairs + 10 main effects)"
@@ -70,24 +80,44 @@ def make_workload(name: str):
         d = synth.config_small(1)
         kappa = 0.5
         label = "iid n=200 p=2000, Y = X_0 o X_1 flipped w.p. 0.1"
-    elif name == "gwas_large":
-        d = synth.config_gwas_large(1)
-        kappa = 0.3
-        label = ("gwas n=4000 p=1000000 (AR(0.6) blocks of 20, MAF U[0.05,0.5], 10 planted pairs "
-                 "U[0.15,0.5] + 10 main effects)")
     else:
         raise SystemExit(f"unknown workload {name}")
     return d, kappa, label
 
 
-def plan(ctx, d, kappa, xyz, samples=10**6):
-    gamma = (1.0 + kappa) / 2.0
-    _, _, agree = ctx.sample_agree(samples, 0x5EED)
-    M, _ = xyz.best_M(d.n, d.p, gamma, agree)
-    targets = [(pr, s) for pr, s in zip(d.planted, d.strengths) if s >= kappa]
+# ------------------------------------------------------------- planning
+# The same arithmetic as the library's host planner (xyz_M_for_gamma0,
+# xyz_runs_for_recall, xyz_eta), written out here so that the reference arm
+# plans without the library; the GPU arm checks the two agree.
+
+def m_for_gamma0(p: int, gamma0: float = 0.55) -> int:
+    m = math.log(p) / math.log(1.0 / gamma0)
+    return max(1, min(64, int(math.floor(m + 0.5))))
+
+
+def _hit(beta: float, L: float) -> float:
+    return 1.0 if beta >= 1.0 else -math.expm1(L * math.log1p(-beta))
+
+
+def runs_for_recall(beta: float, eta: float) -> int:
+    if beta >= 1.0:
+        return 1
+    L = max(1, int(math.ceil(math.log1p(-eta) / math.log1p(-beta))))
+    while _hit(beta, L) < eta:
+        L += 1
+    while L > 1 and _hit(beta, L - 1) >= eta:
+        L -= 1
+    return L
+
+
+def plan(d, kappa: float):
+    """M by the gamma0 = 0.55 rule, L for 95% recall of the weakest target
+    (the planted pairs with strength >= kappa), eta of every target."""
+    M = m_for_gamma0(d.p)
+    targets = [(tuple(pr), s) for pr, s in zip(d.planted, d.strengths) if s >= kappa]
     g_min = (1.0 + min(s for _, s in targets)) / 2.0
-    L = xyz.runs_for_recall(g_min ** M, 0.95)
-    eta = [xyz.eta((1 + s) / 2, M, L) for _, s in targets]
+    L = runs_for_recall(g_min ** M, 0.95)
+    eta = [_hit(((1.0 + s) / 2.0) ** M, L) for _, s in targets]
     return M, L, targets, eta
 
 
@@ -143,7 +173,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------- GPU arm
+# ------------------------------------------------------------- peaks
 
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -166,47 +196,54 @@ def load_traffic():
     except Exception:
         return {}
     out = {}
-    for stage, v in rec.items():
+    for key, v in rec.items():
         src = os.path.join(ROOT, v.get("source", ""))
         if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == v.get("sha"):
-            out[stage] = v
+            out[key] = v
     return out
 
 
-# Work per unit of each stage (one run = p columns):
-#   keys (survivor filter, ALU-bound): 28 integer operations per column and
-#       run -- 12.5 for the 32 x 32 bit transpose that forms the M-bit keys
-#       (400 ops per 32 columns), 6 to insert kx into the blocked Bloom
-#       filter (hash, word, two bits, OR), 9.5 to test kx ^ c (xor, hash,
-#       word, bits, load, compare, keep bit).
-#   sort (HBM): one read + one write of each 8-byte entry that reaches it.
-#   join (HBM): one read of each 4-byte sorted key.
-#   verify (HBM/L2): 2 columns of 4W bytes per candidate.
-FILTER_OPS_PER_COLUMN = 28
-INT32_LANES_PER_SM = 128
+# Algorithmic integer work of the survivor filter per column and run: the
+# 32 x 32 bit transpose that forms the M-bit keys (304 ALU-pipe operations per
+# 32 columns: 64 byte permutes for the 16- and 8-bit rounds, 5 operations for
+# each of the 48 masked swaps of the 4-, 2- and 1-bit rounds), 6 to insert
+# the key into a Bloom filter word (hash, word index, two bit positions, OR)
+# and 8 to test kx ^ c (xor, hash, word, bits, compare).  The denominator is
+# the measured integer ALU-pipe rate (lop3.b32), which also runs the shifts
+# and byte permutes.
+FILTER_OPS_PER_COLUMN = 304 / 32 + 6 + 8
 
 
-def int_peak_tops():
-    """Peak 32-bit integer operations per second from the unit counts and the
-    maximum SM clock: SMs x 128 INT32 lanes x f_max."""
-    import torch
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    peaks = load_peaks()
-    mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    return sms * INT32_LANES_PER_SM * mhz * 1e6 / 1e12, sms, mhz
+# ----------------------------------------------------------- GPU arm
+
+def _device_ctx(d, dev, stream, torch, xyz):
+    with torch.cuda.stream(stream):
+        dX = torch.from_numpy(np.ascontiguousarray(d.X.T)).to(dev)     # (p, n) rows = columns of X
+        dY = torch.from_numpy(d.Y).to(dev)
+    stream.synchronize()
+    ctx = xyz.Context.from_device(dX.data_ptr(), dY.data_ptr(), d.n, d.p, stream.cuda_stream)
+    stream.synchronize()
+    del dX, dY
+    return ctx
 
 
-def stage_work(stage: str, n: int, p: int, M: int, runs: int, candidates: int, survivors: int):
-    W = (n + 31) // 32
-    if stage == "keys":
-        return runs * p * FILTER_OPS_PER_COLUMN, "ops"
-    if stage == "sort":
-        return survivors * 16, "bytes"
-    if stage == "join":
-        return survivors * 4, "bytes"
-    if stage == "verify":
-        return candidates * 8 * W, "bytes"
-    return 0, "bytes"
+def _timed_searches(ctx, stream, flush, torch, L, M, kappa, seeds, hits):
+    """Searches with the given seeds, each bracketed by CUDA events on the
+    library's stream, L2 flushed before each (outside the events)."""
+    ms, found, stats = [], [], []
+    for s in seeds:
+        with torch.cuda.stream(stream):
+            flush.fill_(s & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = ctx.search(L, M, kappa, s)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        found.append(hits(res))
+        stats.append(ctx.stats())
+    return ms, found, stats
 
 
 def gpu_arm(args):
@@ -229,29 +266,46 @@ def gpu_arm(args):
     xyz.load()
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
+    sharded = world > 1 and args.scaling == "strong"
 
+    t0 = time.perf_counter()
     d, kappa, label = make_workload(args.workload)
+    log(f"[bench] rank {rank}: data made in {time.perf_counter() - t0:.1f} s")
     stream = torch.cuda.Stream(device=dev)
-    with torch.cuda.stream(stream):
-        dX = torch.from_numpy(np.ascontiguousarray(d.X.T)).to(dev)     # (p, n) rows = columns of X
-        dY = torch.from_numpy(d.Y).to(dev)
-    stream.synchronize()
-    ctx = xyz.Context.from_device(dX.data_ptr(), dY.data_ptr(), d.n, d.p, stream.cuda_stream)
-    M, L, targets, eta = plan(ctx, d, kappa, xyz)
+    ctx = _device_ctx(d, dev, stream, torch, xyz)
+    M, L, targets, eta = plan(d, kappa)
+    assert M == xyz.M_for_gamma0(d.p, 0.55)
+    assert L == xyz.runs_for_recall(((1 + min(s for _, s in targets)) / 2) ** M, 0.95)
     if args.L:
         L = args.L
     log(f"[bench] rank {rank}: n={d.n} p={d.p} M={M} L={L} kappa={kappa} targets={targets} eta={eta}")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     pairs_per_search = d.p * (d.p - 1) // 2
-    target_set = {tuple(pr) for pr, _ in targets}
+    target_list = [pr for pr, _ in targets]
 
     def hits(res):
-        got = {(int(a), int(b)) for a, b in zip(res["j"], res["k"])}
-        return sum(1 for t in target_set if t in got)
+        got = set(zip(res["j"].tolist(), res["k"].tolist())) if len(res) else set()
+        return [int(t in got) for t in target_list]
 
-    seed_base = 1_000_003 * (rank + 1)
+    peaks_probe = xyz.probe_peaks()
+    seed_base = 1_000_003 * (rank + 1) if not sharded else 1_000_003
+    from paper_1610_05108_gb300 import shard
+
+    def one_search(seed):
+        if not sharded:
+            return ctx.search(L, M, kappa, seed)
+        l0, l1 = shard.run_ranges(L, world)[rank]
+        mine = ctx.search_range(l0, l1, M, kappa, seed) if l1 > l0 else None
+        objs = [None] * world
+        torch.distributed.all_gather_object(objs, shard._as_triples(mine))
+        merged = shard.merge_pairs(objs)
+        out = np.zeros(len(merged), dtype=xyz.PAIR_DTYPE)
+        if len(merged):
+            out["j"], out["k"], out["agree"] = merged[:, 0], merged[:, 1], merged[:, 2]
+        return out
+
     for w in range(args.warmup):
-        ctx.search(L, M, kappa, seed_base + 10_000 + w)
+        one_search(seed_base + 10_000 + w)
     ctx.set_timing(True)
     sampler = ClockSampler(dev.index)
     if world > 1:
@@ -262,76 +316,95 @@ def gpu_arm(args):
     for s in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(s & 0xFF)                       # L2 flush, outside the timed window
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = ctx.search(L, M, kappa, seed_base + s)
+        t_host = time.perf_counter()
+        res = one_search(seed_base + s)
         e1.record(stream)
         e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+        el = e0.elapsed_time(e1) if not sharded else (time.perf_counter() - t_host) * 1e3
+        if world > 1:
+            t = torch.tensor([el], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        step_ms.append(el)
         found.append(hits(res))
         stats.append(ctx.stats())
     torch.cuda.synchronize()
     clocks = sampler.stop()
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = pairs_per_search * args.steps * world / (total_ms / 1e3)
+    searches = args.steps * (world if (world > 1 and not sharded) else 1)
+    value = pairs_per_search * searches / (total_ms / 1e3)
 
-    # per-stage device time and the dominant stage's roofline
+    # per-stage device time and the dominant kernel's roofline
     stages = ["keys", "sort", "join", "verify", "dedup"]
     ms_stage = {st: sum(x[f"ms_{st}"] for x in stats) for st in stages}
     launches_stage = {st: sum(x[f"launches_{st}"] for x in stats) for st in stages}
-    dom = max(stages, key=lambda st: ms_stage[st])
     cand = sum(x["candidates"] for x in stats)
     runs = sum(x["runs"] for x in stats)
     chunks = sum(x["chunks"] for x in stats)
     surv = sum(x["survivors"] for x in stats)
-    work, kind = stage_work(dom, d.n, d.p, M, runs, cand, surv)
-    secs = ms_stage[dom] / 1e3
-    peaks = load_peaks()
-    # the recorded DRAM traffic is that of the SNP-shaped p = 1e5 launch
-    traffic = load_traffic().get(dom) if args.workload == "gwas" else None
-    if kind == "ops":
-        peak, sms, mhz = int_peak_tops()
-        achieved = work / secs / 1e12 if secs > 0 else 0.0
-        kname = "filter_big_kernel" if d.p > 262144 else "filter_kernel"
-        roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 3),
-                    "peak": round(peak, 3), "unit": "TOPS (int32)", "frac": round(achieved / peak, 4),
-                    "peak_source": f"derived: {sms} SMs x {INT32_LANES_PER_SM} INT32 lanes x {mhz:.0f} MHz",
-                    "work_per_unit": f"{FILTER_OPS_PER_COLUMN} int ops per column per run"}
-    else:
-        peak = float(peaks["hbm_gbs"])
-        achieved = work / secs / 1e9 if secs > 0 else 0.0
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                    "unit": "GB/s", "frac": round(achieved / peak, 4),
-                    "peak_source": f"{peaks.get('source')} hbm_gbs"}
-    roofline.update({
+    big = d.p > 262144
+    kname = "filter_big_kernel" if big else "filter_kernel"
+    filt_s = ms_stage["keys"] / 1e3
+    alu_peak = peaks_probe["alu_ops_per_s"]
+    achieved = runs * d.p * FILTER_OPS_PER_COLUMN / filt_s if filt_s > 0 else 0.0
+    traffic = load_traffic().get(f"{kname}:{args.workload}")
+    roofline = {
+        "bound": "alu", "kernel": kname,
+        "achieved": round(achieved / 1e12, 3), "peak": round(alu_peak / 1e12, 3), "unit": "TOPS (int32)",
+        "frac": round(achieved / alu_peak, 4),
+        "peak_source": (f"measured in this run: lop3.b32 chains on {peaks_probe['sms']} SMs at "
+                        f"{peaks_probe['sm_mhz']:.0f} MHz (xyz_probe_peaks)"),
+        "work_per_unit": f"{FILTER_OPS_PER_COLUMN:.1f} integer ALU-pipe ops per column per run "
+                         "(key transpose 9.5, Bloom insert 6, Bloom test 8)",
         "traffic": traffic.get("bytes_per_launch") if traffic else None,
+        "traffic_units": traffic.get("units_per_launch") if traffic else None,
         "traffic_note": traffic.get("note") if traffic else "no ncu capture of the current kernel source",
-        "launches": launches_stage[dom], "launch_groups": chunks,
+        "launches": launches_stage["keys"], "launch_groups": chunks,
         "stage_ms": {k: round(v, 3) for k, v in ms_stage.items()},
-        "stage_share": {k: round(v / max(1e-9, sum(ms_stage.values())), 4) for k, v in ms_stage.items()}})
+        "stage_share": {k: round(v / max(1e-9, sum(ms_stage.values())), 4) for k, v in ms_stage.items()},
+    }
+    W = (d.n + 31) // 32
+    ver_s = ms_stage["verify"] / 1e3
+    popc_done = cand * W
+    verify_roofline = {
+        "bound": "popc", "kernel": "verify_kernel",
+        "achieved": round(popc_done / ver_s / 1e12, 3) if ver_s > 0 else 0.0,
+        "peak": round(peaks_probe["popc_ops_per_s"] / 1e12, 3), "unit": "Tpopc/s",
+        "frac": round(popc_done / ver_s / peaks_probe["popc_ops_per_s"], 4) if ver_s > 0 else 0.0,
+        "work_per_unit": f"{W} popcounts per candidate (one per 32-row word; term (iv) of Section 2.3)",
+        "peak_source": "measured in this run: popc.b32 chains (xyz_probe_peaks)"}
 
-    recall = float(np.mean(found)) / max(1, len(target_set))
+    fr = np.asarray(found, dtype=np.float64)          # steps x targets
+    recall = float(fr.mean()) if fr.size else 0.0
     gpu_launches = sum(x["gpu_launches"] for x in stats)
     lat = sorted(step_ms)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": label, "n": d.n, "p": d.p, "M": M, "L": L, "kappa": kappa,
+                   "M_rule": "gamma0 = 0.55 (Section 5.2): M = round(log p / log(1/0.55))",
+                   "L_rule": "eq. L_choice: least L finding the weakest target with probability >= 0.95",
                    "planted_strengths": [round(s, 4) for s in d.strengths],
-                   "targets": [list(pr) for pr, _ in targets], "eta_per_target": [round(e, 4) for e in eta],
+                   "targets": [list(pr) for pr in target_list],
                    "l2": "256 MiB buffer written between steps (L2 flush), outside the timed window",
-                   "parallelism": f"runs of independent searches per GPU x{world}"},
-        "recall": {"measured": round(recall, 4), "expected_min_eta": round(min(eta), 4),
-                   "steps": args.steps},
+                   "parallelism": (f"one search's runs split over {world} GPUs by run range, merged on the host"
+                                   if sharded else f"independent searches per GPU x{world}")},
+        "recall": {"measured": round(recall, 4), "expected_min_eta": round(min(eta), 4), "steps": args.steps,
+                   "per_target": [{"pair": list(pr), "strength": round(s, 4), "eta": round(e, 4),
+                                   "found_rate": round(float(fr[:, i].mean()), 4) if fr.size else 0.0}
+                                  for i, ((pr, s), e) in enumerate(zip(targets, eta))]},
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                        "p99": round(float(np.percentile(lat, 99)), 3), "n": len(lat)},
         "roofline": roofline,
+        "verify_roofline": verify_roofline,
+        "peaks_measured": {k: (round(v / 1e12, 3) if k.endswith("per_s") else v) for k, v in peaks_probe.items()},
         "search_stats": {"attempts": [int(x["attempts"]) for x in stats],
                          "filter_kept_per_run": round(sum(x["filter_kept"] for x in stats) / max(1, runs), 1),
                          "candidates_per_run": round(cand / max(1, runs), 1),
@@ -341,15 +414,21 @@ def gpu_arm(args):
     }
 
     if rank == 0 and not args.no_extra:
-        out["autotuned"] = autotuned_leg(args, ctx, stream, d, kappa, M, targets, xyz, torch, hits)
-        out["as_written"] = as_written_leg(args, ctx, stream, d, kappa, M, targets, xyz, torch, hits)
+        out["autotuned"] = autotuned_leg(args, ctx, stream, flush, d, kappa, M, targets, xyz, torch, hits)
+        out["paper_bestM"] = bestM_leg(args, ctx, stream, flush, d, kappa, targets, xyz, torch, hits)
         out["exhaustive"] = exhaustive_leg(ctx, stream, d, kappa, pairs_per_search, total_ms / args.steps,
-                                           target_set, torch)
+                                           set(target_list), torch)
+    ctx.close()
+    del flush
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_leg(args, d, kappa, M, L, xyz, torch)
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_leg(d, kappa, M, L, args.cpu_seconds)
-    ctx.close()
+    if rank == 0 and not args.no_patterns:
+        torch.cuda.empty_cache()
+        out["batch"] = batch_summary(args, xyz, torch)
+        torch.cuda.empty_cache()
+        out["serve"] = serve_summary(args, xyz, torch)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -357,60 +436,48 @@ def gpu_arm(args):
         print(json.dumps(out), flush=True)
 
 
-def autotuned_leg(args, ctx, stream, d, kappa, M_rule, targets, xyz, torch, hits):
-    """The operating point chosen by measuring this implementation (xyz_autotune_M
-    over M_rule - 4 .. M_rule + 2 at 95% recall of the weakest target), then
+def autotuned_leg(args, ctx, stream, flush, d, kappa, M_rule, targets, xyz, torch, hits):
+    """The operating point chosen by the library's autotuner (xyz_autotune_M
+    over M_rule - 3 .. M_rule + 3 at 95% recall of the weakest target), then
     timed like the main line."""
     g_min = (1.0 + min(s_ for _, s_ in targets)) / 2.0
     t0 = time.perf_counter()
-    M, L, pred, table = ctx.autotune_M(kappa, g_min, 0.95, max(1, M_rule - 4), min(31, M_rule + 2), seed=77)
+    M, L, pred, table = ctx.autotune_M(kappa, g_min, 0.95, max(1, M_rule - 3), min(31, M_rule + 3), seed=77)
     tune_s = time.perf_counter() - t0
     ctx.search(L, M, kappa, 5_999_999)              # warm-up at the chosen point
-    ms, found = [], []
-    for s in range(args.steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = ctx.search(L, M, kappa, 6_000_000 + s)
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        found.append(hits(res))
+    ms, found, _ = _timed_searches(ctx, stream, flush, torch, L, M, kappa,
+                                   [6_000_000 + s for s in range(args.extra_steps)], hits)
     t = float(np.mean(ms))
     return {"M": M, "L": L, "ms_per_step": round(t, 3), "tuner_ms": round(pred, 3),
-            "value": d.p * (d.p - 1) // 2 / (t / 1e3), "unit": UNIT,
-            "recall_measured": round(float(np.mean(found)) / max(1, len(targets)), 4),
+            "value": d.p * (d.p - 1) // 2 / (t / 1e3), "unit": UNIT, "steps": len(ms),
+            "recall_measured": round(float(np.mean(found)), 4),
             "eta_min": round(xyz.eta(g_min, M, L), 4), "tuning_s": round(tune_s, 3),
             "table": [[int(r[0]), int(r[1]), round(float(r[2]), 3)] for r in table],
-            "note": "M by measured cost instead of eq. bestM's model; same recall target"}
+            "note": "M by this implementation's measured cost; same recall target"}
 
 
-def as_written_leg(args, ctx, stream, d, kappa, M, targets, xyz, torch, hits):
-    """The configuration as stated (L = 100 runs at the same M): time and the
-    measured recall against the predicted eta of each target."""
-    L = 100
-    ms, found = [], []
-    for s in range(args.steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = ctx.search(L, M, kappa, 5_000_000 + s)
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        found.append(hits(res))
+def bestM_leg(args, ctx, stream, flush, d, kappa, targets, xyz, torch, hits):
+    """M by eq. bestM (the plug-in estimate of sum gamma_jk^M from 10^6
+    sampled pairs, gamma = (1 + kappa)/2), L for the same recall target."""
+    _, _, agree = ctx.sample_agree(10**6, 0x5EED)
+    M, _ = xyz.best_M(d.n, d.p, (1.0 + kappa) / 2.0, agree)
+    g_min = (1.0 + min(s_ for _, s_ in targets)) / 2.0
+    L = xyz.runs_for_recall(g_min ** M, 0.95)
+    steps = max(1, min(args.extra_steps, 2))
+    ms, found, _ = _timed_searches(ctx, stream, flush, torch, L, M, kappa,
+                                   [5_000_000 + s for s in range(steps)], hits)
     t = float(np.mean(ms))
-    return {"L": L, "M": M, "kappa": kappa, "ms_per_step": round(t, 3),
-            "value": d.p * (d.p - 1) // 2 / (t / 1e3), "unit": UNIT,
-            "recall_measured": round(float(np.mean(found)) / max(1, len(targets)), 4),
-            "eta_predicted": [round(xyz.eta((1 + s_) / 2, M, L), 4) for _, s_ in targets],
-            "note": "L as in the configuration; recall is far below 95% there, hence the main line's L"}
+    return {"M": M, "L": L, "ms_per_step": round(t, 3), "value": d.p * (d.p - 1) // 2 / (t / 1e3),
+            "unit": UNIT, "steps": steps, "recall_measured": round(float(np.mean(found)), 4),
+            "eta_min": round(xyz.eta(g_min, M, L), 4),
+            "note": "the paper's cost model (eq. bestM), written for its CPU implementation"}
 
 
 def exhaustive_leg(ctx, stream, d, kappa, pairs_per_search, ms_search, target_set, torch):
     """The exhaustive GPU screen of all pairs on the same data (recall 1 by
-    construction), timed beside the search."""
-    ctx.brute_force(kappa)                     # warm-up
+    construction), timed once beside the search."""
+    if d.p <= 300000:
+        ctx.brute_force(kappa)                     # warm-up (the large screen runs once)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -432,7 +499,7 @@ def e2e_leg(args, d, kappa, M, L, xyz, torch):
     Xv = Xh.numpy().T          # column-major view of the pinned buffer
     Yv = Yh.numpy()
     times, d2h = [], []
-    steps = max(1, min(args.steps, 5))
+    steps = max(1, min(args.steps, args.e2e_steps))
     for s in range(steps + 1):
         t0 = time.perf_counter()
         with xyz.Context.from_host(Xv, Yv) as c:
@@ -450,74 +517,107 @@ def e2e_leg(args, d, kappa, M, L, xyz, torch):
 
 # --------------------------------------------------------- CPU oracle leg
 
-def cpu_leg(d, kappa, M, L, seconds):
-    """The oracle as it stands, one thread, on a bounded number of runs,
-    scaled linearly to the L runs of one search (runs are i.i.d.)."""
+def _host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_runs(d, kappa, M, seed, l_start, seconds, cores):
+    """The oracle as it stands (plain C, one run per call) on ``cores`` host
+    threads (the calls release the interpreter lock), each thread taking the
+    next run from a shared counter, until ``seconds`` have passed; returns
+    (runs done, elapsed seconds)."""
+    import threading
+
     import oracle
     oracle.build()
+    lock = threading.Lock()
+    nxt = [l_start]
+    done = [0]
     t0 = time.perf_counter()
-    runs = 0
-    while True:
-        oracle.xyz_range(d.X, d.Y, runs, runs + 1, M, kappa, 99)
-        runs += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or runs >= L:
-            break
-    per_run = el / runs
-    per_search = per_run * L
-    return {"value": d.p * (d.p - 1) // 2 / per_search, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{runs} of {L} runs timed ({el:.1f} s), scaled to one search of {L} runs"}
+
+    def worker():
+        while True:
+            with lock:
+                if time.perf_counter() - t0 >= seconds:
+                    return
+                r = nxt[0]
+                nxt[0] += 1
+            oracle.xyz_range(d.X, d.Y, r, r + 1, M, kappa, seed)
+            with lock:
+                done[0] += 1
+
+    th = [threading.Thread(target=worker) for _ in range(cores)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    return done[0], time.perf_counter() - t0
+
+
+def cpu_leg(d, kappa, M, L, seconds):
+    """The oracle, unchanged, on all host cores for a bounded time, scaled
+    linearly to the L runs of one search (runs are i.i.d.)."""
+    cores = _host_cores()
+    runs, el = oracle_runs(d, kappa, M, 4242, 0, seconds, cores)
+    per_search = el / max(1, runs) * L
+    return {"value": d.p * (d.p - 1) // 2 / per_search, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{runs} of the {L} runs (seed 4242, same M, kappa) on {cores} threads in {el:.1f} s, "
+                      f"scaled to one search"}
 
 
 def reference_arm(args):
+    """The oracle on all host cores at the GPU arm's workload, operating
+    point, metric and unit: each step a bounded sample of runs, scaled to one
+    search.  Under torchrun only rank 0 runs."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     oracle.build()
     d, kappa, label = make_workload(args.workload)
-    # same planning rule as the GPU arm, evaluated on the host oracle's
-    # sampled strengths
-    rng = np.random.default_rng(0x5EED)
-    j = rng.integers(0, d.p, size=20000)
-    k = (j + 1 + rng.integers(0, d.p - 1, size=20000)) % d.p
-    agree = oracle.agree_pairs(d.X, d.Y, j, k)
-    gamma = (1 + kappa) / 2
-    Ms = np.arange(1, 65)
-    means = np.array([np.mean((agree / d.n) ** m) for m in Ms])
-    cost = (Ms * d.p + d.p * np.log(d.p) + d.n * d.p * (d.p - 1) * means) / -np.log1p(-(gamma ** Ms))
-    M = int(Ms[np.argmin(cost)])
-    targets = [s for s in d.strengths if s >= kappa]
-    g_min = (1 + min(targets)) / 2
-    L = int(np.ceil(np.log(0.05) / np.log1p(-(g_min ** M))))
-    per_step = []
-    sample_runs = max(1, int(args.ref_runs))
+    M, L, targets, eta = plan(d, kappa)
+    if args.L:
+        L = args.L
+    cores = _host_cores()
+    per_step, runs_step = [], []
+    l_next = 0
     for w in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        oracle.xyz_range(d.X, d.Y, w * sample_runs, (w + 1) * sample_runs, M, kappa, 4242)
-        el = time.perf_counter() - t0
+        runs, el = oracle_runs(d, kappa, M, 4242, l_next, args.ref_seconds, cores)
+        l_next += runs
         if w >= args.warmup:
-            per_step.append(el / sample_runs * L)
-    t = float(np.mean(per_step))
-    value = d.p * (d.p - 1) // 2 / t
+            per_step.append(el)
+            runs_step.append(runs)
+    sample_s = float(np.sum(per_step))
+    sample_runs = int(np.sum(runs_step))
+    t_search = sample_s / max(1, sample_runs) * L
+    value = d.p * (d.p - 1) // 2 / t_search
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": sample_s / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+           "data": "synthetic",
            "config": {"workload": label, "n": d.n, "p": d.p, "M": M, "L": L, "kappa": kappa},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{sample_runs} runs per step, scaled to {L} runs"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"each step: runs of the search for {args.ref_seconds:g} s on {cores} "
+                                      f"threads; {sample_runs} runs in {sample_s:.1f} s over the timed steps"},
+           "extrapolated_ms_per_search": round(t_search * 1e3, 1),
+           "note": "ms_per_step is the measured sample time of a step; one whole search of L runs would take "
+                   "extrapolated_ms_per_search (runs are i.i.d., so time scales linearly in L)",
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
 # ---------------------------------------------------------- batch pattern
 
-def batch_arm(args):
-    import torch
-    from paper_1610_05108_gb300 import build as _build
-    from paper_1610_05108_gb300 import synth, xyz
-    _build.build()
-    xyz.load()
+def batch_summary(args, xyz, torch):
+    """Config 4: one SNP-shaped X (n = 2000, p = 200000) with B responses
+    (3 planted pairs each, kappa = 0.4, M by eq. bestM, L for 95% recall of
+    the weakest target) screened once by the batched search and once as B
+    plain searches; plus uneven instances launched as one CUDA graph against
+    one search after another."""
+    from paper_1610_05108_gb300 import synth
     n, p, B = 2000, 200000, args.batch_responses
     t0 = time.perf_counter()
     X, _ = synth.gwas_X(n, p, synth.rng_for(21, "X"))
@@ -545,49 +645,57 @@ def batch_arm(args):
         plain.append(ctx.search(L, M, kappa, seed))
     t_plain = time.perf_counter() - t0
     ctx.close()
+    del X
     inst = instances_leg(args, xyz, torch) if args.batch_instances > 0 else None
     same = all(np.array_equal(a, b) for a, b in zip(got, plain))
     found = sum(1 for b in range(B) for pr in targets[b]
                 if any((int(j), int(k)) == tuple(pr) for j, k in zip(got[b]["j"], got[b]["k"])))
+    found_plain = sum(1 for b in range(B) for pr in targets[b]
+                      if any((int(j), int(k)) == tuple(pr) for j, k in zip(plain[b]["j"], plain[b]["k"])))
     ntarget = sum(len(t) for t in targets)
     pairs = B * p * (p - 1) / 2
-    out = {"metric": METRIC, "pattern": "batch", "value": pairs / t_batch, "unit": UNIT,
-           "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
-           "ms_per_response": round(t_batch / B * 1e3, 3),
-           "plain": {"value": pairs / t_plain, "ms_per_response": round(t_plain / B * 1e3, 3),
-                     "path": "xyz_set_y + xyz_search per response"},
-           "speedup_vs_plain": round(t_plain / t_batch, 3), "identical_to_plain": bool(same),
-           "recall": {"found": found, "targets": ntarget,
-                      "expected_min_eta": round(xyz.eta(g_min, M, L), 4)},
-           "instances": inst,
-           "config": {"workload": f"one SNP-shaped X n={n} p={p} with {B} responses x 3 planted pairs "
-                                  f"(strength U[0.45,0.55] before scaling, balanced Y)",
-                      "n": n, "p": p, "B": B, "M": M, "L": L, "kappa": kappa,
-                      "timing": "host wall clock around the whole call, results on the host"}}
-    print(json.dumps(out), flush=True)
+    return {"value": pairs / t_batch, "unit": UNIT, "ms_per_response": round(t_batch / B * 1e3, 3),
+            "plain": {"value": pairs / t_plain, "ms_per_response": round(t_plain / B * 1e3, 3),
+                      "recall": round(found_plain / max(1, ntarget), 4),
+                      "path": "xyz_set_y + xyz_search per response"},
+            "speedup_vs_plain": round(t_plain / t_batch, 3), "identical_to_plain": bool(same),
+            "recall": {"found": found, "targets": ntarget, "measured": round(found / max(1, ntarget), 4),
+                       "expected_min_eta": round(xyz.eta(g_min, M, L), 4)},
+            "instances": inst,
+            "config": {"workload": f"one SNP-shaped X n={n} p={p} with {B} responses x 3 planted pairs "
+                                   f"(strength U[0.45,0.55] before scaling, balanced Y)",
+                       "n": n, "p": p, "B": B, "M": M, "L": L, "kappa": kappa,
+                       "timing": "host wall clock around the whole call, results on the host"}}
 
 
 def instances_leg(args, xyz, torch):
     """Independent instances of log-uniform n in [500, 8000] and p in
-    [1e4, 5e5] (i.i.d. X, one planted pair of strength 0.8 each, M from
-    gamma0 = 0.55, L for 95% recall): one search after another against all
-    of them launched as one CUDA graph (xyz_search_many)."""
+    [1e4, 5e5] (i.i.d. X made on the device from a seeded generator, one
+    planted pair of strength 0.8 each, M from gamma0 = 0.55, L for 95%
+    recall): one search after another against all of them launched as one
+    CUDA graph (xyz_search_many)."""
     from paper_1610_05108_gb300 import synth
     sizes = synth.instance_sizes(args.batch_instances, 44)
-    rng = np.random.default_rng(45)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device=dev)
     ctxs, L, M, kap, seeds, pairs = [], [], [], [], [], 0
     for i, (n, p) in enumerate(sizes):
-        X = np.asfortranarray((rng.integers(0, 2, size=(n, p), dtype=np.int8) * 2 - 1).astype(np.int8))
-        Y = (X[:, 0] * X[:, 1]).astype(np.int8)
-        Y[rng.choice(n, size=n // 10, replace=False)] *= -1
-        ctxs.append(xyz.create(X, Y))
+        g.manual_seed(45_000 + i)
+        dX = (torch.randint(0, 2, (p, n), generator=g, device=dev, dtype=torch.int8) * 2 - 1).to(torch.int8)
+        dY = (dX[0] * dX[1]).to(torch.int8)
+        flips = torch.randperm(n, generator=g, device=dev)[: n // 10]
+        dY[flips] = -dY[flips]
+        torch.cuda.synchronize()
+        ctxs.append(xyz.Context.from_device(dX.data_ptr(), dY.data_ptr(), n, p, 0))
+        torch.cuda.synchronize()
+        del dX, dY
         m = xyz.M_for_gamma0(p, 0.55)
         M.append(m)
         L.append(xyz.runs_for_recall(0.9 ** m, 0.95))
         kap.append(0.6)
         seeds.append(1000 + i)
         pairs += p * (p - 1) // 2
-        del X
+    torch.cuda.empty_cache()
     for c, l_, m_, k_, s_ in zip(ctxs, L, M, kap, seeds):       # warm-up
         c.search(l_, m_, k_, s_)
     xyz.search_many(ctxs, L, M, kap, seeds)
@@ -603,21 +711,37 @@ def instances_leg(args, xyz, torch):
         c.close()
     return {"count": len(sizes), "sizes": [list(x) for x in sizes], "M": M, "L": L,
             "sequential_s": round(t_seq, 4), "graph_s": round(t_many, 4),
-            "speedup": round(t_seq / t_many, 3), "value_graph": pairs / t_many, "unit": UNIT,
+            "speedup": round(t_seq / t_many, 3), "value_graph": pairs / t_many,
+            "value_sequential": pairs / t_seq, "unit": UNIT,
             "identical": all(np.array_equal(a, b) for a, b in zip(alone, many)),
             "planted_found": found}
 
 
-# ---------------------------------------------------------- serve pattern
-
-def serve_arm(args):
-    import threading
-
+def batch_arm(args):
     import torch
     from paper_1610_05108_gb300 import build as _build
-    from paper_1610_05108_gb300 import synth, xyz
+    from paper_1610_05108_gb300 import xyz
     _build.build()
     xyz.load()
+    out = {"metric": METRIC, "pattern": "batch", "n_gpus": 1, "higher_is_better": True, "dtype": "u32",
+           "data": "synthetic"}
+    out.update(batch_summary(args, xyz, torch))
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------- serve pattern
+
+def serve_summary(args, xyz, torch):
+    """Config 5: a Poisson stream (200 requests/s) of searches with L in
+    [20, 200] and kappa in [0.2, 0.6] over resident SNP-shaped datasets of
+    log-uniform n in [500, 8000] and p in [1e4, 5e5] (a pool of 32), each
+    request with its own response (one planted pair of gamma in {0.7, 0.8,
+    0.9}) and M from the gamma0 = 0.55 rule; p50/p99 latency of the paced
+    stream, throughput of the same requests submitted at once, and the plain
+    path (one search after another)."""
+    import threading
+
+    from paper_1610_05108_gb300 import synth
     D, R = args.serve_datasets, 8
     sizes = synth.instance_sizes(D, 31)
     t0 = time.perf_counter()
@@ -630,7 +754,7 @@ def serve_arm(args):
     for q in reqs:
         n, p = sizes[q["dataset"]]
         q["M"] = xyz.M_for_gamma0(p, 0.55)
-    log(f"[bench] serve: {D} datasets {sizes} made in {time.perf_counter() - t0:.1f} s")
+    log(f"[bench] serve: {D} datasets made in {time.perf_counter() - t0:.1f} s")
 
     # plain: the same searches one after another, one context per dataset
     ctxs = [xyz.create(X, Ys[0]) for X, Ys, _, _ in data]
@@ -685,36 +809,49 @@ def serve_arm(args):
     same = all(np.array_equal(a, b) for a, b in zip(served, plain)) and \
         all(np.array_equal(a, b) for a, b in zip(sat, plain))
     pairs_total = sum(sizes[q["dataset"]][1] * (sizes[q["dataset"]][1] - 1) / 2 for q in reqs)
-    found = targets = 0
+    found = found_plain = targets = 0
     eta = []
-    for q, r in zip(reqs, served):
+    for q, r, rp in zip(reqs, served, plain):
         X, Ys, pairs, real = data[q["dataset"]]
         s_ = real[q["response"]]
         if s_ >= q["kappa"]:
             targets += 1
             pr = pairs[q["response"]]
             found += int(any((int(j), int(k)) == pr for j, k in zip(r["j"], r["k"])))
+            found_plain += int(any((int(j), int(k)) == pr for j, k in zip(rp["j"], rp["k"])))
             eta.append(xyz.eta((1 + s_) / 2, q["M"], q["L"]))
-    out = {"metric": METRIC, "pattern": "serve", "value": pairs_total / el, "unit": UNIT,
-           "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
-           "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
-                          "p99": round(float(np.percentile(lat, 99)), 3), "n": len(lat)},
-           "elapsed_s": round(el, 3), "arrivals_span_s": round(reqs[-1]["t"], 3),
-           "saturated": {"value": pairs_total / el_sat, "elapsed_s": round(el_sat, 3),
-                         "p50_ms": round(float(np.percentile(lat_sat, 50)), 3),
-                         "p99_ms": round(float(np.percentile(lat_sat, 99)), 3),
-                         "note": "all requests submitted at once"},
-           "plain": {"value": pairs_total / t_plain, "elapsed_s": round(t_plain, 3),
-                     "path": "one xyz_search per request, one after another"},
-           "identical_to_plain": bool(same),
-           "recall": {"found": found, "targets": targets,
-                      "expected": round(float(np.mean(eta)) if eta else 0.0, 4)},
-           "server": {"workers": args.serve_workers, "slice_runs": args.serve_slice,
-                      "budget_bytes": 120 << 30, "device_bytes": st["device_bytes"]},
-           "config": {"workload": f"Poisson {args.serve_rate:g} req/s, {len(reqs)} requests over {D} "
-                                  "resident SNP-shaped datasets, n in [500,8000], p in [1e4,5e5] "
-                                  "log-uniform, L in [20,200], kappa in [0.2,0.6]",
-                      "datasets": [list(x) for x in sizes]}}
+    return {"value": pairs_total / el, "unit": UNIT,
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                           "p99": round(float(np.percentile(lat, 99)), 3), "n": len(lat)},
+            "elapsed_s": round(el, 3), "arrivals_span_s": round(reqs[-1]["t"], 3),
+            "saturated": {"value": pairs_total / el_sat, "elapsed_s": round(el_sat, 3),
+                          "p50_ms": round(float(np.percentile(lat_sat, 50)), 3),
+                          "p99_ms": round(float(np.percentile(lat_sat, 99)), 3),
+                          "note": "all requests submitted at once"},
+            "plain": {"value": pairs_total / t_plain, "elapsed_s": round(t_plain, 3),
+                      "recall": round(found_plain / max(1, targets), 4),
+                      "path": "one xyz_search per request, one after another"},
+            "speedup_saturated_vs_plain": round(t_plain / el_sat, 3),
+            "identical_to_plain": bool(same),
+            "recall": {"found": found, "targets": targets, "measured": round(found / max(1, targets), 4),
+                       "expected": round(float(np.mean(eta)) if eta else 0.0, 4)},
+            "server": {"workers": args.serve_workers, "slice_runs": args.serve_slice,
+                       "budget_bytes": 120 << 30, "device_bytes": st["device_bytes"]},
+            "config": {"workload": f"Poisson {args.serve_rate:g} req/s, {len(reqs)} requests over {D} "
+                                   "resident SNP-shaped datasets, n in [500,8000], p in [1e4,5e5] "
+                                   "log-uniform, L in [20,200], kappa in [0.2,0.6]",
+                       "datasets": [list(x) for x in sizes]}}
+
+
+def serve_arm(args):
+    import torch
+    from paper_1610_05108_gb300 import build as _build
+    from paper_1610_05108_gb300 import xyz
+    _build.build()
+    xyz.load()
+    out = {"metric": METRIC, "pattern": "serve", "n_gpus": 1, "higher_is_better": True, "dtype": "u32",
+           "data": "synthetic"}
+    out.update(serve_summary(args, xyz, torch))
     print(json.dumps(out), flush=True)
 
 
@@ -903,18 +1040,24 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", default="gwas")
+    ap.add_argument("--workload", default="gwas_large")
+    ap.add_argument("--scaling", choices=["strong", "weak"], default="strong",
+                    help="with --gpus N > 1: split one search's runs over the ranks (strong) or give every "
+                         "rank its own searches (weak)")
     ap.add_argument("--L", type=int, default=0, help="override the number of runs")
+    ap.add_argument("--extra-steps", type=int, default=3, help="timed searches of the autotuned and bestM legs")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-runs", type=int, default=10)
+    ap.add_argument("--ref-seconds", type=float, default=2.0, help="oracle time per step of --impl reference")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the L=100 and exhaustive-screen legs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the autotuned, bestM and exhaustive legs")
+    ap.add_argument("--no-patterns", action="store_true", help="skip the batch and serve keys")
     ap.add_argument("--pattern", choices=["search", "batch", "serve", "scaling", "continuous"],
                     default="search")
     ap.add_argument("--batch-responses", type=int, default=256)
-    ap.add_argument("--batch-instances", type=int, default=16)
-    ap.add_argument("--serve-datasets", type=int, default=6)
+    ap.add_argument("--batch-instances", type=int, default=64)
+    ap.add_argument("--serve-datasets", type=int, default=32)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-workers", type=int, default=8)

@@ -360,6 +360,26 @@ int xyz_best_M(int64_t n, int64_t p, double gamma, const int32_t *agree, int64_t
  * near 0.55): round(log p / log(1/gamma0)), at least 1. */
 int32_t xyz_M_for_gamma0(int64_t p, double gamma0);
 
+/* ------------------------------------------------------ measured peaks */
+
+/* Throughputs of the instruction classes the integer kernels are made of,
+ * measured on the current device (the paper has no counterpart: these are
+ * the denominators of the rooflines reported for this implementation). */
+typedef struct xyz_peaks {
+    double alu_ops_per_s;     /* lop3.b32 (integer ALU pipe: logic, shifts, byte permutes) */
+    double iadd_ops_per_s;    /* add.u32 */
+    double popc_ops_per_s;    /* popc.b32 */
+    double sm_mhz;            /* mean SM clock during the probes (clock64 cycles / elapsed time) */
+    int32_t sms;              /* streaming multiprocessors */
+} xyz_peaks;
+
+/* Runs the three probes on the current device: per SM 1024 threads with 8
+ * independent chains of one instruction each, about 1-2 ms per launch, timed
+ * with CUDA events on the default stream (each probe's second launch is the
+ * measured one).  Allocates a few KB of device memory for the duration of
+ * the call.  XYZ_EINVAL for a null pointer, XYZ_ECUDA on a CUDA error. */
+int xyz_probe_peaks(xyz_peaks *out);
+
 /* --------------------------------------- allocation-free candidate set */
 
 /* Limits of xyz_run_candidates_noalloc. */

@@ -48,6 +48,18 @@ class Stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class Peaks(ctypes.Structure):
+    _fields_ = [("alu_ops_per_s", ctypes.c_double), ("iadd_ops_per_s", ctypes.c_double),
+                ("popc_ops_per_s", ctypes.c_double), ("sm_mhz", ctypes.c_double), ("sms", ctypes.c_int32)]
+
+
+def probe_peaks() -> dict:
+    """Measured instruction throughputs of the current device (xyz_probe_peaks)."""
+    pk = Peaks()
+    _check(load().xyz_probe_peaks(ctypes.byref(pk)))
+    return {name: getattr(pk, name) for name, _ in Peaks._fields_}
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "completed", "canceled", "failed", "queued", "active", "device_bytes", "budget_bytes")] + \
@@ -97,6 +109,7 @@ SIGNATURES = {
     "xyz_best_M": (ctypes.c_int, [_i64, _i64, _dbl, _p, _i64, _i32, _p, _p]),
     "xyz_M_for_gamma0": (_i32, [_i64, _dbl]),
     "xyz_run_candidates_noalloc": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _i64, _p]),
+    "xyz_probe_peaks": (ctypes.c_int, [_p]),
     "xyz_server_create": (ctypes.c_int, [_i32, _i64, _i64, _p]),
     "xyz_server_add_dataset": (ctypes.c_int, [_p, _p, _p, _i64, _i64, _p]),
     "xyz_server_submit": (ctypes.c_int, [_p, _i32, _p, _i32, _i32, _dbl, _u64, _p]),
