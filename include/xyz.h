@@ -99,6 +99,7 @@ typedef struct xyz_stats {
     int64_t survivors;        /* entries that reached the sort (all of them without the filter) */
     int64_t filter_kept;      /* columns kept by the survivor filter, summed over runs (0 without it) */
     int64_t attempts;         /* 1, plus one for every redo after a buffer grew */
+    int64_t bucket_members;   /* columns in buckets grouped on chip, summed over runs (spilled runs excluded) */
 } xyz_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -306,8 +307,12 @@ int xyz_set_spill_flush(xyz_ctx *ctx, int64_t groups);
  * holds is grouped on chip in up to max_parts passes, each over the
  * survivors whose group key hashes into one range of 32 bins (a group never
  * straddles two); a run that needs more passes, or has a single bin above
- * the capacity, goes through the sort as above.  0 sends every such run to
- * the sort.  0 <= max_parts <= 32, default 32.  Results never depend on it. */
+ * the capacity, goes through the sort as above.  The class-split filter
+ * (p > 262144, or xyz_set_filter(ctx, 2)) instead sorts a run's survivors by
+ * bin once and groups every bin on chip -- a bin above the capacity from
+ * global memory, when its distinct group keys fit the on-chip table -- so
+ * there only 0 versus nonzero matters.  0 sends every such run to the sort.
+ * 0 <= max_parts <= 32, default 32.  Results never depend on it. */
 int xyz_set_onchip_partitions(xyz_ctx *ctx, int32_t max_parts);
 
 /* --------------------------------------------------- parity / observability */

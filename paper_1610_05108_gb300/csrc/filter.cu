@@ -131,7 +131,87 @@ struct GroupOut {
     uint32_t *nbuckets;
     uint32_t mcap, bcap;
     int *overflow;
+    unsigned long long *members_total;   // bucket members written, over the search
 };
+
+// Phase II of the on-chip grouping: every slot of the table (tkey / tcnt,
+// side counts packed A << 16 | B) whose group has candidates becomes a
+// bucket (response b in its pad); one global atomic pair per call reserves
+// the bucket and member space.  Afterwards curA / tcnt of a bucket's slot are
+// the end cursors of its sides A / B (curA may be tkey itself when phase III
+// no longer needs the keys), and tcnt is FL_EMPTY for a slot without a
+// bucket.  Returns false when the space ran out (overflow bit 2 set: the host
+// grows it and redoes the search).  Called by every thread of the CTA.
+__device__ __forceinline__ bool assign_buckets(uint32_t *tkey, uint32_t *tcnt, uint32_t *curA, int tsize, bool nz,
+                                               int b, const GroupOut &g)
+{
+    __shared__ uint32_t mbase_sh, bbase_sh;
+    __shared__ uint32_t wsum[FL_THREADS / 32];
+    const int t = threadIdx.x, T = (int)blockDim.x;
+    const int lane = t & 31, wp = t >> 5, nwarps = T >> 5;
+    // each thread owns a contiguous range of slots; the value of a slot is
+    // members << 16 | 1 when its group yields a bucket
+    const int per = (tsize + T - 1) / T;
+    const int s0 = t * per < tsize ? t * per : tsize;
+    const int s1 = s0 + per < tsize ? s0 + per : tsize;
+    auto slot_value = [&](int slot) -> uint32_t {
+        if (tkey[slot] == FL_EMPTY)
+            return 0u;
+        const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
+        const bool ok = nz ? (nA > 0 && nB > 0) : (nA > 1);
+        return ok ? ((nA + nB) << 16) | 1u : 0u;
+    };
+    uint32_t mysum = 0;
+    for (int slot = s0; slot < s1; ++slot)
+        mysum += slot_value(slot);
+    uint32_t incl = mysum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    if (lane == 31)
+        wsum[wp] = incl;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int i = 0; i < nwarps; ++i) {
+        before += (i < wp) ? wsum[i] : 0u;
+        total += wsum[i];
+    }
+    if (t == 0) {
+        const uint32_t mt = total >> 16, bt = total & 0xFFFFu;
+        mbase_sh = bt ? atomicAdd(g.members_count, mt) : 0u;
+        bbase_sh = bt ? atomicAdd(g.nbuckets, bt) : 0u;
+        if (bt && ((uint64_t)mbase_sh + mt > g.mcap || (uint64_t)bbase_sh + bt > g.bcap)) {
+            atomicOr(g.overflow, 2);      // host grows the space and redoes the search
+            mbase_sh = 0xFFFFFFFFu;
+        } else if (bt) {
+            atomicAdd(g.members_total, (unsigned long long)mt);
+        }
+    }
+    __syncthreads();
+    if (mbase_sh == 0xFFFFFFFFu)
+        return false;
+    uint32_t run_off = before + incl - mysum;
+    for (int slot = s0; slot < s1; ++slot) {
+        const uint32_t v = slot_value(slot);
+        if (v) {
+            const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
+            const uint32_t base = mbase_sh + (run_off >> 16);
+            const uint32_t bi = bbase_sh + (run_off & 0xFFFFu);
+            g.buckets[bi] = Bucket{base, nA, nz ? nB : 0u, (uint32_t)b};
+            g.pair_counts[bi] = nz ? (uint64_t)nA * nB : (uint64_t)nA * (nA - 1) / 2;
+            curA[slot] = base + nA;          // end of side A: cursor counts down
+            tcnt[slot] = base + nA + nB;     // end of side B
+        } else {
+            tcnt[slot] = FL_EMPTY;
+        }
+        run_off += v;
+    }
+    __syncthreads();
+    return true;
+}
 
 // Groups the s <= SMAX survivors (Kc << 32 | j) in sv on chip: a hash table
 // of group keys with packed side counts (tkey / tcnt); each group with
@@ -141,13 +221,7 @@ template <class Lay>
 __device__ __forceinline__ void group_on_chip(uint64_t *sv, uint32_t s, uint32_t *tkey, uint32_t *tcnt, bool nz,
                                               int b, const GroupOut &g)
 {
-    __shared__ uint32_t mbase_sh, bbase_sh;
-    __shared__ uint32_t wsum[FL_THREADS / 32];
     const int t = threadIdx.x, T = (int)blockDim.x;
-    const int lane = t & 31, wp = t >> 5, nwarps = T >> 5;
-    uint32_t *members = g.members;
-    Bucket *buckets = g.buckets;
-    uint64_t *pair_counts = g.pair_counts;
     // grouping on chip in the table (the keep mask and, for one
     // response, the filter are dead)
     // table of 2^tlog slots, at least 4/3 of the survivors (load <= 3/4)
@@ -165,12 +239,12 @@ __device__ __forceinline__ void group_on_chip(uint64_t *sv, uint32_t s, uint32_t
     for (uint32_t i = t; i < s; i += T) {
         const uint64_t e = sv[i];
         const uint32_t Kc = (uint32_t)(e >> 32);
-        const uint32_t g = nz ? (Kc >> 1) : Kc;
+        const uint32_t gk = nz ? (Kc >> 1) : Kc;
         const uint32_t side = nz ? (Kc & 1u) : 0u;
-        uint32_t slot = (g * 0x9E3779B1u) >> (32 - tlog);
+        uint32_t slot = (gk * 0x9E3779B1u) >> (32 - tlog);
         for (int probe = 0; probe < tsize; ++probe) {    // s < tsize: always ends
-            const uint32_t old = atomicCAS(&tkey[slot], FL_EMPTY, g);
-            if (old == FL_EMPTY || old == g)
+            const uint32_t old = atomicCAS(&tkey[slot], FL_EMPTY, gk);
+            if (old == FL_EMPTY || old == gk)
                 break;
             slot = (slot + 1) & (tsize - 1);
         }
@@ -178,71 +252,9 @@ __device__ __forceinline__ void group_on_chip(uint64_t *sv, uint32_t s, uint32_t
         sv[i] = ((uint64_t)((side << 31) | slot) << 32) | (uint32_t)e;
     }
     __syncthreads();
-    // phase II: groups with candidates -> buckets; one global atomic
-    // pair per (run, response) reserves their space.  Afterwards
-    // tkey / tcnt of a bucket's slot are the end cursors of its sides
-    // A / B, and tcnt is FL_EMPTY for a slot without a bucket.
-    {
-        // each thread owns a contiguous range of slots; the value of
-        // a slot is members << 16 | 1 when its group yields a bucket
-        const int per = (tsize + T - 1) / T;
-        const int s0 = t * per < tsize ? t * per : tsize;
-        const int s1 = s0 + per < tsize ? s0 + per : tsize;
-        auto slot_value = [&](int slot) -> uint32_t {
-            if (tkey[slot] == FL_EMPTY)
-                return 0u;
-            const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
-            const bool ok = nz ? (nA > 0 && nB > 0) : (nA > 1);
-            return ok ? ((nA + nB) << 16) | 1u : 0u;
-        };
-        uint32_t mysum = 0;
-        for (int slot = s0; slot < s1; ++slot)
-            mysum += slot_value(slot);
-        uint32_t incl = mysum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o)
-                incl += y;
-        }
-        if (lane == 31)
-            wsum[wp] = incl;
-        __syncthreads();
-        uint32_t before = 0, total = 0;
-        for (int i = 0; i < nwarps; ++i) {
-            before += (i < wp) ? wsum[i] : 0u;
-            total += wsum[i];
-        }
-        if (t == 0) {
-            const uint32_t mt = total >> 16, bt = total & 0xFFFFu;
-            mbase_sh = bt ? atomicAdd(g.members_count, mt) : 0u;
-            bbase_sh = bt ? atomicAdd(g.nbuckets, bt) : 0u;
-            if (bt && ((uint64_t)mbase_sh + mt > g.mcap || (uint64_t)bbase_sh + bt > g.bcap)) {
-                atomicOr(g.overflow, 2);      // host grows the space and redoes the search
-                mbase_sh = 0xFFFFFFFFu;
-            }
-        }
-        __syncthreads();
-        if (mbase_sh == 0xFFFFFFFFu)
-            return;          // the host grows the space and redoes the search
-        uint32_t run_off = before + incl - mysum;
-        for (int slot = s0; slot < s1; ++slot) {
-            const uint32_t v = slot_value(slot);
-            if (v) {
-                const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
-                const uint32_t base = mbase_sh + (run_off >> 16);
-                const uint32_t bi = bbase_sh + (run_off & 0xFFFFu);
-                buckets[bi] = Bucket{base, nA, nz ? nB : 0u, (uint32_t)b};
-                pair_counts[bi] = nz ? (uint64_t)nA * nB : (uint64_t)nA * (nA - 1) / 2;
-                tkey[slot] = base + nA;          // end of side A: cursor counts down
-                tcnt[slot] = base + nA + nB;     // end of side B
-            } else {
-                tcnt[slot] = FL_EMPTY;
-            }
-            run_off += v;
-        }
-    }
-    __syncthreads();
+    // phase II (the keys are not needed afterwards: tkey holds the side-A cursors)
+    if (!assign_buckets(tkey, tcnt, tkey, tsize, nz, b, g))
+        return;              // the host grows the space and redoes the search
     // phase III: members, side A first
     for (uint32_t i = t; i < s; i += T) {
         const uint64_t e = sv[i];
@@ -251,9 +263,99 @@ __device__ __forceinline__ void group_on_chip(uint64_t *sv, uint32_t s, uint32_t
         if (tcnt[slot] == FL_EMPTY)
             continue;
         const uint32_t pos = atomicSub((hi >> 31) ? &tcnt[slot] : &tkey[slot], 1u) - 1u;
-        members[pos] = (uint32_t)e;
+        g.members[pos] = (uint32_t)e;
     }
     __syncthreads();
+}
+
+// The same grouping for a bin too large for sv, its n < 2^16 entries
+// (Kc << 32 | j) read from global memory E: the table (all 2^LOGT slots)
+// holds its distinct group keys, so it works whenever those number at most
+// 3/4 of the table, however many entries share them (one group of tens of
+// thousands of low-minor-frequency columns, say).  Phase III finds each
+// entry's slot by probing again, so the side-A cursors go to curA (shared
+// memory of 2^LOGT words outside the table).  Returns false, with nothing
+// written, when the distinct keys did not fit.  Called by every thread.
+template <class Lay>
+__device__ __forceinline__ bool group_stream(const uint64_t *E, uint32_t n, uint32_t *tkey, uint32_t *tcnt,
+                                             uint32_t *curA, bool nz, int b, const GroupOut &g)
+{
+    __shared__ uint32_t ndist, fail;
+    constexpr int GS = 4;                 // entries per thread and step (loads in flight)
+    const int t = threadIdx.x, T = (int)blockDim.x;
+    const int tsize = Lay::T;
+    const uint32_t limit = (uint32_t)(3 * tsize / 4);
+    for (int i = t; i < tsize; i += T) {
+        tkey[i] = FL_EMPTY;
+        tcnt[i] = 0;
+    }
+    if (t == 0) {
+        ndist = 0;
+        fail = 0;
+    }
+    __syncthreads();
+    // phase I: distinct keys into the table; a thread stops inserting once it
+    // sees the limit passed, so at most limit + T slots are ever taken
+    for (uint32_t i0 = t; i0 - t < n; i0 += GS * (uint32_t)T) {
+        uint64_t e[GS];
+#pragma unroll
+        for (int u = 0; u < GS; ++u) {
+            const uint32_t i = i0 + u * (uint32_t)T;
+            e[u] = i < n ? E[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < GS; ++u) {
+            if (i0 + u * (uint32_t)T >= n || *(volatile uint32_t *)&fail)
+                continue;
+            const uint32_t Kc = (uint32_t)(e[u] >> 32);
+            const uint32_t gk = nz ? (Kc >> 1) : Kc;
+            const uint32_t side = nz ? (Kc & 1u) : 0u;
+            uint32_t slot = (gk * 0x9E3779B1u) >> (32 - Lay::LOGT);
+            for (int probe = 0; probe < tsize; ++probe) {
+                const uint32_t old = atomicCAS(&tkey[slot], FL_EMPTY, gk);
+                if (old == FL_EMPTY) {
+                    if (atomicAdd(&ndist, 1u) + 1u > limit)
+                        fail = 1;
+                    break;
+                }
+                if (old == gk)
+                    break;
+                slot = (slot + 1) & (tsize - 1);
+            }
+            atomicAdd(&tcnt[slot], side ? 1u : 0x10000u);
+        }
+    }
+    __syncthreads();
+    if (fail)
+        return false;
+    if (!assign_buckets(tkey, tcnt, curA, tsize, nz, b, g))
+        return true;         // the host grows the space and redoes the search
+    // phase III: members, side A first; each entry's slot found again
+    for (uint32_t i0 = t; i0 - t < n; i0 += GS * (uint32_t)T) {
+        uint64_t e[GS];
+#pragma unroll
+        for (int u = 0; u < GS; ++u) {
+            const uint32_t i = i0 + u * (uint32_t)T;
+            e[u] = i < n ? E[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < GS; ++u) {
+            if (i0 + u * (uint32_t)T >= n)
+                continue;
+            const uint32_t Kc = (uint32_t)(e[u] >> 32);
+            const uint32_t gk = nz ? (Kc >> 1) : Kc;
+            const uint32_t side = nz ? (Kc & 1u) : 0u;
+            uint32_t slot = (gk * 0x9E3779B1u) >> (32 - Lay::LOGT);
+            for (int probe = 0; probe < tsize && tkey[slot] != gk; ++probe)
+                slot = (slot + 1) & (tsize - 1);
+            if (tcnt[slot] == FL_EMPTY)
+                continue;
+            const uint32_t pos = atomicSub(side ? &tcnt[slot] : &curA[slot], 1u) - 1u;
+            g.members[pos] = (uint32_t)e[u];
+        }
+    }
+    __syncthreads();
+    return true;
 }
 
 // The s entries of one (run, response) at seg[seg0 ..) -- key runbits | Kc
@@ -354,6 +456,145 @@ __device__ __forceinline__ bool group_from_segment(const uint64_t *okeys, const 
     return true;
 }
 
+// The s entries of one run at seg[seg0 ..) -- key runbits | Kc and the
+// entry's place in the class lists (class << 27 | index, its column at
+// xlat[class * xcap + index]) -- grouped on chip with one counting sort by
+// a hash of the group key (32 bins) into tmp (tmp_cap entries of global
+// memory, Kc << 32 | column): the entries of contiguous bin ranges of at
+// most SMAX entries are then copied to sv and grouped there, and a bin
+// above SMAX is grouped straight from tmp (group_stream).  A bin whose
+// distinct group keys do not fit the table is written back to the segment
+// (runbits | Kc, column) for the general sort and join.  Returns the number
+// of entries left in the segment at seg0 (their values are columns), or
+// GS_NONE when nothing was done because the run overflowed the segment or
+// s > tmp_cap (the segment then still holds list places: in the first case
+// the host redoes the search with larger segments, in the second the caller
+// looks the columns up).  Called by every thread of the CTA.
+constexpr uint32_t GS_NONE = 0xFFFFFFFFu;
+template <class Lay>
+__device__ __forceinline__ uint32_t group_segment_sorted(uint64_t *okeys, uint32_t *ovals, uint32_t seg0,
+                                                         uint32_t s, uint32_t seg_cap, uint32_t kcmask,
+                                                         uint64_t runbits, uint64_t *sv, uint32_t *tkey,
+                                                         uint32_t *tcnt, bool nz, int b, const GroupOut &g,
+                                                         const uint32_t *xlat, uint32_t xcap, uint64_t *tmp,
+                                                         uint32_t tmp_cap)
+{
+    __shared__ uint32_t bstart[33];     // bin q of tmp: [bstart[q], bstart[q + 1])
+    __shared__ uint32_t wsum2[FL_THREADS / 32];
+    __shared__ uint32_t left_sh;
+    constexpr int GB = 4;               // entries per thread and step (loads in flight)
+    constexpr uint32_t SMAX = (uint32_t)Lay::SMAX;
+    const int t = threadIdx.x, T = (int)blockDim.x;
+    const int lane = t & 31, wp = t >> 5, nwarps = T >> 5;
+    if ((uint64_t)seg0 + s > seg_cap || s > tmp_cap)
+        return GS_NONE;
+    // per-warp bin counts, then cursors, in the survivor array's memory:
+    // entry i is taken by thread i mod T in both passes, so by one warp
+    uint32_t *hw = reinterpret_cast<uint32_t *>(sv);          // [nwarps][32]
+    if (t < 32 * nwarps)
+        hw[t] = 0;
+    if (t == 0)
+        left_sh = 0;
+    __syncthreads();
+    auto bin_of = [&](uint32_t Kc) -> uint32_t { return mix32(nz ? (Kc >> 1) : Kc) >> 27; };
+    for (uint32_t i0 = t; i0 - t < s; i0 += GB * (uint32_t)T) {
+        uint32_t Kc[GB];
+#pragma unroll
+        for (int u = 0; u < GB; ++u) {
+            const uint32_t i = i0 + u * (uint32_t)T;
+            Kc[u] = i < s ? (uint32_t)(okeys[seg0 + i] & kcmask) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < GB; ++u)
+            if (i0 + u * (uint32_t)T < s)
+                atomicAdd(&hw[wp * 32 + bin_of(Kc[u])], 1u);
+    }
+    __syncthreads();
+    // exclusive scan in (bin, warp) order: thread t holds bin t / nwarps of
+    // warp t % nwarps (32 * nwarps == T entries, one per thread)
+    {
+        const uint32_t bn = (uint32_t)t / nwarps, w = (uint32_t)t % nwarps;
+        const uint32_t v = hw[w * 32 + bn];
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        if (lane == 31)
+            wsum2[wp] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int i = 0; i < wp; ++i)
+            before += wsum2[i];
+        const uint32_t ex = before + incl - v;
+        hw[w * 32 + bn] = ex;                   // every thread read its v before the barrier
+        if (w == 0)
+            bstart[bn] = ex;
+        if (t == T - 1)
+            bstart[32] = ex + v;
+    }
+    __syncthreads();
+    // scatter to tmp, columns looked up on the way
+    for (uint32_t i0 = t; i0 - t < s; i0 += GB * (uint32_t)T) {
+        uint32_t Kc[GB], v[GB];
+#pragma unroll
+        for (int u = 0; u < GB; ++u) {
+            const uint32_t i = i0 + u * (uint32_t)T;
+            Kc[u] = i < s ? (uint32_t)(okeys[seg0 + i] & kcmask) : 0u;
+            v[u] = i < s ? ovals[seg0 + i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < GB; ++u)
+            if (i0 + u * (uint32_t)T < s)
+                v[u] = xlat[(int64_t)(v[u] >> 27) * xcap + (v[u] & 0x7FFFFFFu)];
+#pragma unroll
+        for (int u = 0; u < GB; ++u) {
+            if (i0 + u * (uint32_t)T < s) {
+                const uint32_t pos = atomicAdd(&hw[wp * 32 + bin_of(Kc[u])], 1u);
+                tmp[pos] = ((uint64_t)Kc[u] << 32) | v[u];
+            }
+        }
+    }
+    __syncthreads();
+    // bin ranges of at most SMAX entries through sv; larger bins streamed
+    uint32_t *curA = reinterpret_cast<uint32_t *>(sv);    // side-A cursors of group_stream
+    for (uint32_t bn = 0; bn < 32;) {
+        const uint32_t nbin = bstart[bn + 1] - bstart[bn];
+        if (nbin > SMAX) {
+            const uint64_t *E = tmp + bstart[bn];
+            if (nbin >= 65536u || !group_stream<Lay>(E, nbin, tkey, tcnt, curA, nz, b, g)) {
+                // back to the segment for the general path
+                const uint32_t at = left_sh;
+                for (uint32_t i = t; i < nbin; i += (uint32_t)T) {
+                    const uint64_t e = E[i];
+                    okeys[seg0 + at + i] = runbits | (uint64_t)(uint32_t)(e >> 32);
+                    ovals[seg0 + at + i] = (uint32_t)e;
+                }
+                __syncthreads();
+                if (t == 0)
+                    left_sh = at + nbin;
+                __syncthreads();
+            }
+            ++bn;
+            continue;
+        }
+        uint32_t be = bn + 1;
+        while (be < 32 && bstart[be + 1] - bstart[bn] <= SMAX)
+            ++be;
+        const uint32_t n0 = bstart[bn], cnt = bstart[be] - n0;
+        for (uint32_t i = t; i < cnt; i += (uint32_t)T)
+            sv[i] = tmp[n0 + i];
+        __syncthreads();
+        if (cnt)
+            group_on_chip<Lay>(sv, cnt, tkey, tcnt, nz, b, g);
+        bn = be;
+    }
+    __syncthreads();
+    return left_sh;
+}
+
 // One CTA per run at a time (passes 1-2 as described at the top of the
 // file).  When the run keeps at most FL_SMAX columns they are grouped on
 // chip: a hash table of group keys with packed side counts, each group
@@ -410,7 +651,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     __shared__ uint32_t scur;           // survivor array fill after refinement
     const int T = (int)blockDim.x;      // a multiple of 32, at most FL_THREADS
     __shared__ uint32_t seg0_sh;        // first segment entry of the current (run, response)
-    const GroupOut gout{members, members_count, buckets, pair_counts, nbuckets, mcap, bcap, overflow};
+    const GroupOut gout{members, members_count, buckets, pair_counts, nbuckets, mcap, bcap, overflow, kept + 1};
     uint32_t *kcs = kc_scratch + (int64_t)blockIdx.x * 32 * P;
     SegKey *okeys = reinterpret_cast<SegKey *>(seg_keys_v) + (int64_t)blockIdx.x * seg_cap;
     uint32_t *ovals = seg_vals + (int64_t)blockIdx.x * seg_cap;
@@ -822,7 +1063,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     __shared__ int64_t dstoff[16];                 // list index of staged entry i of class q: dstoff[q] + i
     __shared__ uint32_t wsum[FL_THREADS / 32];
     __shared__ int item_sh, lovf_sh;
-    const GroupOut gout{members, members_count, buckets, pair_counts, nbuckets, mcap, bcap, overflow};
+    const GroupOut gout{members, members_count, buckets, pair_counts, nbuckets, mcap, bcap, overflow, kept + 1};
     const uint32_t P32 = (uint32_t)P, p32 = (uint32_t)p;
     const int fshift = 32 - (FL_LOGF - 5);
     const uint32_t kcmask = (1u << M) - 1u;                                  // M <= 28
@@ -1113,30 +1354,37 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         if (t == 0)
             atomicAdd(kept, (unsigned long long)s);
         __syncthreads();                     // every thread has read the cursor
-        if (group_from_segment<Lay>(okeys, ovals, seg0, s, seg_cap, part_max, kcmask, sv, tkey, tcnt, nz, 0,
-                                    gout, lc, lcap)) {
-            if (t == 0)
-                cursor = seg0;               // grouped on chip: the entries leave the segment
-        } else {
-            // left for the general path: the columns in place of the list places
-            const uint32_t sn = seg0 >= seg_cap ? 0u : (s < seg_cap - seg0 ? s : seg_cap - seg0);
-            for (uint32_t i0 = t; i0 - t < sn; i0 += 4 * (uint32_t)T) {
+        // the keys list is dead after the rounds: the run's entries are
+        // sorted by bin there (the columns list is still read)
+        uint32_t left = part_max > 0
+            ? group_segment_sorted<Lay>(okeys, ovals, seg0, s, seg_cap, kcmask, runbits, sv, tkey, tcnt, nz, 0,
+                                        gout, lc, lcap, reinterpret_cast<uint64_t *>(lk), 8 * lcap)
+            : GS_NONE;
+        if (left == GS_NONE && (uint64_t)seg0 + s <= seg_cap) {
+            // nothing grouped (no on-chip grouping, or more entries than the
+            // sort room): the columns in place of the list places
+            for (uint32_t i0 = t; i0 - t < s; i0 += 4 * (uint32_t)T) {
                 uint32_t v[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const uint32_t i = i0 + u * (uint32_t)T;
-                    v[u] = i < sn ? ovals[seg0 + i] : 0u;
+                    v[u] = i < s ? ovals[seg0 + i] : 0u;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (i0 + u * (uint32_t)T < sn)
+                    if (i0 + u * (uint32_t)T < s)
                         v[u] = lc[(int64_t)(v[u] >> FB_QSHIFT) * lcap + (v[u] & ((1u << FB_QSHIFT) - 1u))];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (i0 + u * (uint32_t)T < sn)
+                    if (i0 + u * (uint32_t)T < s)
                         ovals[seg0 + i0 + u * (uint32_t)T] = v[u];
             }
         }
+        if (left == GS_NONE)
+            left = s;
+        __syncthreads();
+        if (t == 0)
+            cursor = seg0 + left;            // what the chip could not group stays for the general path
     }
     if (t == 0) {
         seg_count[blockIdx.x] = cursor < seg_cap ? cursor : seg_cap;

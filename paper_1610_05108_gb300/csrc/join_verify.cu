@@ -130,7 +130,7 @@ __device__ __forceinline__ int32_t word_weight(const uint32_t *__restrict__ plan
 }
 
 template <bool BATCH, bool WEIGHTED, int VQ>
-__global__ void __launch_bounds__(JV_THREADS, (VQ == 2 && !WEIGHTED) ? 5 : 1)   // 5: 48 registers
+__global__ void __launch_bounds__(JV_THREADS, (VQ == 2 && !WEIGHTED) ? 5 : (!WEIGHTED ? 3 : 1))   // 5: 48, 3: 80 registers
     verify_kernel(const uint32_t *__restrict__ Xc, int64_t Wp, const uint32_t *__restrict__ yb,
                   const Bucket *__restrict__ buckets, const uint64_t *__restrict__ pair_off,
                   const uint32_t *__restrict__ nbuckets, const uint64_t *__restrict__ total_pairs,

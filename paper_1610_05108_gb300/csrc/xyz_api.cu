@@ -446,7 +446,8 @@ int ensure_records(xyz_ctx *c, int B)
 // and member counts; per search the spill count and overflow flags, the
 // spill-path bucket count, the record and output counts, the error flag,
 // the group's candidate total, the candidate sum, the spill total, the
-// filter's work-item counter and the columns the filter kept.
+// filter's work-item counter, the columns the filter kept and the bucket
+// members the on-chip grouping wrote.
 uint32_t *ctr_u32(xyz_ctx *c) { return reinterpret_cast<uint32_t *>(c->counters.ptr); }
 uint32_t *ctr_nbuckets(xyz_ctx *c) { return ctr_u32(c) + 0; }
 uint32_t *ctr_members(xyz_ctx *c) { return ctr_u32(c) + 1; }
@@ -797,14 +798,15 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
             CU(launch_weighted_strengths(c->pk, (PairOut *)c->out.ptr, ctr_nout(c), (int64_t)nrec, c->stream,
                                          &launches));
         uint32_t nout = 0;
-        unsigned long long kept = 0;
+        unsigned long long kept[2] = {0, 0};
         CU(cudaMemcpyAsync(&nout, ctr_nout(c), 4, cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaMemcpyAsync(&kept, ctr_kept(c), 8, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(kept, ctr_kept(c), 16, cudaMemcpyDeviceToHost, c->stream));
         CU(cudaStreamSynchronize(c->stream));
         if (nrec == 0)
             nout = 0;
         st.attempts = attempt + 1;
-        st.filter_kept = pl.filter ? (int64_t)kept : 0;
+        st.filter_kept = pl.filter ? (int64_t)kept[0] : 0;
+        st.bucket_members = pl.filter ? (int64_t)kept[1] : 0;
         st.runs = runs;
         st.chunks = chunks;
         st.runs_per_chunk = pl.R;

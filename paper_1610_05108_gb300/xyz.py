@@ -42,7 +42,7 @@ class Stats(ctypes.Structure):
             "ms_keys", "ms_sort", "ms_join", "ms_verify", "ms_dedup", "ms_total")] + \
         [(name, ctypes.c_int64) for name in (
             "launches_keys", "launches_sort", "launches_join", "launches_verify", "launches_dedup",
-            "survivors", "filter_kept", "attempts")]
+            "survivors", "filter_kept", "attempts", "bucket_members")]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

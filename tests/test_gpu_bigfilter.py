@@ -150,3 +150,45 @@ def test_filter_mode_argument_check(xyz):
         with pytest.raises(xyz.XyzError) as e:
             ctx.set_filter(3)
         assert e.value.code == xyz.XYZ_EINVAL
+
+
+def test_class_split_huge_group_grouped_from_global_memory(xyz, orc):
+    # 9000 identical columns v and two columns v o Y: one group of 9002
+    # members -- its hash bin is larger than the on-chip survivor array, so
+    # the bin is grouped straight from the bin-sorted copy of the run's
+    # survivors (its distinct keys fit the table); nothing is left for the
+    # sort path, and every run's candidates equal the oracle's.
+    n, p = 64, 100000
+    X, Y = _rand(n, p, 81)
+    rng = np.random.default_rng(82)
+    v = (rng.integers(0, 2, size=n, dtype=np.int8) * 2 - 1).astype(np.int8)
+    X[:, 1000:10000] = v[:, None]
+    X[:, 20000] = v * Y
+    X[:, 70000] = v * Y
+    L, M, kappa, seed = 3, 20, 0.3, 8
+    want = orc.xyz(X, Y, L, M, kappa, seed)
+    with xyz.create(X, Y) as ctx:
+        ctx.set_filter(2)
+        got = _pairs(ctx.search(L, M, kappa, seed))
+        st = ctx.stats()
+        assert st["survivors"] == 0 and st["bucket_members"] >= 9002
+        for run in (0, 2):
+            assert np.array_equal(ctx.run_candidates(M, seed, run), orc.candidates(X, Y, M, seed, run)), run
+    assert len(want) > 0
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("M", [18, 24])
+def test_class_split_every_column_survives(xyz, orc, M):
+    # Y = +1: c = 0 in every run and every column survives (600000 per run,
+    # more than the room for sorting a run's survivors by bin), so the runs
+    # go to the general sort; the candidates equal the oracle's.
+    n, p = 32, 600000
+    X, _ = _rand(n, p, 91)
+    Y = np.ones(n, np.int8)
+    seed = 12
+    with xyz.create(X, Y) as ctx:
+        for run in (0, 1):
+            got = ctx.run_candidates(M, seed, run)
+            assert ctx.stats()["survivors"] > 0
+            assert np.array_equal(got, orc.candidates(X, Y, M, seed, run)), run
