@@ -100,6 +100,8 @@ typedef struct xyz_stats {
     int64_t filter_kept;      /* columns kept by the survivor filter, summed over runs (0 without it) */
     int64_t attempts;         /* 1, plus one for every redo after a buffer grew */
     int64_t bucket_members;   /* columns in buckets grouped on chip, summed over runs (spilled runs excluded) */
+    int64_t segment_grouped_runs; /* runs past one on-chip grouping, grouped on chip from the segment
+                                     in several passes (hash partitions or bins) instead of the sort */
 } xyz_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -960,8 +960,10 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                     // partitions when they fit, else left to the general path
                     if (group_from_segment<Lay>(okeys, ovals, seg0_sh, s, seg_cap, part_max, kcmask, sv, tkey,
                                                 tcnt, nz, b, gout) &&
-                        t == 0)
+                        t == 0) {
                         cursor = seg0_sh;           // grouped on chip: the entries leave the segment
+                        atomicAdd(kept + 2, 1ull);  // one more run grouped from the segment
+                    }
                     continue;
                 }
             }
@@ -1382,6 +1384,8 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         }
         if (left == GS_NONE)
             left = s;
+        else if (t == 0 && s > (uint32_t)Lay::SMAX)
+            atomicAdd(kept + 2, 1ull);       // one more run grouped from the segment in several passes
         __syncthreads();
         if (t == 0)
             cursor = seg0 + left;            // what the chip could not group stays for the general path

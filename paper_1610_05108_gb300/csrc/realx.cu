@@ -55,25 +55,29 @@ __global__ void scale_kernel(const float *__restrict__ X, int64_t n, int64_t p, 
     }
 }
 
-// Y'_i = Y_i nu_i^2 (double) and its float copy for the verification.
+// Y'_i = Y_i nu_i^2 (double), and its copy padded to the column pitch for
+// the verification.
 __global__ void yprime_kernel(const double *__restrict__ Y, const unsigned *__restrict__ numax, int64_t n,
-                              double *__restrict__ yp, float *__restrict__ ysf)
+                              double *__restrict__ yp, double *__restrict__ ysd)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const double nu = (double)__uint_as_float(numax[i]);
         const double v = Y[i] * (nu * nu);
         yp[i] = v;
-        ysf[i] = (float)v;
+        ysd[i] = v;
     }
 }
 
 // Candidate verification with the real inner product: the candidate
 // decoding of the binary verification (32 consecutive candidates per warp,
 // bucket window search), then eight lanes per candidate summing
-// Y'_i X'_ij X'_ik over 16-byte pieces of the float columns.
+// Y'_i (X'_ij X'_ik) over 16-byte pieces of the float columns, in double:
+// the product of two floats is exact in double, so every term equals the
+// oracle's and the sums differ only by the order of the additions (relative
+// error below n 2^-52 of sum |terms| <= ||Y'||_1).
 __global__ void __launch_bounds__(RX_THREADS)
-    verify_real_kernel(const float *__restrict__ Xcs, int64_t Wf, const float *__restrict__ ysf, float kq,
+    verify_real_kernel(const float *__restrict__ Xcs, int64_t Wf, const double *__restrict__ ysd, double kq,
                        const Bucket *__restrict__ buckets, const uint64_t *__restrict__ pair_off,
                        const uint32_t *__restrict__ nbuckets, const uint64_t *__restrict__ total_pairs,
                        const uint32_t *__restrict__ vals, int kbits, uint64_t *__restrict__ rec_keys,
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(RX_THREADS)
     const int lane = threadIdx.x & 31;
     const int sub = lane & 7;
     const int nq = (int)(Wf >> 2);
-    const float4 *y4 = reinterpret_cast<const float4 *>(ysf);
+    const double2 *y2 = reinterpret_cast<const double2 *>(ysd);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < T; t0 += stride) {
         uint32_t base = 0;
@@ -132,26 +136,28 @@ __global__ void __launch_bounds__(RX_THREADS)
                 k = vals[B.start + y];
             }
         }
-        float dot = 0.0f;
+        double dot = 0.0;
 #pragma unroll
         for (int st = 0; st < 8; ++st) {
             const int cidx = 4 * st + (lane >> 3);
             const uint32_t jj = __shfl_sync(FULL, j, cidx);
             const uint32_t kk = __shfl_sync(FULL, k, cidx);
             const bool vv = __shfl_sync(FULL, (int)valid, cidx) != 0;
-            float part = 0.0f;
+            double part = 0.0;
             if (vv) {
                 const float4 *cj = reinterpret_cast<const float4 *>(Xcs + (int64_t)jj * Wf);
                 const float4 *ck = reinterpret_cast<const float4 *>(Xcs + (int64_t)kk * Wf);
                 for (int q = sub; q < nq; q += 8) {
-                    const float4 a = __ldg(cj + q), b = __ldg(ck + q), y = __ldg(y4 + q);
-                    part += y.x * a.x * b.x + y.y * a.y * b.y + y.z * a.z * b.z + y.w * a.w * b.w;
+                    const float4 a = __ldg(cj + q), b = __ldg(ck + q);
+                    const double2 y0 = __ldg(y2 + 2 * q), y1 = __ldg(y2 + 2 * q + 1);
+                    part += y0.x * ((double)a.x * (double)b.x) + y0.y * ((double)a.y * (double)b.y) +
+                            y1.x * ((double)a.z * (double)b.z) + y1.y * ((double)a.w * (double)b.w);
                 }
             }
             part += __shfl_xor_sync(FULL, part, 4);
             part += __shfl_xor_sync(FULL, part, 2);
             part += __shfl_xor_sync(FULL, part, 1);
-            const float got = __shfl_sync(FULL, part, 8 * (lane & 3));
+            const double got = __shfl_sync(FULL, part, 8 * (lane & 3));
             if ((lane >> 2) == st)
                 dot = got;
         }
@@ -168,7 +174,7 @@ __global__ void __launch_bounds__(RX_THREADS)
 
 // Reported values of the output pairs: agree = -1 (no agreement count for
 // real X), strength = sum_i Y'_i X'_ij X'_ik / ||Y'||_1; one warp per pair.
-__global__ void real_strength_kernel(const float *__restrict__ Xcs, int64_t Wf, const float *__restrict__ ysf,
+__global__ void real_strength_kernel(const float *__restrict__ Xcs, int64_t Wf, const double *__restrict__ ysd,
                                      double rnorm, PairOut *__restrict__ out, const uint32_t *__restrict__ nout)
 {
     const int lane = threadIdx.x & 31;
@@ -179,7 +185,7 @@ __global__ void real_strength_kernel(const float *__restrict__ Xcs, int64_t Wf, 
         const int64_t j = out[t].j, k = out[t].k;
         double s = 0.0;
         for (int64_t i = lane; i < Wf; i += 32)
-            s += (double)ysf[i] * ((double)Xcs[j * Wf + i] * (double)Xcs[k * Wf + i]);
+            s += ysd[i] * ((double)Xcs[j * Wf + i] * (double)Xcs[k * Wf + i]);
         for (int o = 16; o > 0; o >>= 1)
             s += __shfl_xor_sync(FULL, s, o);
         if (lane == 0) {
@@ -220,13 +226,13 @@ cudaError_t launch_unbiased_scale(const float *dX, int64_t n, int64_t p, int64_t
 }
 
 cudaError_t launch_unbiased_y(const double *dY, const float *nu, int64_t n, int64_t Wf, double *yprime,
-                              float *ysf, cudaStream_t s, int64_t *launches)
+                              double *ysd, cudaStream_t s, int64_t *launches)
 {
-    cudaError_t e = cudaMemsetAsync(ysf, 0, (size_t)Wf * sizeof(float), s);
+    cudaError_t e = cudaMemsetAsync(ysd, 0, (size_t)Wf * sizeof(double), s);
     if (e != cudaSuccess)
         return e;
     yprime_kernel<<<grid_of(n, 4096), RX_THREADS, 0, s>>>(dY, reinterpret_cast<const unsigned *>(nu), n, yprime,
-                                                         ysf);
+                                                         ysd);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -240,7 +246,7 @@ cudaError_t launch_verify_real(const Packed &pk, const Bucket *buckets, const ui
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     verify_real_kernel<<<(unsigned)((sms > 0 ? sms : 152) * 8), RX_THREADS, 0, s>>>(
-        pk.Xcs, pk.Wf, pk.ysf, pk.rkq, buckets, pair_off, nbuckets, total_pairs, vals, kbits, rec_keys, rec_agree,
+        pk.Xcs, pk.Wf, pk.ysd, pk.rkq, buckets, pair_off, nbuckets, total_pairs, vals, kbits, rec_keys, rec_agree,
         nrec, rec_cap, abort_flag);
     *launches += 1;
     return cudaGetLastError();
@@ -251,7 +257,7 @@ cudaError_t launch_real_strengths(const Packed &pk, PairOut *out, const uint32_t
 {
     if (cap <= 0)
         return cudaSuccess;
-    real_strength_kernel<<<grid_of(cap * 32, 4096), RX_THREADS, 0, s>>>(pk.Xcs, pk.Wf, pk.ysf, pk.rnorm, out,
+    real_strength_kernel<<<grid_of(cap * 32, 4096), RX_THREADS, 0, s>>>(pk.Xcs, pk.Wf, pk.ysd, pk.rnorm, out,
                                                                        nout);
     *launches += 1;
     return cudaGetLastError();

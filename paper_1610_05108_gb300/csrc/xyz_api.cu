@@ -102,7 +102,7 @@ struct xyz_ctx {
     DevBuf wq, wcdf, wplanes, wq2, wcdf2, wplanes2, wmeta, wscan, yreal;
     int w_exp = 0;               // max|Y| = f 2^w_exp, f in [0.5, 1)
     // real X through the unbiased transform (Section 3.2)
-    DevBuf xrs, xcs, xnu, ypr, ysf, ysf2, rbad;
+    DevBuf xrs, xcs, xnu, ypr, ysd, ysd2, rbad;
     DevBuf vstart;               // verification: bucket of each block of 32 candidates
     DevBuf pXc, pXr, pyb, pbad;  // packed X, response bits, input-check flag (owned contexts)
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
@@ -203,7 +203,7 @@ static int64_t ws_bytes(const xyz_ctx *c)
                            &c->resp, &c->ybs, &c->y_alt, &c->y_stage,
                            &c->wq, &c->wcdf, &c->wplanes, &c->wq2, &c->wcdf2, &c->wplanes2,
                            &c->wmeta, &c->wscan, &c->yreal,
-                           &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->ysf2, &c->rbad, &c->vstart};
+                           &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysd, &c->ysd2, &c->rbad, &c->vstart};
     int64_t s = 0;
     for (const DevBuf *b : all)
         s += (int64_t)b->bytes;
@@ -446,8 +446,9 @@ int ensure_records(xyz_ctx *c, int B)
 // and member counts; per search the spill count and overflow flags, the
 // spill-path bucket count, the record and output counts, the error flag,
 // the group's candidate total, the candidate sum, the spill total, the
-// filter's work-item counter, the columns the filter kept and the bucket
-// members the on-chip grouping wrote.
+// filter's work-item counter, the columns the filter kept, the bucket
+// members the on-chip grouping wrote and the runs grouped on chip from the
+// segment.
 uint32_t *ctr_u32(xyz_ctx *c) { return reinterpret_cast<uint32_t *>(c->counters.ptr); }
 uint32_t *ctr_nbuckets(xyz_ctx *c) { return ctr_u32(c) + 0; }
 uint32_t *ctr_members(xyz_ctx *c) { return ctr_u32(c) + 1; }
@@ -798,15 +799,16 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
             CU(launch_weighted_strengths(c->pk, (PairOut *)c->out.ptr, ctr_nout(c), (int64_t)nrec, c->stream,
                                          &launches));
         uint32_t nout = 0;
-        unsigned long long kept[2] = {0, 0};
+        unsigned long long kept[3] = {0, 0, 0};
         CU(cudaMemcpyAsync(&nout, ctr_nout(c), 4, cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaMemcpyAsync(kept, ctr_kept(c), 16, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(kept, ctr_kept(c), 24, cudaMemcpyDeviceToHost, c->stream));
         CU(cudaStreamSynchronize(c->stream));
         if (nrec == 0)
             nout = 0;
         st.attempts = attempt + 1;
         st.filter_kept = pl.filter ? (int64_t)kept[0] : 0;
         st.bucket_members = pl.filter ? (int64_t)kept[1] : 0;
+        st.segment_grouped_runs = pl.filter ? (int64_t)kept[2] : 0;
         st.runs = runs;
         st.chunks = chunks;
         st.runs_per_chunk = pl.R;
@@ -916,7 +918,7 @@ void destroy_ctx(xyz_ctx *c)
                      &c->pair_off2, &c->scan_tmp2, &c->resp,   &c->ybs, &c->y_alt, &c->y_stage,
                      &c->wq, &c->wcdf, &c->wplanes, &c->wq2, &c->wcdf2, &c->wplanes2,
                      &c->wmeta, &c->wscan, &c->yreal,
-                     &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysf, &c->ysf2, &c->rbad, &c->vstart};
+                     &c->xrs, &c->xcs, &c->xnu, &c->ypr, &c->ysd, &c->ysd2, &c->rbad, &c->vstart};
     for (DevBuf *b : all)
         release(*b);
     if (c->own_stream && c->stream)
@@ -1071,7 +1073,7 @@ int xyz_create_unbiased(const float *X, const double *Y, int64_t n, int64_t p, x
     if ((rc = ensure(dX, count * sizeof(float))) || (rc = ensure(dY, (size_t)n * 8)) ||
         (rc = ensure(c->xrs, (size_t)n * Pf * sizeof(float))) ||
         (rc = ensure(c->xcs, (size_t)p * Wf * sizeof(float))) || (rc = ensure(c->xnu, (size_t)n * 4)) ||
-        (rc = ensure(c->ysf, (size_t)Wf * 4)) || (rc = ensure(c->rbad, 16)))
+        (rc = ensure(c->ysd, (size_t)Wf * 8)) || (rc = ensure(c->rbad, 16)))
         return bail(rc);
     int64_t launches = 0;
     unsigned bad = 0;
@@ -1097,7 +1099,7 @@ int xyz_create_unbiased(const float *X, const double *Y, int64_t n, int64_t p, x
     c->pk.Pf = Pf;
     c->pk.Xcs = (const float *)c->xcs.ptr;
     c->pk.Wf = Wf;
-    c->pk.ysf = (const float *)c->ysf.ptr;
+    c->pk.ysd = (const double *)c->ysd.ptr;
     if ((rc = xyz_set_y_real_dev(c, (const double *)dY.ptr)))
         return bail(rc);
     release(dX);
@@ -1182,12 +1184,12 @@ int xyz_set_y_real_dev(xyz_ctx *ctx, const double *dY)
     const int64_t n = ctx->pk.n, Wp = ctx->pk.Wp;
     if (ctx->pk.Xrs) {
         // real X: the response of the scaled rows, Y'_i = Y_i nu_i^2 (its
-        // float copy goes to a second buffer, swapped in once Y' is accepted)
+        // padded copy goes to a second buffer, swapped in once Y' is accepted)
         int64_t launches = 0;
-        if ((rc = ensure(ctx->ypr, (size_t)n * 8)) || (rc = ensure(ctx->ysf2, (size_t)ctx->pk.Wf * 4)))
+        if ((rc = ensure(ctx->ypr, (size_t)n * 8)) || (rc = ensure(ctx->ysd2, (size_t)ctx->pk.Wf * 8)))
             return rc;
         CU(launch_unbiased_y(dY, (const float *)ctx->xnu.ptr, n, ctx->pk.Wf, (double *)ctx->ypr.ptr,
-                             (float *)ctx->ysf2.ptr, ctx->stream, &launches));
+                             (double *)ctx->ysd2.ptr, ctx->stream, &launches));
         dY = (const double *)ctx->ypr.ptr;
     }
     if ((rc = ensure(ctx->y_alt, (size_t)Wp * 4)) || (rc = ensure(ctx->wq2, (size_t)n * 8)) ||
@@ -1212,8 +1214,8 @@ int xyz_set_y_real_dev(xyz_ctx *ctx, const double *dY)
     std::swap(ctx->wcdf, ctx->wcdf2);
     std::swap(ctx->wplanes, ctx->wplanes2);
     if (ctx->pk.Xrs) {
-        std::swap(ctx->ysf, ctx->ysf2);
-        ctx->pk.ysf = (const float *)ctx->ysf.ptr;
+        std::swap(ctx->ysd, ctx->ysd2);
+        ctx->pk.ysd = (const double *)ctx->ysd.ptr;
     }
     ctx->pk.cdf = (const uint64_t *)ctx->wcdf.ptr;
     ctx->pk.planes = (const uint32_t *)ctx->wplanes.ptr;
@@ -1291,7 +1293,7 @@ int xyz_search_range(xyz_ctx *ctx, int64_t l0, int64_t l1, int32_t M, double kap
     int64_t nout = 0;
     ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;     // real response: 2S - Q >= kappa Q
     ctx->pk.wscale = 0.0;
-    ctx->pk.rkq = (float)(kappa * ctx->pk.rnorm);      // real X: dot >= kappa ||Y'||_1
+    ctx->pk.rkq = kappa * ctx->pk.rnorm;               // real X: dot >= kappa ||Y'||_1 (as the oracle)
     if (amin > ctx->pk.n && !ctx->pk.cdf) {
         std::memset(&ctx->stats, 0, sizeof(ctx->stats));
         *pairs = nullptr;

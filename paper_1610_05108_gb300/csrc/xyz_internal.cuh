@@ -53,8 +53,8 @@ struct Packed {
     int64_t Pf = 0;                    // row pitch in floats, a multiple of 32
     const float *Xcs = nullptr;        // [p][Wf] columns of X' (padding 0)
     int64_t Wf = 0;                    // column pitch in floats, a multiple of 32
-    const float *ysf = nullptr;        // [Wf] Y' = Y nu_i^2 as float (padding 0)
-    float rkq = 0.0f;                  // pass: sum_i Y'_i X'_ij X'_ik >= rkq
+    const double *ysd = nullptr;       // [Wf] Y' = Y nu_i^2 (padding 0)
+    double rkq = 0.0;                  // pass: sum_i Y'_i X'_ij X'_ik >= rkq
     double rnorm = 0.0;                // ||Y'||_1 (reported strength = dot / rnorm)
 };
 
@@ -224,7 +224,7 @@ cudaError_t launch_sign_transform(const float *dX, int64_t count, uint64_t coin_
 cudaError_t launch_unbiased_scale(const float *dX, int64_t n, int64_t p, int64_t Pf, int64_t Wf, float *Xrs,
                                   float *Xcs, float *nu, unsigned *bad, cudaStream_t s, int64_t *launches);
 cudaError_t launch_unbiased_y(const double *dY, const float *nu, int64_t n, int64_t Wf, double *yprime,
-                              float *ysf, cudaStream_t s, int64_t *launches);
+                              double *ysd, cudaStream_t s, int64_t *launches);
 cudaError_t launch_verify_real(const Packed &pk, const Bucket *buckets, const uint64_t *pair_off,
                                const uint32_t *nbuckets, const uint64_t *total_pairs, const uint32_t *vals,
                                int kbits, uint64_t *rec_keys, uint32_t *rec_agree, uint32_t *nrec,

@@ -42,7 +42,8 @@ class Stats(ctypes.Structure):
             "ms_keys", "ms_sort", "ms_join", "ms_verify", "ms_dedup", "ms_total")] + \
         [(name, ctypes.c_int64) for name in (
             "launches_keys", "launches_sort", "launches_join", "launches_verify", "launches_dedup",
-            "survivors", "filter_kept", "attempts", "bucket_members")]
+            "survivors", "filter_kept", "attempts", "bucket_members",
+            "segment_grouped_runs")]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -339,17 +339,29 @@ def gwas_full():
     return synth.config_gwas(1)
 
 
-def test_full_size_gwas_sampled_parity(xyz, orc, gwas_full):
-    """The SNP-shaped n=2000, p=100000 workload at the benchmark's M: exact
-    E_l on sampled runs, and every reported pair's agreement recomputed one
-    by one by the oracle."""
+@pytest.mark.parametrize("M", [19, 21])
+def test_full_size_gwas_sampled_parity(xyz, orc, gwas_full, M):
+    """The SNP-shaped n=2000, p=100000 workload at the M of the gamma0 = 0.55
+    rule (19) and of eq. bestM (21): exact E_l on sampled runs -- one of
+    them a run whose survivors exceed one on-chip grouping and are grouped
+    in hash partitions, found through the stats -- and every reported pair's
+    agreement recomputed one by one by the oracle."""
     d = gwas_full
-    M, L, kappa, seed = 22, 400, 0.3, 2026
+    L, kappa, seed = 400, 0.3, 2026
     with xyz.create(d.X, d.Y) as ctx:
         for run in (0, 123):
             got = ctx.run_candidates(M, seed, run)
             want = orc.candidates(d.X, d.Y, M, seed, run)
             assert np.array_equal(got, want), run
+        part_run = None
+        for run in range(1000, 6000):
+            ctx.run_candidates(M, seed, run)
+            if ctx.stats()["segment_grouped_runs"] == 1:
+                part_run = run
+                break
+        assert part_run is not None, "no run needed the on-chip partitions"
+        got = ctx.run_candidates(M, seed, part_run)
+        assert np.array_equal(got, orc.candidates(d.X, d.Y, M, seed, part_run)), part_run
         res = ctx.search(L, M, kappa, seed)
     amin = orc.amin(d.n, kappa)
     assert np.all(res["agree"] >= amin)
@@ -363,6 +375,36 @@ def test_full_size_gwas_sampled_parity(xyz, orc, gwas_full):
     assert _as_set(_pairs_array(part)) <= _as_set(_pairs_array(res))
     want_part = orc.xyz_range(d.X, d.Y, 0, 50, M, kappa, seed)
     assert np.array_equal(_pairs_array(part), want_part)
+
+
+@pytest.fixture(scope="module")
+def gwas_large():
+    return synth.config_gwas_large(1)
+
+
+@pytest.mark.parametrize("M", [23, 26])
+def test_at_scale_operating_points(xyz, orc, gwas_large, M):
+    """The benchmark's workload (SNP-shaped n=4000, p=10^6, class-split
+    filter) at its operating point M = 23 (gamma0 = 0.55 rule) and at eq.
+    bestM's M = 26: E_l of two sampled runs equals the oracle's, a short run
+    range equals the oracle's search pair for pair (agreement counts
+    included), and at M = 23 the runs' survivors are grouped on chip in
+    several passes rather than by the sort."""
+    d = gwas_large
+    kappa, seed = 0.28, 777
+    with xyz.create(d.X, d.Y) as ctx:
+        for run in (5, 4242):
+            got = ctx.run_candidates(M, seed, run)
+            want = orc.candidates(d.X, d.Y, M, seed, run)
+            assert len(want) > 0
+            assert np.array_equal(got, want), run
+        part = ctx.search_range(0, 3, M, kappa, seed)
+        st = ctx.stats()
+    want_part = orc.xyz_range(d.X, d.Y, 0, 3, M, kappa, seed)
+    assert np.array_equal(_pairs_array(part), want_part)
+    assert st["filter_kept"] > 0 and st["bucket_members"] > 0
+    if M == 23:
+        assert st["segment_grouped_runs"] >= 1 and st["survivors"] == 0, st
 
 
 def test_sharded_search_through_library(xyz):
