@@ -512,20 +512,27 @@ def e2e_leg(args, d, kappa, M, L, xyz, torch):
     Yh = torch.from_numpy(d.Y).pin_memory()
     Xv = Xh.numpy().T          # column-major view of the pinned buffer
     Yv = Yh.numpy()
-    times, d2h = [], []
+    times, d2h, split = [], [], []
     steps = max(1, min(args.steps, args.e2e_steps))
     for s in range(steps + 1):
         t0 = time.perf_counter()
-        with xyz.Context.from_host(Xv, Yv) as c:
-            res = c.search(L, M, kappa, 7_000_000 + s)
+        c = xyz.Context.from_host(Xv, Yv)
         t1 = time.perf_counter()
+        res = c.search(L, M, kappa, 7_000_000 + s)
+        t2 = time.perf_counter()
+        c.close()
+        t3 = time.perf_counter()
         if s > 0:                       # first call warms the allocator
-            times.append(t1 - t0)
+            times.append(t3 - t0)
+            split.append((t1 - t0, t2 - t1, t3 - t2))
             d2h.append(len(res) * 16 + 16)
     t = float(np.mean(times))
+    sp = np.mean(np.asarray(split), axis=0) * 1e3
     return {"value": d.p * (d.p - 1) // 2 / t, "unit": UNIT,
             "h2d_bytes_per_step": int(d.n * d.p + d.n), "d2h_bytes_per_step": int(np.mean(d2h)),
             "ms_per_step": round(t * 1e3, 3), "steps": steps,
+            "split_ms": {"create": round(float(sp[0]), 3), "search": round(float(sp[1]), 3),
+                         "destroy": round(float(sp[2]), 3)},
             "path": "pinned host X,Y -> xyz_create (H2D + pack) -> xyz_search -> pairs to host -> xyz_destroy"}
 
 

@@ -1006,7 +1006,8 @@ __device__ __forceinline__ uint32_t key_class(uint32_t k)
 //           by the keys k of class q ^ class(c) -- exactly those with
 //           k ^ c in class q, so every key k ^ c is looked up in the filter
 //           that holds its class; survivors go to the CTA's segment as
-//           (runbits | Kc, j).
+//           (runbits | Kc, list place).  A run with c == 0 keeps the keys
+//           that occur at least twice (two filters per class).
 //
 // Each round's filter holds about p/16 keys, which keeps its load, and with
 // it the false-positive rate, near that of filter_kernel at p/16 columns.
@@ -1265,7 +1266,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         // (and a run left in the segment has its columns looked up in place),
         // so no warp waits on that load here.
         uint64_t *wbuf = reinterpret_cast<uint64_t *>(fl_smem + FB_EMIT) + wp * (FB_EB * 32);
-        auto emit_class = [&](uint32_t q2, bool test) {
+        auto emit_class = [&](uint32_t q2, const uint32_t *Ft, int fs) {
             const uint32_t n2 = cls_n[q2] < lcap ? cls_n[q2] : lcap;
             const uint32_t *lkq = lk + (int64_t)q2 * lcap;
             for (uint32_t i0 = t; i0 - t < n2; i0 += FB_RB * (uint32_t)T) {
@@ -1279,7 +1280,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
 #pragma unroll
                 for (int u = 0; u < FB_RB; ++u) {
                     const uint32_t i = i0 + u * (uint32_t)T;
-                    if (i < n2 && (!test || bloom_has3(F, k[u] ^ c, fshift)))
+                    if (i < n2 && bloom_has3(Ft, k[u] ^ c, fs))
                         pm |= 1u << u;
                 }
 #pragma unroll
@@ -1319,9 +1320,43 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             }
         };
         if (!nz) {
-            // c == 0: every column survives
-            for (uint32_t q = 0; q < 16; ++q)
-                emit_class(q, false);
+            // c == 0: a column pairs only with an equal key, so only keys
+            // that occur at least twice can be in a candidate.  Per class a
+            // filter of the keys seen once (F1) and one of the keys seen
+            // again (F2): an insert that finds all its bits already set in F1
+            // sets them in F2, and the class's keys are tested against F2.
+            // No false negatives: the inserts of two equal keys touch the same
+            // word with the same mask, the atomics order them, and the later
+            // sees the earlier's bits.
+            uint32_t *F1 = F, *F2 = F + FL_FWORDS / 2;
+            const int fs2 = fshift + 1;                 // half the words each
+            for (uint32_t q = 0; q < 16; ++q) {
+                for (int i = t; i < FL_FWORDS / 4; i += T)
+                    reinterpret_cast<uint4 *>(F)[i] = make_uint4(0u, 0u, 0u, 0u);
+                __syncthreads();
+                const uint32_t nq = cls_n[q] < lcap ? cls_n[q] : lcap;
+                const uint32_t *lkq = lk + (int64_t)q * lcap;
+                for (uint32_t i0 = t; i0 - t < nq; i0 += FB_RB * (uint32_t)T) {
+                    uint32_t k[FB_RB];
+#pragma unroll
+                    for (int u = 0; u < FB_RB; ++u) {
+                        const uint32_t i = i0 + u * (uint32_t)T;
+                        k[u] = i < nq ? lkq[i] : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < FB_RB; ++u) {
+                        if (i0 + u * (uint32_t)T < nq) {
+                            uint32_t word, mask;
+                            bloom_pos3(k[u], fs2, word, mask);
+                            if ((atomicOr(F1 + word, mask) & mask) == mask)
+                                atomicOr(F2 + word, mask);
+                        }
+                    }
+                }
+                __syncthreads();
+                emit_class(q, F2, fs2);
+                __syncthreads();
+            }
         } else {
             const uint32_t cq = key_class(c);
             for (uint32_t q = 0; q < 16; ++q) {
@@ -1347,7 +1382,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                     }
                 }
                 __syncthreads();
-                emit_class(q ^ cq, true);
+                emit_class(q ^ cq, F, fshift);
                 __syncthreads();
             }
         }
@@ -1476,10 +1511,19 @@ bool filter_big_supported(int64_t p, int M) { return M >= 1 && M <= 28 && p >= 2
 
 uint32_t filter_big_lcap(int64_t p)
 {
-    // a class list holds p / 16 keys on average: room for 1.5 times that,
-    // plus some slack for small p; list places must stay below 2^27
-    const int64_t l = (3 * p + 31) / 32 + 16 * (FL_THREADS / 32);
+    // a class list holds p / 16 keys on average, but skewed data fill some
+    // classes far more: columns of low minor frequency share a few keys with
+    // few bits set, whose classes are the few of even parities (every
+    // all-zero key is in class 0).  Room for p / 4 first, plus some slack
+    // for small p.
+    const int64_t l = (p + 3) / 4 + 512;
     return (uint32_t)((l + 15) / 16 * 16);
+}
+
+uint32_t filter_big_lcap_max(int64_t p)
+{
+    // every key of a run in one class
+    return (uint32_t)((p + 512 + 15) / 16 * 16);
 }
 
 size_t filter_big_list_words(int64_t p, uint32_t lcap)

@@ -554,14 +554,24 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                     redo = true;
                 }
                 if (sovf & 4) {
-                    // a class list of the class-split filter did: twice the
-                    // room once, then (classes that uneven) the path without it
-                    const uint32_t lmax = 2 * filter_big_lcap(p);
-                    if (c->big_lcap >= lmax) {
+                    // a class list of the class-split filter did: room for
+                    // all of a run's keys in one class (it cannot overflow
+                    // again), or, when the device has no room for that, the
+                    // path without the class-split filter
+                    const uint32_t lmax = filter_big_lcap_max(p);
+                    bool give_up = c->big_lcap >= lmax;
+                    if (!give_up) {
+                        const size_t words = filter_big_list_words(p, lmax);
+                        if (ensure(c->lst_keys, words * 4) || ensure(c->lst_cols, words * 4)) {
+                            g_err.clear();
+                            give_up = true;
+                        } else {
+                            c->big_lcap = lmax;
+                        }
+                    }
+                    if (give_up) {
                         c->big_off = true;
                         pl = make_plan(c, runs, M, B);
-                    } else {
-                        c->big_lcap = lmax;
                     }
                     redo = true;
                 }
@@ -648,6 +658,34 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  B > 1 ? ybs : nullptr, ctr_sovf(c), (uint32_t *)c->vstart.ptr, VSTART_CAP,
                                  ctr_err(c)));
                 tm.end();
+                if (phase == SP_ALL && g0 == l0 && g0 + pl.R < l1) {
+                    // the first of several launch groups tells whether the
+                    // member space and the record space suffice: when not,
+                    // they grow now and the search restarts after one group
+                    // (a whole search would be lost at the end)
+                    int sovf = 0;
+                    uint32_t mem_tried = 0, nrec1 = 0;
+                    CU(cudaMemcpyAsync(&sovf, ctr_sovf(c), 4, cudaMemcpyDeviceToHost, c->stream));
+                    CU(cudaMemcpyAsync(&mem_tried, ctr_members(c), 4, cudaMemcpyDeviceToHost, c->stream));
+                    CU(cudaMemcpyAsync(&nrec1, ctr_nrec(c), 4, cudaMemcpyDeviceToHost, c->stream));
+                    CU(cudaStreamSynchronize(c->stream));
+                    if (sovf & 2) {
+                        const int64_t want = (int64_t)mem_tried + (int64_t)mem_tried / 4;
+                        c->mem_cap = want > 2 * c->mem_cap ? want : 2 * c->mem_cap;
+                        redo = true;
+                    }
+                    if ((sovf & 5) && (rc = flush_spills()))      // segments or class lists: grown there
+                        return rc;
+                    const int64_t groups = (runs + pl.R - 1) / pl.R;
+                    const int64_t want_rec = 2 * (int64_t)nrec1 * groups;
+                    if (want_rec > c->rec_cap && !(sovf & 2)) {
+                        int64_t cap = c->rec_cap;
+                        while (cap < want_rec && cap < (int64_t)0xF0000000LL / 2)
+                            cap *= 2;
+                        c->rec_cap = cap;
+                        redo = true;
+                    }
+                }
                 if (phase == SP_ALL && c->spill_flush && ++since_flush == c->spill_flush && g0 + pl.R < l1) {
                     since_flush = 0;
                     if ((rc = flush_spills()))

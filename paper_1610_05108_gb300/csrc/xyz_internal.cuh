@@ -173,6 +173,7 @@ bool filter_supported(int64_t p, int M);
 // at any p up to 2^27: per-CTA lists of lcap entries for each of 16 classes.
 bool filter_big_supported(int64_t p, int M);
 uint32_t filter_big_lcap(int64_t p);
+uint32_t filter_big_lcap_max(int64_t p);
 size_t filter_big_list_words(int64_t p, uint32_t lcap);
 cudaError_t launch_filter_big(const Packed &pk, int M, uint64_t seed, int64_t l0, int R, int rbits, int64_t rbase,
                               int grid, uint32_t mcap, uint32_t bcap, uint32_t *lst_keys, uint32_t *lst_cols,

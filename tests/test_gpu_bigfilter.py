@@ -122,10 +122,10 @@ def test_class_split_sub_bucket_overflow_regrows(xyz, orc):
     assert np.array_equal(got, want)
 
 
-def test_class_split_gives_way_when_classes_are_too_uneven(xyz, orc):
+def test_class_split_lists_grow_for_one_class(xyz, orc):
     # 163840 identical columns: every key of a run is in one class -- more
-    # than twice the room of class lists sized for 16 balanced classes.  The
-    # search falls back to the path without the class-split filter and
+    # than the first room of the class lists (a quarter of the columns).  The
+    # lists grow to hold every key in one class and the search is redone; it
     # gives the oracle's (empty) result; c != 0 in every run (half the rows
     # of Y are -1), so no pair is a candidate.
     n, p = 64, 163840
@@ -179,16 +179,21 @@ def test_class_split_huge_group_grouped_from_global_memory(xyz, orc):
 
 
 @pytest.mark.parametrize("M", [18, 24])
-def test_class_split_every_column_survives(xyz, orc, M):
-    # Y = +1: c = 0 in every run and every column survives (600000 per run,
-    # more than the room for sorting a run's survivors by bin), so the runs
-    # go to the general sort; the candidates equal the oracle's.
-    n, p = 32, 600000
+def test_class_split_c_zero_runs_keep_repeated_keys(xyz, orc, M):
+    # Y = +1: c = 0 in every run, so a pair is a candidate exactly when its
+    # two columns have equal keys.  The filter keeps the columns whose key
+    # occurs at least twice (with M = 24 a good share of the 600000 keys is
+    # unique and dropped, with M = 18 nearly none), and the candidates equal
+    # the oracle's.
+    n, p = 64, 600000
     X, _ = _rand(n, p, 91)
     Y = np.ones(n, np.int8)
     seed = 12
     with xyz.create(X, Y) as ctx:
         for run in (0, 1):
             got = ctx.run_candidates(M, seed, run)
-            assert ctx.stats()["survivors"] > 0
+            st = ctx.stats()
             assert np.array_equal(got, orc.candidates(X, Y, M, seed, run)), run
+            assert 0 < st["filter_kept"] <= p
+            if M == 24:
+                assert st["filter_kept"] < p
