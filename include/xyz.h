@@ -27,9 +27,10 @@
  *     mix(s + (t+1) * 0x9E3779B97F4A7C15) with the splitmix64 finaliser of
  *     Steele, Lea & Flood (2014), and the row is floor(u * n / 2^64).
  *   - A candidate of run l is an unordered pair j != k that agrees on every
- *     sampled row: X_{s j} = Y_s X_{s k} for all sampled s (Algorithm 2 steps
- *     3-4; equality of the projections x_j = z_k happens exactly then, see the
- *     remark on minimal subsampling in Section 2).
+ *     sampled row: X_{s j} = Y_s X_{s k} for all sampled s (the projection
+ *     and equal-pairs steps of Algorithm 2; equality of the projections
+ *     x_j = z_k happens exactly then, see the remark on minimal subsampling
+ *     in Section 2).
  *   - Results are deterministic: they depend only on (X, Y, M, L, kappa,
  *     seed), never on tuning, chunking or batching.
  *
@@ -106,7 +107,7 @@ typedef struct xyz_stats {
 
 /* ---------------------------------------------------------------- context */
 
-/* Algorithm 2 step 1 ("form Z"): copy X and Y to the device and pack them
+/* the form-Z step of Algorithm 2 ("form Z"): copy X and Y to the device and pack them
  * into bit columns (for verification), bit rows (for key building) and the
  * response bits; Z is never materialised (its bits are X's bits xor Y's).
  * X: host pointer, n*p int8, column-major.  Y: host pointer, n int8.
@@ -229,7 +230,7 @@ int xyz_search_abs(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t se
                    int64_t *npairs);
 
 /* The interaction half of the KKT check of the Lasso active-set strategy
- * (Section 4, Algorithm 3 line 4): with a real residual r (n doubles, e.g.
+ * (Section 4, the KKT check of Algorithm 3): with a real residual r (n doubles, e.g.
  * Y - X_A beta_A - W_B theta_B, centred), the pairs with
  * |r^T (X_j o X_k)| / n > lambda, searched with Y set to +r and to -r.  The
  * context switches to the real response r (as xyz_set_y_real).  In the
@@ -319,13 +320,13 @@ int xyz_set_onchip_partitions(xyz_ctx *ctx, int32_t max_parts);
 
 /* --------------------------------------------------- parity / observability */
 
-/* Keys of run `run` (Algorithm 2 step 3 with the integer reading of the
+/* Keys of run `run` (the projection step of Algorithm 2 with the integer reading of the
  * projection): kx[j] = sum_m bit(X_{s_m j}) 2^m with bit(v) = 1 iff v = -1,
  * for j < p, and c = sum_m bit(Y_{s_m}) 2^m, so that the Z-key of column k is
  * kx[k] xor c.  kx: host array of p uint64; c: host pointer. */
 int xyz_run_keys(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, uint64_t *kx, uint64_t *c);
 
-/* Candidate set E_run (Algorithm 2 step 4) as unordered pairs j < k,
+/* Candidate set E_run (the equal-pairs step of Algorithm 2) as unordered pairs j < k,
  * sorted; *jk gets 2*count int32 (j0,k0,j1,k1,...), free with xyz_free. */
 int xyz_run_candidates(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, int32_t **jk,
                        int64_t *count);

@@ -154,7 +154,7 @@ def brute_force(X, Y, kappa: float) -> np.ndarray:
 
 
 def keys(X, Y, rows: np.ndarray):
-    """Integer keys (x, z) of the M sampled rows (Algorithm 2 step 3, R3)."""
+    """Integer keys (x, z) of the M sampled rows (the projection step of Algorithm 2, R3)."""
     X, Y, n, p = _check_xy(X, Y)
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     x = np.zeros(p, dtype=np.uint64)

@@ -171,7 +171,7 @@ void orc_keys(const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
     }
 }
 
-/* The paper's own projection (eq. projR, Algorithm 2 step 3):
+/* The paper's own projection (eq. projR, the projection step of Algorithm 2):
  * R_i = sum_m D_m 1{i_m = i}, x = X^T R, z = Z^T R, in double precision.
  * D holds the M weights (drawn from U[0,1] by the caller). */
 void orc_project_real(const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
@@ -231,7 +231,7 @@ static int orc_rpoint_cmp(const void *pa, const void *pb)
     return a->idx - b->idx;
 }
 
-/* Algorithm 2 step 4 by the procedure of Section 2.2 (Figure 2): sort the 2p
+/* the equal-pairs step of Algorithm 2 by the procedure of Section 2.2 (Figure 2): sort the 2p
  * values of (x, z), walk the distinct values, and wherever both colours are
  * present record the Cartesian product {j : x_j = v} x {k : z_k = v}.
  * Writes up to `cap` ORDERED pairs (j, k) with x_j = z_k (the diagonal
@@ -275,7 +275,7 @@ int64_t orc_equal_pairs(const uint64_t *x, const uint64_t *z, int64_t p,
 }
 
 /* The same walk over the paper's real-valued projections, with exact
- * floating-point equality as in Algorithm 2 step 4. */
+ * floating-point equality as in the equal-pairs step of Algorithm 2. */
 int64_t orc_equal_pairs_real(const double *x, const double *z, int64_t p,
                              int32_t *out, int64_t cap)
 {
@@ -360,7 +360,7 @@ static void orc_vec_push(orc_vec *vec, int32_t j, int32_t k, int32_t a)
     vec->n++;
 }
 
-/* Candidate set E_l of run `run` (Algorithm 2 steps 3-4) as unordered pairs
+/* Candidate set E_l of run `run` (the projection and equal-pairs steps of Algorithm 2) as unordered pairs
  * j < k (reading R4), sorted, each once.  The ordered pairs (j, k) and (k, j)
  * of the equal-pairs walk name the same unordered pair. */
 static int64_t orc_rows_candidates(const int8_t *X, const int8_t *Y, int64_t n,
@@ -625,7 +625,7 @@ int64_t orc_brute_force_weighted(const int8_t *X, const double *Y, int64_t n, in
 
 /* Section 4 runs the search with Y set to each of +r and -r to find the
  * pairs with |r^T (X_j o X_k)| above a threshold.  The KKT check of
- * Algorithm 3 (line 4) keeps the pairs with |r^T (X_j o X_k)| / n > lambda.
+ * The KKT check of Algorithm 3 keeps the pairs with |r^T (X_j o X_k)| / n > lambda.
  *
  * Reading R12: with the fixed-point weights of R9 (q_i = floor(|r_i|
  * 2^(24-e) + 1/2)), r^T (X_j o X_k) is taken as (2 S_jk - Q) 2^(e-24), so the

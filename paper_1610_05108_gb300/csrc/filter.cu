@@ -1,7 +1,8 @@
-// Per-run survivor filter for the equal-pairs search (Algorithm 2 steps
-// 3-4): filter_kernel for M <= 31 when p is small enough for one
-// shared-memory filter of a run's keys, filter_big_kernel (further down)
-// for larger p with the keys split into 16 linear classes.
+// Per-run survivor filter for the equal-pairs search (the projection and
+// equal-pairs steps of Algorithm 2): filter_kernel for M <= 31 when p is
+// small enough for one shared-memory filter of a run's keys,
+// filter_big_kernel (further down) for larger p with the keys split into 16
+// linear classes.
 //
 // In run l with response key c, columns j and k form a candidate exactly
 // when kx_j ^ kx_k = c (keys.cu: X_j and Z_k agree on the sampled rows).  A

@@ -1,5 +1,6 @@
-// Partitioned equal-pairs search (Algorithm 2 steps 3-4, Section 2.2) for
-// M <= 31, in two kernels per launch group of R runs.
+// Partitioned equal-pairs search (the projection and equal-pairs steps of
+// Algorithm 2, Section 2.2) for M <= 31, in two kernels per launch group of
+// R runs.
 //
 // keybuild_part: one thread per (run, 32-column word).  The thread loads
 // the word of each of the M sampled rows (neighbouring threads read

@@ -9,7 +9,7 @@
 // appends one bucket with its pair count.  Singleton groups -- almost every
 // entry -- cost three coalesced key reads.
 //
-// Verify (Algorithm 2 step 5): candidate t of the launch group is decoded to
+// Verify (the verification step of Algorithm 2): candidate t of the launch group is decoded to
 // (bucket, a, b) through the exclusive scan of the bucket pair counts, so
 // every thread gets one candidate regardless of how skewed the buckets are.
 // The agreement is a_jk = sum_w popc(~(Xc_j[w] ^ Xc_k[w] ^ yb[w])): bit i of

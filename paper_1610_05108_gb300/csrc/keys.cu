@@ -1,4 +1,4 @@
-// K2 keybuild: Algorithm 2 step 3 for a group of runs.
+// K2 keybuild: the projection step of Algorithm 2 for a group of runs.
 //
 // Run l draws M rows s_0..s_{M-1} (eq. projR, subsampling with replacement)
 // from the splitmix64 counter stream, and column j gets the key

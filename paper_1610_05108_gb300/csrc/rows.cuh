@@ -1,4 +1,4 @@
-// Row draws of a run (Algorithm 2 step 2 with the counter-based stream):
+// Row draws of a run (the row draw of Algorithm 2 with the counter-based stream):
 // draw t of a search with seed s uses u = splitmix64 output t (the finaliser
 // of Steele, Lea & Flood applied to s + (t + 1) * 0x9E3779B97F4A7C15).
 //   uniform rows (binary Y):      row = floor(u * n / 2^64);

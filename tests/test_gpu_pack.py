@@ -1,4 +1,4 @@
-"""Packing of X and Y (Algorithm 2 step 1, "form Z"): one tiled kernel reads
+"""Packing of X and Y (the form-Z step of Algorithm 2, "form Z"): one tiled kernel reads
 every entry of X once -- from device memory, from a device copy of a
 pageable host array, or in place from pinned host memory -- and writes the
 bit columns and bit rows.  The bit rows are checked through the keys of

@@ -166,7 +166,7 @@ def test_candidates_are_pairs_equal_on_sampled_rows(orc, seed):
 
 @pytest.mark.parametrize("seed", [4, 5])
 def test_real_projection_gives_the_same_equal_pairs(orc, seed):
-    # Algorithm 2 step 3 with F = U[0,1]: the real projection and the integer
+    # the projection step of Algorithm 2 with F = U[0,1]: the real projection and the integer
     # keys of the sampled bits give the same equal pairs (Section 2.2: any
     # continuous F gives identical results).
     rng = np.random.default_rng(seed)
@@ -213,7 +213,7 @@ def test_perfect_interaction_found_every_run(orc):
 
 
 def test_xyz_is_subset_of_brute_force(orc):
-    # Algorithm 2 step 5: I only holds verified pairs, with their exact counts.
+    # the verification step of Algorithm 2: I only holds verified pairs, with their exact counts.
     rng = np.random.default_rng(13)
     n, p = 100, 120
     X = np.asfortranarray(_rand_pm1(rng, n, p))
