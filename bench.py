@@ -451,23 +451,27 @@ def gpu_arm(args):
 
 
 def autotuned_leg(args, ctx, stream, flush, d, kappa, M_rule, targets, xyz, torch, hits):
-    """The operating point chosen by the library's autotuner (xyz_autotune_M
-    over M_rule - 3 .. M_rule + 3 at 95% recall of the weakest target), then
-    timed like the main line."""
+    """The operating point chosen by the library's autotuners (xyz_autotune_M
+    over M_rule - 3 .. M_rule + 3 at 95% recall of the weakest target, then
+    xyz_autotune_tiles for the launch shapes at that M), timed like the main
+    line."""
     g_min = (1.0 + min(s_ for _, s_ in targets)) / 2.0
     t0 = time.perf_counter()
     M, L, pred, table = ctx.autotune_M(kappa, g_min, 0.95, max(1, M_rule - 3), min(31, M_rule + 3), seed=77)
+    tiles, tiles_ms = ctx.autotune_tiles(M, kappa, seed=78, trial_runs=min(L, 4096))
     tune_s = time.perf_counter() - t0
     ctx.search(L, M, kappa, 5_999_999)              # warm-up at the chosen point
     ms, found, _ = _timed_searches(ctx, stream, flush, torch, L, M, kappa,
                                    [6_000_000 + s for s in range(args.extra_steps)], hits)
     t = float(np.mean(ms))
-    return {"M": M, "L": L, "ms_per_step": round(t, 3), "tuner_ms": round(pred, 3),
+    ctx.set_tiles(0, 0, 0)                          # the main line's shapes again
+    return {"M": M, "L": L, "tiles": tiles, "tiles_trial_ms": round(tiles_ms, 3),
+            "ms_per_step": round(t, 3), "tuner_ms": round(pred, 3),
             "value": d.p * (d.p - 1) // 2 / (t / 1e3), "unit": UNIT, "steps": len(ms),
             "recall_measured": round(float(np.mean(found)), 4),
             "eta_min": round(xyz.eta(g_min, M, L), 4), "tuning_s": round(tune_s, 3),
             "table": [[int(r[0]), int(r[1]), round(float(r[2]), 3)] for r in table],
-            "note": "M by this implementation's measured cost; same recall target"}
+            "note": "M and launch shapes by this implementation's measured cost; same recall target"}
 
 
 def bestM_leg(args, ctx, stream, flush, d, kappa, targets, xyz, torch, hits):

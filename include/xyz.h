@@ -257,6 +257,30 @@ int xyz_autotune_M(xyz_ctx *ctx, double kappa, double gamma, double recall, int3
                    uint64_t seed, int64_t trial_runs, int32_t *M_best, int64_t *L_best, double *ms_best,
                    double *table);
 
+/* Launch shapes of the search on the survivor-filter path (no counterpart
+ * in the paper).  Results never depend on them. */
+typedef struct xyz_tiles {
+    int32_t filter_threads;        /* threads per filter CTA: a multiple of 32 in [512, 1024];
+                                      0 = chosen from p (least waste in the last round) */
+    int32_t verify_blocks_per_sm;  /* verification blocks per SM, 1 or more; 0 = as many as fit */
+    int64_t group_runs;            /* runs per launch group, 1 or more; 0 = the default rule */
+} xyz_tiles;
+
+/* Sets the launch shapes of later searches on ctx (XYZ_EINVAL for values
+ * out of range; all zero restores the defaults). */
+int xyz_set_tiles(xyz_ctx *ctx, const xyz_tiles *tiles);
+
+/* Picks the launch shapes by measurement, one after another: the filter's
+ * CTA size among {default, 640, 768, 896, 1024}, then the launch-group size
+ * among {default, 1/2, 1/4 of it} (at least 2 runs per SM), then the
+ * verification's blocks per SM among {as many as fit, 2, 1}; each candidate
+ * is timed (CUDA events) on a search of trial_runs runs with (M, kappa) after
+ * one warm-up search.  The best shapes are set on ctx and returned in *best,
+ * with their time in *ms_best.  trial_runs >= 8, kappa finite in [-1, 1],
+ * 0 <= M <= 31 (the filter path), else XYZ_EINVAL. */
+int xyz_autotune_tiles(xyz_ctx *ctx, int32_t M, double kappa, uint64_t seed, int64_t trial_runs, xyz_tiles *best,
+                       double *ms_best);
+
 /* Many independent searches at once, each on its own context (instances of
  * different n and p): search i is xyz_search(ctxs[i], L[i], M[i],
  * kappa[i], seed[i]) and its result is identical to that call.  The launch

@@ -1577,7 +1577,7 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    kern<<<grid, filter_threads(pk.P), smem, s>>>(pk.Xr, pk.Pp, pk.P, ybs, pk.Wp, B, pk.n, pk.p, M, seed, l0, R,
+    kern<<<grid, pk.filter_threads > 0 ? pk.filter_threads : filter_threads(pk.P), smem, s>>>(pk.Xr, pk.Pp, pk.P, ybs, pk.Wp, B, pk.n, pk.p, M, seed, l0, R,
                                         NB, BB, rbits, rbase, mcap, bcap, kc_scratch, seg_keys, seg_vals,
                                         seg_count, seg_cap, overflow, cnz, members, members_count,
                                         buckets, pair_counts, nbuckets, pk.cdf, pk.wtotal, pk.Xrs, pk.Pf,
@@ -1605,7 +1605,7 @@ cudaError_t launch_filter_big(const Packed &pk, int M, uint64_t seed, int64_t l0
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    kern<<<grid, filter_threads(pk.P), smem, s>>>(pk.Xr, pk.Pp, pk.P, pk.yb, pk.n, pk.p, M, seed, l0, R, rbits, rbase,
+    kern<<<grid, pk.filter_threads > 0 ? pk.filter_threads : filter_threads(pk.P), smem, s>>>(pk.Xr, pk.Pp, pk.P, pk.yb, pk.n, pk.p, M, seed, l0, R, rbits, rbase,
                                                   mcap, bcap, lst_keys, lst_cols, lcap, seg_keys, seg_vals, seg_count,
                                                   seg_cap, overflow, cnz, members, members_count, buckets,
                                                   pair_counts, nbuckets, pk.cdf, pk.wtotal, part_max, work, kept);

@@ -504,11 +504,13 @@ int64_t max_resident_blocks()
 // One block per resident slot of the kernel on every SM: the grid-stride
 // loops then finish in a single wave, with no half-filled second one.
 template <typename Kern>
-unsigned resident_grid(Kern kernel)
+unsigned resident_grid(Kern kernel, int cap_per_sm = 0)
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, JV_THREADS, 0) != cudaSuccess || per_sm < 1)
         per_sm = 4;
+    if (cap_per_sm > 0 && cap_per_sm < per_sm)
+        per_sm = cap_per_sm;
     return (unsigned)(max_resident_blocks() / 8 * per_sm);
 }
 
@@ -566,18 +568,18 @@ cudaError_t launch_verify(const Packed &pk, const Bucket *buckets, const uint64_
     const bool short_cols = pk.Wp <= 64;
     if (ybs) {
         auto k = short_cols ? verify_kernel<true, false, 2> : verify_kernel<true, false, 4>;
-        k<<<resident_grid(k), JV_THREADS, 0, s>>>(pk.Xc, pk.Wp, ybs, buckets, pair_off, nbuckets, total_pairs,
+        k<<<resident_grid(k, pk.verify_bpsm), JV_THREADS, 0, s>>>(pk.Xc, pk.Wp, ybs, buckets, pair_off, nbuckets, total_pairs,
                                                   vals, amin, kbits, rec_keys, rec_agree, nrec, rec_cap,
                                                   abort_flag, nullptr, 0, 0.0, bstart, bstart_cap, verr);
     } else if (pk.cdf) {
         auto k = short_cols ? verify_kernel<false, true, 2> : verify_kernel<false, true, 4>;
-        k<<<resident_grid(k), JV_THREADS, 0, s>>>(pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs,
+        k<<<resident_grid(k, pk.verify_bpsm), JV_THREADS, 0, s>>>(pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs,
                                                   vals, amin, kbits, rec_keys, rec_agree, nrec, rec_cap,
                                                   abort_flag, pk.planes, (int64_t)pk.wtotal, pk.wkq, bstart,
                                                   bstart_cap, verr);
     } else {
         auto k = short_cols ? verify_kernel<false, false, 2> : verify_kernel<false, false, 4>;
-        k<<<resident_grid(k), JV_THREADS, 0, s>>>(pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs,
+        k<<<resident_grid(k, pk.verify_bpsm), JV_THREADS, 0, s>>>(pk.Xc, pk.Wp, pk.yb, buckets, pair_off, nbuckets, total_pairs,
                                                   vals, amin, kbits, rec_keys, rec_agree, nrec, rec_cap,
                                                   abort_flag, nullptr, 0, 0.0, bstart, bstart_cap, verr);
     }

@@ -28,6 +28,9 @@ namespace xyz {
 
 static thread_local std::string g_err;
 
+// entry budget of a launch group (the filter path holds 64 times that in runs' columns)
+constexpr int64_t kDefaultChunkEntries = (int64_t)1 << 25;
+
 void set_error(const std::string &msg) { g_err = msg; }
 
 int fail(int code, const std::string &msg)
@@ -107,7 +110,8 @@ struct xyz_ctx {
     DevBuf pXc, pXr, pyb, pbad;  // packed X, response bits, input-check flag (owned contexts)
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
     int64_t rec_cap = 1 << 16;
-    int64_t chunk_entries = (int64_t)1 << 25;
+    int64_t chunk_entries = kDefaultChunkEntries;
+    xyz_tiles tiles{0, 0, 0};    // launch shapes set by xyz_set_tiles
     bool use_filter = true;
     bool force_big = false;      // class-split filter wherever it applies (xyz_set_filter 2)
     uint32_t big_lcap = 0;       // class-split filter: entries per class list and CTA (grown on overflow)
@@ -1830,6 +1834,118 @@ int xyz_set_timing(xyz_ctx *ctx, int enable)
     if (!ctx)
         return fail(XYZ_EINVAL, "null context");
     ctx->timing = enable != 0;
+    return XYZ_OK;
+}
+
+int xyz_set_tiles(xyz_ctx *ctx, const xyz_tiles *tiles)
+{
+    if (!ctx || !tiles)
+        return fail(XYZ_EINVAL, "null argument");
+    const int ft = tiles->filter_threads;
+    if (ft != 0 && (ft < 512 || ft > 1024 || ft % 32 != 0))
+        return fail(XYZ_EINVAL, "filter_threads must be 0 or a multiple of 32 in [512, 1024]");
+    if (tiles->verify_blocks_per_sm < 0 || tiles->group_runs < 0)
+        return fail(XYZ_EINVAL, "verify_blocks_per_sm and group_runs must be >= 0");
+    ctx->pk.filter_threads = ft;
+    ctx->pk.verify_bpsm = tiles->verify_blocks_per_sm;
+    // the filter path's launch group holds 64 entries' worth of runs per
+    // entry budget: group_runs runs of p columns need group_runs * p / 64
+    ctx->chunk_entries = tiles->group_runs == 0 ? kDefaultChunkEntries
+                                                : (tiles->group_runs * ctx->pk.p + 63) / 64;
+    ctx->tiles = *tiles;
+    return XYZ_OK;
+}
+
+int xyz_autotune_tiles(xyz_ctx *ctx, int32_t M, double kappa, uint64_t seed, int64_t trial_runs, xyz_tiles *best,
+                       double *ms_best)
+{
+    int rc = check_ctx(ctx);
+    if (rc)
+        return rc;
+    if (!best || !ms_best)
+        return fail(XYZ_EINVAL, "null output pointer");
+    if ((rc = check_kappa(kappa)))
+        return rc;
+    if (M < 0 || M > 31 || trial_runs < 8)
+        return fail(XYZ_EINVAL, "need 0 <= M <= 31 and trial_runs >= 8");
+    const int64_t amin = amin_rule(ctx->pk.n, kappa);
+    ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;
+    ctx->pk.wscale = 0.0;
+    ctx->pk.rkq = kappa * ctx->pk.rnorm;
+    const bool timing = ctx->timing;
+    ctx->timing = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    uint64_t trial = 0;
+    // one warm-up search, then the timed one, with the shapes t
+    auto measure = [&](const xyz_tiles &t, double *ms) -> int {
+        int r = xyz_set_tiles(ctx, &t);
+        int64_t nout = 0;
+        if (!r)
+            r = run_search(ctx, 0, trial_runs, M, amin, seed + 2 * trial, &nout);
+        if (r)
+            return r;
+        cudaEventRecord(e0, ctx->stream);
+        r = run_search(ctx, 0, trial_runs, M, amin, seed + 2 * trial + 1, &nout);
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        ++trial;
+        float f = 0.0f;
+        cudaEventElapsedTime(&f, e0, e1);
+        *ms = f;
+        return r;
+    };
+    xyz_tiles cur{0, 0, 0};
+    double cur_ms = 0.0;
+    rc = measure(cur, &cur_ms);
+    // the default launch group of the filter path (make_plan's rule)
+    const int64_t rdef = 64 * kDefaultChunkEntries / ctx->pk.p < 16384 ? 64 * kDefaultChunkEntries / ctx->pk.p : 16384;
+    const int64_t rmin = 2 * (int64_t)filter_grid();
+    const int32_t threads[4] = {640, 768, 896, 1024};
+    for (int i = 0; i < 4 && !rc; ++i) {
+        xyz_tiles t = cur;
+        t.filter_threads = threads[i];
+        double ms = 0.0;
+        if ((rc = measure(t, &ms)))
+            break;
+        if (ms < cur_ms) {
+            cur = t;
+            cur_ms = ms;
+        }
+    }
+    for (int i = 1; i <= 2 && !rc; ++i) {
+        xyz_tiles t = cur;
+        t.group_runs = rdef >> i;
+        if (t.group_runs < rmin)
+            break;
+        double ms = 0.0;
+        if ((rc = measure(t, &ms)))
+            break;
+        if (ms < cur_ms) {
+            cur = t;
+            cur_ms = ms;
+        }
+    }
+    for (int b = 2; b >= 1 && !rc; --b) {
+        xyz_tiles t = cur;
+        t.verify_blocks_per_sm = b;
+        double ms = 0.0;
+        if ((rc = measure(t, &ms)))
+            break;
+        if (ms < cur_ms) {
+            cur = t;
+            cur_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->timing = timing;
+    if (rc)
+        return rc;
+    xyz_set_tiles(ctx, &cur);
+    *best = cur;
+    *ms_best = cur_ms;
     return XYZ_OK;
 }
 

@@ -56,6 +56,10 @@ struct Packed {
     const double *ysd = nullptr;       // [Wf] Y' = Y nu_i^2 (padding 0)
     double rkq = 0.0;                  // pass: sum_i Y'_i X'_ij X'_ik >= rkq
     double rnorm = 0.0;                // ||Y'||_1 (reported strength = dot / rnorm)
+    // launch shapes (xyz_set_tiles; 0 = the default rule); results never
+    // depend on them
+    int filter_threads = 0;            // threads per filter CTA
+    int verify_bpsm = 0;               // verification blocks per SM
 };
 
 constexpr int XYZ_WPLANES = 25;        // weights are integers in [0, 2^24]

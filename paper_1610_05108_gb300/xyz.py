@@ -49,6 +49,11 @@ class Stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class Tiles(ctypes.Structure):
+    _fields_ = [("filter_threads", ctypes.c_int32), ("verify_blocks_per_sm", ctypes.c_int32),
+                ("group_runs", ctypes.c_int64)]
+
+
 class Peaks(ctypes.Structure):
     _fields_ = [("alu_ops_per_s", ctypes.c_double), ("iadd_ops_per_s", ctypes.c_double),
                 ("popc_ops_per_s", ctypes.c_double), ("sm_mhz", ctypes.c_double), ("sms", ctypes.c_int32)]
@@ -111,6 +116,8 @@ SIGNATURES = {
     "xyz_M_for_gamma0": (_i32, [_i64, _dbl]),
     "xyz_run_candidates_noalloc": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _i64, _p]),
     "xyz_probe_peaks": (ctypes.c_int, [_p]),
+    "xyz_set_tiles": (ctypes.c_int, [_p, _p]),
+    "xyz_autotune_tiles": (ctypes.c_int, [_p, _i32, _dbl, _u64, _i64, _p, _p]),
     "xyz_server_create": (ctypes.c_int, [_i32, _i64, _i64, _p]),
     "xyz_server_add_dataset": (ctypes.c_int, [_p, _p, _p, _i64, _i64, _p]),
     "xyz_server_submit": (ctypes.c_int, [_p, _i32, _p, _i32, _i32, _dbl, _u64, _p]),
@@ -369,6 +376,20 @@ class Context:
 
     def set_spill_flush(self, groups: int):
         _check(load().xyz_set_spill_flush(self.handle, int(groups)))
+
+    def set_tiles(self, filter_threads: int = 0, verify_blocks_per_sm: int = 0, group_runs: int = 0):
+        """Launch shapes of later searches (0 = the default rule); results never depend on them."""
+        t = Tiles(filter_threads, verify_blocks_per_sm, group_runs)
+        _check(load().xyz_set_tiles(self.handle, ctypes.byref(t)))
+
+    def autotune_tiles(self, M: int, kappa: float, seed: int = 1, trial_runs: int = 4096):
+        """Launch shapes picked by timing searches of trial_runs runs; set on the context.
+        Returns (dict of the shapes, ms of the best trial)."""
+        t = Tiles()
+        ms = ctypes.c_double()
+        _check(load().xyz_autotune_tiles(self.handle, M, kappa, seed & (2**64 - 1), trial_runs, ctypes.byref(t),
+                                         ctypes.byref(ms)))
+        return {name: getattr(t, name) for name, _ in Tiles._fields_}, ms.value
 
     def set_onchip_partitions(self, max_parts: int):
         _check(load().xyz_set_onchip_partitions(self.handle, int(max_parts)))
