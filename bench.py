@@ -388,6 +388,8 @@ def gpu_arm(args):
         "frac": round(max(t_bytes, t_popc) / ver_s, 4) if ver_s > 0 else 0.0,
         "work_per_unit": f"{4 * W} bytes per distinct bucket column (columns of spilled runs not counted) "
                          f"and {W} popcounts per candidate",
+        "traffic": (load_traffic().get(f"verify_kernel:{args.workload}") or {}).get("bytes_per_launch"),
+        "traffic_units": (load_traffic().get(f"verify_kernel:{args.workload}") or {}).get("units_per_launch"),
         "bytes_alg": members * 4 * W, "popc_alg": cand * W, "t_hbm_ms": round(t_bytes * 1e3, 3),
         "t_popc_ms": round(t_popc * 1e3, 3),
         "peak_source": f"HBM: MEASURED_PEAKS.json hbm_gbs ({load_peaks().get('source')}); popc: measured in "
