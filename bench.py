@@ -72,6 +72,13 @@ def make_workload(name: str):
         kappa = 0.28
         label = ("gwas n=4000 p=1000000 (AR(0.6) blocks of 20, MAF U[0.05,0.5], 10 planted pairs "
                  "U[0.15,0.5] + 10 main effects)")
+    elif name == "gwas_mid":
+        from paper_1610_05108_gb300 import synth as _s
+        r = _s.rng_for(1, "plant")
+        d = _s.gwas(4000, 300000, 1, targets=tuple(float(t) for t in r.uniform(0.15, 0.5, size=10)))
+        kappa = 0.28
+        label = ("gwas n=4000 p=300000 (AR(0.6) blocks of 20, MAF U[0.05,0.5], 10 planted pairs "
+                 "U[0.15,0.5] + 10 main effects): a smaller case of the class-split filter")
     elif name == "gwas":
         d = synth.config_gwas(1)
         kappa = 0.3
@@ -276,6 +283,10 @@ def gpu_arm(args):
     M, L, targets, eta = plan(d, kappa)
     assert M == xyz.M_for_gamma0(d.p, 0.55)
     assert L == xyz.runs_for_recall(((1 + min(s for _, s in targets)) / 2) ** M, 0.95)
+    if args.M:
+        M = args.M
+        L = runs_for_recall(((1 + min(s for _, s in targets)) / 2) ** M, 0.95)
+        eta = [_hit(((1.0 + s) / 2.0) ** M, L) for _, s in targets]
     if args.L:
         L = args.L
     log(f"[bench] rank {rank}: n={d.n} p={d.p} M={M} L={L} kappa={kappa} targets={targets} eta={eta}")
@@ -376,7 +387,11 @@ def gpu_arm(args):
     ver_s = ms_stage["verify"] / 1e3
     members = sum(x["bucket_members"] for x in stats)
     hbm = float(load_peaks()["hbm_gbs"]) * 1e9
-    t_bytes = members * 4 * W / hbm
+    # packed columns that fit in L2 (half of its 126 MB, say) are not read
+    # from HBM after the first touch: then only the popcounts bound it
+    Wp = (W + 3) // 4 * 4
+    l2_resident = d.p * 4 * Wp <= 64 * 2**20
+    t_bytes = 0.0 if l2_resident else members * 4 * W / hbm
     t_popc = cand * W / peaks_probe["popc_ops_per_s"]
     vb = "hbm" if t_bytes >= t_popc else "popc"
     verify_roofline = {
@@ -386,8 +401,9 @@ def gpu_arm(args):
         "peak": round(hbm / 1e9, 1) if vb == "hbm" else round(peaks_probe["popc_ops_per_s"] / 1e12, 3),
         "unit": "GB/s" if vb == "hbm" else "Tpopc/s",
         "frac": round(max(t_bytes, t_popc) / ver_s, 4) if ver_s > 0 else 0.0,
-        "work_per_unit": f"{4 * W} bytes per distinct bucket column (columns of spilled runs not counted) "
-                         f"and {W} popcounts per candidate",
+        "work_per_unit": f"{4 * W} bytes per distinct bucket column (columns of spilled runs not counted; "
+                         f"none when the packed columns fit in L2) and {W} popcounts per candidate",
+        "packed_columns_l2_resident": l2_resident,
         "traffic": (load_traffic().get(f"verify_kernel:{args.workload}") or {}).get("bytes_per_launch"),
         "traffic_units": (load_traffic().get(f"verify_kernel:{args.workload}") or {}).get("units_per_launch"),
         "bytes_alg": members * 4 * W, "popc_alg": cand * W, "t_hbm_ms": round(t_bytes * 1e3, 3),
@@ -733,14 +749,25 @@ def instances_leg(args, xyz, torch):
     t0 = time.perf_counter()
     many = xyz.search_many(ctxs, L, M, kap, seeds)
     t_many = time.perf_counter() - t0
+    for c in ctxs:
+        c.set_fused_filter(False)
+    xyz.search_many(ctxs, L, M, kap, seeds)           # warm-up of the unfused graph
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    unfused = xyz.search_many(ctxs, L, M, kap, seeds)
+    t_unfused = time.perf_counter() - t0
     found = sum(int((0, 1) in set(zip(r["j"].tolist(), r["k"].tolist()))) for r in many)
     for c in ctxs:
         c.close()
     return {"count": len(sizes), "sizes": [list(x) for x in sizes], "M": M, "L": L,
             "sequential_s": round(t_seq, 4), "graph_s": round(t_many, 4),
+            "graph_unfused_s": round(t_unfused, 4),
             "speedup": round(t_seq / t_many, 3), "value_graph": pairs / t_many,
             "value_sequential": pairs / t_seq, "unit": UNIT,
-            "identical": all(np.array_equal(a, b) for a, b in zip(alone, many)),
+            "graph": "filters of one-group searches fused into one persistent launch per key class "
+                     "(graph_unfused_s: each filter its own launch)",
+            "identical": all(np.array_equal(a, b) for a, b in zip(alone, many))
+                         and all(np.array_equal(a, b) for a, b in zip(alone, unfused)),
             "planted_found": found}
 
 
@@ -1072,6 +1099,7 @@ def main(argv=None):
                     help="with --gpus N > 1: split one search's runs over the ranks (strong) or give every "
                          "rank its own searches (weak)")
     ap.add_argument("--L", type=int, default=0, help="override the number of runs")
+    ap.add_argument("--M", type=int, default=0, help="override M (L then follows the recall rule)")
     ap.add_argument("--extra-steps", type=int, default=3, help="timed searches of the autotuned and bestM legs")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -285,7 +285,9 @@ int xyz_autotune_tiles(xyz_ctx *ctx, int32_t M, double kappa, uint64_t seed, int
  * different n and p): search i is xyz_search(ctxs[i], L[i], M[i],
  * kappa[i], seed[i]) and its result is identical to that call.  The launch
  * groups of all searches are captured into one CUDA graph, forked over the
- * contexts' streams so that they run concurrently, and launched once; each
+ * contexts' streams so that they run concurrently, and launched once; the
+ * searches of one launch group on the single-filter path share one
+ * persistent filter launch per key class (xyz_set_fused_filter).  Each
  * search then finishes (spilled runs, union) on its own stream.  Results go
  * to one array: search i owns (*pairs)[offsets[i] .. offsets[i+1]); offsets
  * has count + 1 entries.  Contexts must be distinct, on one device, with
@@ -341,6 +343,15 @@ int xyz_set_spill_flush(xyz_ctx *ctx, int64_t groups);
  * there only 0 versus nonzero matters.  0 sends every such run to the sort.
  * 0 <= max_parts <= 32, default 32.  Results never depend on it. */
 int xyz_set_onchip_partitions(xyz_ctx *ctx, int32_t max_parts);
+
+/* Tuning (xyz_search_many): 1 (default) lets this context's search share a
+ * fused filter launch with the other searches of the call -- one persistent
+ * grid whose CTAs take the runs of all of them from one counter -- when the
+ * search is one launch group on the single-filter path (M <= 31,
+ * p <= 262144, binary X; at most 64 searches per launch, one launch per key
+ * class M <= 16, <= 24, <= 31).  0 keeps its filter a launch of its own.
+ * XYZ_EINVAL for other values.  Results never depend on it. */
+int xyz_set_fused_filter(xyz_ctx *ctx, int enable);
 
 /* --------------------------------------------------- parity / observability */
 

@@ -32,6 +32,7 @@
 // the general sort and join.  The survivors of a run are grouped on chip
 // into buckets and members, ready for verification.  In a run with c == 0
 // every column survives.
+#include <cstring>
 #include <type_traits>
 
 #include "bits.cuh"
@@ -596,18 +597,11 @@ __device__ __forceinline__ uint32_t group_segment_sorted(uint64_t *okeys, uint32
     return left_sh;
 }
 
-// One CTA per run at a time (passes 1-2 as described at the top of the
-// file).  When the run keeps at most FL_SMAX columns they are grouped on
-// chip: a hash table of group keys with packed side counts, each group
-// with candidates becomes a bucket (bucket and member space reserved with
-// one global atomic pair per run) and its members are written side A first.
-// A run that keeps more, after refinement (for example every column of a run
-// whose c is 0), goes to the CTA's global segment instead, for the general
-// sort and join.  Spilled survivors carry ((b << rbits | run) << M) | Kc in
-// 64-bit keys, run counted from the start of the search, and the per-CTA
-// segments fill across launch groups until the host sorts them.  kc_scratch
-// holds, per CTA, the keys of its current run in bit-major order: kx of
-// column 32w + cc at cc * P + w.
+// One work item of the survivor filter -- run r of the launch group and a
+// block of responses [b0, b1) -- as described at the top of the file: passes
+// 1-2, refinement and the on-chip grouping, for every thread of the CTA.
+// `cursor` is the CTA's fill of its global segment (shared memory, kept by
+// the caller across items of the same search).
 //
 // MB = 0: real X through the unbiased transform (Section 3.2); the keys are
 // drawn from the scaled real rows Xrs (row pitch Pf floats) instead of the
@@ -618,20 +612,38 @@ __device__ __forceinline__ uint32_t group_segment_sorted(uint64_t *okeys, uint32
 // response b (its response key c_b), and buckets carry b in their `pad`
 // field.  cnz is indexed (b << rbits) | run.
 template <int MB, bool BATCH>
-__global__ void __launch_bounds__(FL_THREADS, 1)
-    filter_kernel(const uint32_t *__restrict__ Xr, int64_t Pp, int64_t P,
-                  const uint32_t *__restrict__ ybs, int64_t Wp, int B, int64_t n, int64_t p, int M,
-                  uint64_t seed, int64_t l0, int R, int NB, int BB, int rbits, int64_t rbase,
-                  uint32_t mcap, uint32_t bcap, uint32_t *__restrict__ kc_scratch,
-                  void *__restrict__ seg_keys_v, uint32_t *__restrict__ seg_vals,
-                  uint32_t *__restrict__ seg_count, uint32_t seg_cap, int *__restrict__ overflow,
-                  uint8_t *__restrict__ cnz, uint32_t *__restrict__ members,
-                  uint32_t *__restrict__ members_count, Bucket *__restrict__ buckets,
-                  uint64_t *__restrict__ pair_counts, uint32_t *__restrict__ nbuckets,
-                  const uint64_t *__restrict__ cdf, uint64_t wtot, const float *__restrict__ Xrs,
-                  int64_t Pf, int part_max, uint32_t *__restrict__ work,
-                  unsigned long long *__restrict__ kept)
+__device__ __forceinline__ void filter_item(const FilterArgs &a, int item, uint32_t &cursor)
 {
+    // the launch group's arguments under their usual names
+    const uint32_t *__restrict__ Xr = a.Xr;
+    const int64_t Pp = a.Pp, P = a.P;
+    const uint32_t *__restrict__ ybs = a.ybs;
+    const int64_t Wp = a.Wp;
+    const int B = a.B;
+    const int64_t n = a.n, p = a.p;
+    const int M = a.M;
+    const uint64_t seed = a.seed;
+    const int64_t l0 = a.l0;
+    const int NB = a.NB, BB = a.BB, rbits = a.rbits;
+    const int64_t rbase = a.rbase;
+    const uint32_t mcap = a.mcap, bcap = a.bcap;
+    uint32_t *__restrict__ kc_scratch = a.kc_scratch;
+    void *__restrict__ seg_keys_v = a.seg_keys_v;
+    uint32_t *__restrict__ seg_vals = a.seg_vals;
+    const uint32_t seg_cap = a.seg_cap;
+    int *__restrict__ overflow = a.overflow;
+    uint8_t *__restrict__ cnz = a.cnz;
+    uint32_t *__restrict__ members = a.members;
+    uint32_t *__restrict__ members_count = a.members_count;
+    Bucket *__restrict__ buckets = a.buckets;
+    uint64_t *__restrict__ pair_counts = a.pair_counts;
+    uint32_t *__restrict__ nbuckets = a.nbuckets;
+    const uint64_t *__restrict__ cdf = a.cdf;
+    const uint64_t wtot = a.wtot;
+    const float *__restrict__ Xrs = a.Xrs;
+    const int64_t Pf = a.Pf;
+    const int part_max = a.part_max;
+    unsigned long long *__restrict__ kept = a.kept;
     using SegKey = uint64_t;
     extern __shared__ __align__(16) uint32_t fl_smem[];
     using Lay = FlLayout<BATCH>;
@@ -647,7 +659,6 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     __shared__ int64_t rowoff[32];      // row s_m times the row pitch
     __shared__ int64_t rowidx[32];      // row s_m
     __shared__ uint32_t c_sh;
-    __shared__ uint32_t cursor;         // global segment fill
     __shared__ uint32_t ns;             // survivors of the current (run, response)
     __shared__ uint32_t scur;           // survivor array fill after refinement
     const int T = (int)blockDim.x;      // a multiple of 32, at most FL_THREADS
@@ -665,20 +676,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         ++flog;
     const int fwords = 1 << (flog - 5);
     const int fshift = 32 - (flog - 5);
-    if (t == 0)
-        cursor = seg_count[blockIdx.x];     // segments fill across launch groups
-
-    // work item = (run r, block of responses [b0, b1)); the keys of the run
-    // and its filter are built once per item.  Items are taken from a
-    // launch-wide counter, so a CTA that drew an expensive run takes fewer.
-    __shared__ int item_sh;
-    for (;;) {
-        if (t == 0)
-            item_sh = (int)atomicAdd(work, 1u);
-        __syncthreads();
-        const int item = item_sh;           // every thread reads it before the next barrier
-        if (item >= R * NB)
-            break;
+    {
         const int r = item / NB;
         const int b0 = (item - r * NB) * BB;
         const int b1 = (b0 + BB < B) ? b0 + BB : B;
@@ -971,10 +969,100 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             group_on_chip<Lay>(sv, s, tkey, tcnt, nz, b, gout);
         }
     }
-    if (t == 0) {
-        seg_count[blockIdx.x] = cursor < seg_cap ? cursor : seg_cap;
-        if (cursor > seg_cap)
-            atomicOr(overflow, 1);
+}
+
+// One CTA per run at a time: the work items of one launch group of one
+// search, taken from a launch-wide counter, so a CTA that drew an expensive
+// run takes fewer.  When a run keeps at most SMAX columns they are grouped
+// on chip (a hash table of group keys with packed side counts; each group
+// with candidates becomes a bucket, its members written side A first); a
+// run that keeps more, after refinement, goes to the CTA's global segment
+// and is grouped from there in hash partitions, or left for the general
+// sort and join.  Spilled survivors carry ((b << rbits | run) << M) | Kc in
+// 64-bit keys, run counted from the start of the search, and the per-CTA
+// segments fill across launch groups until the host sorts them.
+// kc_scratch holds, per CTA, the keys of its current run in bit-major order:
+// kx of column 32w + cc at cc * P + w.
+template <int MB, bool BATCH>
+__global__ void __launch_bounds__(FL_THREADS, 1) filter_kernel(const __grid_constant__ FilterArgs a,
+                                                               uint32_t *__restrict__ work)
+{
+    __shared__ uint32_t cursor;         // global segment fill
+    __shared__ int item_sh;
+    if (threadIdx.x == 0)
+        cursor = a.seg_count[blockIdx.x];     // segments fill across launch groups
+    for (;;) {
+        if (threadIdx.x == 0)
+            item_sh = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int item = item_sh;           // every thread reads it before the next barrier
+        if (item >= a.R * a.NB)
+            break;
+        filter_item<MB, BATCH>(a, item, cursor);
+    }
+    if (threadIdx.x == 0) {
+        a.seg_count[blockIdx.x] = cursor < a.seg_cap ? cursor : a.seg_cap;
+        if (cursor > a.seg_cap)
+            atomicOr(a.overflow, 1);
+    }
+}
+
+// The arguments of the searches of one fused launch, and the first global
+// work item of each (item_start[count] = all items).
+struct FusedTable {
+    int count;
+    int item_start[XYZ_FUSED_MAX + 1];
+    FilterArgs args[XYZ_FUSED_MAX];
+};
+static_assert(sizeof(FusedTable) <= 32764, "the fused table fits the kernel parameter space");
+
+// Several independent searches (one launch group each, one response, binary
+// or weighted Y, the single filter) in one persistent launch: the work items
+// of all of them are taken from one launch-wide counter, in search order, so
+// the CTAs move on to the next search's runs as soon as the current one's
+// are handed out.  Each search keeps its own buffers; a CTA's segment fill
+// of a search is loaded when it takes that search's first item and stored
+// when it moves on.
+template <int MB>
+__global__ void __launch_bounds__(FL_THREADS, 1) filter_fused_kernel(const __grid_constant__ FusedTable tab,
+                                                                     uint32_t *__restrict__ work)
+{
+    __shared__ uint32_t cursor;
+    __shared__ int item_sh, inst_sh;
+    if (threadIdx.x == 0)
+        inst_sh = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int item = (int)atomicAdd(work, 1u);
+            item_sh = item;
+            if (item < tab.item_start[tab.count]) {
+                int i = inst_sh < 0 ? 0 : inst_sh;
+                while (tab.item_start[i + 1] <= item)
+                    ++i;
+                if (i != inst_sh) {
+                    if (inst_sh >= 0) {
+                        const FilterArgs &o = tab.args[inst_sh];
+                        o.seg_count[blockIdx.x] = cursor < o.seg_cap ? cursor : o.seg_cap;
+                        if (cursor > o.seg_cap)
+                            atomicOr(o.overflow, 1);
+                    }
+                    cursor = tab.args[i].seg_count[blockIdx.x];
+                    inst_sh = i;
+                }
+            }
+        }
+        __syncthreads();
+        const int item = item_sh;
+        if (item >= tab.item_start[tab.count])
+            break;
+        const int i = inst_sh;
+        filter_item<MB, false>(tab.args[i], item - tab.item_start[i], cursor);
+    }
+    if (threadIdx.x == 0 && inst_sh >= 0) {
+        const FilterArgs &o = tab.args[inst_sh];
+        o.seg_count[blockIdx.x] = cursor < o.seg_cap ? cursor : o.seg_cap;
+        if (cursor > o.seg_cap)
+            atomicOr(o.overflow, 1);
     }
 }
 
@@ -1556,15 +1644,53 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
                           uint32_t *seg_vals, uint32_t *seg_count, uint32_t seg_cap, int *overflow,
                           uint8_t *cnz, uint32_t *members, uint32_t *members_count, Bucket *buckets,
                           uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
-                          int64_t *launches, int part_max, uint32_t *work, unsigned long long *kept)
+                          int64_t *launches, int part_max, uint32_t *work, unsigned long long *kept,
+                          FilterArgs *defer)
 {
+    FilterArgs a;
+    a.Xr = pk.Xr;
+    a.Pp = pk.Pp;
+    a.P = pk.P;
+    a.ybs = ybs;
+    a.Wp = pk.Wp;
+    a.B = B;
+    a.n = pk.n;
+    a.p = pk.p;
+    a.M = M;
+    a.seed = seed;
+    a.l0 = l0;
+    a.R = R;
+    a.NB = NB;
+    a.BB = BB;
+    a.rbits = rbits;
+    a.rbase = rbase;
+    a.mcap = mcap;
+    a.bcap = bcap;
+    a.kc_scratch = kc_scratch;
+    a.seg_keys_v = seg_keys;
+    a.seg_vals = seg_vals;
+    a.seg_count = seg_count;
+    a.seg_cap = seg_cap;
+    a.overflow = overflow;
+    a.cnz = cnz;
+    a.members = members;
+    a.members_count = members_count;
+    a.buckets = buckets;
+    a.pair_counts = pair_counts;
+    a.nbuckets = nbuckets;
+    a.cdf = pk.cdf;
+    a.wtot = pk.wtotal;
+    a.Xrs = pk.Xrs;
+    a.Pf = pk.Pf;
+    a.part_max = part_max;
+    a.kept = kept;
+    if (defer) {
+        *defer = a;
+        return cudaSuccess;
+    }
     const bool batch = B > 1;
     const size_t smem = filter_smem_bytes(batch);
-    using KernT = void (*)(const uint32_t *, int64_t, int64_t, const uint32_t *, int64_t, int, int64_t,
-                           int64_t, int, uint64_t, int64_t, int, int, int, int, int64_t, uint32_t, uint32_t,
-                           uint32_t *, void *, uint32_t *, uint32_t *, uint32_t, int *, uint8_t *,
-                           uint32_t *, uint32_t *, Bucket *, uint64_t *, uint32_t *, const uint64_t *,
-                           uint64_t, const float *, int64_t, int, uint32_t *, unsigned long long *);
+    using KernT = void (*)(const FilterArgs, uint32_t *);
     KernT kern;
     if (batch)
         kern = M <= 8 ? filter_kernel<8, true> : M <= 16 ? filter_kernel<16, true>
@@ -1577,11 +1703,39 @@ cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, u
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    kern<<<grid, pk.filter_threads > 0 ? pk.filter_threads : filter_threads(pk.P), smem, s>>>(pk.Xr, pk.Pp, pk.P, ybs, pk.Wp, B, pk.n, pk.p, M, seed, l0, R,
-                                        NB, BB, rbits, rbase, mcap, bcap, kc_scratch, seg_keys, seg_vals,
-                                        seg_count, seg_cap, overflow, cnz, members, members_count,
-                                        buckets, pair_counts, nbuckets, pk.cdf, pk.wtotal, pk.Xrs, pk.Pf,
-                                        part_max, work, kept);
+    kern<<<grid, pk.filter_threads > 0 ? pk.filter_threads : filter_threads(pk.P), smem, s>>>(a, work);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+int fused_key_class(int M)
+{
+    return M <= 16 ? 16 : M <= 24 ? 24 : 32;
+}
+
+cudaError_t launch_filter_fused(const FilterArgs *args, int count, int key_class, int grid, uint32_t *work,
+                                cudaStream_t s, int64_t *launches)
+{
+    if (count < 1 || count > XYZ_FUSED_MAX)
+        return cudaErrorInvalidValue;
+    FusedTable tab;
+    std::memset(&tab, 0, sizeof(tab));
+    tab.count = count;
+    tab.item_start[0] = 0;
+    for (int i = 0; i < count; ++i) {
+        if (args[i].B != 1 || args[i].Xrs || fused_key_class(args[i].M) != key_class)
+            return cudaErrorInvalidValue;
+        tab.args[i] = args[i];
+        tab.item_start[i + 1] = tab.item_start[i] + args[i].R * args[i].NB;
+    }
+    using KernT = void (*)(const FusedTable, uint32_t *);
+    const KernT kern = key_class == 16 ? filter_fused_kernel<16>
+                       : key_class == 24 ? filter_fused_kernel<24> : filter_fused_kernel<32>;
+    const size_t smem = filter_smem_bytes(false);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    kern<<<grid, FL_THREADS, smem, s>>>(tab, work);
     *launches += 1;
     return cudaGetLastError();
 }

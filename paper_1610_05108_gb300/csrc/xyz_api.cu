@@ -98,6 +98,7 @@ struct xyz_ctx {
     int64_t mem_cap = 0;         // filter path: members of on-chip groups per launch group
     int64_t spill_flush = 0;     // filter path: launch groups per spill flush (0: one per search)
     int onchip_parts = 32;       // filter path: hash partitions on chip for runs past its capacity
+    int fuse_filters = 1;        // xyz_search_many: may join a fused filter launch
     DevBuf resp, ybs;            // batched search: response of each output pair, response bits
     DevBuf y_alt, y_stage;       // response updates: packed copy checked before use, host staging
     // real response (Section 3.1): live weights and a staging set swapped in
@@ -489,13 +490,41 @@ unsigned long long *ctr_kept(xyz_ctx *c)
 // enqueues the launch groups (no host synchronisation, no allocation, spills
 // left for the end); SP_FINISH does the rest (spills, union) after they ran,
 // and returns SP_RERUN when a buffer overflowed so the caller redoes the
-// search with SP_ALL.
-enum SearchPhase { SP_ALL = 0, SP_ENQUEUE = 1, SP_FINISH = 2, SP_PREPARE = 3 };
+// search with SP_ALL.  A search of one launch group whose filter joins a
+// fused launch with others (search_fusable) splits SP_ENQUEUE in two:
+// SP_ENQUEUE_PRE enqueues what comes before the filter and stores the
+// filter's arguments in *defer; SP_ENQUEUE_POST, after the fused launch,
+// what comes after it.
+enum SearchPhase { SP_ALL = 0, SP_ENQUEUE = 1, SP_FINISH = 2, SP_PREPARE = 3, SP_ENQUEUE_PRE = 4,
+                   SP_ENQUEUE_POST = 5 };
 constexpr int SP_RERUN = 100;
 
-int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t l1, int M,
-                     int64_t amin, uint64_t seed, int64_t *nout_host, int phase = SP_ALL)
+// Thresholds of a search at kappa: a real response passes when
+// 2S - Q >= kappa Q (Q the total weight), a real X when the dot product of
+// the transformed columns reaches kappa ||Y'||_1 (the oracle's reading).
+void set_kappa(xyz_ctx *c, double kappa)
 {
+    c->pk.wkq = kappa * (double)c->pk.wtotal;
+    c->pk.wscale = 0.0;
+    c->pk.rkq = kappa * c->pk.rnorm;
+}
+
+// Key class of the fused filter launch that a search of `runs` runs at M
+// can join (after SP_PREPARE), 0 when it cannot: one launch group, one
+// response, binary X and the single-filter path.
+int search_fusable(xyz_ctx *c, int64_t runs, int M)
+{
+    const Plan pl = make_plan(c, runs, M, 1);
+    if (!pl.filter || pl.big || c->pk.Xrs || runs > pl.R)
+        return 0;
+    return fused_key_class(M);
+}
+
+int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t l1, int M,
+                     int64_t amin, uint64_t seed, int64_t *nout_host, int phase = SP_ALL,
+                     FilterArgs *defer = nullptr)
+{
+    const bool enq = phase == SP_ENQUEUE || phase == SP_ENQUEUE_PRE || phase == SP_ENQUEUE_POST;
     const int64_t runs = l1 - l0;
     const int64_t p = c->pk.p;
     Plan pl = make_plan(c, runs, M, B);            // replanned when the class-split filter is given up
@@ -519,8 +548,11 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
         Timer tm(c->timing && phase == SP_ALL, c->stream, &launches);
         xyz_stats st;
         std::memset(&st, 0, sizeof(st));
-        if (phase != SP_FINISH)
+        if (phase != SP_FINISH && phase != SP_ENQUEUE_POST)
             CU(cudaMemsetAsync(c->counters.ptr, 0, 128, c->stream));
+        if ((phase == SP_ENQUEUE_PRE || phase == SP_ENQUEUE_POST) &&
+            (!pl.filter || pl.big || B != 1 || c->pk.Xrs || runs > pl.R || (phase == SP_ENQUEUE_PRE && !defer)))
+            return fail(XYZ_EINVAL, "search cannot join a fused filter launch");
         int64_t chunks = phase == SP_FINISH ? (runs + pl.R - 1) / pl.R : 0;
         int64_t surv_total = 0;
         int key_bits_max = 0;
@@ -618,16 +650,20 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                 CU(launch_seg_reset((uint32_t *)c->seg_count.ptr, c->stream, &launches));
                 return XYZ_OK;
             };
-            if (phase != SP_FINISH)
+            if (phase != SP_FINISH && phase != SP_ENQUEUE_POST)
                 CU(launch_seg_reset((uint32_t *)c->seg_count.ptr, c->stream, &launches));
             int64_t since_flush = 0;
             for (int64_t g0 = l0; g0 < l1 && !redo && phase != SP_FINISH; g0 += pl.R) {
                 const int64_t Rc = (l1 - g0) < pl.R ? (l1 - g0) : pl.R;
                 ++chunks;
-                CU(cudaMemsetAsync(ctr_u32(c), 0, 8, c->stream));   // buckets, members
-                CU(cudaMemsetAsync(ctr_work(c), 0, 4, c->stream));  // the filter's work items
+                if (phase != SP_ENQUEUE_POST) {
+                    CU(cudaMemsetAsync(ctr_u32(c), 0, 8, c->stream));   // buckets, members
+                    CU(cudaMemsetAsync(ctr_work(c), 0, 4, c->stream));  // the filter's work items
+                }
                 tm.begin(ST_KEYS);
-                if (pl.big)
+                if (phase == SP_ENQUEUE_POST)
+                    ;                                   // the filter ran in the fused launch
+                else if (pl.big)
                     CU(launch_filter_big(c->pk, M, seed, g0, (int)Rc, rbits, g0 - l0, grid,
                                          (uint32_t)(c->mem_cap < 0xFFFFFFFELL ? c->mem_cap : 0xFFFFFFFELL),
                                          (uint32_t)mb, (uint32_t *)c->lst_keys.ptr, (uint32_t *)c->lst_cols.ptr,
@@ -646,8 +682,10 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                      (uint8_t *)c->cnz.ptr, (uint32_t *)c->members.ptr, ctr_members(c),
                                      (Bucket *)c->buckets.ptr, (uint64_t *)c->pair_counts.ptr,
                                      ctr_nbuckets(c), c->stream, &launches, c->onchip_parts, ctr_work(c),
-                                         ctr_kept(c)));
+                                     ctr_kept(c), phase == SP_ENQUEUE_PRE ? defer : nullptr));
                 tm.end();
+                if (phase == SP_ENQUEUE_PRE)
+                    return XYZ_OK;                      // one launch group: the rest after the fused launch
                 tm.begin(ST_JOIN);
                 CU(scan_u64_dev((const uint64_t *)c->pair_counts.ptr, (uint64_t *)c->pair_off.ptr,
                                 ctr_nbuckets(c), mb, ctr_total(c), ctr_cand(c), c->scan_tmp.ptr,
@@ -696,7 +734,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                         return rc;
                 }
             }
-            if (phase == SP_ENQUEUE)
+            if (enq)
                 return XYZ_OK;
             if (redo)
                 continue;
@@ -789,7 +827,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                 tm.end();
             }
         }
-        if (phase == SP_ENQUEUE)
+        if (enq)
             return XYZ_OK;
         // record count -> host
         uint32_t nrec = 0;
@@ -1333,9 +1371,7 @@ int xyz_search_range(xyz_ctx *ctx, int64_t l0, int64_t l1, int32_t M, double kap
         return rc;
     const int64_t amin = amin_rule(ctx->pk.n, kappa);
     int64_t nout = 0;
-    ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;     // real response: 2S - Q >= kappa Q
-    ctx->pk.wscale = 0.0;
-    ctx->pk.rkq = kappa * ctx->pk.rnorm;               // real X: dot >= kappa ||Y'||_1 (as the oracle)
+    set_kappa(ctx, kappa);
     if (amin > ctx->pk.n && !ctx->pk.cdf) {
         std::memset(&ctx->stats, 0, sizeof(ctx->stats));
         *pairs = nullptr;
@@ -1538,8 +1574,7 @@ int xyz_search_abs(xyz_ctx *ctx, int32_t L, int32_t M, double kappa, uint64_t se
     if (!ctx->owns_packed || ctx->pk.Xrs)
         return fail(XYZ_EINVAL, "needs a binary X on a context that owns its response");
     const int64_t amin = amin_rule(ctx->pk.n, kappa);
-    ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;
-    ctx->pk.wscale = 0.0;
+    set_kappa(ctx, kappa);
     *pairs = nullptr;
     *npairs = 0;
     if (amin > ctx->pk.n && !ctx->pk.cdf)
@@ -1592,8 +1627,7 @@ int xyz_autotune_M(xyz_ctx *ctx, double kappa, double gamma, double recall, int3
     if (M_lo < 1 || M_hi < M_lo || M_hi > XYZ_MAX_M || trial_runs < 8)
         return fail(XYZ_EINVAL, "need 1 <= M_lo <= M_hi <= 64 and trial_runs >= 8");
     const int64_t amin = amin_rule(ctx->pk.n, kappa);
-    ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;
-    ctx->pk.wscale = 0.0;
+    set_kappa(ctx, kappa);
     const bool timing = ctx->timing;
     ctx->timing = false;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1712,8 +1746,7 @@ int xyz_search_many(xyz_ctx **ctxs, int32_t count, const int32_t *L, const int32
         if (ctxs[i]->device != ctxs[0]->device || !ctxs[i]->stream)
             return fail(XYZ_EINVAL, "contexts must share a device and own non-default streams");
         amin[(size_t)i] = amin_rule(ctxs[i]->pk.n, kappa[i]);
-        ctxs[i]->pk.wkq = kappa[i] * (double)ctxs[i]->pk.wtotal;
-        ctxs[i]->pk.wscale = 0.0;
+        set_kappa(ctxs[i], kappa[i]);
         live[(size_t)i] = amin[(size_t)i] <= ctxs[i]->pk.n || ctxs[i]->pk.cdf;
     }
     // 1. workspace of every search, before any capture
@@ -1723,12 +1756,24 @@ int xyz_search_many(xyz_ctx **ctxs, int32_t count, const int32_t *L, const int32
             (rc = run_search_multi(ctxs[i], ctxs[i]->pk.yb, 1, 0, L[i], M[i], amin[(size_t)i], seed[i], &nout,
                                    SP_PREPARE)))
             return rc;
+    // searches of one launch group on the single-filter path share fused
+    // filter launches, one per key class (in search order, at most
+    // XYZ_FUSED_MAX each), on the capture stream between their own work
+    std::vector<int> fclass((size_t)count, 0);
+    int nfused = 0;
+    for (int32_t i = 0; i < count; ++i)
+        if (live[(size_t)i] && ctxs[i]->fuse_filters) {
+            fclass[(size_t)i] = search_fusable(ctxs[i], L[i], M[i]);
+            nfused += fclass[(size_t)i] != 0;
+        }
+    if (nfused < 2)
+        std::fill(fclass.begin(), fclass.end(), 0);
     // 2. the launch groups of all searches, one stream each, captured into
     //    one graph that forks from and joins to a capture stream
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    std::vector<cudaEvent_t> ev((size_t)count + 1, nullptr);
+    std::vector<cudaEvent_t> ev((size_t)count + 2, nullptr);     // fork, one per search, fused filters done
     auto cleanup = [&]() {
         if (exec)
             cudaGraphExecDestroy(exec);
@@ -1748,8 +1793,61 @@ int xyz_search_many(xyz_ctx **ctxs, int32_t count, const int32_t *L, const int32
     if (e == cudaSuccess)
         e = cudaEventRecord(ev[0], cs);
     rc = XYZ_OK;
+    if (nfused >= 2 && e == cudaSuccess) {
+        // what precedes each fused search's filter, on its own stream
+        std::vector<FilterArgs> args((size_t)count);
+        std::vector<int32_t> order;
+        for (int32_t i = 0; i < count && e == cudaSuccess && !rc; ++i) {
+            if (!fclass[(size_t)i])
+                continue;
+            e = cudaStreamWaitEvent(ctxs[i]->stream, ev[0], 0);
+            if (e == cudaSuccess)
+                rc = run_search_multi(ctxs[i], ctxs[i]->pk.yb, 1, 0, L[i], M[i], amin[(size_t)i], seed[i], &nout,
+                                      SP_ENQUEUE_PRE, &args[(size_t)i]);
+            if (e == cudaSuccess && !rc)
+                e = cudaEventRecord(ev[(size_t)i + 1], ctxs[i]->stream);
+            if (e == cudaSuccess && !rc)
+                e = cudaStreamWaitEvent(cs, ev[(size_t)i + 1], 0);
+        }
+        // the fused launches; each takes its work counter from its first search
+        int64_t fl = 0;
+        const int kcls[3] = {16, 24, 32};
+        for (int k = 0; k < 3 && e == cudaSuccess && !rc; ++k) {
+            std::vector<FilterArgs> batch;
+            uint32_t *work = nullptr;
+            for (int32_t i = 0; i <= count && e == cudaSuccess; ++i) {
+                if (i < count && fclass[(size_t)i] == kcls[k]) {
+                    if (!work)
+                        work = ctr_work(ctxs[i]);
+                    batch.push_back(args[(size_t)i]);
+                }
+                if (!batch.empty() && (i == count || (int)batch.size() == XYZ_FUSED_MAX)) {
+                    e = cudaMemsetAsync(work, 0, 4, cs);
+                    if (e == cudaSuccess)
+                        e = launch_filter_fused(batch.data(), (int)batch.size(), kcls[k], filter_grid(),
+                                                work, cs, &fl);
+                    batch.clear();
+                    work = nullptr;
+                }
+            }
+        }
+        if (e == cudaSuccess && !rc)
+            e = cudaEventRecord(ev[(size_t)count + 1], cs);
+        for (int32_t i = 0; i < count && e == cudaSuccess && !rc; ++i) {
+            if (!fclass[(size_t)i])
+                continue;
+            e = cudaStreamWaitEvent(ctxs[i]->stream, ev[(size_t)count + 1], 0);
+            if (e == cudaSuccess)
+                rc = run_search_multi(ctxs[i], ctxs[i]->pk.yb, 1, 0, L[i], M[i], amin[(size_t)i], seed[i], &nout,
+                                      SP_ENQUEUE_POST);
+            if (e == cudaSuccess && !rc)
+                e = cudaEventRecord(ev[(size_t)i + 1], ctxs[i]->stream);
+            if (e == cudaSuccess && !rc)
+                e = cudaStreamWaitEvent(cs, ev[(size_t)i + 1], 0);
+        }
+    }
     for (int32_t i = 0; i < count && e == cudaSuccess && !rc; ++i) {
-        if (!live[(size_t)i])
+        if (!live[(size_t)i] || fclass[(size_t)i])
             continue;
         e = cudaStreamWaitEvent(ctxs[i]->stream, ev[0], 0);
         if (e == cudaSuccess)
@@ -1869,9 +1967,7 @@ int xyz_autotune_tiles(xyz_ctx *ctx, int32_t M, double kappa, uint64_t seed, int
     if (M < 0 || M > 31 || trial_runs < 8)
         return fail(XYZ_EINVAL, "need 0 <= M <= 31 and trial_runs >= 8");
     const int64_t amin = amin_rule(ctx->pk.n, kappa);
-    ctx->pk.wkq = kappa * (double)ctx->pk.wtotal;
-    ctx->pk.wscale = 0.0;
-    ctx->pk.rkq = kappa * ctx->pk.rnorm;
+    set_kappa(ctx, kappa);
     const bool timing = ctx->timing;
     ctx->timing = false;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -2122,6 +2218,14 @@ int xyz_set_onchip_partitions(xyz_ctx *ctx, int32_t max_parts)
     if (!ctx || max_parts < 0 || max_parts > 32)
         return fail(XYZ_EINVAL, "need a context and max_parts in [0, 32]");
     ctx->onchip_parts = max_parts;
+    return XYZ_OK;
+}
+
+int xyz_set_fused_filter(xyz_ctx *ctx, int enable)
+{
+    if (!ctx || (enable != 0 && enable != 1))
+        return fail(XYZ_EINVAL, "need a context and enable in {0, 1}");
+    ctx->fuse_filters = enable;
     return XYZ_OK;
 }
 

@@ -75,6 +75,44 @@ struct Bucket {
     uint32_t pad;
 };
 
+// Arguments of the single-filter survivor kernel for one launch group of
+// one search (see filter.cu); an array of them describes the instances of a
+// fused launch over several searches.
+struct FilterArgs {
+    const uint32_t *Xr;
+    int64_t Pp, P;
+    const uint32_t *ybs;
+    int64_t Wp;
+    int B;
+    int64_t n, p;
+    int M;
+    uint64_t seed;
+    int64_t l0;
+    int R, NB, BB, rbits;
+    int64_t rbase;
+    uint32_t mcap, bcap;
+    uint32_t *kc_scratch;
+    void *seg_keys_v;
+    uint32_t *seg_vals, *seg_count;
+    uint32_t seg_cap;
+    int *overflow;
+    uint8_t *cnz;
+    uint32_t *members, *members_count;
+    Bucket *buckets;
+    uint64_t *pair_counts;
+    uint32_t *nbuckets;
+    const uint64_t *cdf;
+    uint64_t wtot;
+    const float *Xrs;
+    int64_t Pf;
+    int part_max;
+    unsigned long long *kept;
+};
+
+// At most this many searches share one fused filter launch (their
+// arguments travel as one kernel parameter of about 18 KB).
+constexpr int XYZ_FUSED_MAX = 64;
+
 // ------------------------------------------------------ kernel launchers
 // Each returns cudaError_t of its launch(es); `launches` is incremented by
 // the number of kernels launched.
@@ -198,14 +236,26 @@ int64_t filter_run_cap();
 // member/bucket space (mcap/bcap) did.  A run whose survivors pass the
 // on-chip capacity is grouped on chip in at most part_max hash partitions
 // of its group keys when they fit (0: never; it then always spills).  work:
-// a zeroed counter from which the CTAs take their work items.
+// a zeroed counter from which the CTAs take their work items.  defer: when
+// not null, the launch's arguments are stored there and nothing is launched
+// (for launch_filter_fused).
 cudaError_t launch_filter(const Packed &pk, const uint32_t *ybs, int B, int M, uint64_t seed,
                           int64_t l0, int R, int NB, int BB, int rbits, int64_t rbase, int grid,
                           uint32_t mcap, uint32_t bcap, uint32_t *kc_scratch, uint64_t *seg_keys,
                           uint32_t *seg_vals, uint32_t *seg_count, uint32_t seg_cap, int *overflow,
                           uint8_t *cnz, uint32_t *members, uint32_t *members_count, Bucket *buckets,
                           uint64_t *pair_counts, uint32_t *nbuckets, cudaStream_t s,
-                          int64_t *launches, int part_max, uint32_t *work, unsigned long long *kept);
+                          int64_t *launches, int part_max, uint32_t *work, unsigned long long *kept,
+                          FilterArgs *defer = nullptr);
+// Searches of one key class (fused_key_class of their M: 16, 24 or 32) in one
+// persistent launch of `grid` CTAs of the largest filter CTA size (results
+// do not depend on it): args as recorded by
+// launch_filter with `defer` (one launch group each, B = 1, binary X); the
+// CTAs take the work items of all of them, in order, from the zeroed
+// counter `work`.  Every search's buffers must be sized for `grid` CTAs.
+int fused_key_class(int M);
+cudaError_t launch_filter_fused(const FilterArgs *args, int count, int key_class, int grid, uint32_t *work,
+                                cudaStream_t s, int64_t *launches);
 cudaError_t launch_seg_reset(uint32_t *seg_count, cudaStream_t s, int64_t *launches);
 cudaError_t launch_compact(const uint64_t *seg_keys, const uint32_t *seg_vals,
                            const uint32_t *seg_count, uint32_t seg_cap, int nseg, uint64_t *out_keys,

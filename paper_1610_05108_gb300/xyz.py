@@ -105,6 +105,7 @@ SIGNATURES = {
     "xyz_set_filter": (ctypes.c_int, [_p, ctypes.c_int]),
     "xyz_set_spill_flush": (ctypes.c_int, [_p, _i64]),
     "xyz_set_onchip_partitions": (ctypes.c_int, [_p, ctypes.c_int32]),
+    "xyz_set_fused_filter": (ctypes.c_int, [_p, ctypes.c_int]),
     "xyz_run_keys": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _p]),
     "xyz_run_candidates": (ctypes.c_int, [_p, _i32, _u64, _i64, _p, _p]),
     "xyz_agree": (ctypes.c_int, [_p, _p, _p, _i64, _p]),
@@ -393,6 +394,11 @@ class Context:
 
     def set_onchip_partitions(self, max_parts: int):
         _check(load().xyz_set_onchip_partitions(self.handle, int(max_parts)))
+
+    def set_fused_filter(self, enable: bool):
+        """Whether search_many may run this context's filter in a fused
+        launch with the other searches of the call."""
+        _check(load().xyz_set_fused_filter(self.handle, int(bool(enable))))
 
     def info(self) -> dict:
         n, p, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

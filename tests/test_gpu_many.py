@@ -2,7 +2,8 @@
 the same search run alone (and the oracle's, where it is small), for
 instances of uneven n and p that take the filter, general-sort (M >= 32)
 and partitioned (p > 262144) paths, including searches whose spilled runs
-and empty results finish outside the graph.
+and empty results finish outside the graph, and searches whose filters
+share fused persistent launches.
 """
 import numpy as np
 import pytest
@@ -68,4 +69,68 @@ def test_many_rejects_shared_context(xyz):
     with xyz.create(X, Y) as c:
         with pytest.raises(xyz.XyzError) as e:
             xyz.search_many([c, c], [2, 2], [5, 5], [0.3, 0.3], [1, 2])
+        assert e.value.code == xyz.XYZ_EINVAL
+
+
+def test_fused_filter_launch_equals_alone(xyz, orc):
+    # 70 searches of the key class M <= 16 (two fused launches: 64 + 6), some
+    # of M in 17..24 and 25..31, one weighted response, one real X through
+    # the unbiased transform and one class-split search (p > 262144), which
+    # keep launches of their own; fused, unfused and alone all agree
+    rng = np.random.default_rng(77)
+    specs = []
+    for i in range(70):
+        n = int(rng.integers(40, 400))
+        p = int(rng.integers(300, 6000))
+        specs.append((n, p, int(rng.integers(2, 40)), int(rng.integers(4, 17)), float(rng.uniform(0.2, 0.7))))
+    for i in range(6):
+        specs.append((int(rng.integers(100, 600)), int(rng.integers(2000, 40000)), int(rng.integers(2, 12)),
+                      int(rng.integers(17, 32)), float(rng.uniform(0.1, 0.5))))
+    ctxs, data = [], []
+    try:
+        for i, (n, p, L, M, kappa) in enumerate(specs):
+            X, Y = _inst(n, p, 500 + i, pair=(0, p - 1))
+            data.append((X, Y))
+            ctxs.append(xyz.create(X, Y))
+        # weighted response on one binary X
+        Xw, Yw = _inst(300, 3000, 999, pair=(2, 5))
+        yw = Yw.astype(np.float64) * np.random.default_rng(3).uniform(0.5, 2.0, size=300)
+        cw = xyz.create(Xw, Yw)
+        cw.set_y_real(yw)
+        ctxs.append(cw)
+        specs.append((300, 3000, 20, 10, 0.3))
+        # real X (unbiased transform) and a class-split search: not fused
+        Xr = np.asfortranarray(np.random.default_rng(4).standard_normal((100, 800)))
+        Yr = Xr[:, 3] * Xr[:, 7] + 0.1 * np.random.default_rng(5).standard_normal(100)
+        ctxs.append(xyz.Context.from_real_unbiased(Xr, Yr))
+        specs.append((100, 800, 10, 8, 0.3))
+        Xb, Yb = _inst(64, 300000, 998, pair=(1, 2))
+        ctxs.append(xyz.create(Xb, Yb))
+        specs.append((64, 300000, 2, 12, 0.6))
+        Ls, Ms, ks = [s[2] for s in specs], [s[3] for s in specs], [s[4] for s in specs]
+        seeds = [1000 + i for i in range(len(specs))]
+        fused = xyz.search_many(ctxs, Ls, Ms, ks, seeds)
+        for c in ctxs:
+            c.set_fused_filter(False)
+        plain = xyz.search_many(ctxs, Ls, Ms, ks, seeds)
+        for c in ctxs:
+            c.set_fused_filter(True)
+        for i, c in enumerate(ctxs):
+            want = c.search(Ls[i], Ms[i], ks[i], seeds[i])
+            assert np.array_equal(fused[i], want), i
+            assert np.array_equal(plain[i], want), i
+        for i in range(0, 70, 9):                       # oracle on a sample of the binary searches
+            X, Y = data[i]
+            assert np.array_equal(_arr(fused[i]), orc.xyz(X, Y, Ls[i], Ms[i], ks[i], seeds[i])), i
+        assert sum(len(f) for f in fused) > 0
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_fused_filter_setting_checked(xyz):
+    X, Y = _inst(64, 100, 1)
+    with xyz.create(X, Y) as c:
+        with pytest.raises(xyz.XyzError) as e:
+            xyz._check(xyz.load().xyz_set_fused_filter(c.handle, 2))
         assert e.value.code == xyz.XYZ_EINVAL
