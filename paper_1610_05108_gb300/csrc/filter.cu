@@ -458,33 +458,29 @@ __device__ __forceinline__ bool group_from_segment(const uint64_t *okeys, const 
     return true;
 }
 
-// The s entries of one run at seg[seg0 ..) -- key runbits | Kc and the
-// entry's place in the class lists (class << 27 | index, its column at
-// xlat[class * xcap + index]) -- grouped on chip with one counting sort by
-// a hash of the group key (32 bins) into tmp (tmp_cap entries of global
-// memory, Kc << 32 | column): the entries of contiguous bin ranges of at
-// most SMAX entries are then copied to sv and grouped there, and a bin
-// above SMAX is grouped straight from tmp (group_stream).  A bin whose
-// distinct group keys do not fit the table is written back to the segment
-// (runbits | Kc, column) for the general sort and join.  Returns the number
-// of entries left in the segment at seg0 (their values are columns), or
+// The s entries of one run at seg[seg0 ..) -- key runbits | Kc and column
+// -- grouped on chip with one counting sort by a hash of the group key (32
+// bins) into tmp (tmp_cap entries of global memory, Kc << 32 | column): the
+// entries of contiguous bin ranges of at most SMAX entries are then copied
+// to sv and grouped there, and a bin above SMAX is grouped straight from
+// tmp (group_stream).  A bin whose distinct group keys do not fit the table
+// is written back to the segment (runbits | Kc, column) for the general sort
+// and join.  Returns the number of entries left in the segment at seg0, or
 // GS_NONE when nothing was done because the run overflowed the segment or
-// s > tmp_cap (the segment then still holds list places: in the first case
-// the host redoes the search with larger segments, in the second the caller
-// looks the columns up).  Called by every thread of the CTA.
+// s > tmp_cap (the segment then still holds all of them).  Called by every
+// thread of the CTA.
 constexpr uint32_t GS_NONE = 0xFFFFFFFFu;
 template <class Lay>
 __device__ __forceinline__ uint32_t group_segment_sorted(uint64_t *okeys, uint32_t *ovals, uint32_t seg0,
                                                          uint32_t s, uint32_t seg_cap, uint32_t kcmask,
                                                          uint64_t runbits, uint64_t *sv, uint32_t *tkey,
                                                          uint32_t *tcnt, bool nz, int b, const GroupOut &g,
-                                                         const uint32_t *xlat, uint32_t xcap, uint64_t *tmp,
-                                                         uint32_t tmp_cap)
+                                                         uint64_t *tmp, uint32_t tmp_cap)
 {
     __shared__ uint32_t bstart[33];     // bin q of tmp: [bstart[q], bstart[q + 1])
     __shared__ uint32_t wsum2[FL_THREADS / 32];
     __shared__ uint32_t left_sh;
-    constexpr int GB = 4;               // entries per thread and step (loads in flight)
+    constexpr int GB = 8;               // entries per thread and step (loads in flight)
     constexpr uint32_t SMAX = (uint32_t)Lay::SMAX;
     const int t = threadIdx.x, T = (int)blockDim.x;
     const int lane = t & 31, wp = t >> 5, nwarps = T >> 5;
@@ -538,7 +534,7 @@ __device__ __forceinline__ uint32_t group_segment_sorted(uint64_t *okeys, uint32
             bstart[32] = ex + v;
     }
     __syncthreads();
-    // scatter to tmp, columns looked up on the way
+    // scatter to tmp
     for (uint32_t i0 = t; i0 - t < s; i0 += GB * (uint32_t)T) {
         uint32_t Kc[GB], v[GB];
 #pragma unroll
@@ -547,10 +543,6 @@ __device__ __forceinline__ uint32_t group_segment_sorted(uint64_t *okeys, uint32
             Kc[u] = i < s ? (uint32_t)(okeys[seg0 + i] & kcmask) : 0u;
             v[u] = i < s ? ovals[seg0 + i] : 0u;
         }
-#pragma unroll
-        for (int u = 0; u < GB; ++u)
-            if (i0 + u * (uint32_t)T < s)
-                v[u] = xlat[(int64_t)(v[u] >> 27) * xcap + (v[u] & 0x7FFFFFFu)];
 #pragma unroll
         for (int u = 0; u < GB; ++u) {
             if (i0 + u * (uint32_t)T < s) {
@@ -586,8 +578,18 @@ __device__ __forceinline__ uint32_t group_segment_sorted(uint64_t *okeys, uint32
         while (be < 32 && bstart[be + 1] - bstart[bn] <= SMAX)
             ++be;
         const uint32_t n0 = bstart[bn], cnt = bstart[be] - n0;
-        for (uint32_t i = t; i < cnt; i += (uint32_t)T)
-            sv[i] = tmp[n0 + i];
+        for (uint32_t i0 = t; i0 - t < cnt; i0 += GB * (uint32_t)T) {     // GB loads in flight
+            uint64_t e[GB];
+#pragma unroll
+            for (int u = 0; u < GB; ++u) {
+                const uint32_t i = i0 + u * (uint32_t)T;
+                e[u] = i < cnt ? tmp[n0 + i] : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < GB; ++u)
+                if (i0 + u * (uint32_t)T < cnt)
+                    sv[i0 + u * (uint32_t)T] = e[u];
+        }
         __syncthreads();
         if (cnt)
             group_on_chip<Lay>(sv, cnt, tkey, tcnt, nz, b, g);
@@ -1095,7 +1097,7 @@ __device__ __forceinline__ uint32_t key_class(uint32_t k)
 //           by the keys k of class q ^ class(c) -- exactly those with
 //           k ^ c in class q, so every key k ^ c is looked up in the filter
 //           that holds its class; survivors go to the CTA's segment as
-//           (runbits | Kc, list place).  A run with c == 0 keeps the keys
+//           (runbits | Kc, column).  A run with c == 0 keeps the keys
 //           that occur at least twice (two filters per class).
 //
 // Each round's filter holds about p/16 keys, which keeps its load, and with
@@ -1127,11 +1129,11 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     // accesses are then free of bank conflicts.
     constexpr int FB_STAGE = 16 * FL_THREADS;      // entries of a half-tile, 8 bytes each
     constexpr int FB_CUR = 2 * FB_STAGE;
-    constexpr int FB_RB = 8;                       // list entries per thread and step in the rounds
-    constexpr int FB_EB = 8;                       // of which emitted together
+    constexpr int FB_V = 2;                        // 16-byte list words per thread and step in the rounds
+    constexpr int FB_EB = 8;                       // list entries emitted together
     constexpr int FB_EMIT = FL_FWORDS;            // rounds: per-warp buffers of passing entries
-    constexpr int FB_QSHIFT = 27;                  // list place = class << 27 | index (lcap < 2^27)
     static_assert(FB_EMIT + (FL_THREADS / 32) * FB_EB * 32 * 2 <= Lay::WORDS, "emission buffers fit");
+    static_assert((4 * FB_V) % FB_EB == 0, "whole emission groups per step");
     static_assert(FB_CUR + 16 * (FL_THREADS + FL_THREADS / 8) <= Lay::WORDS,
                   "staging and cursors fit the shared memory");
     static_assert(FB_STAGE < 65536, "a half-tile's positions fit 16 bits");
@@ -1346,34 +1348,44 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         const uint64_t runbits = rl << M;
 
         // entries of class q2 that pass (all of them when c == 0) to the
-        // segment; the whole CTA walks the class list, each thread FB_RB
-        // entries at a time (independent loads in flight).  A warp gathers
-        // its passing entries (key, list index) in its shared buffer and
-        // writes them to the segment with consecutive lanes, after one
-        // reservation.  The segment value is the entry's place in the class
-        // lists, q2 << FB_QSHIFT | index; the grouping looks the column up
-        // (and a run left in the segment has its columns looked up in place),
-        // so no warp waits on that load here.
+        // segment with their columns.  The whole CTA walks the class list in
+        // 16-byte words (four keys, and the same word of the columns), each
+        // thread FB_V words at a time (independent loads in flight; the
+        // list's memory runs to a multiple of 16 bytes, and keys past its
+        // fill are masked).  A warp gathers its passing entries (column,
+        // key) in its shared buffer and writes them to the segment with
+        // consecutive lanes, after one reservation.
         uint64_t *wbuf = reinterpret_cast<uint64_t *>(fl_smem + FB_EMIT) + wp * (FB_EB * 32);
         auto emit_class = [&](uint32_t q2, const uint32_t *Ft, int fs) {
             const uint32_t n2 = cls_n[q2] < lcap ? cls_n[q2] : lcap;
-            const uint32_t *lkq = lk + (int64_t)q2 * lcap;
-            for (uint32_t i0 = t; i0 - t < n2; i0 += FB_RB * (uint32_t)T) {
-                uint32_t k[FB_RB];
+            const uint32_t n4 = (n2 + 3) >> 2;
+            const uint4 *lkq = reinterpret_cast<const uint4 *>(lk + (int64_t)q2 * lcap);
+            const uint4 *lcq = reinterpret_cast<const uint4 *>(lc + (int64_t)q2 * lcap);
+            for (uint32_t j0 = t; j0 - t < n4; j0 += FB_V * (uint32_t)T) {
+                uint32_t k[4 * FB_V], cl[4 * FB_V];
 #pragma unroll
-                for (int u = 0; u < FB_RB; ++u) {
-                    const uint32_t i = i0 + u * (uint32_t)T;
-                    k[u] = i < n2 ? lkq[i] : 0u;
+                for (int u = 0; u < FB_V; ++u) {
+                    const uint32_t j = j0 + u * (uint32_t)T;
+                    const uint4 v = j < n4 ? __ldcg(lkq + j) : make_uint4(0u, 0u, 0u, 0u);
+                    const uint4 w = j < n4 ? __ldcg(lcq + j) : make_uint4(0u, 0u, 0u, 0u);
+                    k[4 * u] = v.x;
+                    k[4 * u + 1] = v.y;
+                    k[4 * u + 2] = v.z;
+                    k[4 * u + 3] = v.w;
+                    cl[4 * u] = w.x;
+                    cl[4 * u + 1] = w.y;
+                    cl[4 * u + 2] = w.z;
+                    cl[4 * u + 3] = w.w;
                 }
-                uint32_t pm = 0;           // bit u: entry i0 + u T passes
+                uint32_t pm = 0;           // bit 4u + x: key x of word j0 + u T passes
 #pragma unroll
-                for (int u = 0; u < FB_RB; ++u) {
-                    const uint32_t i = i0 + u * (uint32_t)T;
-                    if (i < n2 && bloom_has3(Ft, k[u] ^ c, fs))
-                        pm |= 1u << u;
+                for (int e = 0; e < 4 * FB_V; ++e) {
+                    const uint32_t i = 4 * (j0 + (e >> 2) * (uint32_t)T) + (e & 3);
+                    if (i < n2 && bloom_has3(Ft, k[e] ^ c, fs))
+                        pm |= 1u << e;
                 }
 #pragma unroll
-                for (int e0 = 0; e0 < FB_RB; e0 += FB_EB) {
+                for (int e0 = 0; e0 < 4 * FB_V; e0 += FB_EB) {
                     const uint32_t pe = (pm >> e0) & ((1u << FB_EB) - 1u);
                     const uint32_t cnt = __popc(pe);
                     uint32_t incl = cnt;
@@ -1388,9 +1400,11 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                         continue;
                     uint32_t o = incl - cnt;
 #pragma unroll
-                    for (int u = 0; u < FB_EB; ++u)
+                    for (int u = 0; u < FB_EB; ++u) {
+                        const int e = e0 + u;
                         if ((pe >> u) & 1u)
-                            wbuf[o++] = ((uint64_t)(i0 + (e0 + u) * (uint32_t)T) << 32) | k[e0 + u];
+                            wbuf[o++] = ((uint64_t)cl[e] << 32) | k[e];
+                    }
                     uint32_t base = 0;
                     if (lane == 0)
                         base = atomicAdd(&cursor, wt);
@@ -1401,10 +1415,37 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                         const uint32_t at = base + e;
                         if (at < seg_cap) {
                             okeys[at] = runbits | canon((uint32_t)v, c, tb, lowmask);
-                            ovals[at] = (q2 << FB_QSHIFT) | (uint32_t)(v >> 32);   // column looked up later
+                            ovals[at] = (uint32_t)(v >> 32);
                         }
                     }
                     __syncwarp();
+                }
+            }
+        };
+        // keys of class q into the round's filter(s), FB_V 16-byte words per
+        // thread and step; ins(key) does the insert
+        auto insert_class = [&](uint32_t q, auto ins) {
+            const uint32_t nq = cls_n[q] < lcap ? cls_n[q] : lcap;
+            const uint32_t n4 = (nq + 3) >> 2;
+            const uint4 *lkq = reinterpret_cast<const uint4 *>(lk + (int64_t)q * lcap);
+            for (uint32_t j0 = t; j0 - t < n4; j0 += FB_V * (uint32_t)T) {
+                uint4 v[FB_V];
+#pragma unroll
+                for (int u = 0; u < FB_V; ++u) {
+                    const uint32_t j = j0 + u * (uint32_t)T;
+                    v[u] = j < n4 ? __ldcg(lkq + j) : make_uint4(0u, 0u, 0u, 0u);
+                }
+#pragma unroll
+                for (int u = 0; u < FB_V; ++u) {
+                    const uint32_t i = 4 * (j0 + u * (uint32_t)T);
+                    if (i < nq)
+                        ins(v[u].x);
+                    if (i + 1 < nq)
+                        ins(v[u].y);
+                    if (i + 2 < nq)
+                        ins(v[u].z);
+                    if (i + 3 < nq)
+                        ins(v[u].w);
                 }
             }
         };
@@ -1423,25 +1464,12 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 for (int i = t; i < FL_FWORDS / 4; i += T)
                     reinterpret_cast<uint4 *>(F)[i] = make_uint4(0u, 0u, 0u, 0u);
                 __syncthreads();
-                const uint32_t nq = cls_n[q] < lcap ? cls_n[q] : lcap;
-                const uint32_t *lkq = lk + (int64_t)q * lcap;
-                for (uint32_t i0 = t; i0 - t < nq; i0 += FB_RB * (uint32_t)T) {
-                    uint32_t k[FB_RB];
-#pragma unroll
-                    for (int u = 0; u < FB_RB; ++u) {
-                        const uint32_t i = i0 + u * (uint32_t)T;
-                        k[u] = i < nq ? lkq[i] : 0u;
-                    }
-#pragma unroll
-                    for (int u = 0; u < FB_RB; ++u) {
-                        if (i0 + u * (uint32_t)T < nq) {
-                            uint32_t word, mask;
-                            bloom_pos3(k[u], fs2, word, mask);
-                            if ((atomicOr(F1 + word, mask) & mask) == mask)
-                                atomicOr(F2 + word, mask);
-                        }
-                    }
-                }
+                insert_class(q, [&](uint32_t key) {
+                    uint32_t word, mask;
+                    bloom_pos3(key, fs2, word, mask);
+                    if ((atomicOr(F1 + word, mask) & mask) == mask)
+                        atomicOr(F2 + word, mask);
+                });
                 __syncthreads();
                 emit_class(q, F2, fs2);
                 __syncthreads();
@@ -1452,24 +1480,11 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
                 for (int i = t; i < FL_FWORDS / 4; i += T)
                     reinterpret_cast<uint4 *>(F)[i] = make_uint4(0u, 0u, 0u, 0u);
                 __syncthreads();
-                const uint32_t nq = cls_n[q] < lcap ? cls_n[q] : lcap;
-                const uint32_t *lkq = lk + (int64_t)q * lcap;
-                for (uint32_t i0 = t; i0 - t < nq; i0 += FB_RB * (uint32_t)T) {
-                    uint32_t k[FB_RB];
-#pragma unroll
-                    for (int u = 0; u < FB_RB; ++u) {
-                        const uint32_t i = i0 + u * (uint32_t)T;
-                        k[u] = i < nq ? lkq[i] : 0u;
-                    }
-#pragma unroll
-                    for (int u = 0; u < FB_RB; ++u) {
-                        if (i0 + u * (uint32_t)T < nq) {
-                            uint32_t word, mask;
-                            bloom_pos3(k[u], fshift, word, mask);
-                            atomicOr(F + word, mask);
-                        }
-                    }
-                }
+                insert_class(q, [&](uint32_t key) {
+                    uint32_t word, mask;
+                    bloom_pos3(key, fshift, word, mask);
+                    atomicOr(F + word, mask);
+                });
                 __syncthreads();
                 emit_class(q ^ cq, F, fshift);
                 __syncthreads();
@@ -1481,31 +1496,11 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
             atomicAdd(kept, (unsigned long long)s);
         __syncthreads();                     // every thread has read the cursor
         // the keys list is dead after the rounds: the run's entries are
-        // sorted by bin there (the columns list is still read)
+        // sorted by bin there
         uint32_t left = part_max > 0
             ? group_segment_sorted<Lay>(okeys, ovals, seg0, s, seg_cap, kcmask, runbits, sv, tkey, tcnt, nz, 0,
-                                        gout, lc, lcap, reinterpret_cast<uint64_t *>(lk), 8 * lcap)
+                                        gout, reinterpret_cast<uint64_t *>(lk), 8 * lcap)
             : GS_NONE;
-        if (left == GS_NONE && (uint64_t)seg0 + s <= seg_cap) {
-            // nothing grouped (no on-chip grouping, or more entries than the
-            // sort room): the columns in place of the list places
-            for (uint32_t i0 = t; i0 - t < s; i0 += 4 * (uint32_t)T) {
-                uint32_t v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t i = i0 + u * (uint32_t)T;
-                    v[u] = i < s ? ovals[seg0 + i] : 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (i0 + u * (uint32_t)T < s)
-                        v[u] = lc[(int64_t)(v[u] >> FB_QSHIFT) * lcap + (v[u] & ((1u << FB_QSHIFT) - 1u))];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (i0 + u * (uint32_t)T < s)
-                        ovals[seg0 + i0 + u * (uint32_t)T] = v[u];
-            }
-        }
         if (left == GS_NONE)
             left = s;
         else if (t == 0 && s > (uint32_t)Lay::SMAX)
