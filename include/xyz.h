@@ -460,14 +460,20 @@ int xyz_run_candidates_noalloc(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t r
  * is a request.  Datasets (packed X and a
  * default response) stay resident on the device; requests carry their own
  * response, L, M, kappa and seed.  Requests are admitted in arrival order
- * while the device memory in use (resident datasets + the workers'
- * workspaces + about one packed response and 1 MiB per admitted request)
- * stays within hbm_budget_bytes; the others wait (the oldest waiting request
- * is admitted whenever nothing is running, so none waits forever).  Admitted
- * requests are cut into slices of slice_runs runs, and `workers` threads --
- * each with its own CUDA stream and workspace -- take slices round-robin
- * over all admitted requests (continuous batching at run granularity).  The
- * result of a request is the union over its slices, which equals
+ * while the device memory in use stays within hbm_budget_bytes: the
+ * resident datasets, the workers' workspaces as measured after their last
+ * slice, and for each admitted request a reservation sized at admission --
+ * its packed response (when it has its own) plus the growth its slices may
+ * cause in every worker's workspace, by the library's own workspace sizing
+ * for a search of slice_runs runs at the request's M (buffers that a search
+ * grows on overflow count at their starting size).  The others wait (the
+ * oldest waiting request is admitted whenever nothing is running, so none
+ * waits forever).  Admitted requests are cut into slices of slice_runs runs,
+ * and `workers` threads -- each with its own CUDA stream and workspace --
+ * take slices round-robin over all admitted requests (continuous batching
+ * at run granularity).  Each slice is a search over its run range, whose
+ * results are deduplicated and sorted on the device; a request's result is
+ * the merge of its slices' sorted results, each pair once, which equals
  * xyz_search(L, M, kappa, seed) on its (X, Y) exactly, whatever else is
  * being served.  All xyz_server_* calls are thread-safe. */
 typedef struct xyz_server xyz_server;

@@ -52,8 +52,9 @@ struct Request {
     uint64_t seed = 0;
     int64_t next_run = 0;         // first run not yet handed out
     int slices_out = 0, slices_done = 0;
-    int64_t reserve = 0;          // bytes counted against the budget
-    std::vector<xyz_pair> acc;
+    int64_t reserve = 0;          // bytes counted against the budget while admitted
+    std::vector<std::vector<xyz_pair>> parts;   // slice results, each sorted by (j, k), each pair once
+    std::vector<xyz_pair> acc;    // their union (finish)
     ReqState state = RQ_QUEUED;
     int err_code = 0;
     std::string err;
@@ -85,6 +86,7 @@ struct xyz_server {
     std::vector<int64_t> worker_bytes;
     std::vector<std::thread> threads;
     std::vector<xyz_ctx *> views;
+    std::vector<xyz_ctx *> shadows;   // sizing snapshot of each worker's view, updated under the lock
     // device buffers for requests' packed responses, reused across requests
     std::vector<std::pair<size_t, uint32_t *>> yb_free;
     bool stop = false;
@@ -147,6 +149,23 @@ uint32_t *take_yb(xyz_server *s, size_t bytes)
     return p;
 }
 
+// Device bytes to reserve for a request while it is admitted: its own
+// response bits, and the growth its slices may cause in the workers'
+// workspaces -- for every worker, since any may take a slice -- sized by the
+// library's own workspace rules from each worker's current sizes (lock
+// held).  Growth that has happened shows in the workers' measured bytes
+// from then on, so until the request finishes it is counted twice: the
+// estimate errs towards waiting.
+int64_t reservation(xyz_server *s, const Request &r)
+{
+    const xyz_ctx *base = s->datasets[r.dataset].base;
+    int64_t b = r.yb ? (int64_t)ctx_packed(base)->Wp * 4 : 0;
+    const int64_t runs = std::min<int64_t>(r.L, s->slice_runs);
+    for (const xyz_ctx *sh : s->shadows)
+        b += ctx_slice_growth(sh, base, runs, r.M);
+    return b;
+}
+
 // Move queued requests to active while the budget allows (lock held).
 // The oldest waiting request is always admitted when nothing is active,
 // so a request larger than the budget cannot wait forever.
@@ -163,6 +182,7 @@ void admit(xyz_server *s)
             s->cv_done.notify_all();
             continue;
         }
+        r.reserve = reservation(s, r);
         if (!s->active.empty() && in_use(s) + r.reserve > s->budget)
             break;
         r.state = RQ_ACTIVE;
@@ -173,15 +193,44 @@ void admit(xyz_server *s)
     }
 }
 
+// Union of sorted, duplicate-free slice results into one sorted list with
+// each pair once: a merge over the slices' heads (the union within a slice
+// ran on the device, in the search).
+std::vector<xyz_pair> merge_parts(std::vector<std::vector<xyz_pair>> &parts)
+{
+    auto later = [](const std::pair<xyz_pair, size_t> &a, const std::pair<xyz_pair, size_t> &b) {
+        return a.first.j != b.first.j ? a.first.j > b.first.j : a.first.k > b.first.k;
+    };
+    std::vector<std::pair<xyz_pair, size_t>> heap;
+    std::vector<size_t> at(parts.size(), 0);
+    size_t total = 0;
+    for (size_t i = 0; i < parts.size(); ++i) {
+        total += parts[i].size();
+        if (!parts[i].empty())
+            heap.emplace_back(parts[i][0], i);
+    }
+    std::make_heap(heap.begin(), heap.end(), later);
+    std::vector<xyz_pair> out;
+    out.reserve(total);
+    while (!heap.empty()) {
+        std::pop_heap(heap.begin(), heap.end(), later);
+        const xyz_pair e = heap.back().first;
+        const size_t i = heap.back().second;
+        heap.pop_back();
+        if (out.empty() || out.back().j != e.j || out.back().k != e.k)
+            out.push_back(e);
+        if (++at[i] < parts[i].size()) {
+            heap.emplace_back(parts[i][at[i]], i);
+            std::push_heap(heap.begin(), heap.end(), later);
+        }
+    }
+    parts.clear();
+    return out;
+}
+
 void finish(xyz_server *s, Request &r)
 {
-    // union of the slices' results: each pair once, sorted by (j, k)
-    std::sort(r.acc.begin(), r.acc.end(), [](const xyz_pair &a, const xyz_pair &b) {
-        return a.j != b.j ? a.j < b.j : a.k < b.k;
-    });
-    r.acc.erase(std::unique(r.acc.begin(), r.acc.end(),
-                            [](const xyz_pair &a, const xyz_pair &b) { return a.j == b.j && a.k == b.k; }),
-                r.acc.end());
+    r.acc = merge_parts(r.parts);
     r.t_done = Clock::now();
     s->reserved -= r.reserve;
     if (r.cancel) {
@@ -252,12 +301,13 @@ void worker_main(xyz_server *s, int w)
 
         lk.lock();
         s->worker_bytes[w] = wb;
+        ctx_sizing_update(s->shadows[w], view);
         Request &q = s->reqs[rid];
         if (rc) {
             q.err_code = rc;
             q.err = msg;
         } else if (np > 0) {
-            q.acc.insert(q.acc.end(), pairs, pairs + np);
+            q.parts.emplace_back(pairs, pairs + np);
         }
         xyz_free_pairs(pairs);
         q.slices_done++;
@@ -316,10 +366,21 @@ int xyz_server_create(int32_t workers, int64_t hbm_budget_bytes, int64_t slice_r
         if (rc) {
             for (xyz_ctx *x : s->views)
                 xyz_destroy(x);
+            for (xyz_ctx *x : s->shadows)
+                ctx_sizing_free(x);
             delete s;
             return rc;
         }
         s->views.push_back(v);
+        s->shadows.push_back(ctx_sizing_copy(v));
+        if (!s->shadows.back()) {
+            for (xyz_ctx *x : s->views)
+                xyz_destroy(x);
+            for (xyz_ctx *x : s->shadows)
+                ctx_sizing_free(x);
+            delete s;
+            return fail(XYZ_ENOMEM, "host allocation failed");
+        }
     }
     for (int w = 0; w < workers; ++w)
         s->threads.emplace_back(worker_main, s, w);
@@ -391,9 +452,7 @@ int xyz_server_submit(xyz_server *s, int32_t dataset, const int8_t *Y, int32_t L
     r.M = M;
     r.kappa = kappa;
     r.seed = seed;
-    // response bits plus room for results (records of a slice)
-    r.reserve = (int64_t)pk.Wp * 4 + ((int64_t)1 << 20);
-    r.t_submit = Clock::now();
+    r.t_submit = Clock::now();       // the reservation is sized at admission
     if (!s->started) {
         s->started = true;
         s->first_submit = r.t_submit;
@@ -515,6 +574,8 @@ void xyz_server_destroy(xyz_server *s)
         t.join();
     for (xyz_ctx *v : s->views)
         xyz_destroy(v);
+    for (xyz_ctx *x : s->shadows)
+        ctx_sizing_free(x);
     for (auto &kv : s->reqs)
         if (kv.second.yb)
             cudaFree(kv.second.yb);

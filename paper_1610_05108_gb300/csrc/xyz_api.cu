@@ -162,10 +162,22 @@ void *pool_get(size_t want, size_t *got)
     return p;
 }
 
+// While set (by the calling thread), ensure() allocates nothing: it adds to
+// *t_size_only the bytes by which the buffer would grow and records the new
+// size in the (copied) buffer descriptor, which is never dereferenced.
+thread_local int64_t *t_size_only = nullptr;
+
 static int ensure(DevBuf &b, size_t bytes)
 {
     if (b.bytes >= bytes && b.ptr)
         return XYZ_OK;
+    if (t_size_only) {
+        const size_t want = bytes < 256 ? 256 : bytes;
+        *t_size_only += (int64_t)want - (int64_t)(b.ptr ? b.bytes : 0);
+        b.bytes = want;
+        b.ptr = &b;
+        return XYZ_OK;
+    }
     if (b.ptr)
         pool_put(b.ptr, b.bytes);
     b.ptr = nullptr;
@@ -2386,6 +2398,30 @@ void view_target(xyz_ctx *view, const xyz_ctx *base, uint32_t *yb)
 }
 
 int64_t ctx_device_bytes(const xyz_ctx *c) { return (c->owns_packed ? c->packed_bytes : 0) + ws_bytes(c); }
+
+// Sizing snapshots of a context (its buffer sizes and capacities); a copy
+// shares the original's buffers and frees none of them.
+xyz_ctx *ctx_sizing_copy(const xyz_ctx *c) { return new (std::nothrow) xyz_ctx(*c); }
+void ctx_sizing_update(xyz_ctx *dst, const xyz_ctx *src) { *dst = *src; }
+void ctx_sizing_free(xyz_ctx *c) { delete c; }
+
+// Bytes by which the workspace of `view` (a sizing snapshot) grows to run
+// `runs` runs at M of a search on base's packed X: the same sizing as a
+// search, on a copy, with nothing allocated.  Searches grow some buffers on
+// overflow as they go (members, records, segments); this counts their sizes
+// at the start of a search.
+int64_t ctx_slice_growth(const xyz_ctx *view, const xyz_ctx *base, int64_t runs, int M)
+{
+    xyz_ctx tmp = *view;
+    view_target(&tmp, base, nullptr);
+    int64_t grow = 0;
+    t_size_only = &grow;
+    const Plan pl = make_plan(&tmp, runs, M, 1);
+    ensure_search_ws(&tmp, pl, 1, runs);
+    ensure_records(&tmp, 1);
+    t_size_only = nullptr;
+    return grow;
+}
 
 // Pack a host response into yb_dev (Wp words) on c's stream; -1/+1 only.
 // Uses c's staging buffer: calls on one context must not overlap.

@@ -310,6 +310,10 @@ int ctx_device(const xyz_ctx *c);
 int view_create(int device, xyz_ctx **out);
 void view_target(xyz_ctx *view, const xyz_ctx *base, uint32_t *yb);
 int64_t ctx_device_bytes(const xyz_ctx *c);
+xyz_ctx *ctx_sizing_copy(const xyz_ctx *c);
+void ctx_sizing_update(xyz_ctx *dst, const xyz_ctx *src);
+void ctx_sizing_free(xyz_ctx *c);
+int64_t ctx_slice_growth(const xyz_ctx *view, const xyz_ctx *base, int64_t runs, int M);
 int pack_response(xyz_ctx *c, const int8_t *Y, uint32_t *yb_dev);
 
 }  // namespace xyz

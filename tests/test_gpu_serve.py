@@ -110,6 +110,24 @@ def test_budget_makes_requests_queue(xyz):
             assert np.array_equal(got[i], ctx.search(40, 9, 0.3, 200 + i))
 
 
+def test_reservation_sized_from_workspace(xyz):
+    # a request's reservation is its share of the workers' workspace growth,
+    # sized by the library's workspace rules at admission: on fresh workers
+    # it is of the order of what they measure after serving it
+    X, Ys = _data(160, 3000, 5)
+    with xyz.Server(workers=2, hbm_budget_bytes=8 << 30, slice_runs=64) as srv:
+        d = srv.add_dataset(X, Ys[0])
+        base = srv.stats()["device_bytes"]
+        r = srv.submit(d, 2000, 9, 0.3, 7)
+        held = srv.stats()["device_bytes"] - base       # reservation (+ any workspace measured already)
+        got = srv.wait(r, timeout_ms=120000)[0]
+        after = srv.stats()["device_bytes"] - base      # the workers' measured workspaces
+    assert after > 0
+    assert held >= 0.5 * after
+    with xyz.create(X, Ys[0]) as ctx:
+        assert np.array_equal(got, ctx.search(2000, 9, 0.3, 7))
+
+
 def test_cancel_timeout_poll(xyz):
     X, Ys = _data(150, 4000, 5)
     with xyz.Server(workers=1, hbm_budget_bytes=8 << 30, slice_runs=16) as srv:
