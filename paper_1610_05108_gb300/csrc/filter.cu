@@ -366,15 +366,13 @@ __device__ __forceinline__ bool group_stream(const uint64_t *E, uint32_t n, uint
 // into sv and grouped one after the other (a group lies in one bin).
 // Returns false, with nothing grouped, when a bin is above SMAX, more than
 // part_max ranges are needed or the entries did not all fit the segment;
-// the run then stays in the segment for the general path.  With xlat, the
-// segment values are places in the class lists (class << 27 | index) and the
-// column is xlat[class * xcap + index].  Called by every thread of the CTA.
+// the run then stays in the segment for the general path.  Called by every
+// thread of the CTA.
 template <class Lay>
 __device__ __forceinline__ bool group_from_segment(const uint64_t *okeys, const uint32_t *ovals, uint32_t seg0,
                                                    uint32_t s, uint32_t seg_cap, int part_max, uint32_t kcmask,
                                                    uint64_t *sv, uint32_t *tkey, uint32_t *tcnt, bool nz, int b,
-                                                   const GroupOut &g, const uint32_t *xlat = nullptr,
-                                                   uint32_t xcap = 0)
+                                                   const GroupOut &g)
 {
     __shared__ uint32_t hist[32];       // entries per bin of the group-key hash
     __shared__ uint32_t pstart[33];     // partition q covers bins [pstart[q], pstart[q + 1])
@@ -440,12 +438,6 @@ __device__ __forceinline__ bool group_from_segment(const uint64_t *okeys, const 
                 const uint32_t bn = mix32(nz ? (Kc[u] >> 1) : Kc[u]) >> 27;
                 in[u] = i0 + u * (uint32_t)T < s && bn >= blo && bn < bhi;
                 col[u] = in[u] ? ovals[seg0 + i0 + u * (uint32_t)T] : 0u;
-            }
-            if (xlat) {
-#pragma unroll
-                for (int u = 0; u < GB; ++u)
-                    if (in[u])
-                        col[u] = xlat[(int64_t)(col[u] >> 27) * xcap + (col[u] & 0x7FFFFFFu)];
             }
 #pragma unroll
             for (int u = 0; u < GB; ++u)
