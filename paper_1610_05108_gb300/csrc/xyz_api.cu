@@ -108,6 +108,7 @@ struct xyz_ctx {
     // real X through the unbiased transform (Section 3.2)
     DevBuf xrs, xcs, xnu, ypr, ysd, ysd2, rbad;
     DevBuf vstart;               // verification: bucket of each block of 32 candidates
+    int64_t vstart_cap = (int64_t)1 << 22;   // blocks of 32 candidates that vstart holds
     DevBuf pXc, pXr, pyb, pbad;  // packed X, response bits, input-check flag (owned contexts)
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
     int64_t rec_cap = 1 << 16;
@@ -441,13 +442,17 @@ int ensure_search_ws(xyz_ctx *c, const Plan &pl, int B, int64_t runs)
     return XYZ_OK;
 }
 
-constexpr int64_t VSTART_CAP = (int64_t)1 << 22;   // blocks of 32 candidates with a precomputed bucket
+// The verification's table of the bucket of each block of 32 candidates
+// (4 bytes per block) starts at 2^22 blocks and grows, after a search's
+// first launch group, to twice the blocks that group had (at most 2^27);
+// candidates past the table find their bucket by a binary search instead.
+constexpr int64_t VSTART_MAX = (int64_t)1 << 27;
 
 int ensure_records(xyz_ctx *c, int B)
 {
     const int64_t cap = c->rec_cap;
     int rc;
-    if ((rc = ensure(c->vstart, (size_t)VSTART_CAP * 4)))
+    if ((rc = ensure(c->vstart, (size_t)c->vstart_cap * 4)))
         return rc;
     if ((rc = ensure(c->rec_keys, cap * 8)) || (rc = ensure(c->rec_keys_alt, cap * 8)) ||
         (rc = ensure(c->rec_agree, cap * 4)) || (rc = ensure(c->rec_agree_alt, cap * 4)) ||
@@ -657,7 +662,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
                                  (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
                                  c->stream, &launches, B > 1 ? ybs : nullptr, nullptr,
-                                 (uint32_t *)c->vstart.ptr, VSTART_CAP, ctr_err(c)));
+                                 (uint32_t *)c->vstart.ptr, c->vstart_cap, ctr_err(c)));
                 tm.end();
                 CU(launch_seg_reset((uint32_t *)c->seg_count.ptr, c->stream, &launches));
                 return XYZ_OK;
@@ -709,7 +714,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  (const uint32_t *)c->members.ptr, amin, pl.kbits,
                                  (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
                                  ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches,
-                                 B > 1 ? ybs : nullptr, ctr_sovf(c), (uint32_t *)c->vstart.ptr, VSTART_CAP,
+                                 B > 1 ? ybs : nullptr, ctr_sovf(c), (uint32_t *)c->vstart.ptr, c->vstart_cap,
                                  ctr_err(c)));
                 tm.end();
                 if (phase == SP_ALL && g0 == l0 && g0 + pl.R < l1) {
@@ -719,10 +724,30 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                     // (a whole search would be lost at the end)
                     int sovf = 0;
                     uint32_t mem_tried = 0, nrec1 = 0;
+                    uint64_t cand1 = 0;
                     CU(cudaMemcpyAsync(&sovf, ctr_sovf(c), 4, cudaMemcpyDeviceToHost, c->stream));
                     CU(cudaMemcpyAsync(&mem_tried, ctr_members(c), 4, cudaMemcpyDeviceToHost, c->stream));
                     CU(cudaMemcpyAsync(&nrec1, ctr_nrec(c), 4, cudaMemcpyDeviceToHost, c->stream));
+                    CU(cudaMemcpyAsync(&cand1, ctr_total(c), 8, cudaMemcpyDeviceToHost, c->stream));
                     CU(cudaStreamSynchronize(c->stream));
+                    // room in the block-start table for the later groups'
+                    // candidates (nothing is in flight: the table may move)
+                    const int64_t want_blocks = 2 * (int64_t)((cand1 + 31) / 32);
+                    if (!(sovf & 2) && want_blocks > c->vstart_cap && c->vstart_cap < VSTART_MAX) {
+                        int64_t cap = c->vstart_cap;
+                        while (cap < want_blocks && cap < VSTART_MAX)
+                            cap *= 2;
+                        if (ensure(c->vstart, (size_t)cap * 4) == XYZ_OK) {
+                            c->vstart_cap = cap;
+                        } else {
+                            // no room: a table of the old size again (the
+                            // failed attempt released it); the candidates
+                            // past it find their bucket by binary search
+                            g_err.clear();
+                            if ((rc = ensure(c->vstart, (size_t)c->vstart_cap * 4)))
+                                return rc;
+                        }
+                    }
                     if (sovf & 2) {
                         const int64_t want = (int64_t)mem_tried + (int64_t)mem_tried / 4;
                         c->mem_cap = want > 2 * c->mem_cap ? want : 2 * c->mem_cap;
@@ -789,7 +814,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                      (const uint32_t *)c->members.ptr, amin, pl.kbits,
                                      (uint64_t *)c->rec_keys.ptr, (uint32_t *)c->rec_agree.ptr,
                                      ctr_nrec(c), (uint32_t)c->rec_cap, c->stream, &launches, nullptr,
-                                     nullptr, (uint32_t *)c->vstart.ptr, VSTART_CAP, ctr_err(c)));
+                                     nullptr, (uint32_t *)c->vstart.ptr, c->vstart_cap, ctr_err(c)));
                     tm.end();
                     continue;
                 }
@@ -835,7 +860,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                  amin, pl.kbits, (uint64_t *)c->rec_keys.ptr,
                                  (uint32_t *)c->rec_agree.ptr, ctr_nrec(c), (uint32_t)c->rec_cap,
                                  c->stream, &launches, nullptr, nullptr, (uint32_t *)c->vstart.ptr,
-                                 VSTART_CAP, ctr_err(c)));
+                                 c->vstart_cap, ctr_err(c)));
                 tm.end();
             }
         }
