@@ -70,3 +70,31 @@ def test_bad_shapes_are_refused(xyz):
             with pytest.raises(xyz.XyzError) as e:
                 ctx.set_tiles(*bad)
             assert e.value.code == xyz.XYZ_EINVAL
+
+
+def test_block_start_table_growth_keeps_results(xyz):
+    # M = 7 on 40000 random columns: about 6e6 candidates per run, 4e8 per
+    # search, past the verification's first block-start table (2^22 blocks
+    # of 32 candidates).  One launch group (most blocks find their bucket by
+    # binary search), groups of 4 and 16 runs (the table grows after the
+    # first group) and a second search on the grown table must agree, and
+    # every pair must be one of the exhaustive screen's with its agreement
+    rng = np.random.default_rng(77)
+    X = np.asfortranarray((rng.integers(0, 2, size=(64, 40000), dtype=np.int8) * 2 - 1).astype(np.int8))
+    Y = (X[:, 3] * X[:, 39000]).astype(np.int8)
+    L, M, kappa, seed = 64, 7, 0.5, 5
+    with xyz.create(X, Y) as ctx:
+        one = ctx.search(L, M, kappa, seed)
+        cand = ctx.stats()["candidates"]
+        brute = ctx.brute_force(kappa)
+    assert cand > 2 ** 27
+    for gr in (4, 16):
+        with xyz.create(X, Y) as ctx:
+            ctx.set_tiles(group_runs=gr)
+            a = ctx.search(L, M, kappa, seed)
+            b = ctx.search(L, M, kappa, seed)
+        assert np.array_equal(a, one), gr
+        assert np.array_equal(b, one), gr
+    bs = {(int(j), int(k)): int(g) for j, k, g in zip(brute["j"], brute["k"], brute["agree"])}
+    assert len(one) > 0
+    assert all(bs.get((int(j), int(k))) == int(g) for j, k, g in zip(one["j"], one["k"], one["agree"]))
