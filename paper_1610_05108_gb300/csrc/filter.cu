@@ -139,23 +139,28 @@ struct GroupOut {
 // Phase II of the on-chip grouping: every slot of the table (tkey / tcnt,
 // side counts packed A << 16 | B) whose group has candidates becomes a
 // bucket (response b in its pad); one global atomic pair per call reserves
-// the bucket and member space.  Afterwards curA / tcnt of a bucket's slot are
+// the bucket and member space.  With occ, only the nocc slots listed there
+// (every occupied slot, in any order) are visited; otherwise all tsize.  Afterwards curA / tcnt of a bucket's slot are
 // the end cursors of its sides A / B (curA may be tkey itself when phase III
 // no longer needs the keys), and tcnt is FL_EMPTY for a slot without a
 // bucket.  Returns false when the space ran out (overflow bit 2 set: the host
 // grows it and redoes the search).  Called by every thread of the CTA.
 __device__ __forceinline__ bool assign_buckets(uint32_t *tkey, uint32_t *tcnt, uint32_t *curA, int tsize, bool nz,
-                                               int b, const GroupOut &g)
+                                               int b, const GroupOut &g, const uint32_t *occ = nullptr,
+                                               int nocc = 0)
 {
     __shared__ uint32_t mbase_sh, bbase_sh;
     __shared__ uint32_t wsum[FL_THREADS / 32];
     const int t = threadIdx.x, T = (int)blockDim.x;
     const int lane = t & 31, wp = t >> 5, nwarps = T >> 5;
-    // each thread owns a contiguous range of slots; the value of a slot is
-    // members << 16 | 1 when its group yields a bucket
-    const int per = (tsize + T - 1) / T;
-    const int s0 = t * per < tsize ? t * per : tsize;
-    const int s1 = s0 + per < tsize ? s0 + per : tsize;
+    // each thread owns a contiguous range of slots (of the list's entries
+    // with occ); the value of a slot is members << 16 | 1 when its group
+    // yields a bucket
+    const int items = occ ? nocc : tsize;
+    const int per = (items + T - 1) / T;
+    const int s0 = t * per < items ? t * per : items;
+    const int s1 = s0 + per < items ? s0 + per : items;
+    auto slot_of = [&](int i) -> int { return occ ? (int)occ[i] : i; };
     auto slot_value = [&](int slot) -> uint32_t {
         if (tkey[slot] == FL_EMPTY)
             return 0u;
@@ -164,8 +169,8 @@ __device__ __forceinline__ bool assign_buckets(uint32_t *tkey, uint32_t *tcnt, u
         return ok ? ((nA + nB) << 16) | 1u : 0u;
     };
     uint32_t mysum = 0;
-    for (int slot = s0; slot < s1; ++slot)
-        mysum += slot_value(slot);
+    for (int i = s0; i < s1; ++i)
+        mysum += slot_value(slot_of(i));
     uint32_t incl = mysum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -196,7 +201,8 @@ __device__ __forceinline__ bool assign_buckets(uint32_t *tkey, uint32_t *tcnt, u
     if (mbase_sh == 0xFFFFFFFFu)
         return false;
     uint32_t run_off = before + incl - mysum;
-    for (int slot = s0; slot < s1; ++slot) {
+    for (int i = s0; i < s1; ++i) {
+        const int slot = slot_of(i);
         const uint32_t v = slot_value(slot);
         if (v) {
             const uint32_t nA = tcnt[slot] >> 16, nB = tcnt[slot] & 0xFFFFu;
@@ -218,11 +224,14 @@ __device__ __forceinline__ bool assign_buckets(uint32_t *tkey, uint32_t *tcnt, u
 // Groups the s <= SMAX survivors (Kc << 32 | j) in sv on chip: a hash table
 // of group keys with packed side counts (tkey / tcnt); each group with
 // candidates becomes a bucket (response b in its pad) and its members are
-// written side A first.  Called by every thread of the CTA.
+// written side A first.  occ (optional, room for s entries of shared memory
+// outside the table and sv): the inserts list the slots they occupy there,
+// and phase II visits only those.  Called by every thread of the CTA.
 template <class Lay>
 __device__ __forceinline__ void group_on_chip(uint64_t *sv, uint32_t s, uint32_t *tkey, uint32_t *tcnt, bool nz,
-                                              int b, const GroupOut &g)
+                                              int b, const GroupOut &g, uint32_t *occ = nullptr)
 {
+    __shared__ uint32_t nocc_sh;
     const int t = threadIdx.x, T = (int)blockDim.x;
     // grouping on chip in the table (the keep mask and, for one
     // response, the filter are dead)
@@ -235,6 +244,8 @@ __device__ __forceinline__ void group_on_chip(uint64_t *sv, uint32_t s, uint32_t
         tkey[i] = FL_EMPTY;
         tcnt[i] = 0;
     }
+    if (t == 0)
+        nocc_sh = 0;
     __syncthreads();
     // phase I: insert group keys, count sides (A high half, B low
     // half); keep (side, slot, j)
@@ -246,7 +257,12 @@ __device__ __forceinline__ void group_on_chip(uint64_t *sv, uint32_t s, uint32_t
         uint32_t slot = (gk * 0x9E3779B1u) >> (32 - tlog);
         for (int probe = 0; probe < tsize; ++probe) {    // s < tsize: always ends
             const uint32_t old = atomicCAS(&tkey[slot], FL_EMPTY, gk);
-            if (old == FL_EMPTY || old == gk)
+            if (old == FL_EMPTY) {
+                if (occ)
+                    occ[atomicAdd(&nocc_sh, 1u)] = slot;   // at most s slots become occupied
+                break;
+            }
+            if (old == gk)
                 break;
             slot = (slot + 1) & (tsize - 1);
         }
@@ -255,7 +271,7 @@ __device__ __forceinline__ void group_on_chip(uint64_t *sv, uint32_t s, uint32_t
     }
     __syncthreads();
     // phase II (the keys are not needed afterwards: tkey holds the side-A cursors)
-    if (!assign_buckets(tkey, tcnt, tkey, tsize, nz, b, g))
+    if (!assign_buckets(tkey, tcnt, tkey, tsize, nz, b, g, occ, (int)nocc_sh))
         return;              // the host grows the space and redoes the search
     // phase III: members, side A first
     for (uint32_t i = t; i < s; i += T) {
@@ -459,15 +475,16 @@ __device__ __forceinline__ bool group_from_segment(const uint64_t *okeys, const 
 // is written back to the segment (runbits | Kc, column) for the general sort
 // and join.  Returns the number of entries left in the segment at seg0, or
 // GS_NONE when nothing was done because the run overflowed the segment or
-// s > tmp_cap (the segment then still holds all of them).  Called by every
-// thread of the CTA.
+// s > tmp_cap (the segment then still holds all of them).  occ: SMAX words
+// of shared memory for the on-chip grouping's list of occupied slots.
+// Called by every thread of the CTA.
 constexpr uint32_t GS_NONE = 0xFFFFFFFFu;
 template <class Lay>
 __device__ __forceinline__ uint32_t group_segment_sorted(uint64_t *okeys, uint32_t *ovals, uint32_t seg0,
                                                          uint32_t s, uint32_t seg_cap, uint32_t kcmask,
                                                          uint64_t runbits, uint64_t *sv, uint32_t *tkey,
                                                          uint32_t *tcnt, bool nz, int b, const GroupOut &g,
-                                                         uint64_t *tmp, uint32_t tmp_cap)
+                                                         uint64_t *tmp, uint32_t tmp_cap, uint32_t *occ)
 {
     __shared__ uint32_t bstart[33];     // bin q of tmp: [bstart[q], bstart[q + 1])
     __shared__ uint32_t wsum2[FL_THREADS / 32];
@@ -584,7 +601,7 @@ __device__ __forceinline__ uint32_t group_segment_sorted(uint64_t *okeys, uint32
         }
         __syncthreads();
         if (cnt)
-            group_on_chip<Lay>(sv, cnt, tkey, tcnt, nz, b, g);
+            group_on_chip<Lay>(sv, cnt, tkey, tcnt, nz, b, g, occ);
         bn = be;
     }
     __syncthreads();
@@ -1132,6 +1149,8 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
     extern __shared__ __align__(16) uint32_t fl_smem[];
     uint32_t *F = fl_smem;                                                   // [FL_FWORDS], in the rounds
     uint64_t *sv = reinterpret_cast<uint64_t *>(fl_smem + Lay::OFF_SV);      // [SMAX], after the rounds
+    uint32_t *occ = fl_smem + Lay::OFF_KM;                                   // [SMAX] occupied slots, grouping
+    static_assert(FL_KWORDS >= Lay::SMAX, "the occupied-slot list fits its region");
     uint32_t *tkey = fl_smem + Lay::OFF_TAB;                                 // [Lay::T], after the rounds
     uint32_t *tcnt = fl_smem + Lay::OFF_TAB + Lay::T;
     uint64_t *stg = reinterpret_cast<uint64_t *>(fl_smem);                   // [16 T] staged entries
@@ -1491,7 +1510,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1)
         // sorted by bin there
         uint32_t left = part_max > 0
             ? group_segment_sorted<Lay>(okeys, ovals, seg0, s, seg_cap, kcmask, runbits, sv, tkey, tcnt, nz, 0,
-                                        gout, reinterpret_cast<uint64_t *>(lk), 8 * lcap)
+                                        gout, reinterpret_cast<uint64_t *>(lk), 8 * lcap, occ)
             : GS_NONE;
         if (left == GS_NONE)
             left = s;
