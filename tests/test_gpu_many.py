@@ -134,3 +134,26 @@ def test_fused_filter_setting_checked(xyz):
         with pytest.raises(xyz.XyzError) as e:
             xyz._check(xyz.load().xyz_set_fused_filter(c.handle, 2))
         assert e.value.code == xyz.XYZ_EINVAL
+
+
+def test_fused_search_that_overflows_is_redone(xyz, orc):
+    # M = 13 over 30000 random columns: nearly every column survives and the
+    # first attempt's groups overflow the member space reserved for them; in
+    # a fused filter launch that search must be redone on its own after the
+    # graph, and every result must still equal the search alone
+    rng = np.random.default_rng(29)
+    Xo = np.asfortranarray((rng.integers(0, 2, size=(64, 30000), dtype=np.int8) * 2 - 1).astype(np.int8))
+    Yo = (rng.integers(0, 2, size=64, dtype=np.int8) * 2 - 1).astype(np.int8)
+    specs = [(12, 13, 0.5, 3)] + [(20, 9, 0.3, 10 + i) for i in range(3)]
+    data = [(Xo, Yo)] + [_inst(150, 3000, 60 + i, pair=(0, 2999)) for i in range(3)]
+    ctxs = [xyz.create(X, Y) for X, Y in data]
+    try:
+        got = xyz.search_many(ctxs, [s[0] for s in specs], [s[1] for s in specs], [s[2] for s in specs],
+                              [s[3] for s in specs])
+        for i, ((L, M, kappa, seed), (X, Y)) in enumerate(zip(specs, data)):
+            with xyz.create(X, Y) as alone:
+                assert np.array_equal(got[i], alone.search(L, M, kappa, seed)), i
+        assert np.array_equal(_arr(got[0]), orc.xyz(Xo, Yo, 12, 13, 0.5, 3))
+    finally:
+        for c in ctxs:
+            c.close()
