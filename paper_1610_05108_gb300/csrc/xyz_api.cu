@@ -572,6 +572,16 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
             return fail(XYZ_EINVAL, "search cannot join a fused filter launch");
         int64_t chunks = phase == SP_FINISH ? (runs + pl.R - 1) / pl.R : 0;
         int64_t surv_total = 0;
+        // host copy of the device counters (one copy of the block per
+        // synchronisation); hc_fresh while no kernel has run since it was taken
+        alignas(8) uint32_t hc[32];
+        bool hc_fresh = false;
+        auto read_counters = [&]() -> int {
+            CU(cudaMemcpyAsync(hc, c->counters.ptr, sizeof(hc), cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+            hc_fresh = true;
+            return XYZ_OK;
+        };
         int key_bits_max = 0;
         bool redo = false;
         if (pl.filter) {
@@ -589,12 +599,10 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                                   (uint64_t *)c->keysA.ptr, (uint32_t *)c->valsA.ptr, ctr_nsurv(c),
                                   c->stream, &launches));
                 tm.end();
-                uint32_t ns = 0, mem_tried = 0;
-                int sovf = 0;
-                CU(cudaMemcpyAsync(&ns, ctr_nsurv(c), 4, cudaMemcpyDeviceToHost, c->stream));
-                CU(cudaMemcpyAsync(&sovf, ctr_sovf(c), 4, cudaMemcpyDeviceToHost, c->stream));
-                CU(cudaMemcpyAsync(&mem_tried, ctr_members(c), 4, cudaMemcpyDeviceToHost, c->stream));
-                CU(cudaStreamSynchronize(c->stream));
+                if (int r = read_counters())
+                    return r;
+                const uint32_t ns = hc[2], mem_tried = hc[1];
+                const int sovf = (int)hc[3];
                 if (sovf & 1) {
                     // a spill segment overflowed: larger segments up to a
                     // bound, then more frequent flushes
@@ -636,7 +644,8 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
                     redo = true;
                 }
                 if (redo || ns == 0)
-                    return XYZ_OK;
+                    return XYZ_OK;               // nothing launched since the counters were read
+                hc_fresh = false;
                 surv_total += ns;
                 const int64_t sb = c->surv_cap / 2 + 1;
                 bool alt = false;
@@ -866,14 +875,17 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
         }
         if (enq)
             return XYZ_OK;
-        // record count -> host
-        uint32_t nrec = 0;
-        uint64_t cand = 0;
-        int err = 0;
-        CU(cudaMemcpyAsync(&nrec, ctr_nrec(c), 4, cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaMemcpyAsync(&cand, ctr_cand(c), 8, cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaMemcpyAsync(&err, ctr_err(c), 4, cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
+        // record count, candidates, errors, kept columns and the last group's
+        // buckets -> host (already there when the spill flush read them last)
+        if (!hc_fresh && (rc = read_counters()))
+            return rc;
+        const uint32_t nrec = hc[5];
+        const uint64_t cand = (uint64_t)hc[10] | ((uint64_t)hc[11] << 32);
+        const int err = (int)hc[7];
+        const uint32_t nb_last = hc[0];
+        unsigned long long kept[3];
+        for (int i = 0; i < 3; ++i)
+            kept[i] = (unsigned long long)hc[16 + 2 * i] | ((unsigned long long)hc[17 + 2 * i] << 32);
         if (err & 2)
             return fail(XYZ_ECUDA, "internal error: a candidate's offset lies outside its bucket");
         if (err)
@@ -916,12 +928,10 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
             CU(launch_weighted_strengths(c->pk, (PairOut *)c->out.ptr, ctr_nout(c), (int64_t)nrec, c->stream,
                                          &launches));
         uint32_t nout = 0;
-        unsigned long long kept[3] = {0, 0, 0};
-        CU(cudaMemcpyAsync(&nout, ctr_nout(c), 4, cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaMemcpyAsync(kept, ctr_kept(c), 24, cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
-        if (nrec == 0)
-            nout = 0;
+        if (nrec > 0) {
+            CU(cudaMemcpyAsync(&nout, ctr_nout(c), 4, cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+        }
         st.attempts = attempt + 1;
         st.filter_kept = pl.filter ? (int64_t)kept[0] : 0;
         st.bucket_members = pl.filter ? (int64_t)kept[1] : 0;
@@ -937,10 +947,7 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
         st.survivors = pl.filter ? surv_total : runs * c->pk.p;
         st.gpu_launches = launches;
         tm.collect(st);
-        uint32_t nb = 0;
-        CU(cudaMemcpyAsync(&nb, ctr_nbuckets(c), 4, cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
-        st.buckets = nb;
+        st.buckets = nb_last;
         c->stats = st;
         *nout_host = nout;
         return XYZ_OK;
