@@ -108,6 +108,12 @@ struct xyz_ctx {
     // real X through the unbiased transform (Section 3.2)
     DevBuf xrs, xcs, xnu, ypr, ysd, ysd2, rbad;
     DevBuf vstart;               // verification: bucket of each block of 32 candidates
+    // host copy of the last search's output pairs (and their responses),
+    // taken with its output count when the record count was small;
+    // hout_n = -1 when there is none
+    std::vector<PairOut> hout;
+    std::vector<uint32_t> hresp;
+    int64_t hout_n = -1;
     int64_t vstart_cap = (int64_t)1 << 22;   // blocks of 32 candidates that vstart holds
     DevBuf pXc, pXr, pyb, pbad;  // packed X, response bits, input-check flag (owned contexts)
     DevBuf rec_keys, rec_keys_alt, rec_agree, rec_agree_alt, flags, pos, out, dedup_tmp, raw;
@@ -447,6 +453,9 @@ int ensure_search_ws(xyz_ctx *c, const Plan &pl, int B, int64_t runs)
 // first launch group, to twice the blocks that group had (at most 2^27);
 // candidates past the table find their bucket by a binary search instead.
 constexpr int64_t VSTART_MAX = (int64_t)1 << 27;
+// a search copies its output to the host with the output count when it has
+// at most this many records (the output is at most that long)
+constexpr int64_t HOUT_MAX = 65536;
 
 int ensure_records(xyz_ctx *c, int B)
 {
@@ -927,10 +936,26 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
         else if (c->pk.cdf && nrec > 0)
             CU(launch_weighted_strengths(c->pk, (PairOut *)c->out.ptr, ctr_nout(c), (int64_t)nrec, c->stream,
                                          &launches));
+        // the output count, and, when the records are few, the output
+        // itself (at most nrec pairs), under one synchronisation
         uint32_t nout = 0;
+        c->hout_n = -1;
         if (nrec > 0) {
+            const bool stage = (int64_t)nrec <= HOUT_MAX;
             CU(cudaMemcpyAsync(&nout, ctr_nout(c), 4, cudaMemcpyDeviceToHost, c->stream));
+            if (stage) {
+                c->hout.resize(nrec);
+                CU(cudaMemcpyAsync(c->hout.data(), c->out.ptr, (size_t)nrec * sizeof(PairOut), cudaMemcpyDeviceToHost,
+                                   c->stream));
+                if (B > 1) {
+                    c->hresp.resize(nrec);
+                    CU(cudaMemcpyAsync(c->hresp.data(), c->resp.ptr, (size_t)nrec * 4, cudaMemcpyDeviceToHost,
+                                       c->stream));
+                }
+            }
             CU(cudaStreamSynchronize(c->stream));
+            if (stage)
+                c->hout_n = nout;
         }
         st.attempts = attempt + 1;
         st.filter_kept = pl.filter ? (int64_t)kept[0] : 0;
@@ -953,6 +978,25 @@ int run_search_multi(xyz_ctx *c, const uint32_t *ybs, int B, int64_t l0, int64_t
         return XYZ_OK;
     }
     return fail(XYZ_ENOMEM, "search buffers kept overflowing");
+}
+
+// The last search's n output pairs (and, with resp_dst, their responses)
+// into host memory: from the copy the search took, else from the device.
+int copy_pairs(xyz_ctx *c, int64_t n, void *dst, uint32_t *resp_dst = nullptr)
+{
+    if (n <= 0)
+        return XYZ_OK;
+    if (c->hout_n == n && (!resp_dst || c->hresp.size() >= (size_t)n)) {
+        std::memcpy(dst, c->hout.data(), (size_t)n * sizeof(PairOut));
+        if (resp_dst)
+            std::memcpy(resp_dst, c->hresp.data(), (size_t)n * 4);
+        return XYZ_OK;
+    }
+    CU(cudaMemcpyAsync(dst, c->out.ptr, (size_t)n * sizeof(PairOut), cudaMemcpyDeviceToHost, c->stream));
+    if (resp_dst)
+        CU(cudaMemcpyAsync(resp_dst, c->resp.ptr, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return XYZ_OK;
 }
 
 int run_search(xyz_ctx *c, int64_t l0, int64_t l1, int M, int64_t amin, uint64_t seed,
@@ -1430,13 +1474,9 @@ int xyz_search_range(xyz_ctx *ctx, int64_t l0, int64_t l1, int32_t M, double kap
         host = (xyz_pair *)std::malloc((size_t)nout * sizeof(xyz_pair));
         if (!host)
             return fail(XYZ_ENOMEM, "host allocation of results failed");
-        cudaError_t e = cudaMemcpyAsync(host, ctx->out.ptr, (size_t)nout * sizeof(xyz_pair),
-                                        cudaMemcpyDeviceToHost, ctx->stream);
-        if (e == cudaSuccess)
-            e = cudaStreamSynchronize(ctx->stream);
-        if (e != cudaSuccess) {
+        if ((rc = copy_pairs(ctx, nout, host))) {
             std::free(host);
-            return fail(XYZ_ECUDA, std::string("copy of results: ") + cudaGetErrorString(e));
+            return rc;
         }
     }
     *pairs = host;
@@ -1542,12 +1582,7 @@ int search_collect(xyz_ctx *c, int32_t L, int32_t M, int64_t amin, uint64_t seed
         return rc;
     const size_t at = out.size();
     out.resize(at + (size_t)nout);
-    if (nout > 0) {
-        CU(cudaMemcpyAsync(out.data() + at, c->out.ptr, (size_t)nout * sizeof(xyz_pair), cudaMemcpyDeviceToHost,
-                           c->stream));
-        CU(cudaStreamSynchronize(c->stream));
-    }
-    return XYZ_OK;
+    return copy_pairs(c, nout, out.data() + at);
 }
 
 // Both signs of the response (Section 4 runs xyz with Y set to +r and -r):
@@ -1934,11 +1969,8 @@ int xyz_search_many(xyz_ctx **ctxs, int32_t count, const int32_t *L, const int32
         }
         const size_t at = acc.size();
         acc.resize(at + (size_t)no);
-        if (no > 0) {
-            CU(cudaMemcpyAsync(acc.data() + at, c->out.ptr, (size_t)no * sizeof(xyz_pair), cudaMemcpyDeviceToHost,
-                               c->stream));
-            CU(cudaStreamSynchronize(c->stream));
-        }
+        if ((rc = copy_pairs(c, no, acc.data() + at)))
+            return rc;
         offsets[i + 1] = offsets[i] + no;
     }
     xyz_pair *host = nullptr;
@@ -2131,15 +2163,12 @@ int collect_batch(xyz_ctx *ctx, int32_t B, int64_t nout, bool have_resp, int32_t
         return XYZ_OK;
     const size_t at = acc.size();
     acc.resize(at + (size_t)nout);
-    CU(cudaMemcpyAsync(acc.data() + at, ctx->out.ptr, (size_t)nout * sizeof(xyz_pair),
-                       cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<uint32_t> resp;
-    if (have_resp) {
+    if (have_resp)
         resp.resize((size_t)nout);
-        CU(cudaMemcpyAsync(resp.data(), ctx->resp.ptr, (size_t)nout * 4, cudaMemcpyDeviceToHost,
-                           ctx->stream));
-    }
-    CU(cudaStreamSynchronize(ctx->stream));
+    int rc = copy_pairs(ctx, nout, acc.data() + at, have_resp ? resp.data() : nullptr);
+    if (rc)
+        return rc;
     for (int64_t i = 0; i < nout; ++i) {
         const uint32_t b = have_resp ? resp[(size_t)i] : (uint32_t)only;
         if (b >= (uint32_t)B)
@@ -2325,9 +2354,8 @@ int xyz_run_candidates(xyz_ctx *ctx, int32_t M, uint64_t seed, int64_t run, int3
     int32_t *host = nullptr;
     if (nout > 0) {
         std::vector<PairOut> tmp((size_t)nout);
-        CU(cudaMemcpyAsync(tmp.data(), ctx->out.ptr, (size_t)nout * sizeof(PairOut),
-                           cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
+        if ((rc = copy_pairs(ctx, nout, tmp.data())))
+            return rc;
         host = (int32_t *)std::malloc((size_t)nout * 2 * sizeof(int32_t));
         if (!host)
             return fail(XYZ_ENOMEM, "host allocation failed");
