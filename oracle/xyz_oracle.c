@@ -24,7 +24,7 @@
  *   R2  the random stream is a counter-based splitmix64 (Steele, Lea & Flood
  *       2014): draw t of a search with seed s is mix(s + (t+1)*0x9E3779B97F4A7C15)
  *       with t = run*M + m, and the row is floor(u * n / 2^64).
- *   R3  the projection R of eq. projR with F = U[0,1] (Algorithm 2, step 3)
+ *   R3  the projection R of eq. projR with F = U[0,1] (Algorithm 2's projection of the sampled rows)
  *       makes x_j = z_k exactly when X_{i_m j} = Z_{i_m k} for every sampled
  *       row (Section 2, the remark after the definition of the classes);
  *       keys are therefore the M sampled bits, bit(v) = 1 iff v = -1.
@@ -32,7 +32,7 @@
  *       the tests can check that both give the same equal pairs.
  *   R4  the diagonal j = k is not an interaction; candidates are reported as
  *       unordered pairs j < k (the model of eq. inter_mod sums over j < k).
- *   R5  the verification keeps gamma_jk >= gamma (Algorithm 2, step 5), in
+ *   R5  the verification keeps gamma_jk >= gamma (Algorithm 2's check of the equal pairs), in
  *       kappa form: keep (2a - n) >= kappa*n, with a the agreement count of
  *       eq. def_gamma.  a_min is the least integer a in [0, n] with
  *       (double)(2a - n) >= kappa * (double)n (one IEEE double multiply).
@@ -150,7 +150,7 @@ int64_t orc_brute_force(const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
 /* ------------------------------------------------------------ projection */
 
 /* Reading R3: x_j = sum_m 2^m bit(X_{i_m j}), z_k = sum_m 2^m bit(Z_{i_m k})
- * with Z_ik = Y_i X_ik (Algorithm 2, step 1) and bit(v) = 1 iff v = -1.
+ * with Z_ik = Y_i X_ik (Algorithm 2's product of Y with X) and bit(v) = 1 iff v = -1.
  * Two columns get equal keys exactly when they agree on every sampled row. */
 void orc_keys(const int8_t *X, const int8_t *Y, int64_t n, int64_t p,
               const int64_t *rows, int32_t M, uint64_t *x, uint64_t *z)
