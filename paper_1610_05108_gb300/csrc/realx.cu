@@ -9,6 +9,8 @@
 // the unbiased transform is its interaction strength gamma^g_jk in kappa
 // form.  X' is kept twice in HBM as float: row-major for the draws and
 // column-major for the verification.
+#include <cmath>
+
 #include "xyz_internal.cuh"
 
 namespace xyz {
@@ -55,10 +57,10 @@ __global__ void scale_kernel(const float *__restrict__ X, int64_t n, int64_t p, 
     }
 }
 
-// Y'_i = Y_i nu_i^2 (double), and its copy padded to the column pitch for
-// the verification.
+// Y'_i = Y_i nu_i^2 (double), and its copies padded to the column pitch for
+// the verification: in double (ysd) and rounded to float (ysf).
 __global__ void yprime_kernel(const double *__restrict__ Y, const unsigned *__restrict__ numax, int64_t n,
-                              double *__restrict__ yp, double *__restrict__ ysd)
+                              double *__restrict__ yp, double *__restrict__ ysd, float *__restrict__ ysf)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -66,18 +68,25 @@ __global__ void yprime_kernel(const double *__restrict__ Y, const unsigned *__re
         const double v = Y[i] * (nu * nu);
         yp[i] = v;
         ysd[i] = v;
+        ysf[i] = (float)v;
     }
 }
 
 // Candidate verification with the real inner product: the candidate
 // decoding of the binary verification (32 consecutive candidates per warp,
 // bucket window search), then eight lanes per candidate summing
-// Y'_i (X'_ij X'_ik) over 16-byte pieces of the float columns, in double:
-// the product of two floats is exact in double, so every term equals the
-// oracle's and the sums differ only by the order of the additions (relative
-// error below n 2^-52 of sum |terms| <= ||Y'||_1).
+// Y'_i (X'_ij X'_ik) over 16-byte pieces of the float columns.  The sums
+// are first taken in float (Y' rounded to float); a candidate whose float
+// sum lies within `band` of the threshold -- a bound on the float sum's
+// error, widened -- is summed again in double, where the product of two
+// floats is exact, so every term equals the oracle's and the sums differ
+// only by the order of the additions (relative error below n 2^-52 of
+// sum |terms| <= ||Y'||_1).  Every pass decision is therefore the double
+// sum's, at the float path's cost for all but the candidates near the
+// threshold.  Without use_float every candidate takes the double path.
 __global__ void __launch_bounds__(RX_THREADS)
-    verify_real_kernel(const float *__restrict__ Xcs, int64_t Wf, const double *__restrict__ ysd, double kq,
+    verify_real_kernel(const float *__restrict__ Xcs, int64_t Wf, const double *__restrict__ ysd,
+                       const float *__restrict__ ysf, bool use_float, double band, double kq,
                        const Bucket *__restrict__ buckets, const uint64_t *__restrict__ pair_off,
                        const uint32_t *__restrict__ nbuckets, const uint64_t *__restrict__ total_pairs,
                        const uint32_t *__restrict__ vals, int kbits, uint64_t *__restrict__ rec_keys,
@@ -92,6 +101,7 @@ __global__ void __launch_bounds__(RX_THREADS)
     const int sub = lane & 7;
     const int nq = (int)(Wf >> 2);
     const double2 *y2 = reinterpret_cast<const double2 *>(ysd);
+    const float4 *yf4 = reinterpret_cast<const float4 *>(ysf);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < T; t0 += stride) {
         uint32_t base = 0;
@@ -136,30 +146,64 @@ __global__ void __launch_bounds__(RX_THREADS)
                 k = vals[B.start + y];
             }
         }
-        double dot = 0.0;
+        // first in float; a candidate whose float sum lies within `band` of
+        // the threshold (or every candidate, without use_float) again in
+        // double, so that every decision is the double sum's
+        float dotf = 0.0f;
+        if (use_float) {
 #pragma unroll
-        for (int st = 0; st < 8; ++st) {
-            const int cidx = 4 * st + (lane >> 3);
-            const uint32_t jj = __shfl_sync(FULL, j, cidx);
-            const uint32_t kk = __shfl_sync(FULL, k, cidx);
-            const bool vv = __shfl_sync(FULL, (int)valid, cidx) != 0;
-            double part = 0.0;
-            if (vv) {
-                const float4 *cj = reinterpret_cast<const float4 *>(Xcs + (int64_t)jj * Wf);
-                const float4 *ck = reinterpret_cast<const float4 *>(Xcs + (int64_t)kk * Wf);
-                for (int q = sub; q < nq; q += 8) {
-                    const float4 a = __ldg(cj + q), b = __ldg(ck + q);
-                    const double2 y0 = __ldg(y2 + 2 * q), y1 = __ldg(y2 + 2 * q + 1);
-                    part += y0.x * ((double)a.x * (double)b.x) + y0.y * ((double)a.y * (double)b.y) +
-                            y1.x * ((double)a.z * (double)b.z) + y1.y * ((double)a.w * (double)b.w);
+            for (int st = 0; st < 8; ++st) {
+                const int cidx = 4 * st + (lane >> 3);
+                const uint32_t jj = __shfl_sync(FULL, j, cidx);
+                const uint32_t kk = __shfl_sync(FULL, k, cidx);
+                const bool vv = __shfl_sync(FULL, (int)valid, cidx) != 0;
+                float part = 0.0f;
+                if (vv) {
+                    const float4 *cj = reinterpret_cast<const float4 *>(Xcs + (int64_t)jj * Wf);
+                    const float4 *ck = reinterpret_cast<const float4 *>(Xcs + (int64_t)kk * Wf);
+                    for (int q = sub; q < nq; q += 8) {
+                        const float4 a = __ldg(cj + q), b = __ldg(ck + q), y = __ldg(yf4 + q);
+                        part = fmaf(y.x, a.x * b.x, part);
+                        part = fmaf(y.y, a.y * b.y, part);
+                        part = fmaf(y.z, a.z * b.z, part);
+                        part = fmaf(y.w, a.w * b.w, part);
+                    }
                 }
+                part += __shfl_xor_sync(FULL, part, 4);
+                part += __shfl_xor_sync(FULL, part, 2);
+                part += __shfl_xor_sync(FULL, part, 1);
+                const float got = __shfl_sync(FULL, part, 8 * (lane & 3));
+                if ((lane >> 2) == st)
+                    dotf = got;
             }
-            part += __shfl_xor_sync(FULL, part, 4);
-            part += __shfl_xor_sync(FULL, part, 2);
-            part += __shfl_xor_sync(FULL, part, 1);
-            const double got = __shfl_sync(FULL, part, 8 * (lane & 3));
-            if ((lane >> 2) == st)
-                dot = got;
+        }
+        double dot = (double)dotf;
+        const bool needd = valid && (!use_float || fabs((double)dotf - kq) <= band);
+        if (__any_sync(FULL, needd)) {
+#pragma unroll
+            for (int st = 0; st < 8; ++st) {
+                const int cidx = 4 * st + (lane >> 3);
+                const uint32_t jj = __shfl_sync(FULL, j, cidx);
+                const uint32_t kk = __shfl_sync(FULL, k, cidx);
+                const bool vv = __shfl_sync(FULL, (int)needd, cidx) != 0;
+                double part = 0.0;
+                if (vv) {
+                    const float4 *cj = reinterpret_cast<const float4 *>(Xcs + (int64_t)jj * Wf);
+                    const float4 *ck = reinterpret_cast<const float4 *>(Xcs + (int64_t)kk * Wf);
+                    for (int q = sub; q < nq; q += 8) {
+                        const float4 a = __ldg(cj + q), b = __ldg(ck + q);
+                        const double2 y0 = __ldg(y2 + 2 * q), y1 = __ldg(y2 + 2 * q + 1);
+                        part += y0.x * ((double)a.x * (double)b.x) + y0.y * ((double)a.y * (double)b.y) +
+                                y1.x * ((double)a.z * (double)b.z) + y1.y * ((double)a.w * (double)b.w);
+                    }
+                }
+                part += __shfl_xor_sync(FULL, part, 4);
+                part += __shfl_xor_sync(FULL, part, 2);
+                part += __shfl_xor_sync(FULL, part, 1);
+                const double got = __shfl_sync(FULL, part, 8 * (lane & 3));
+                if ((lane >> 2) == st && needd)
+                    dot = got;
+            }
         }
         if (valid && dot >= kq) {
             uint32_t idx = atomicAdd(nrec, 1u);
@@ -228,11 +272,12 @@ cudaError_t launch_unbiased_scale(const float *dX, int64_t n, int64_t p, int64_t
 cudaError_t launch_unbiased_y(const double *dY, const float *nu, int64_t n, int64_t Wf, double *yprime,
                               double *ysd, cudaStream_t s, int64_t *launches)
 {
-    cudaError_t e = cudaMemsetAsync(ysd, 0, (size_t)Wf * sizeof(double), s);
+    // ysd holds Wf doubles and then Wf floats
+    cudaError_t e = cudaMemsetAsync(ysd, 0, (size_t)Wf * (sizeof(double) + sizeof(float)), s);
     if (e != cudaSuccess)
         return e;
     yprime_kernel<<<grid_of(n, 4096), RX_THREADS, 0, s>>>(dY, reinterpret_cast<const unsigned *>(nu), n, yprime,
-                                                         ysd);
+                                                         ysd, reinterpret_cast<float *>(ysd + Wf));
     *launches += 1;
     return cudaGetLastError();
 }
@@ -245,9 +290,15 @@ cudaError_t launch_verify_real(const Packed &pk, const Bucket *buckets, const ui
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // float sums are within (n/8 + 6) 2^-24 ||Y'||_1 of the exact ones (|X'| <= 1:
+    // each term carries at most two roundings, each lane adds n/8 terms, the
+    // reduction three more); the band is taken eight times wider, and the
+    // float path is used only while ||Y'||_1 is far inside float's range
+    const double band = ((double)pk.n + 64.0) * std::ldexp(1.0, -23) * pk.rnorm;
+    const bool use_float = pk.rnorm > 1e-30 && pk.rnorm < 1e30;
     verify_real_kernel<<<(unsigned)((sms > 0 ? sms : 152) * 8), RX_THREADS, 0, s>>>(
-        pk.Xcs, pk.Wf, pk.ysd, pk.rkq, buckets, pair_off, nbuckets, total_pairs, vals, kbits, rec_keys, rec_agree,
-        nrec, rec_cap, abort_flag);
+        pk.Xcs, pk.Wf, pk.ysd, reinterpret_cast<const float *>(pk.ysd + pk.Wf), use_float, band, pk.rkq, buckets,
+        pair_off, nbuckets, total_pairs, vals, kbits, rec_keys, rec_agree, nrec, rec_cap, abort_flag);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -1241,7 +1241,7 @@ int xyz_create_unbiased(const float *X, const double *Y, int64_t n, int64_t p, x
     if ((rc = ensure(dX, count * sizeof(float))) || (rc = ensure(dY, (size_t)n * 8)) ||
         (rc = ensure(c->xrs, (size_t)n * Pf * sizeof(float))) ||
         (rc = ensure(c->xcs, (size_t)p * Wf * sizeof(float))) || (rc = ensure(c->xnu, (size_t)n * 4)) ||
-        (rc = ensure(c->ysd, (size_t)Wf * 8)) || (rc = ensure(c->rbad, 16)))
+        (rc = ensure(c->ysd, (size_t)Wf * 12)) || (rc = ensure(c->rbad, 16)))
         return bail(rc);
     int64_t launches = 0;
     unsigned bad = 0;
@@ -1354,7 +1354,7 @@ int xyz_set_y_real_dev(xyz_ctx *ctx, const double *dY)
         // real X: the response of the scaled rows, Y'_i = Y_i nu_i^2 (its
         // padded copy goes to a second buffer, swapped in once Y' is accepted)
         int64_t launches = 0;
-        if ((rc = ensure(ctx->ypr, (size_t)n * 8)) || (rc = ensure(ctx->ysd2, (size_t)ctx->pk.Wf * 8)))
+        if ((rc = ensure(ctx->ypr, (size_t)n * 8)) || (rc = ensure(ctx->ysd2, (size_t)ctx->pk.Wf * 12)))
             return rc;
         CU(launch_unbiased_y(dY, (const float *)ctx->xnu.ptr, n, ctx->pk.Wf, (double *)ctx->ypr.ptr,
                              (double *)ctx->ysd2.ptr, ctx->stream, &launches));

@@ -53,7 +53,7 @@ struct Packed {
     int64_t Pf = 0;                    // row pitch in floats, a multiple of 32
     const float *Xcs = nullptr;        // [p][Wf] columns of X' (padding 0)
     int64_t Wf = 0;                    // column pitch in floats, a multiple of 32
-    const double *ysd = nullptr;       // [Wf] Y' = Y nu_i^2 (padding 0)
+    const double *ysd = nullptr;       // [Wf] Y' = Y nu_i^2 (padding 0), then [Wf] floats of it
     double rkq = 0.0;                  // pass: sum_i Y'_i X'_ij X'_ik >= rkq
     double rnorm = 0.0;                // ||Y'||_1 (reported strength = dot / rnorm)
     // launch shapes (xyz_set_tiles; 0 = the default rule); results never
